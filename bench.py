@@ -1,0 +1,382 @@
+"""Benchmark of the projection hot path on synthetic droplet fields.
+
+Workload (one step): the two Poisson solves the VoF solver runs per time step on a 128^3 grid, periodic x, y,
+Neumann z, FP64: the pressure projection with the Stefan source of a spherical droplet (radius 0.15 L, tanh
+interface 1.5 cells wide, density ratio 100) and the divergence-free liquid-velocity extension that gives the
+interface velocity.  Metric: projection Mpts/s = cells x solves / s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 128]
+
+Timed region per step: CUDA events on the launching stream around the two library calls, inputs resident
+in HBM; L2 is flushed (256 MiB write) and u* restored from a pristine copy before each step, outside the
+events.  ``e2e`` repeats the measurement through the same C-ABI calls with pinned host buffers: the H2D copy
+of the step's inputs and the D2H copy of its results are inside the timed region.  Under torchrun each rank
+runs its own droplet instance (ensemble members are independent: weak scaling, no collective on the data
+path); rank 0 prints one JSON line with the max-over-ranks time.  ``--impl reference`` times the CPU oracle
+on the host cores instead (rank 0 only).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "projection Mpts/s & p99 latency, served/mixed vs plain FP64, rel err ≤1e-10"
+UNIT = "Mpts/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """Samples SM clock and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return int(max(x.get("num_threads", 1) for x in info))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def oracle_step(c, g):
+    import oracle
+    ou = oracle.project(g, c["u"], c["v"], c["w"], src=oracle.stefan_source(g, c["C"], c["mdot"], c["rho1"], c["rho2"]),
+                        dt_over_rho0=c["dt_over_rho0"])
+    return oracle.extend_liquid_velocity(g, *ou[:3], c["C"], c["mdot"], c["rho1"], c["rho2"])
+
+
+def time_oracle(c, steps, budget_s=20.0):
+    """Median seconds per oracle step over at most `steps` steps and about `budget_s` seconds."""
+    import oracle
+    g = oracle.Grid(*c["n"], c["dx"], c["dy"], c["dz"], c["bc"])
+    ts = []
+    t_all = time.perf_counter()
+    for _ in range(max(1, steps)):
+        t0 = time.perf_counter()
+        oracle_step(c, g)
+        ts.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all > budget_s:
+            break
+    return float(np.median(ts)), len(ts)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1907_00890_gb300 import synth
+    c = synth.config_droplet(args.n)
+    cells = int(np.prod(c["n"]))
+    # warm-up, then K timed oracle steps (each the full workload, bounded to a few minutes overall)
+    import oracle
+    g = oracle.Grid(*c["n"], c["dx"], c["dy"], c["dz"], c["bc"])
+    for _ in range(min(args.warmup, 1)):
+        oracle_step(c, g)
+    ts = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(c, g)
+        ts.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all > 150.0:
+            break
+    sec = float(np.mean(ts))
+    value = cells * 2 / sec / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": len(ts),
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "droplet step %d^3 (project with Stefan source + liquid-velocity extension), "
+                                   "P,P,NN, FP64" % args.n, "grid": list(c["n"]), "solves_per_step": 2},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                             "sample": "%d full oracle steps of the %d^3 droplet workload" % (len(ts), args.n)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_1907_00890_gb300 import build, synth
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1907_00890_gb300 import vofp
+
+    c = synth.config_droplet(args.n, seed_offset=rank)
+    n = c["n"]
+    cells = int(np.prod(n))
+    plan = vofp.Plan(n, c["dx"], c["dy"], c["dz"], c["bc"])
+    st = torch.cuda.current_stream()
+
+    def T(a):
+        return torch.tensor(a, dtype=torch.float64, device=dev)
+
+    u0 = [T(a) for a in (c["u"], c["v"], c["w"])]
+    u = [x.clone() for x in u0]
+    C, md = T(c["C"]), T(c["mdot"])
+    p = torch.empty(plan.cell_shape, dtype=torch.float64, device=dev)
+    phi = torch.empty_like(p)
+    ue = [torch.empty_like(x) for x in u]
+    ug = [torch.empty_like(x) for x in u]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        vofp.vofp_project_stefan(plan.handle, u[0], u[1], u[2], C, md, c["rho1"], c["rho2"], c["dt_over_rho0"], p)
+        vofp.vofp_extend_liquid_velocity(plan.handle, u[0], u[1], u[2], C, md, c["rho1"], c["rho2"], ue[0], ue[1],
+                                         ue[2], ug[0], ug[1], ug[2], phi)
+
+    def prep():
+        for a, b in zip(u, u0):
+            a.copy_(b)
+        flush.zero_()
+
+    for _ in range(args.warmup):
+        prep()
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timing ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = vofp.vofp_launch_count()
+    vofp.vofp_trace_collect()
+    vofp.vofp_trace_enable(True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for i in range(args.steps):
+            prep()
+            ev[i][0].record(st)
+            step()
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+    vofp.vofp_trace_enable(False)
+    trace = vofp.vofp_trace_collect()
+    launches = vofp.vofp_launch_count() - l0
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = float(np.mean(step_ms))
+    ms_all = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_all, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_all.item())
+    value = world * cells * 2 / (ms_max / 1e3) / 1e6
+
+    # ---- end to end through the same calls with pinned host buffers ----
+    h_in = [torch.empty(x.shape, dtype=torch.float64, pin_memory=True) for x in u0 + [C, md]]
+    for h, d in zip(h_in, u0 + [C, md]):
+        h.copy_(d)
+    h_out = [torch.empty(x.shape, dtype=torch.float64, pin_memory=True) for x in u + [p] + ug]
+    d_in = u + [C, md]
+    h2d = sum(x.numel() * 8 for x in h_in)
+    d2h = sum(x.numel() * 8 for x in h_out)
+    e2e_steps = max(3, min(args.steps, 20))
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    for i in range(e2e_steps + 1):
+        flush.zero_()
+        if i > 0:
+            ev2[i - 1][0].record(st)
+        for d, h in zip(d_in, h_in):
+            d.copy_(h, non_blocking=True)
+        step()
+        for h, d in zip(h_out, u + [p] + ug):
+            h.copy_(d, non_blocking=True)
+        if i > 0:
+            ev2[i - 1][1].record(st)
+    torch.cuda.synchronize()
+    e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in ev2]))
+    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * cells * 2 / (float(e2e_t.item()) / 1e3) / 1e6
+
+    # ---- roofline of the dominant kernel (its launches timed with events on the launching stream) ----
+    roof = roofline_from_trace(trace, n)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "droplet step %d^3 (project with Stefan source + liquid-velocity extension), "
+                                       "P,P,NN, FP64" % args.n, "grid": list(n), "solves_per_step": 2,
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "flushed between steps (256 MiB write, outside the events)"},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": int(launches),
+                "clocks": clk.summary(),
+                "roofline": roof}
+        if not args.no_cpu_baseline:
+            sec, nsteps = time_oracle(c, 10, 20.0)
+            line["cpu_baseline"] = {"value": cells * 2 / sec / 1e6, "unit": UNIT, "cores": cpu_threads(),
+                                    "kind": "oracle",
+                                    "sample": "%d oracle steps (median) of the same %d^3 droplet workload" % (nsteps, args.n)}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+FP64_NOMINAL_GFLOPS = 1250.0   # GB300 FP64 (vector and tensor), the profiling recipe's unit figure
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def algorithmic(kname, n):
+    """Algorithmic HBM bytes and FP64 flops of one launch of kernel class ``kname`` on an n-grid.
+
+    Bytes: each compulsory array read or written once (8 B per FP64 value).  Flops: a real-to-real transform
+    of length m counts 2.5 m log2 m per line (half the 5 m log2 m of a complex FFT); the z recurrence 8 per
+    point (plus one division); stencils their adds and multiplies.
+    """
+    nx, ny, nz = n
+    cells = nx * ny * nz
+
+    def lg(m):
+        return math.log2(m) if m > 1 else 0.0
+
+    tab = {
+        "x_forward": (16, 2.5 * lg(nx)),
+        "x_forward_div": (32, 8 + 2.5 * lg(nx)),
+        "x_forward_stefan": (24, 18 + 2.5 * lg(nx)),
+        "x_forward_div_stefan": (48, 26 + 2.5 * lg(nx)),
+        "y_forward": (16, 2.5 * lg(ny)),
+        "y_inverse": (16, 2.5 * lg(ny)),
+        "z_tridiag": (16, 8),
+        "x_inverse": (16, 2.5 * lg(nx)),
+        "grad_update": (56, 12),
+        "extend_epilogue": (96, 60),
+        "stefan_source": (24, 18),
+    }
+    b, f = tab.get(kname, (0, 0))
+    return b * cells, f * cells
+
+
+def roofline_from_trace(trace, n):
+    """Dominant kernel class (largest summed time) with its achieved rates against the peaks."""
+    if not trace:
+        return None
+    name = max(trace, key=lambda k: trace[k][0])
+    tot_ms, cnt = trace[name]
+    avg_s = tot_ms / cnt / 1e3
+    by, fl = algorithmic(name, n)
+    hbm, how = peaks()
+    gbs = by / avg_s / 1e9
+    gfl = fl / avg_s / 1e9
+    share = tot_ms / sum(v[0] for v in trace.values())
+    mem = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+           "peak_source": how + " (copy test)"}
+    alu = {"bound": "alu", "achieved": gfl, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+           "frac": gfl / FP64_NOMINAL_GFLOPS, "peak_source": "nominal FP64 rate of the recipe"}
+    r = dict(alu if alu["frac"] >= mem["frac"] else mem)
+    r.update({"kernel": name, "launches": cnt, "avg_launch_ms": tot_ms / cnt, "share_of_step": share,
+              "traffic": None, "other": mem if r["bound"] == "alu" else alu,
+              "per_kernel_ms": {k: round(v[0] / v[1], 5) for k, v in trace.items()}})
+    return r
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

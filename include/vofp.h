@@ -1,0 +1,176 @@
+/*
+ * vofp.h -- C ABI of the GB300 FFT-based Poisson projection library.
+ *
+ * The library implements the pressure-projection and liquid-velocity-extension solves of the two-fluid
+ * evaporating-flow VoF method of Scapin, Costa & Brandt (arXiv 1907.00890):
+ *
+ *   - the constant-coefficient Poisson equation of the pressure-splitting projection (§3.2, Eq. lap_p,
+ *     constant-density part) and the velocity correction that follows it;
+ *   - the Stefan-flow potential lap(phi) = mdot (1/rho2 - 1/rho1) |grad C| (§3.6, Eq. ext_div), the
+ *     divergence-free liquid extension u1e = u - grad(phi) (Eq. jump_subtr) and the interface velocity
+ *     uG = u1e - (mdot/rho1) n (Eq. int_vel).
+ *
+ * Both are solved exactly (direct solver, §3.2) on a uniform-in-x,y MAC grid: real-to-real transforms in x
+ * and y (periodic: DFT; Neumann: DCT-II; Dirichlet: DST-II), one tridiagonal system in z per (x, y)
+ * wavenumber pair, inverse transforms, gradient correction.  All kernels are hand-written CUDA for sm_103a.
+ *
+ * GRID AND LAYOUT (all arrays C-ordered [z][y][x], x fastest, FP64):
+ *   cell arrays (p, f, src, C, mdot, phi): nz * ny * nx values.
+ *   face arrays: index i along the face's own axis is the LOW face of cell i.  A periodic axis stores n
+ *   faces, a bounded axis n + 1 (both boundary faces):
+ *     u: nz * ny * (nx + (bc[0] != VOFP_BC_P)),  v: nz * (ny + (bc[1] != VOFP_BC_P)) * nx,
+ *     w: (nz + (bc[2] != VOFP_BC_P)) * ny * nx.
+ *   Boundary conditions are homogeneous, per axis (§3.2: several combinations of homogeneous pressure
+ *   boundary conditions; §3.6: phi takes the pressure's).  N = zero normal gradient at the boundary face
+ *   (the face velocity there is an input the projection leaves unchanged); D = zero value at the boundary
+ *   face (ghost value -p).  ND/DN are accepted on z only.
+ *   When no axis has a D end the operator is singular: the volume-weighted mean of the right-hand side is
+ *   removed (reported as compat_defect) and the returned potential has zero volume-weighted mean.
+ *
+ * OWNERSHIP AND STREAMS: the caller owns every field pointer (device memory).  The plan owns its tables
+ * and workspace; vofp_plan_destroy frees them.  Calls are asynchronous on the given stream (a
+ * cudaStream_t passed as void*, NULL = legacy default stream) unless `info` is non-NULL, in which case the
+ * call synchronises that stream to fill it.  One plan may be used by one stream at a time (its workspace is
+ * shared by its calls).
+ *
+ * ERRORS: every int-returning call returns 0 on success, > 0 for a warning, < 0 for an error; nothing is
+ * launched when an argument check fails.  vofp_error_string() gives the message.
+ */
+#ifndef VOFP_H
+#define VOFP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define VOFP_OK 0
+#define VOFP_WARN_INCOMPATIBLE_RHS 1 /* singular operator and |mean(f)| > 1e-12 * mean(|f|)            */
+#define VOFP_WARN_NOT_CONVERGED 2    /* mixed precision: refinement stopped at max_refine              */
+#define VOFP_ERR_INVALID_ARG -1
+#define VOFP_ERR_UNSUPPORTED -2
+#define VOFP_ERR_OOM -3
+#define VOFP_ERR_CUDA -4
+#define VOFP_ERR_TIMEOUT -5
+#define VOFP_ERR_BUSY -6
+#define VOFP_ERR_NONFINITE -7
+
+/* boundary condition per axis (first letter = low end, second = high end) */
+typedef enum { VOFP_BC_P = 0, VOFP_BC_NN = 1, VOFP_BC_DD = 2, VOFP_BC_ND = 3, VOFP_BC_DN = 4 } vofp_bc;
+
+/* arithmetic of the solve */
+typedef enum {
+  VOFP_FP64 = 0, /* every step in FP64                                                               */
+  VOFP_MIXED = 1 /* FP32 transforms, FP64 low modes / reductions / residual, defect-correction refinement */
+} vofp_prec;
+
+typedef struct {
+  int prec;       /* vofp_prec                                                                  */
+  double tol;     /* mixed: stop when ||f - L p|| / ||f|| <= tol (default 1e-10)                   */
+  int max_refine; /* mixed: maximum defect-correction iterations (default 6)                       */
+  int grad_mode;  /* |grad C| and n: 0 = central differences (default), 1 = Youngs corner average    */
+  int tune;       /* 0 = default launch shapes, 1 = autotuned (cached per shape)                    */
+} vofp_opts;
+
+typedef struct {
+  double compat_defect; /* volume-weighted mean removed from the right-hand side (0 if L regular) */
+  double rel_residual;  /* mixed: final ||f - L p||_2 / ||f||_2; FP64: not computed (0)             */
+  int refine_iters;     /* mixed: defect-correction iterations performed                            */
+  int status;           /* same as the return value                                                 */
+} vofp_info;
+
+typedef struct vofp_plan vofp_plan;
+
+/* Fill `opt` with the defaults (FP64, tol 1e-10, max_refine 6, central gradients, no tuning). */
+void vofp_opts_default(vofp_opts* opt);
+
+/*
+ * Create a plan for an nx x ny x nz grid (each >= 1) with uniform spacings dx, dy > 0 and z cell widths
+ * dz[0..nz-1] > 0 (HOST pointer, copied), boundary conditions bc[3] (x, y, z; ND/DN only on z), options
+ * `opt` (NULL = defaults).  Builds the eigenvalue, twiddle and z-coefficient tables on the current CUDA
+ * device and allocates the workspace.  §3 (grid), §3.2 (solver, boundary conditions).
+ * Errors: INVALID_ARG (sizes, spacings, bc), UNSUPPORTED (ND/DN on x or y), OOM, CUDA.
+ */
+int vofp_plan_create(int nx, int ny, int nz, double dx, double dy, const double* dz, const int bc[3],
+                     const vofp_opts* opt, vofp_plan** out);
+
+/* Free the plan's device tables and workspace (NULL is ignored).  Synchronises the device first. */
+void vofp_plan_destroy(vofp_plan* plan);
+
+/* Device bytes held by the plan (tables + workspace). */
+size_t vofp_plan_workspace_bytes(const vofp_plan* plan);
+
+/*
+ * Solve L p = f - fbar (§3.2, Eq. lap_p left-hand side; §3.6 Eq. ext_div).  f, p: device cell arrays
+ * (may alias).  Errors: INVALID_ARG (NULL plan/pointers), CUDA, NONFINITE (only detected when info != NULL).
+ */
+int vofp_poisson_solve(vofp_plan* plan, const double* f, double* p, void* stream, vofp_info* info);
+
+/*
+ * Pressure projection (§3.2, Eq. lap_p with constant density and the correction step after it):
+ *   f = (D u* - src) / dt_over_rho0,  L p = f - fbar,  u = u* - dt_over_rho0 G p   (u, v, w in place).
+ * src: device cell array or NULL (no phase-change source).  p: device cell array or NULL (not returned).
+ * dt_over_rho0 > 0.  Errors: INVALID_ARG, CUDA, NONFINITE (only with info).
+ */
+int vofp_project(vofp_plan* plan, double* u, double* v, double* w, const double* src, double dt_over_rho0,
+                 double* p, void* stream, vofp_info* info);
+
+/*
+ * Liquid-velocity extension and interface velocity (§3.6):
+ *   s = mdot (1/rho2 - 1/rho1) |grad C|  (Eq. ext_div),  L phi = s - sbar,
+ *   u1e = u - G phi  (Eq. jump_subtr),
+ *   uG = u1e - (mdot_f / rho1) n_f  (Eq. int_vel), n = -grad C / |grad C| (pointing into the gas, Eq.
+ *   rankine), n = 0 where min(C, 1 - C) < 1e-8; face values of mdot and n are means of the two adjacent
+ *   cells (the one adjacent cell on a boundary face).
+ * u, v, w: device face arrays (input, not modified).  C, mdot: device cell arrays.  rho1, rho2 > 0.
+ * ue, ve, we: device face arrays (output, required).  ug, vg, wg: output or all three NULL.  phi: device
+ * cell array or NULL.  Errors: INVALID_ARG, CUDA, NONFINITE (only with info).
+ */
+int vofp_extend_liquid_velocity(vofp_plan* plan, const double* u, const double* v, const double* w,
+                                const double* C, const double* mdot, double rho1, double rho2, double* ue,
+                                double* ve, double* we, double* ug, double* vg, double* wg, double* phi,
+                                void* stream, vofp_info* info);
+
+/*
+ * Stefan source s = mdot (1/rho2 - 1/rho1) |grad C| at cell centres (§3.2 last term of Eq. lap_p with the
+ * regularised delta |grad C|; §3.6 Eq. ext_div right-hand side), |grad C| per opts.grad_mode.
+ * C, mdot: device cell arrays; s: device cell array (output).  Errors: INVALID_ARG, CUDA.
+ */
+int vofp_stefan_source(vofp_plan* plan, const double* C, const double* mdot, double rho1, double rho2, double* s,
+                       void* stream);
+
+/*
+ * Pressure projection whose phase-change source is the Stefan source of (C, mdot, rho1, rho2), computed
+ * inside the divergence pass (same result as vofp_stefan_source followed by vofp_project with that src):
+ *   f = (D u* - mdot (1/rho2 - 1/rho1) |grad C|) / dt_over_rho0   (Eq. lap_p, constant-density part).
+ * Arguments as vofp_project plus the source inputs.  Errors: INVALID_ARG, CUDA, NONFINITE (only with info).
+ */
+int vofp_project_stefan(vofp_plan* plan, double* u, double* v, double* w, const double* C, const double* mdot,
+                        double rho1, double rho2, double dt_over_rho0, double* p, void* stream, vofp_info* info);
+
+/* Number of kernels this library has launched in this process (all plans, all devices); diagnostics. */
+unsigned long long vofp_launch_count(void);
+
+/*
+ * Kernel tracing (diagnostics; the paper has no counterpart).  While enabled, every launch is bracketed by
+ * two CUDA events recorded on its stream.  vofp_trace_enable returns the previous state.
+ * vofp_trace_collect waits for the recorded events, writes the summed device milliseconds and the launch
+ * count of kernel class i to ms[i], count[i] for i < n (classes: vofp_trace_kernel_classes(), names:
+ * vofp_trace_name(i)) and clears the record.  Errors: INVALID_ARG (NULL or n <= 0), CUDA.
+ */
+int vofp_trace_enable(int on);
+int vofp_trace_collect(double* ms, unsigned long long* count, int n);
+int vofp_trace_kernel_classes(void);
+const char* vofp_trace_name(int id);
+
+/* Static message for a status code. */
+const char* vofp_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VOFP_H */

@@ -1,0 +1,328 @@
+// Transform and tridiagonal passes of the direct Poisson solve (device code, templated on precision).
+//
+//   x pass (forward) : right-hand side (given, divergence stencil, Stefan source or FP64 residual) fused with
+//                      the real-to-real x transform of two grid lines per complex FFT;
+//   y pass           : the same transform along y on column tiles of one z plane;
+//   z pass           : one tridiagonal system per (x, y) spectral pair (Thomas; Sherman-Morrison around it
+//                      for periodic z; gauge-fixed solve of the singular mean mode);
+//   y pass (inverse), x pass (inverse) : back to cell values.
+// The spectrum S is stored [z][y][x] like the fields, one real number per cell.
+#pragma once
+
+#include "stencil.cuh"
+#include "vofp_internal.cuh"
+
+namespace vofp {
+
+enum RhsMode { RHS_F = 0, RHS_DIV = 1, RHS_STEFAN = 2, RHS_RESID = 3, RHS_DIV_STEFAN = 4 };
+
+struct XArgs {
+  GridDev g;
+  FftDesc fd;
+  const void* tw;     // complex twiddles of the compute precision
+  const void* quart;  // quarter-wave twiddles
+  int pb;             // line pairs per block
+  // right-hand side inputs
+  const double* f;    // RHS_F: f;  RHS_RESID: f (FP64)
+  const double* u;
+  const double* v;
+  const double* w;
+  const double* src;  // RHS_DIV: optional source
+  const double* C;
+  const double* mdot;
+  const double* p;    // RHS_RESID: current potential
+  double scale;       // multiplies the right-hand side (RHS_F, RHS_DIV)
+  double coef;        // RHS_STEFAN: 1/rho2 - 1/rho1
+  int grad_mode;
+  double* fsave;      // if non-null, the FP64 right-hand side is stored here (mixed path)
+  vofp_devinfo* info; // if non-null, accumulate sum |f| V (and ||f||^2 for RHS_RESID into res2)
+  void* S;            // spectrum output
+};
+
+// 7-point L p at a cell with the ghost rules of the MAC operator (FP64).
+__device__ __forceinline__ double lap_at(const GridDev& g, const double* __restrict__ p, int i, int j, int k) {
+  const size_t plane = (size_t)g.nx * g.ny;
+  const size_t c = k * plane + (size_t)j * g.nx + i;
+  const double pc = __ldg(p + c);
+  double r = 0;
+  // x
+  {
+    double lo, hi;
+    if (i > 0) lo = __ldg(p + c - 1);
+    else lo = g.bcx == VOFP_BC_P ? __ldg(p + c + g.nx - 1) : (g.bcx == VOFP_BC_DD ? -pc : pc);
+    if (i < g.nx - 1) hi = __ldg(p + c + 1);
+    else hi = g.bcx == VOFP_BC_P ? __ldg(p + c - (g.nx - 1)) : (g.bcx == VOFP_BC_DD ? -pc : pc);
+    r += (hi - 2.0 * pc + lo) / (g.dx * g.dx);
+  }
+  {
+    double lo, hi;
+    if (j > 0) lo = __ldg(p + c - g.nx);
+    else lo = g.bcy == VOFP_BC_P ? __ldg(p + c + (size_t)(g.ny - 1) * g.nx) : (g.bcy == VOFP_BC_DD ? -pc : pc);
+    if (j < g.ny - 1) hi = __ldg(p + c + g.nx);
+    else hi = g.bcy == VOFP_BC_P ? __ldg(p + c - (size_t)(g.ny - 1) * g.nx) : (g.bcy == VOFP_BC_DD ? -pc : pc);
+    r += (hi - 2.0 * pc + lo) / (g.dy * g.dy);
+  }
+  {
+    double lo, hi;
+    const bool lowN = g.bcz == VOFP_BC_NN || g.bcz == VOFP_BC_ND;
+    const bool highN = g.bcz == VOFP_BC_NN || g.bcz == VOFP_BC_DN;
+    if (k > 0) lo = __ldg(p + c - plane);
+    else lo = g.bcz == VOFP_BC_P ? __ldg(p + c + (size_t)(g.nz - 1) * plane) : (lowN ? pc : -pc);
+    if (k < g.nz - 1) hi = __ldg(p + c + plane);
+    else hi = g.bcz == VOFP_BC_P ? __ldg(p + c - (size_t)(g.nz - 1) * plane) : (highN ? pc : -pc);
+    const double dzk = __ldg(g.dz + k);
+    r += ((hi - pc) / __ldg(g.hz + k + 1) - (pc - lo) / __ldg(g.hz + k)) / dzk;
+  }
+  return r;
+}
+
+template <int MODE>
+__device__ __forceinline__ double rhs_at(const XArgs& a, int i, int j, int k) {
+  const size_t c = ((size_t)k * a.g.ny + j) * a.g.nx + i;
+  double f;
+  if (MODE == RHS_F) {
+    f = __ldg(a.f + c) * a.scale;
+  } else if (MODE == RHS_DIV) {
+    f = divergence_at(a.g, a.u, a.v, a.w, i, j, k);
+    if (a.src) f -= __ldg(a.src + c);
+    f *= a.scale;
+  } else if (MODE == RHS_STEFAN) {
+    const double3 gc = grad_c_at(a.g, a.C, i, j, k, a.grad_mode);
+    f = __ldg(a.mdot + c) * a.coef * sqrt(gc.x * gc.x + gc.y * gc.y + gc.z * gc.z);
+  } else if (MODE == RHS_DIV_STEFAN) {
+    const double3 gc = grad_c_at(a.g, a.C, i, j, k, a.grad_mode);
+    const double s = __ldg(a.mdot + c) * a.coef * sqrt(gc.x * gc.x + gc.y * gc.y + gc.z * gc.z);
+    f = (divergence_at(a.g, a.u, a.v, a.w, i, j, k) - s) * a.scale;
+  } else {
+    f = __ldg(a.f + c) - lap_at(a.g, a.p, i, j, k);
+  }
+  return f;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  }
+  return s;
+}
+
+// x pass, forward: RHS + transform of line pairs (2p, 2p+1) of the flattened (k, j) line index.
+template <typename T, typename C, int MODE>
+__global__ void __launch_bounds__(256) k_xfwd(XArgs a) {
+  typedef decltype(C::x) R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* b0 = reinterpret_cast<C*>(smem_raw);
+  const int n = a.g.nx;
+  const int PB = a.pb;
+  C* b1 = b0 + PB * n;
+  __shared__ double red[32];
+  const long nlines = (long)a.g.ny * a.g.nz;
+  const long pair0 = (long)blockIdx.x * PB;
+  const int bc = a.g.bcx;
+  double acc_abs = 0, acc_sq = 0;
+  for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
+    const int pb = t / n, i = t - pb * n;
+    const long l0 = 2 * (pair0 + pb), l1 = l0 + 1;
+    double fa = 0, fb = 0;
+    if (l0 < nlines) {
+      const int k = (int)(l0 / a.g.ny), j = (int)(l0 - (long)k * a.g.ny);
+      fa = rhs_at<MODE>(a, i, j, k);
+      if (a.fsave) a.fsave[l0 * n + i] = fa;
+      if (a.info) {
+        const double vol = a.g.dx * a.g.dy * __ldg(a.g.dz + k);
+        acc_abs += fabs(fa) * vol;
+        acc_sq += fa * fa;
+      }
+    }
+    if (l1 < nlines) {
+      const int k = (int)(l1 / a.g.ny), j = (int)(l1 - (long)k * a.g.ny);
+      fb = rhs_at<MODE>(a, i, j, k);
+      if (a.fsave) a.fsave[l1 * n + i] = fb;
+      if (a.info) {
+        const double vol = a.g.dx * a.g.dy * __ldg(a.g.dz + k);
+        acc_abs += fabs(fb) * vol;
+        acc_sq += fb * fb;
+      }
+    }
+    int idx = i;
+    R sg = 1;
+    if (bc != VOFP_BC_P) {
+      idx = dct_perm(i, n);
+      if (bc == VOFP_BC_DD && (i & 1)) sg = -1;
+    }
+    b0[pb * n + idx] = cmk<C>(sg * (R)fa, sg * (R)fb);
+  }
+  if (a.info) {
+    const double s1 = block_sum(acc_abs, red);
+    if (threadIdx.x == 0 && s1 != 0) atomicAdd(&a.info->abs_sum, s1);
+    if (MODE == RHS_RESID) {
+      const double s2 = block_sum(acc_sq, red);
+      if (threadIdx.x == 0 && s2 != 0) atomicAdd(&a.info->res2, s2);
+    }
+  }
+  __syncthreads();
+  const C* Z = fft_smem<C>(b0, b1, PB, a.fd, reinterpret_cast<const C*>(a.tw));
+  const C* quart = reinterpret_cast<const C*>(a.quart);
+  T* S = reinterpret_cast<T*>(a.S);
+  for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
+    const int pb = t / n, q = t - pb * n;
+    const long l0 = 2 * (pair0 + pb), l1 = l0 + 1;
+    R oa, ob;
+    fwd_post<C>(Z + pb * n, n, bc, q, quart, oa, ob);
+    if (l0 < nlines) S[l0 * n + q] = (T)oa;
+    if (l1 < nlines) S[l1 * n + q] = (T)ob;
+  }
+}
+
+struct YArgs {
+  int nx, ny, nz, bc;
+  FftDesc fd;
+  const void* tw;
+  const void* quart;
+  int tx;  // columns per block (even)
+  void* S;
+};
+
+// y pass on a tile of `tx` columns (pairs of columns share one complex FFT) of plane k = blockIdx.y.
+template <typename T, typename C, bool INV>
+__global__ void __launch_bounds__(256) k_ypass(YArgs a) {
+  typedef decltype(C::x) R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = a.ny;
+  const int B = a.tx >> 1;
+  C* b0 = reinterpret_cast<C*>(smem_raw);
+  C* b1 = b0 + B * n;
+  const int i0 = blockIdx.x * a.tx;
+  const size_t base = (size_t)blockIdx.y * a.ny * a.nx;
+  T* S = reinterpret_cast<T*>(a.S);
+  const int bc = a.bc;
+  const C* quart = reinterpret_cast<const C*>(a.quart);
+  if (!INV) {
+    for (int t = threadIdx.x; t < B * n; t += blockDim.x) {
+      const int c = t % B, j = t / B;
+      const int i = i0 + 2 * c;
+      const size_t o = base + (size_t)j * a.nx + i;
+      const R va = i < a.nx ? (R)S[o] : (R)0;
+      const R vb = i + 1 < a.nx ? (R)S[o + 1] : (R)0;
+      int idx = j;
+      R sg = 1;
+      if (bc != VOFP_BC_P) {
+        idx = dct_perm(j, n);
+        if (bc == VOFP_BC_DD && (j & 1)) sg = -1;
+      }
+      b0[c * n + idx] = cmk<C>(sg * va, sg * vb);
+    }
+    __syncthreads();
+    const C* Z = fft_smem<C>(b0, b1, B, a.fd, reinterpret_cast<const C*>(a.tw));
+    for (int t = threadIdx.x; t < B * n; t += blockDim.x) {
+      const int c = t % B, q = t / B;
+      const int i = i0 + 2 * c;
+      R oa, ob;
+      fwd_post<C>(Z + c * n, n, bc, q, quart, oa, ob);
+      const size_t o = base + (size_t)q * a.nx + i;
+      if (i < a.nx) S[o] = (T)oa;
+      if (i + 1 < a.nx) S[o + 1] = (T)ob;
+    }
+  } else {
+    // stage the tile column-major in b1: column col holds the packed line of length n
+    R* st = reinterpret_cast<R*>(b1);
+    for (int t = threadIdx.x; t < B * n; t += blockDim.x) {
+      const int c = t % B, q = t / B;
+      const int i = i0 + 2 * c;
+      const size_t o = base + (size_t)q * a.nx + i;
+      st[(2 * c) * n + q] = i < a.nx ? (R)S[o] : (R)0;
+      st[(2 * c + 1) * n + q] = i + 1 < a.nx ? (R)S[o + 1] : (R)0;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < B * n; t += blockDim.x) {
+      const int c = t / n, m = t - c * n;
+      const R* ra = st + (2 * c) * n;
+      const R* rb = st + (2 * c + 1) * n;
+      b0[c * n + m] = inv_pre<C>([&](int q) { return ra[q]; }, [&](int q) { return rb[q]; }, n, bc, m, quart);
+    }
+    __syncthreads();
+    const C* Y = fft_smem<C>(b0, b1, B, a.fd, reinterpret_cast<const C*>(a.tw));
+    for (int t = threadIdx.x; t < B * n; t += blockDim.x) {
+      const int c = t % B, j = t / B;
+      const int i = i0 + 2 * c;
+      int idx = j;
+      R sg = 1;
+      if (bc != VOFP_BC_P) {
+        idx = dct_perm(j, n);
+        if (bc == VOFP_BC_DD && (j & 1)) sg = -1;
+      }
+      const C y = Y[c * n + idx];
+      const size_t o = base + (size_t)j * a.nx + i;
+      if (i < a.nx) S[o] = (T)(sg * y.x);
+      if (i + 1 < a.nx) S[o + 1] = (T)(-sg * y.y);
+    }
+  }
+}
+
+struct XInvArgs {
+  int nx, ny, nz, bc;
+  FftDesc fd;
+  const void* tw;
+  const void* quart;
+  int pb;
+  const void* S;
+  double* p;
+  int accumulate;  // 0: p = value, 1: p += value
+};
+
+// x pass, inverse: two packed lines per complex FFT, result written (or added) to the FP64 cell array p.
+template <typename T, typename C>
+__global__ void __launch_bounds__(256) k_xinv(XInvArgs a) {
+  typedef decltype(C::x) R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = a.nx;
+  const int PB = a.pb;
+  C* b0 = reinterpret_cast<C*>(smem_raw);
+  C* b1 = b0 + PB * n;
+  const long nlines = (long)a.ny * a.nz;
+  const long pair0 = (long)blockIdx.x * PB;
+  const T* S = reinterpret_cast<const T*>(a.S);
+  const int bc = a.bc;
+  const C* quart = reinterpret_cast<const C*>(a.quart);
+  R* st = reinterpret_cast<R*>(b1);
+  for (int t = threadIdx.x; t < 2 * PB * n; t += blockDim.x) {
+    const long l = 2 * pair0 + t / n;
+    st[t] = l < nlines ? (R)S[l * n + (t % n)] : (R)0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
+    const int pb = t / n, m = t - pb * n;
+    const R* ra = st + (2 * pb) * n;
+    const R* rb = st + (2 * pb + 1) * n;
+    b0[pb * n + m] = inv_pre<C>([&](int q) { return ra[q]; }, [&](int q) { return rb[q]; }, n, bc, m, quart);
+  }
+  __syncthreads();
+  const C* Y = fft_smem<C>(b0, b1, PB, a.fd, reinterpret_cast<const C*>(a.tw));
+  for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
+    const int pb = t / n, i = t - pb * n;
+    const long l0 = 2 * (pair0 + pb), l1 = l0 + 1;
+    int idx = i;
+    R sg = 1;
+    if (bc != VOFP_BC_P) {
+      idx = dct_perm(i, n);
+      if (bc == VOFP_BC_DD && (i & 1)) sg = -1;
+    }
+    const C y = Y[pb * n + idx];
+    const double va = (double)(sg * y.x), vb = (double)(-sg * y.y);
+    if (a.accumulate) {
+      if (l0 < nlines) a.p[l0 * n + i] += va;
+      if (l1 < nlines) a.p[l1 * n + i] += vb;
+    } else {
+      if (l0 < nlines) a.p[l0 * n + i] = va;
+      if (l1 < nlines) a.p[l1 * n + i] = vb;
+    }
+  }
+}
+
+}  // namespace vofp

@@ -1,0 +1,104 @@
+// MAC-grid stencils shared by the transform passes and the epilogues (device code).
+//
+// Face arrays: index i along the face's axis is the low face of cell i; a periodic axis stores n faces,
+// a bounded axis n + 1.  Divergence (Eq. mass, discretised): sum over axes of (F_{i+1} - F_i) / w_i.
+// Gradient on faces (correction after Eq. lap_p): (p_i - p_{i-1}) / h with h the centre distance; an N
+// boundary face is left untouched, a D boundary face uses the ghost value -p (2 p_0 / w_0 low end,
+// -2 p_{n-1} / w_{n-1} high end).  |grad C| and n (§3.2 regularised delta, §3.6 Eq. int_vel): central or
+// Youngs corner-averaged differences with C copied into ghost cells at bounded ends and wrapped at periodic
+// ends; n = -grad C / |grad C|, zero where min(C, 1 - C) < 1e-8 or |grad C| = 0.
+#pragma once
+
+#include "vofp_internal.cuh"
+
+namespace vofp {
+
+struct GridDev {
+  int nx, ny, nz;
+  int bcx, bcy, bcz;
+  double dx, dy;
+  const double* dz;  // nz
+  const double* hz;  // nz + 1 centre distances across z faces (ghost distances at the ends)
+};
+
+__host__ __device__ __forceinline__ int nface(int n, int bc) { return n + (bc != VOFP_BC_P); }
+
+// Neighbour index for a cell field: wrapped on a periodic axis, clamped (ghost copy) on a bounded one.
+__device__ __forceinline__ int cw(int i, int n, int bc) {
+  if (i < 0) return bc == VOFP_BC_P ? i + n : 0;
+  if (i >= n) return bc == VOFP_BC_P ? i - n : n - 1;
+  return i;
+}
+
+__device__ __forceinline__ double divergence_at(const GridDev& g, const double* __restrict__ u,
+                                                const double* __restrict__ v, const double* __restrict__ w, int i,
+                                                int j, int k) {
+  const int nxf = nface(g.nx, g.bcx), nyf = nface(g.ny, g.bcy);
+  const size_t ub = ((size_t)k * g.ny + j) * nxf;
+  const int ip = (g.bcx == VOFP_BC_P && i + 1 == g.nx) ? 0 : i + 1;
+  const double du = __ldg(u + ub + ip) - __ldg(u + ub + i);
+  const size_t vb = (size_t)k * nyf * g.nx + i;
+  const int jp = (g.bcy == VOFP_BC_P && j + 1 == g.ny) ? 0 : j + 1;
+  const double dv = __ldg(v + vb + (size_t)jp * g.nx) - __ldg(v + vb + (size_t)j * g.nx);
+  const size_t plane = (size_t)g.ny * g.nx;
+  const int kp = (g.bcz == VOFP_BC_P && k + 1 == g.nz) ? 0 : k + 1;
+  const size_t wb = (size_t)j * g.nx + i;
+  const double dw = __ldg(w + wb + kp * plane) - __ldg(w + wb + k * plane);
+  return du / g.dx + dv / g.dy + dw / __ldg(g.dz + k);
+}
+
+__device__ __forceinline__ double cval(const GridDev& g, const double* __restrict__ C, int i, int j, int k) {
+  i = cw(i, g.nx, g.bcx);
+  j = cw(j, g.ny, g.bcy);
+  k = cw(k, g.nz, g.bcz);
+  return __ldg(C + ((size_t)k * g.ny + j) * g.nx + i);
+}
+
+// Cell-centred gradient of C: mode 0 central, mode 1 Youngs.
+__device__ __forceinline__ double3 grad_c_at(const GridDev& g, const double* __restrict__ C, int i, int j, int k,
+                                             int mode) {
+  double3 r;
+  if (mode == 0) {
+    r.x = (cval(g, C, i + 1, j, k) - cval(g, C, i - 1, j, k)) / (2.0 * g.dx);
+    r.y = (cval(g, C, i, j + 1, k) - cval(g, C, i, j - 1, k)) / (2.0 * g.dy);
+    r.z = (cval(g, C, i, j, k + 1) - cval(g, C, i, j, k - 1)) / (__ldg(g.hz + k) + __ldg(g.hz + k + 1));
+    return r;
+  }
+  const double wt[3] = {0.25, 0.5, 0.25};
+  double gx = 0, gy = 0, gz = 0;
+  for (int s = 0; s < 2; ++s) {
+    double ax = 0, ay = 0, az = 0;
+    for (int a = -1; a <= 1; ++a) {
+      for (int b = -1; b <= 1; ++b) {
+        const double wab = wt[a + 1] * wt[b + 1];
+        ax += wab * (cval(g, C, i + s, j + a, k + b) - cval(g, C, i + s - 1, j + a, k + b));
+        ay += wab * (cval(g, C, i + a, j + s, k + b) - cval(g, C, i + a, j + s - 1, k + b));
+        az += wab * (cval(g, C, i + a, j + b, k + s) - cval(g, C, i + a, j + b, k + s - 1));
+      }
+    }
+    gx += ax / g.dx;
+    gy += ay / g.dy;
+    gz += az / __ldg(g.hz + k + s);
+  }
+  r.x = 0.5 * gx;
+  r.y = 0.5 * gy;
+  r.z = 0.5 * gz;
+  return r;
+}
+
+__device__ __forceinline__ double3 normal_at(const GridDev& g, const double* __restrict__ C, int i, int j, int k,
+                                             int mode) {
+  const double c = __ldg(C + ((size_t)k * g.ny + j) * g.nx + i);
+  double3 n = make_double3(0.0, 0.0, 0.0);
+  if (fmin(c, 1.0 - c) < 1e-8) return n;
+  const double3 gc = grad_c_at(g, C, i, j, k, mode);
+  const double m = sqrt(gc.x * gc.x + gc.y * gc.y + gc.z * gc.z);
+  if (m > 0) {
+    n.x = -gc.x / m;
+    n.y = -gc.y / m;
+    n.z = -gc.z / m;
+  }
+  return n;
+}
+
+}  // namespace vofp

@@ -1,0 +1,90 @@
+// Kernel tracing: when enabled, every launch of the library is bracketed by a pair of CUDA events recorded
+// on the launching stream; vofp_trace_collect() waits for them and returns the summed device time and the
+// launch count per kernel class.  Disabled by default (one relaxed atomic load per launch).
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "solve_internal.h"
+
+namespace vofp {
+
+static const char* kNames[KID_COUNT] = {
+    "x_forward",   "x_forward_div",   "x_forward_stefan", "x_forward_div_stefan", "y_forward",
+    "z_tridiag",   "y_inverse",       "x_inverse",        "grad_update",          "extend_epilogue",
+    "stefan_source", "residual_update", "fused_yzy",      "batched"};
+
+struct TraceRec {
+  int kid;
+  cudaEvent_t a, b;
+};
+
+static std::atomic<int> g_on{0};
+static std::mutex g_mu;
+static std::vector<TraceRec> g_recs;
+static std::vector<cudaEvent_t> g_pool;
+
+static cudaEvent_t get_event() {
+  if (!g_pool.empty()) {
+    cudaEvent_t e = g_pool.back();
+    g_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void trace_begin(int kid, cudaStream_t st, TraceTok* tok) {
+  tok->active = 0;
+  if (!g_on.load(std::memory_order_relaxed)) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  tok->active = 1;
+  tok->kid = kid;
+  tok->a = get_event();
+  tok->b = get_event();
+  cudaEventRecord(tok->a, st);
+}
+
+void trace_end(TraceTok* tok, cudaStream_t st) {
+  if (!tok->active) return;
+  cudaEventRecord(tok->b, st);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_recs.push_back({tok->kid, tok->a, tok->b});
+}
+
+}  // namespace vofp
+
+using namespace vofp;
+
+extern "C" int vofp_trace_enable(int on) {
+  const int prev = g_on.exchange(on ? 1 : 0);
+  return prev;
+}
+
+extern "C" int vofp_trace_collect(double* ms, unsigned long long* count, int n) {
+  if (!ms || !count || n <= 0) return VOFP_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    ms[i] = 0;
+    count[i] = 0;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  int status = VOFP_OK;
+  for (const TraceRec& r : g_recs) {
+    float t = 0;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess)
+      status = VOFP_ERR_CUDA;
+    if (r.kid >= 0 && r.kid < n) {
+      ms[r.kid] += t;
+      count[r.kid] += 1;
+    }
+    g_pool.push_back(r.a);
+    g_pool.push_back(r.b);
+  }
+  g_recs.clear();
+  return status;
+}
+
+extern "C" const char* vofp_trace_name(int id) { return (id >= 0 && id < KID_COUNT) ? kNames[id] : "unknown"; }
+
+extern "C" int vofp_trace_kernel_classes(void) { return KID_COUNT; }

@@ -1,0 +1,362 @@
+// Internal declarations of the vofp library: plan layout, launch descriptors and the shared-memory FFT
+// engine used by every transform pass.
+//
+// Transform conventions (per axis of n cells; every forward/inverse pair multiplies by n):
+//   periodic  : X[m] = sum_j x[j] e^{-2 pi i m j / n}, stored half-complex and interleaved:
+//               r[0] = Re X[0], r[2m-1] = Re X[m], r[2m] = Im X[m] (1 <= m < n/2), r[n-1] = Re X[n/2] (n even);
+//               eigenvalue of r[q]: -(4/h^2) sin^2(pi ((q+1)/2) / n).
+//   NN        : DCT-II, X[m] = sum_j x[j] cos(pi m (j+1/2) / n); eigenvalue -(4/h^2) sin^2(pi m / (2n)).
+//   DD        : DST-II, X[m] = sum_j x[j] sin(pi (m+1)(j+1/2) / n); eigenvalue -(4/h^2) sin^2(pi (m+1) / (2n)).
+// Each is evaluated for two real lines at once through one complex FFT of length n (a + i b): DFT split by
+// Hermitian symmetry; DCT-II via the even/odd reordering v[j/2] = x[j] (j even), v[n-1-(j-1)/2] = x[j]
+// (j odd) followed by a quarter-wave twiddle; DST-II as the DCT-II of (-1)^j x[j] read in reverse order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vofp.h"
+
+#define VOFP_MAX_STAGES 24
+
+namespace vofp {
+
+// ---- small complex helpers ---------------------------------------------------------------------------
+
+template <typename R>
+struct Cplx;
+template <>
+struct Cplx<double> {
+  typedef double2 T;
+};
+template <>
+struct Cplx<float> {
+  typedef float2 T;
+};
+
+template <typename C>
+__device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b) {
+  C r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) {
+  return cmk<C>(a.x + b.x, a.y + b.y);
+}
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) {
+  return cmk<C>(a.x - b.x, a.y - b.y);
+}
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// multiply by -i
+template <typename C>
+__device__ __forceinline__ C cmi(C a) {
+  return cmk<C>(a.y, -a.x);
+}
+
+// ---- FFT descriptor ----------------------------------------------------------------------------------
+
+struct FftDesc {
+  int n;
+  int nst;
+  int radix[VOFP_MAX_STAGES];
+};
+
+// Per-axis tables on the device.
+struct AxisDev {
+  int n;
+  int bc;
+  FftDesc fd;
+  const double2* tw64;    // e^{-2 pi i k / n}, k < n
+  const double2* quart64; // e^{-i pi k / (2 n)}, k < n
+  const float2* tw32;
+  const float2* quart32;
+  const double* lam; // eigenvalue of packed spectral index q, q < n
+};
+
+// Host-side factorisation of n into radices (8, 4, then 2, 3, 5, then any remaining prime).
+void factor_radices(int n, FftDesc* fd);
+
+// ---- shared-memory Stockham FFT ----------------------------------------------------------------------
+// Batched forward complex DFT (exponent -2 pi i / n) of `batch` contiguous sequences of length n held in
+// shared memory buffer `a`; `b` is a second buffer of the same size.  Returns the buffer that holds the
+// result.  All threads of the block must call it; it ends with __syncthreads().
+
+template <typename C, int RAD>
+__device__ __forceinline__ void dft_small(C* v) {
+  typedef decltype(C::x) R;
+  if (RAD == 2) {
+    C t = v[0];
+    v[0] = cadd(t, v[1]);
+    v[1] = csub(t, v[1]);
+  } else if (RAD == 3) {
+    const R h = (R)0.86602540378443864676;  // sin(2 pi / 3)
+    C s = cadd(v[1], v[2]);
+    C d = csub(v[1], v[2]);
+    C m = cmk<C>(v[0].x - (R)0.5 * s.x, v[0].y - (R)0.5 * s.y);
+    C r = cmk<C>(h * d.y, -h * d.x);  // -i h d
+    v[0] = cadd(v[0], s);
+    v[1] = cadd(m, r);
+    v[2] = csub(m, r);
+  } else if (RAD == 4) {
+    C a0 = cadd(v[0], v[2]);
+    C a1 = csub(v[0], v[2]);
+    C b0 = cadd(v[1], v[3]);
+    C b1 = cmi(csub(v[1], v[3]));
+    v[0] = cadd(a0, b0);
+    v[2] = csub(a0, b0);
+    v[1] = cadd(a1, b1);
+    v[3] = csub(a1, b1);
+  } else if (RAD == 5) {
+    const R c1 = (R)0.30901699437494742410;   // cos(2 pi / 5)
+    const R c2 = (R)-0.80901699437494742410;  // cos(4 pi / 5)
+    const R s1 = (R)0.95105651629515357212;   // sin(2 pi / 5)
+    const R s2 = (R)0.58778525229247312917;   // sin(4 pi / 5)
+    C a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+    C a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+    C m1 = cmk<C>(v[0].x + c1 * a1.x + c2 * a2.x, v[0].y + c1 * a1.y + c2 * a2.y);
+    C m2 = cmk<C>(v[0].x + c2 * a1.x + c1 * a2.x, v[0].y + c2 * a1.y + c1 * a2.y);
+    C t1 = cmk<C>(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y);
+    C t2 = cmk<C>(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y);
+    v[0] = cmk<C>(v[0].x + a1.x + a2.x, v[0].y + a1.y + a2.y);
+    v[1] = cadd(m1, cmi(t1));
+    v[4] = csub(m1, cmi(t1));
+    v[2] = cadd(m2, cmi(t2));
+    v[3] = csub(m2, cmi(t2));
+  } else if (RAD == 8) {
+    const R r2 = (R)0.70710678118654752440;
+    // two radix-4 transforms on even and odd samples
+    C e[4] = {v[0], v[2], v[4], v[6]};
+    C o[4] = {v[1], v[3], v[5], v[7]};
+    dft_small<C, 4>(e);
+    dft_small<C, 4>(o);
+    // twiddles W8^k, k = 1..3 with W8 = e^{-i pi / 4}
+    C o1 = cmk<C>(r2 * (o[1].x + o[1].y), r2 * (o[1].y - o[1].x));
+    C o2 = cmi(o[2]);
+    C o3 = cmk<C>(r2 * (o[3].y - o[3].x), -r2 * (o[3].x + o[3].y));
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);
+    v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);
+    v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);
+    v[7] = csub(e[3], o3);
+  }
+}
+
+template <typename C, int RAD>
+__device__ __forceinline__ void fft_stage(const C* __restrict__ src, C* __restrict__ dst, int batch, int n, int Ns,
+                                          const C* __restrict__ tw) {
+  const int NR = n / RAD;
+  const int twstep = n / (Ns * RAD);
+  const int total = batch * NR;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int bi = t / NR;
+    const int j = t - bi * NR;
+    const C* s = src + bi * n;
+    C* d = dst + bi * n;
+    const int k = j % Ns;
+    C v[RAD];
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[r] = s[j + r * NR];
+    if (k != 0) {
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], tw[r * k * twstep]);
+    }
+    dft_small<C, RAD>(v);
+    const int base = (j - k) * RAD + k;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) d[base + r * Ns] = v[r];
+  }
+}
+
+// Stage of a radix that has no hand-written butterfly: one output per thread, O(RAD) work each.
+template <typename C>
+__device__ __forceinline__ void fft_stage_generic(const C* __restrict__ src, C* __restrict__ dst, int batch, int n,
+                                                  int Ns, int RAD, const C* __restrict__ tw) {
+  typedef decltype(C::x) R;
+  const int NR = n / RAD;
+  const int twstep = n / (Ns * RAD);
+  const int total = batch * n;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int bi = t / n;
+    const int rem = t - bi * n;
+    const int rout = rem / NR;
+    const int j = rem - rout * NR;
+    const int k = j % Ns;
+    const C* s = src + bi * n;
+    const int e = (k * twstep + rout * NR) % n;  // exponent step per input r
+    R ax = 0, ay = 0;
+    int idx = 0;
+    for (int r = 0; r < RAD; ++r) {
+      C x = s[j + r * NR];
+      C w = tw[idx];
+      ax += x.x * w.x - x.y * w.y;
+      ay += x.x * w.y + x.y * w.x;
+      idx += e;
+      if (idx >= n) idx -= n;
+    }
+    dst[bi * n + (j - k) * RAD + k + rout * Ns] = cmk<C>(ax, ay);
+  }
+}
+
+template <typename C>
+__device__ C* fft_smem(C* a, C* b, int batch, const FftDesc& fd, const C* __restrict__ tw) {
+  const int n = fd.n;
+  int Ns = 1;
+  for (int s = 0; s < fd.nst; ++s) {
+    const int R = fd.radix[s];
+    switch (R) {
+      case 2: fft_stage<C, 2>(a, b, batch, n, Ns, tw); break;
+      case 3: fft_stage<C, 3>(a, b, batch, n, Ns, tw); break;
+      case 4: fft_stage<C, 4>(a, b, batch, n, Ns, tw); break;
+      case 5: fft_stage<C, 5>(a, b, batch, n, Ns, tw); break;
+      case 8: fft_stage<C, 8>(a, b, batch, n, Ns, tw); break;
+      default: fft_stage_generic<C>(a, b, batch, n, Ns, R, tw); break;
+    }
+    __syncthreads();
+    C* t = a;
+    a = b;
+    b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+// ---- pre/post-processing of the real-to-real transforms ----------------------------------------------
+
+// Position of sample j in the reordered sequence used by DCT-II / DST-II.
+__device__ __forceinline__ int dct_perm(int j, int n) { return (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1); }
+
+// Split the FFT Z of (a + i b) at index m into the spectra of a and b: A = (Z[m] + conj Z[n-m]) / 2,
+// B = (Z[m] - conj Z[n-m]) / (2 i).
+template <typename C>
+__device__ __forceinline__ void split_two(const C* Z, int n, int m, C& A, C& B) {
+  typedef decltype(C::x) R;
+  const C P = Z[m];
+  const C Q = Z[m == 0 ? 0 : n - m];
+  A = cmk<C>((R)0.5 * (P.x + Q.x), (R)0.5 * (P.y - Q.y));
+  B = cmk<C>((R)0.5 * (P.y + Q.y), (R)-0.5 * (P.x - Q.x));
+}
+
+// Forward post-processing: spectral output q of both lines from the FFT result Z.
+template <typename C>
+__device__ __forceinline__ void fwd_post(const C* Z, int n, int bc, int q, const C* __restrict__ quart,
+                                         decltype(C::x)& oa, decltype(C::x)& ob) {
+  if (bc == VOFP_BC_P) {
+    const int m = (q + 1) >> 1;
+    C A, B;
+    split_two(Z, n, m, A, B);
+    const bool re = (q == 0) || (q & 1);
+    oa = re ? A.x : A.y;
+    ob = re ? B.x : B.y;
+  } else {
+    const int m = (bc == VOFP_BC_DD) ? (n - 1 - q) : q;
+    C A, B;
+    split_two(Z, n, m, A, B);
+    const C w = quart[m];
+    oa = w.x * A.x - w.y * A.y;
+    ob = w.x * B.x - w.y * B.y;
+  }
+}
+
+// Half-complex unpacking: spectrum value X[m] (0 <= m < n) of a packed periodic line r.
+template <typename C, typename LOAD>
+__device__ __forceinline__ C unpack_hc(LOAD r, int n, int m) {
+  typedef decltype(C::x) R;
+  if (m == 0) return cmk<C>(r(0), (R)0);
+  const bool conj = 2 * m > n;
+  const int mm = conj ? n - m : m;
+  if (2 * mm == n) return cmk<C>(r(n - 1), (R)0);
+  C v = cmk<C>(r(2 * mm - 1), r(2 * mm));
+  if (conj) v.y = -v.y;
+  return v;
+}
+
+// Inverse pre-processing: complex input (already conjugated for the forward engine) at FFT index m for
+// two packed spectral lines ra, rb.  After the forward FFT of this input, Y = conj(n (a + i b)) at the
+// reordered positions.
+template <typename C, typename LA, typename LB>
+__device__ __forceinline__ C inv_pre(LA ra, LB rb, int n, int bc, int m, const C* __restrict__ quart) {
+  typedef decltype(C::x) R;
+  C Z;
+  if (bc == VOFP_BC_P) {
+    const C A = unpack_hc<C>(ra, n, m);
+    const C B = unpack_hc<C>(rb, n, m);
+    Z = cmk<C>(A.x - B.y, A.y + B.x);
+  } else {
+    // V[m] = e^{+i pi m / (2n)} (X[m] - i X[n-m]), X[n] = 0; DD reads X in reverse order
+    R xa, xb, ya = 0, yb = 0;
+    if (bc == VOFP_BC_DD) {
+      xa = ra(n - 1 - m);
+      xb = rb(n - 1 - m);
+      if (m > 0) {
+        ya = ra(m - 1);
+        yb = rb(m - 1);
+      }
+    } else {
+      xa = ra(m);
+      xb = rb(m);
+      if (m > 0) {
+        ya = ra(n - m);
+        yb = rb(n - m);
+      }
+    }
+    const C w = quart[m];  // (c, -s)
+    const R c = w.x, s = -w.y;
+    const C Va = cmk<C>(c * xa + s * ya, s * xa - c * ya);
+    const C Vb = cmk<C>(c * xb + s * yb, s * xb - c * yb);
+    Z = cmk<C>(Va.x - Vb.y, Va.y + Vb.x);
+  }
+  return cmk<C>(Z.x, -Z.y);
+}
+
+}  // namespace vofp
+
+// ---- plan ---------------------------------------------------------------------------------------------
+
+struct vofp_devinfo {
+  double compat_defect;
+  double abs_sum;  // sum |f| V over the grid (for the incompatibility warning)
+  double res2;     // mixed: ||f - L p||^2
+  double f2;       // mixed: ||f||^2
+  unsigned int nonfinite;
+  unsigned int pad;
+};
+
+struct vofp_plan {
+  int n[3];
+  int bc[3];
+  double dx, dy;
+  double* dz_host;
+  vofp_opts opts;
+  int device;
+  int singular;
+  double volume;  // total volume
+  vofp::AxisDev ax[2];
+  // z tables
+  double* za;  // coefficient of p_{k-1} in row k (wraps for periodic z)
+  double* zb;  // diagonal
+  double* zc;  // coefficient of p_{k+1}
+  double* dz;  // widths
+  double* hz;  // centre distance across face k (k = 0..nz; ghost distances at the ends)
+  // workspace
+  double* S;   // spectrum, nx*ny*nz (FP64 path)
+  double* P;   // potential scratch when the caller passes none
+  float* S32;  // spectrum (mixed path)
+  double* F;   // mixed: right-hand side kept in FP64
+  double* R;   // mixed: residual
+  vofp_devinfo* info;
+  void* table_block;  // one allocation for all tables
+  size_t bytes;
+  // launch shapes
+  int xpb;  // line pairs per block, x pass
+  int ytx;  // columns per block, y pass
+  int zti;  // systems per block, z pass
+};

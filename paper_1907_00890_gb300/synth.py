@@ -61,6 +61,8 @@ def stretched_dz(nz, ratio=1.05, L=1.0):
     """Face positions z_k = (L/2)(1 + tanh(a (2k/nz - 1)) / tanh a), k = 0..nz; a chosen so that the largest
     ratio of neighbouring widths is ``ratio`` (clustered at both walls)."""
     k = np.arange(nz + 1)
+    if nz < 3:
+        return uniform_dz(nz, L)
 
     def widths(a):
         z = 0.5 * L * (1.0 + np.tanh(a * (2.0 * k / nz - 1.0)) / math.tanh(a))

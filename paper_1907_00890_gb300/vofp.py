@@ -1,0 +1,283 @@
+"""Thin Python binding of the vofp C ABI (``include/vofp.h``): argument marshalling only.
+
+Every function keeps the C name and passes device pointers (``tensor.data_ptr()``) and the current CUDA
+stream to the library; all arithmetic of the solve runs in the library's kernels.  Importing this module
+fails loudly if the library has not been built (``python -m paper_1907_00890_gb300.build``); there is no
+CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+BC = {"P": 0, "NN": 1, "DD": 2, "ND": 3, "DN": 4}
+FP64, MIXED = 0, 1
+
+if not os.path.exists(LIB):
+    raise ImportError("vofp library not built: %s is missing (run paper_1907_00890_gb300.build.build())" % LIB)
+_lib = ctypes.CDLL(LIB)
+
+
+class vofp_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("tol", ctypes.c_double), ("max_refine", ctypes.c_int),
+                ("grad_mode", ctypes.c_int), ("tune", ctypes.c_int)]
+
+
+class vofp_info(ctypes.Structure):
+    _fields_ = [("compat_defect", ctypes.c_double), ("rel_residual", ctypes.c_double),
+                ("refine_iters", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_lib.vofp_opts_default.argtypes = [ctypes.POINTER(vofp_opts)]
+_lib.vofp_opts_default.restype = None
+_lib.vofp_plan_create.argtypes = [_I, _I, _I, _D, _D, ctypes.POINTER(_D), ctypes.POINTER(_I),
+                                  ctypes.POINTER(vofp_opts), ctypes.POINTER(_P)]
+_lib.vofp_plan_create.restype = _I
+_lib.vofp_plan_destroy.argtypes = [_P]
+_lib.vofp_plan_destroy.restype = None
+_lib.vofp_plan_workspace_bytes.argtypes = [_P]
+_lib.vofp_plan_workspace_bytes.restype = ctypes.c_size_t
+_lib.vofp_poisson_solve.argtypes = [_P, _P, _P, _P, ctypes.POINTER(vofp_info)]
+_lib.vofp_poisson_solve.restype = _I
+_lib.vofp_project.argtypes = [_P, _P, _P, _P, _P, _D, _P, _P, ctypes.POINTER(vofp_info)]
+_lib.vofp_project.restype = _I
+_lib.vofp_extend_liquid_velocity.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P,
+                                             ctypes.POINTER(vofp_info)]
+_lib.vofp_extend_liquid_velocity.restype = _I
+_lib.vofp_stefan_source.argtypes = [_P, _P, _P, _D, _D, _P, _P]
+_lib.vofp_stefan_source.restype = _I
+_lib.vofp_project_stefan.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _D, _P, _P, ctypes.POINTER(vofp_info)]
+_lib.vofp_project_stefan.restype = _I
+_lib.vofp_trace_enable.argtypes = [_I]
+_lib.vofp_trace_enable.restype = _I
+_lib.vofp_trace_collect.argtypes = [ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_ulonglong), _I]
+_lib.vofp_trace_collect.restype = _I
+_lib.vofp_trace_kernel_classes.argtypes = []
+_lib.vofp_trace_kernel_classes.restype = _I
+_lib.vofp_trace_name.argtypes = [_I]
+_lib.vofp_trace_name.restype = ctypes.c_char_p
+_lib.vofp_launch_count.argtypes = []
+_lib.vofp_launch_count.restype = ctypes.c_ulonglong
+_lib.vofp_error_string.argtypes = [_I]
+_lib.vofp_error_string.restype = ctypes.c_char_p
+
+EXPORTED = ["vofp_opts_default", "vofp_plan_create", "vofp_plan_destroy", "vofp_plan_workspace_bytes",
+            "vofp_poisson_solve", "vofp_project", "vofp_extend_liquid_velocity", "vofp_error_string",
+            "vofp_stefan_source", "vofp_project_stefan", "vofp_launch_count", "vofp_trace_enable",
+            "vofp_trace_collect", "vofp_trace_kernel_classes", "vofp_trace_name"]
+
+
+def vofp_trace_enable(on):
+    return int(_lib.vofp_trace_enable(1 if on else 0))
+
+
+def vofp_trace_kernel_classes():
+    return int(_lib.vofp_trace_kernel_classes())
+
+
+def vofp_trace_name(i):
+    return _lib.vofp_trace_name(int(i)).decode()
+
+
+def vofp_trace_collect():
+    """Return {kernel class name: (total ms, launches)} for the traced launches and clear the record."""
+    n = vofp_trace_kernel_classes()
+    ms = (_D * n)()
+    cnt = (ctypes.c_ulonglong * n)()
+    _check(_lib.vofp_trace_collect(ms, cnt, n), "vofp_trace_collect")
+    return {vofp_trace_name(i): (ms[i], int(cnt[i])) for i in range(n) if cnt[i]}
+
+
+def vofp_launch_count():
+    return int(_lib.vofp_launch_count())
+
+
+class VofpError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__("%s failed: %s (status %d)" % (what, vofp_error_string(status), status))
+        self.status = status
+
+
+def vofp_error_string(status):
+    return _lib.vofp_error_string(int(status)).decode()
+
+
+def _check(status, what):
+    if status < 0:
+        raise VofpError(status, what)
+    return status
+
+
+def _ptr(t, numel=None, name="array"):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous float64 CUDA tensor" % name)
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def vofp_opts_default():
+    o = vofp_opts()
+    _lib.vofp_opts_default(ctypes.byref(o))
+    return o
+
+
+def vofp_plan_create(nx, ny, nz, dx, dy, dz, bc, opts=None):
+    """Return a plan handle (int).  ``dz``: host array of nz widths; ``bc``: three names or codes."""
+    dz = np.ascontiguousarray(np.broadcast_to(np.asarray(dz, dtype=np.float64), (int(nz),)))
+    codes = (_I * 3)(*[BC[b] if isinstance(b, str) else int(b) for b in bc])
+    h = _P()
+    o = ctypes.byref(opts) if opts is not None else None
+    _check(_lib.vofp_plan_create(int(nx), int(ny), int(nz), float(dx), float(dy),
+                                 dz.ctypes.data_as(ctypes.POINTER(_D)), codes, o, ctypes.byref(h)),
+           "vofp_plan_create")
+    return h.value
+
+
+def vofp_plan_destroy(plan):
+    _lib.vofp_plan_destroy(plan)
+
+
+def vofp_plan_workspace_bytes(plan):
+    return int(_lib.vofp_plan_workspace_bytes(plan))
+
+
+def _info_dict(i):
+    return {"compat_defect": i.compat_defect, "rel_residual": i.rel_residual, "refine_iters": i.refine_iters,
+            "status": i.status}
+
+
+def vofp_poisson_solve(plan, f, p, stream=None, info=False):
+    inf = vofp_info() if info else None
+    s = _check(_lib.vofp_poisson_solve(plan, _ptr(f, name="f"), _ptr(p, name="p"), _stream(stream),
+                                       ctypes.byref(inf) if info else None), "vofp_poisson_solve")
+    return (s, _info_dict(inf)) if info else s
+
+
+def vofp_project(plan, u, v, w, src, dt_over_rho0, p, stream=None, info=False):
+    inf = vofp_info() if info else None
+    s = _check(_lib.vofp_project(plan, _ptr(u, name="u"), _ptr(v, name="v"), _ptr(w, name="w"),
+                                 _ptr(src, name="src"), float(dt_over_rho0), _ptr(p, name="p"), _stream(stream),
+                                 ctypes.byref(inf) if info else None), "vofp_project")
+    return (s, _info_dict(inf)) if info else s
+
+
+def vofp_stefan_source(plan, C, mdot, rho1, rho2, s, stream=None):
+    return _check(_lib.vofp_stefan_source(plan, _ptr(C, name="C"), _ptr(mdot, name="mdot"), float(rho1),
+                                          float(rho2), _ptr(s, name="s"), _stream(stream)), "vofp_stefan_source")
+
+
+def vofp_project_stefan(plan, u, v, w, C, mdot, rho1, rho2, dt_over_rho0, p, stream=None, info=False):
+    inf = vofp_info() if info else None
+    s = _check(_lib.vofp_project_stefan(plan, _ptr(u, name="u"), _ptr(v, name="v"), _ptr(w, name="w"),
+                                        _ptr(C, name="C"), _ptr(mdot, name="mdot"), float(rho1), float(rho2),
+                                        float(dt_over_rho0), _ptr(p, name="p"), _stream(stream),
+                                        ctypes.byref(inf) if info else None), "vofp_project_stefan")
+    return (s, _info_dict(inf)) if info else s
+
+
+def vofp_extend_liquid_velocity(plan, u, v, w, C, mdot, rho1, rho2, ue, ve, we, ug=None, vg=None, wg=None,
+                                phi=None, stream=None, info=False):
+    inf = vofp_info() if info else None
+    s = _check(_lib.vofp_extend_liquid_velocity(
+        plan, _ptr(u, name="u"), _ptr(v, name="v"), _ptr(w, name="w"), _ptr(C, name="C"),
+        _ptr(mdot, name="mdot"), float(rho1), float(rho2), _ptr(ue, name="ue"), _ptr(ve, name="ve"),
+        _ptr(we, name="we"), _ptr(ug, name="ug"), _ptr(vg, name="vg"), _ptr(wg, name="wg"), _ptr(phi, name="phi"),
+        _stream(stream), ctypes.byref(inf) if info else None), "vofp_extend_liquid_velocity")
+    return (s, _info_dict(inf)) if info else s
+
+
+def face_shapes(n, bc):
+    nx, ny, nz = n
+    ex = [int((BC[b] if isinstance(b, str) else b) != 0) for b in bc]
+    return ((nz, ny, nx + ex[0]), (nz, ny + ex[1], nx), (nz + ex[2], ny, nx))
+
+
+class Plan:
+    """Owns a plan handle; convenience wrappers that allocate outputs with torch (marshalling only)."""
+
+    def __init__(self, n, dx, dy, dz, bc, prec=FP64, tol=1e-10, max_refine=6, grad_mode=0, tune=0):
+        o = vofp_opts_default()
+        o.prec, o.tol, o.max_refine, o.grad_mode, o.tune = prec, tol, max_refine, grad_mode, tune
+        self.n = tuple(int(x) for x in n)
+        self.bc = tuple(bc)
+        self.handle = vofp_plan_create(self.n[0], self.n[1], self.n[2], dx, dy, dz, bc, o)
+
+    @property
+    def cell_shape(self):
+        return (self.n[2], self.n[1], self.n[0])
+
+    def face_shapes(self):
+        return face_shapes(self.n, self.bc)
+
+    def workspace_bytes(self):
+        return vofp_plan_workspace_bytes(self.handle)
+
+    def poisson_solve(self, f, p=None, stream=None, info=False):
+        import torch
+        if p is None:
+            p = torch.empty_like(f)
+        r = vofp_poisson_solve(self.handle, f, p, stream, info)
+        return (p, r[1]) if info else p
+
+    def project(self, u, v, w, src=None, dt_over_rho0=1.0, p=None, want_p=True, stream=None, info=False):
+        import torch
+        if p is None and want_p:
+            p = torch.empty(self.cell_shape, dtype=torch.float64, device=u.device)
+        r = vofp_project(self.handle, u, v, w, src, dt_over_rho0, p, stream, info)
+        return (p, r[1]) if info else p
+
+    def stefan_source(self, C, mdot, rho1, rho2, stream=None):
+        import torch
+        s = torch.empty_like(C)
+        vofp_stefan_source(self.handle, C, mdot, rho1, rho2, s, stream)
+        return s
+
+    def project_stefan(self, u, v, w, C, mdot, rho1, rho2, dt_over_rho0=1.0, p=None, want_p=True, stream=None,
+                       info=False):
+        import torch
+        if p is None and want_p:
+            p = torch.empty(self.cell_shape, dtype=torch.float64, device=u.device)
+        r = vofp_project_stefan(self.handle, u, v, w, C, mdot, rho1, rho2, dt_over_rho0, p, stream, info)
+        return (p, r[1]) if info else p
+
+    def extend(self, u, v, w, C, mdot, rho1, rho2, want_ug=True, want_phi=True, stream=None, info=False):
+        import torch
+        ue, ve, we = torch.empty_like(u), torch.empty_like(v), torch.empty_like(w)
+        ug = vg = wg = phi = None
+        if want_ug:
+            ug, vg, wg = torch.empty_like(u), torch.empty_like(v), torch.empty_like(w)
+        if want_phi:
+            phi = torch.empty(self.cell_shape, dtype=torch.float64, device=u.device)
+        r = vofp_extend_liquid_velocity(self.handle, u, v, w, C, mdot, rho1, rho2, ue, ve, we, ug, vg, wg, phi,
+                                        stream, info)
+        out = (ue, ve, we, ug, vg, wg, phi)
+        return (out, r[1]) if info else out
+
+    def close(self):
+        if self.handle:
+            vofp_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,54 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point ``include/vofp.h`` declares.
+
+No compute call is made here (no GPU on the build machine)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names.update(re.findall(r"\b(vofp_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1907_00890_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert "vofp_plan_create" in names and "vofp_project" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_wraps_every_declared_symbol(lib):
+    from paper_1907_00890_gb300 import vofp
+    for n in declared_symbols():
+        assert n in vofp.EXPORTED or n.startswith("vofp_batch") or n.startswith("vofp_server") or \
+            n.startswith("vofp_tune") or n.startswith("vofp_") and hasattr(vofp, n), n
+
+
+def test_error_strings_and_default_opts(lib):
+    from paper_1907_00890_gb300 import vofp
+    assert vofp.vofp_error_string(0) == "ok"
+    assert "invalid" in vofp.vofp_error_string(-1)
+    o = vofp.vofp_opts_default()
+    assert o.prec == 0 and o.tol == 1e-10 and o.max_refine == 6
+
+
+def test_sm103a_only_build_flags():
+    from paper_1907_00890_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

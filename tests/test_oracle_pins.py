@@ -304,3 +304,15 @@ def test_paper_constants_fixture():
         c = json.load(fh)
     assert c["normal_clip"]["value"] == 1e-8
     assert 100 in c["density_ratios"]["value"]
+
+
+@pytest.mark.parametrize("bc", Z_BCS)
+@pytest.mark.parametrize("n", [1, 2, 3, 8, 31, 250])
+def test_oracle_basis_diagonalises_stencil(bc, n):
+    # the oracle's x/y basis must be orthonormal and diagonalise the stencil matrix to roundoff
+    from oracle.poisson import _eig_axis
+    w = np.full(n, 0.01)
+    lam, Q = _eig_axis(w, bc)
+    A = oracle.operator_matrix_1d(w, bc)
+    assert np.abs(Q.T @ Q - np.eye(n)).max() < 1e-13
+    assert np.abs(Q.T @ A @ Q - np.diag(lam)).max() <= 1e-12 * max(np.abs(A).max(), 1.0)
