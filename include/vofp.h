@@ -151,6 +151,28 @@ int vofp_stefan_source(vofp_plan* plan, const double* C, const double* mdot, dou
 int vofp_project_stefan(vofp_plan* plan, double* u, double* v, double* w, const double* C, const double* mdot,
                         double rho1, double rho2, double dt_over_rho0, double* p, void* stream, vofp_info* info);
 
+/*
+ * Allocation-free FP64 Poisson solve (the paper has no counterpart; it is a deployment variant of
+ * vofp_poisson_solve).  For callers that cannot call cudaMalloc when they need a solve -- e.g. a host code
+ * whose device memory is handed out entirely by its own pool allocator at start-up, or a time-stepping loop
+ * that must not pay cudaMalloc's implicit device synchronisation -- it takes no plan and allocates nothing:
+ * its workspace and tables live in one fixed file-scope device array of the library, sized for at most
+ * VOFP_NOALLOC_MAX_CELLS cells with no axis longer than VOFP_NOALLOC_MAX_N (about 16.3 MiB, held by every
+ * GPU that loads the library until the process exits).
+ *   Arguments: grid as vofp_plan_create (dz is a HOST array of nz widths, copied on the stream), f and p
+ *   device cell arrays (may alias), stream as elsewhere.  Result identical (to rounding) to
+ *   vofp_poisson_solve with a default FP64 plan.
+ *   The first call on each device looks up the array's device address with that device current; make that
+ *   first call before any stream capture.  All calls share the one array, which keeps the last call's
+ *   contents (each call rebuilds what it reads): calls that overlap on the GPU race.
+ *   Errors: INVALID_ARG, UNSUPPORTED (ND/DN on x or y), TOO_LARGE (beyond the limits above), CUDA.
+ */
+#define VOFP_ERR_TOO_LARGE -8
+#define VOFP_NOALLOC_MAX_CELLS 2097152
+#define VOFP_NOALLOC_MAX_N 1024
+int vofp_poisson_solve_noalloc(int nx, int ny, int nz, double dx, double dy, const double* dz, const int bc[3],
+                               const double* f, double* p, void* stream);
+
 /* Number of kernels this library has launched in this process (all plans, all devices); diagnostics. */
 unsigned long long vofp_launch_count(void);
 

@@ -90,6 +90,7 @@ extern "C" const char* vofp_error_string(int s) {
     case VOFP_ERR_TIMEOUT: return "timed out";
     case VOFP_ERR_BUSY: return "busy: over the memory budget";
     case VOFP_ERR_NONFINITE: return "non-finite values in the result";
+    case VOFP_ERR_TOO_LARGE: return "problem larger than the static scratch of the allocation-free solve";
     default: return "unknown status";
   }
 }

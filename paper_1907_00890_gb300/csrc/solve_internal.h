@@ -23,6 +23,7 @@ enum KernelId {
   KID_RESID,
   KID_FUSED_YZY,
   KID_BATCHED,
+  KID_NOALLOC_TABLES,
   KID_COUNT
 };
 

@@ -72,6 +72,22 @@ EXPORTED = ["vofp_opts_default", "vofp_plan_create", "vofp_plan_destroy", "vofp_
             "vofp_trace_collect", "vofp_trace_kernel_classes", "vofp_trace_name"]
 
 
+_lib.vofp_poisson_solve_noalloc.argtypes = [_I, _I, _I, _D, _D, ctypes.POINTER(_D), ctypes.POINTER(_I), _P, _P,
+                                            _P]
+_lib.vofp_poisson_solve_noalloc.restype = _I
+EXPORTED.append("vofp_poisson_solve_noalloc")
+
+
+def vofp_poisson_solve_noalloc(nx, ny, nz, dx, dy, dz, bc, f, p, stream=None):
+    """Allocation-free solve for callers that cannot call cudaMalloc (see include/vofp.h)."""
+    dz = np.ascontiguousarray(np.broadcast_to(np.asarray(dz, dtype=np.float64), (int(nz),)))
+    codes = (_I * 3)(*[BC[b] if isinstance(b, str) else int(b) for b in bc])
+    return _check(_lib.vofp_poisson_solve_noalloc(int(nx), int(ny), int(nz), float(dx), float(dy),
+                                                  dz.ctypes.data_as(ctypes.POINTER(_D)), codes,
+                                                  _ptr(f, name="f"), _ptr(p, name="p"), _stream(stream)),
+                  "vofp_poisson_solve_noalloc")
+
+
 def vofp_trace_enable(on):
     return int(_lib.vofp_trace_enable(1 if on else 0))
 
