@@ -209,9 +209,8 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
-        vofp.vofp_project_stefan(plan.handle, u[0], u[1], u[2], C, md, c["rho1"], c["rho2"], c["dt_over_rho0"], p)
-        vofp.vofp_extend_liquid_velocity(plan.handle, u[0], u[1], u[2], C, md, c["rho1"], c["rho2"], ue[0], ue[1],
-                                         ue[2], ug[0], ug[1], ug[2], phi)
+        vofp.vofp_project_extend(plan.handle, u[0], u[1], u[2], C, md, c["rho1"], c["rho2"], c["dt_over_rho0"], p,
+                                 ue[0], ue[1], ue[2], ug[0], ug[1], ug[2], phi)
 
     def prep():
         for a, b in zip(u, u0):
@@ -341,7 +340,7 @@ def algorithmic(kname, n):
         "x_inverse": (16, 2.5 * lg(nx)),
         "grad_update": (56, 12),
         "extend_epilogue": (96, 60),
-        "stefan_source": (24, 18),
+        "stefan_source": (48, 40),
     }
     b, f = tab.get(kname, (0, 0))
     return b * cells, f * cells

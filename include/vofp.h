@@ -97,6 +97,16 @@ void vofp_opts_default(vofp_opts* opt);
 int vofp_plan_create(int nx, int ny, int nz, double dx, double dy, const double* dz, const int bc[3],
                      const vofp_opts* opt, vofp_plan** out);
 
+/*
+ * Autotune the plan's launch shapes (line pairs per x block, columns per y block, systems per z block) by
+ * timing whole solves on the plan's scratch workspace (coordinate descent over the candidates that fit in
+ * shared memory).  Results are cached per process and, if the environment variable VOFP_TUNE_CACHE names a
+ * file, across processes.  Called by vofp_plan_create when opts.tune != 0.  Synchronises the device.
+ * No counterpart in the paper (performance only; results stay within the parity tolerance).
+ * Errors: INVALID_ARG, CUDA.
+ */
+int vofp_plan_tune(vofp_plan* plan);
+
 /* Free the plan's device tables and workspace (NULL is ignored).  Synchronises the device first. */
 void vofp_plan_destroy(vofp_plan* plan);
 
@@ -150,6 +160,82 @@ int vofp_stefan_source(vofp_plan* plan, const double* C, const double* mdot, dou
  */
 int vofp_project_stefan(vofp_plan* plan, double* u, double* v, double* w, const double* C, const double* mdot,
                         double rho1, double rho2, double dt_over_rho0, double* p, void* stream, vofp_info* info);
+
+/*
+ * Both Poisson solves of one time step of the paper's solver (§3.7: the pressure correction, then the
+ * interface-velocity construction of §3.6), sharing one interface-geometry pass (|grad C| and n computed once
+ * per cell): the projection of vofp_project_stefan (u, v, w in place, p optional) followed by the extension
+ * of vofp_extend_liquid_velocity applied to the projected velocity (ue, ve, we required; ug, vg, wg all or
+ * none; phi optional).  Same results as calling the two entry points in that order.
+ * Errors: INVALID_ARG, CUDA, NONFINITE (only with info; info reports the worse status of the two solves).
+ */
+int vofp_project_extend(vofp_plan* plan, double* u, double* v, double* w, const double* C, const double* mdot,
+                        double rho1, double rho2, double dt_over_rho0, double* p, double* ue, double* ve,
+                        double* we, double* ug, double* vg, double* wg, double* phi, void* stream,
+                        vofp_info* info);
+
+/*
+ * Batched projection of independent instances (an ensemble of droplet runs with uneven grids; the paper's
+ * solver runs one instance, so this is the data-parallel form of vofp_project).  plans[0..n-1]: distinct
+ * VOFP_MIXED plans on one device (each plan's workspace serves exactly one instance).  Every pass of the
+ * mixed-precision projection runs as one launch over all instances and the whole sequence is captured once
+ * into a CUDA graph and replayed per call.  Each instance's result is bitwise identical to running it alone
+ * in a batch of one.
+ * Errors: INVALID_ARG (NULL, n < 1, repeated plan, mixed devices), UNSUPPORTED (an FP64 plan), OOM.
+ */
+typedef struct vofp_batch vofp_batch;
+int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** out);
+/*
+ * Project every instance i (vofp_project semantics): u[i], v[i], w[i] device face arrays in place;
+ * src[i] device cell array or NULL (src itself may be NULL); dt_over_rho0[i] > 0 (HOST array);
+ * p[i] device cell array or NULL (p itself may be NULL).  Asynchronous on `stream`.  The argument records
+ * are re-uploaded only when a pointer or dt_over_rho0 changes (the call then waits for `stream`).
+ */
+int vofp_batch_project(vofp_batch* b, double* const* u, double* const* v, double* const* w,
+                       const double* const* src, const double* dt_over_rho0, double* const* p, void* stream);
+int vofp_batch_size(const vofp_batch* b);
+void vofp_batch_destroy(vofp_batch* b);
+
+/*
+ * Serving (continuous batching of projection requests from an ensemble of independent runs; the paper
+ * solves one run, so this is a deployment form of vofp_project).
+ *
+ * vofp_server_create: `mem_budget_bytes` of device memory (0 = half of the free memory) become the server's
+ * arena, allocated once; `max_inflight` (1..256) requests may be on the GPU at once, each on its own stream;
+ * `opt` (NULL = defaults) is the plan options of every request (precision, tolerance).
+ * A request names its grid (n, dx, dy, dz HOST array copied at submission, bc) and its device fields
+ * (u, v, w in place; src and p optional; dt_over_rho0 > 0); the caller keeps the fields valid and untouched
+ * until the request completes.  vofp_server_submit returns at once with a ticket.  A worker thread admits
+ * pending requests oldest first whenever a slot and an arena block of the plan's size are free (requests
+ * arriving while others run are admitted as those complete), builds each plan in its arena block and runs
+ * the projection asynchronously; no device memory is allocated or freed while serving.  A request whose
+ * plan alone exceeds the arena completes with VOFP_ERR_BUSY.
+ * vofp_server_poll: 0 = done (the ticket is consumed; *latency_s = completion - submission), 1 = pending,
+ * < 0 = the request's error (also consumes the ticket).  vofp_server_wait: the same, blocking up to
+ * timeout_s (VOFP_ERR_TIMEOUT, ticket kept).  vofp_server_stats: out[0..9] = completed, admitted, rejected,
+ * pending, arena bytes in use, arena bytes, p50 and p99 latency (s), cells solved, seconds since creation
+ * or the last reset (reset != 0 clears the counters).  vofp_server_destroy waits for in-flight work.
+ */
+typedef struct {
+  int n[3];
+  double dx, dy;
+  const double* dz;
+  int bc[3];
+  double* u;
+  double* v;
+  double* w;
+  const double* src;
+  double dt_over_rho0;
+  double* p;
+} vofp_request;
+typedef struct vofp_server vofp_server;
+int vofp_server_create(size_t mem_budget_bytes, int max_inflight, const vofp_opts* opt, vofp_server** out);
+int vofp_server_submit(vofp_server* s, const vofp_request* r, unsigned long long* ticket);
+int vofp_server_poll(vofp_server* s, unsigned long long ticket, vofp_info* info, double* latency_s);
+int vofp_server_wait(vofp_server* s, unsigned long long ticket, double timeout_s, vofp_info* info,
+                     double* latency_s);
+int vofp_server_stats(vofp_server* s, double* out, int n, int reset);
+void vofp_server_destroy(vofp_server* s);
 
 /*
  * Allocation-free FP64 Poisson solve (the paper has no counterpart; it is a deployment variant of

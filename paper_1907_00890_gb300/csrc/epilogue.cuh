@@ -1,6 +1,9 @@
-// Face epilogues: pressure correction u = u* - (dt/rho0) G p (§3.2, the step after Eq. lap_p) and the
-// liquid-velocity extension u1e = u - G phi (Eq. jump_subtr) with the interface velocity
-// uG = u1e - (mdot_f / rho1) n_f (Eq. int_vel).
+// Face epilogues and the interface-geometry pass:
+//   * pressure correction u = u* - (dt/rho0) G p (§3.2, the step after Eq. lap_p);
+//   * interface geometry per cell: s = mdot (1/rho2 - 1/rho1) |grad C| (Eq. ext_div right-hand side, the
+//     source of Eq. lap_p) and n = -grad C / |grad C| (Eq. int_vel), computed once and kept in the plan;
+//   * liquid-velocity extension u1e = u - G phi (Eq. jump_subtr) and interface velocity
+//     uG = u1e - (mdot_f / rho1) n_f (Eq. int_vel), reading the stored n.
 #pragma once
 
 #include "stencil.cuh"
@@ -8,35 +11,34 @@
 namespace vofp {
 
 // Face-normal gradient of a cell field at face `f` (low face of cell f) along a line of n cells with
-// stride `st` starting at `base`.  Returns false for an N boundary face (left unchanged).
+// stride `st` starting at `base`; `rh` is 1 / centre distance across that face, `rw_lo`, `rw_hi` the
+// reciprocal end widths.  Returns false for an N boundary face (left unchanged).
 __device__ __forceinline__ bool face_grad(const double* __restrict__ p, size_t base, size_t st, int n, int bc, int f,
-                                          double h_lo_ghost, double h_interior_or_wrap, double w_lo, double w_hi,
-                                          double& g) {
+                                          double rh, double rw_lo, double rw_hi, double& g) {
   if (bc == VOFP_BC_P) {
     const int fm = f == 0 ? n - 1 : f - 1;
-    g = (__ldg(p + base + f * st) - __ldg(p + base + fm * st)) / h_interior_or_wrap;
+    g = (__ldg(p + base + f * st) - __ldg(p + base + fm * st)) * rh;
     return true;
   }
   const bool lowN = bc == VOFP_BC_NN || bc == VOFP_BC_ND;
   const bool highN = bc == VOFP_BC_NN || bc == VOFP_BC_DN;
   if (f == 0) {
     if (lowN) return false;
-    g = 2.0 * __ldg(p + base) / w_lo;
+    g = 2.0 * __ldg(p + base) * rw_lo;
     return true;
   }
   if (f == n) {
     if (highN) return false;
-    g = -2.0 * __ldg(p + base + (size_t)(n - 1) * st) / w_hi;
+    g = -2.0 * __ldg(p + base + (size_t)(n - 1) * st) * rw_hi;
     return true;
   }
-  g = (__ldg(p + base + f * st) - __ldg(p + base + (size_t)(f - 1) * st)) / h_interior_or_wrap;
-  (void)h_lo_ghost;
+  g = (__ldg(p + base + f * st) - __ldg(p + base + (size_t)(f - 1) * st)) * rh;
   return true;
 }
 
 // Decode a flat face index over the three face arrays; returns the axis and sets (i, j, k) and the offset.
 __device__ __forceinline__ int decode_face(const GridDev& g, size_t t, int& i, int& j, int& k, size_t& off) {
-  const int nxf = nface(g.nx, g.bcx), nyf = nface(g.ny, g.bcy), nzf = nface(g.nz, g.bcz);
+  const int nxf = nface(g.nx, g.bcx), nyf = nface(g.ny, g.bcy);
   const size_t nu = (size_t)nxf * g.ny * g.nz, nv = (size_t)g.nx * nyf * g.nz;
   if (t < nu) {
     off = t;
@@ -61,7 +63,6 @@ __device__ __forceinline__ int decode_face(const GridDev& g, size_t t, int& i, i
   const size_t r = t / g.nx;
   j = (int)(r % g.ny);
   k = (int)(r / g.ny);
-  (void)nzf;
   return 2;
 }
 
@@ -69,18 +70,22 @@ __device__ __forceinline__ bool grad_on_face(const GridDev& g, const double* __r
                                              int k, double& gr) {
   const size_t plane = (size_t)g.nx * g.ny;
   if (axis == 0) {
-    return face_grad(p, (size_t)k * plane + (size_t)j * g.nx, 1, g.nx, g.bcx, i, 0, g.dx, g.dx, g.dx, gr);
+    return face_grad(p, (size_t)k * plane + (size_t)j * g.nx, 1, g.nx, g.bcx, i, g.rdx, g.rdx, g.rdx, gr);
   } else if (axis == 1) {
-    return face_grad(p, (size_t)k * plane + i, g.nx, g.ny, g.bcy, j, 0, g.dy, g.dy, g.dy, gr);
+    return face_grad(p, (size_t)k * plane + i, g.nx, g.ny, g.bcy, j, g.rdy, g.rdy, g.rdy, gr);
   }
-  const double h = __ldg(g.hz + k);  // centre distance across z face k (wrap distance at k = 0 if periodic)
-  return face_grad(p, (size_t)j * g.nx + i, plane, g.nz, g.bcz, k, 0, h, __ldg(g.dz), __ldg(g.dz + g.nz - 1), gr);
+  return face_grad(p, (size_t)j * g.nx + i, plane, g.nz, g.bcz, k, __ldg(g.rhz + k), __ldg(g.rdz),
+                   __ldg(g.rdz + g.nz - 1), gr);
+}
+
+__host__ __device__ __forceinline__ size_t total_faces(const GridDev& g) {
+  return (size_t)nface(g.nx, g.bcx) * g.ny * g.nz + (size_t)g.nx * nface(g.ny, g.bcy) * g.nz +
+         (size_t)g.nx * g.ny * nface(g.nz, g.bcz);
 }
 
 // u -= s * G p on all three face arrays (one flat index space).
-__global__ void k_grad_update(GridDev g, const double* __restrict__ p, double* u, double* v, double* w, double s) {
-  const size_t total = (size_t)nface(g.nx, g.bcx) * g.ny * g.nz + (size_t)g.nx * nface(g.ny, g.bcy) * g.nz +
-                       (size_t)g.nx * g.ny * nface(g.nz, g.bcz);
+static __global__ void k_grad_update(GridDev g, const double* __restrict__ p, double* u, double* v, double* w, double s) {
+  const size_t total = total_faces(g);
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     int i, j, k;
     size_t off;
@@ -92,22 +97,40 @@ __global__ void k_grad_update(GridDev g, const double* __restrict__ p, double* u
   }
 }
 
-// Mean of a cell quantity over the cells adjacent to face (axis, i, j, k).
-template <typename FN>
-__device__ __forceinline__ double face_mean(const GridDev& g, int axis, int i, int j, int k, FN cell) {
+// Interface geometry per cell: s = coef * mdot * |grad C| and n = -grad C / |grad C| (clipped).
+static __global__ void k_geometry(GridDev g, const double* __restrict__ C, const double* __restrict__ mdot, double coef,
+                           int mode, double* __restrict__ s, double* __restrict__ nx, double* __restrict__ ny,
+                           double* __restrict__ nz) {
+  const size_t total = (size_t)g.nx * g.ny * g.nz;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % g.nx);
+    const size_t r = t / g.nx;
+    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    double3 n;
+    const double m = geometry_at(g, C, i, j, k, mode, n);
+    s[t] = __ldg(mdot + t) * coef * m;
+    if (nx) {
+      nx[t] = n.x;
+      ny[t] = n.y;
+      nz[t] = n.z;
+    }
+  }
+}
+
+// Twice the mean of a cell array over the cells adjacent to face (axis, i, j, k): the sum of the two
+// neighbours, or twice the one adjacent cell on a bounded axis' end face.
+__device__ __forceinline__ double face_sum_arr(const GridDev& g, const double* __restrict__ q, int axis, int i,
+                                                int j, int k) {
   int n, bc, f;
+  size_t st;
+  const size_t plane = (size_t)g.nx * g.ny;
+  size_t base;
   if (axis == 0) {
-    n = g.nx;
-    bc = g.bcx;
-    f = i;
+    n = g.nx, bc = g.bcx, f = i, st = 1, base = (size_t)k * plane + (size_t)j * g.nx;
   } else if (axis == 1) {
-    n = g.ny;
-    bc = g.bcy;
-    f = j;
+    n = g.ny, bc = g.bcy, f = j, st = g.nx, base = (size_t)k * plane + i;
   } else {
-    n = g.nz;
-    bc = g.bcz;
-    f = k;
+    n = g.nz, bc = g.bcz, f = k, st = plane, base = (size_t)j * g.nx + i;
   }
   int lo = f - 1, hi = f;
   if (bc == VOFP_BC_P) {
@@ -116,12 +139,7 @@ __device__ __forceinline__ double face_mean(const GridDev& g, int axis, int i, i
     if (lo < 0) lo = 0;
     if (hi >= n) hi = n - 1;
   }
-  auto at = [&](int c) {
-    if (axis == 0) return cell(c, j, k);
-    if (axis == 1) return cell(i, c, k);
-    return cell(i, j, c);
-  };
-  return 0.5 * (at(lo) + at(hi));
+  return __ldg(q + base + lo * st) + __ldg(q + base + hi * st);
 }
 
 struct ExtArgs {
@@ -130,10 +148,9 @@ struct ExtArgs {
   const double* u;
   const double* v;
   const double* w;
-  const double* C;
   const double* mdot;
-  double inv_rho1;
-  int grad_mode;
+  const double* n[3];  // stored cell normals
+  double quarter_inv_rho1;  // 1 / (4 rho1)
   double* ue;
   double* ve;
   double* we;
@@ -142,10 +159,9 @@ struct ExtArgs {
   double* wg;
 };
 
-__global__ void k_extend_epi(ExtArgs a) {
+static __global__ void k_extend_epi(ExtArgs a) {
   const GridDev& g = a.g;
-  const size_t total = (size_t)nface(g.nx, g.bcx) * g.ny * g.nz + (size_t)g.nx * nface(g.ny, g.bcy) * g.nz +
-                       (size_t)g.nx * g.ny * nface(g.nz, g.bcz);
+  const size_t total = total_faces(g);
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     int i, j, k;
     size_t off;
@@ -156,14 +172,10 @@ __global__ void k_extend_epi(ExtArgs a) {
     const double ue = __ldg(U + off) - gr;
     (axis == 0 ? a.ue : (axis == 1 ? a.ve : a.we))[off] = ue;
     if (a.ug) {
-      const double md = face_mean(g, axis, i, j, k, [&](int ci, int cj, int ck) {
-        return __ldg(a.mdot + ((size_t)ck * g.ny + cj) * g.nx + ci);
-      });
-      const double nf = face_mean(g, axis, i, j, k, [&](int ci, int cj, int ck) {
-        const double3 n = normal_at(g, a.C, ci, cj, ck, a.grad_mode);
-        return axis == 0 ? n.x : (axis == 1 ? n.y : n.z);
-      });
-      (axis == 0 ? a.ug : (axis == 1 ? a.vg : a.wg))[off] = ue - md * a.inv_rho1 * nf;
+      // (mean mdot)(mean n) / rho1 = (sum mdot)(sum n) / (4 rho1)
+      const double md = face_sum_arr(g, a.mdot, axis, i, j, k);
+      const double nf = face_sum_arr(g, a.n[axis], axis, i, j, k);
+      (axis == 0 ? a.ug : (axis == 1 ? a.vg : a.wg))[off] = fma(-a.quarter_inv_rho1 * md, nf, ue);
     }
   }
 }

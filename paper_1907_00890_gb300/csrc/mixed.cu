@@ -1,13 +1,236 @@
-// Mixed-precision path (FP32 transforms, FP64 low modes, residual and reductions, defect correction).
+// Mixed-precision path: FP32 transforms and FP32 z recurrences for the bulk of the spectrum, FP64 for the
+// low-eigenvalue z systems, the right-hand side, the residual stencil, the accumulated potential and every
+// reduction; defect-correction refinement (p += S32(f - fbar - L p)) back to the accuracy of an FP64 solve.
+//
+// The loop is fully asynchronous: the residual norm of correction k is accumulated in FP64 by the residual
+// pass itself, and every launch of correction k + 1 reads it on the device and returns at once when
+// ||r_k|| <= tol ||f|| (so there is no host round trip and the whole sequence can be replayed as a graph).
+// The singular operator's mean is removed from the residual in FP64 (the compatibility defect is the
+// FP64 volume-weighted mean of f, not the FP32 spectrum's), and the gauge of p (zero volume-weighted mean)
+// is restored in FP64 at the end from the exact sums of the corrections.
+#include <cmath>
+#include <vector>
+
 #include "passes.cuh"
 #include "solve_internal.h"
+#include "zsolve.cuh"
 
 namespace vofp {
 
-void init_kernel_attributes_mixed() {}
+static const int kMaxDynSmem = 200 * 1024;
 
-int mixed_solve(vofp_plan*, int, const XArgs*, const double*, double*, cudaStream_t, vofp_info*) {
-  return VOFP_ERR_UNSUPPORTED;
+template <typename K>
+static void allow_smem(K kern) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+}
+
+void init_kernel_attributes_mixed() {
+  allow_smem(k_xfwd<float, float2, RHS_F>);
+  allow_smem(k_xfwd<float, float2, RHS_DIV>);
+  allow_smem(k_xfwd<float, float2, RHS_DIV_STEFAN>);
+  allow_smem(k_xfwd<float, float2, RHS_RESID>);
+  allow_smem(k_ypass<float, float2, false>);
+  allow_smem(k_ypass<float, float2, true>);
+  allow_smem(k_xinv<float, float2>);
+  allow_smem(k_zsolve<float, float>);
+}
+
+// p -= (*sum) * scale  (gauge restoration)
+__global__ void k_shift(double* p, size_t n, const double* sum, double scale) {
+  const double m = *sum * scale;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    p[t] -= m;
+}
+
+// ||f - fbar - L p||^2 into *out (reporting pass after the last correction).
+__global__ void k_resid_norm(GridDev g, const double* __restrict__ F, const double* __restrict__ p,
+                             const double* defect_sum, double inv_volume, double* out, const double* skip_conv,
+                             int skip_k, double tol2) {
+  __shared__ double red[32];
+  if (launch_skipped(skip_conv, skip_k, tol2)) return;
+  const size_t total = (size_t)g.nx * g.ny * g.nz;
+  const double fbar = defect_sum ? *defect_sum * inv_volume : 0.0;
+  double acc = 0;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % g.nx);
+    const size_t r = t / g.nx;
+    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    const double v = __ldg(F + t) - fbar - lap_at(g, p, i, j, k);
+    acc += v * v;
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0 && s != 0) atomicAdd(out, s);
+}
+
+// y forward, z (FP32 bulk + FP64 low modes), y inverse on the FP32 spectrum; skipped when converged.
+static void solve32(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, bool stats) {
+  const int nx = pl->n[0], ny = pl->n[1], nz = pl->n[2];
+  YArgs ya = {};
+  ya.nx = nx;
+  ya.ny = ny;
+  ya.nz = nz;
+  ya.bc = pl->bc[1];
+  ya.fd = pl->ax[1].fd;
+  ya.tw = pl->ax[1].tw32;
+  ya.quart = pl->ax[1].quart32;
+  ya.tx = pl->ytx32;
+  ya.S = pl->S32;
+  ya.skip_conv = pl->conv;
+  ya.skip_k = skip_k;
+  ya.tol2 = tol2;
+  const dim3 ygrid((nx + ya.tx - 1) / ya.tx, nz);
+  const size_t ysm = 2 * (size_t)(ya.tx / 2) * ny * sizeof(float2);
+  if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, (k_ypass<float, float2, false><<<ygrid, 256, ysm, st>>>(ya)));
+  ZArgs za = z_args(pl, stats);
+  za.S = pl->S32;
+  za.ti = pl->zti32;
+  za.lowthr = pl->lowthr;
+  za.skip_conv = pl->conv;
+  za.skip_k = skip_k;
+  za.tol2 = tol2;
+  const int nvec = pl->bc[2] == VOFP_BC_P ? 3 : 2;
+  const dim3 zgrid((nx + za.ti - 1) / za.ti, ny);
+  const size_t zsm = (size_t)nvec * za.ti * nz * sizeof(float);
+  VOFP_LAUNCH(KID_ZSOLVE, st, (k_zsolve<float, float><<<zgrid, 128, zsm, st>>>(za)));
+  if (pl->nlow > 0)
+    VOFP_LAUNCH(KID_ZSOLVE, st,
+                k_zlow64<<<(pl->nlow + 63) / 64, 64, 0, st>>>(za, pl->lowmodes, pl->nlow, pl->lowscratch));
+  if (ny > 1) VOFP_LAUNCH(KID_YINV, st, (k_ypass<float, float2, true><<<ygrid, 256, ysm, st>>>(ya)));
+}
+
+static void xinv32(vofp_plan* pl, double* pout, int accumulate, int skip_k, double tol2, double* d2_out,
+                   cudaStream_t st) {
+  XInvArgs xi = {};
+  xi.nx = pl->n[0];
+  xi.ny = pl->n[1];
+  xi.nz = pl->n[2];
+  xi.bc = pl->bc[0];
+  xi.fd = pl->ax[0].fd;
+  xi.tw = pl->ax[0].tw32;
+  xi.quart = pl->ax[0].quart32;
+  xi.pb = pl->xpb;
+  xi.S = pl->S32;
+  xi.p = pout;
+  xi.accumulate = accumulate;
+  xi.skip_conv = pl->conv;
+  xi.skip_k = skip_k;
+  xi.tol2 = tol2;
+  xi.dz = pl->dz;
+  xi.mean_out = pl->singular ? pl->conv + VOFP_CONV_MEAN : nullptr;
+  xi.d2_out = d2_out;
+  const long npairs = ((long)xi.ny * xi.nz + 1) / 2;
+  const int xgrid = (int)((npairs + xi.pb - 1) / xi.pb);
+  const size_t xsm = 2 * (size_t)xi.pb * xi.nx * sizeof(float2);
+  VOFP_LAUNCH(KID_XINV, st, (k_xinv<float, float2><<<xgrid, 256, xsm, st>>>(xi)));
+}
+
+static void xfwd32(vofp_plan* pl, int mode, XArgs xa, cudaStream_t st) {
+  xa.g = grid_dev(pl);
+  xa.fd = pl->ax[0].fd;
+  xa.tw = pl->ax[0].tw32;
+  xa.quart = pl->ax[0].quart32;
+  xa.pb = pl->xpb;
+  xa.S = pl->S32;
+  const long npairs = ((long)pl->n[1] * pl->n[2] + 1) / 2;
+  const int xgrid = (int)((npairs + xa.pb - 1) / xa.pb);
+  const size_t xsm = 2 * (size_t)xa.pb * pl->n[0] * sizeof(float2);
+  switch (mode) {
+    case RHS_F: VOFP_LAUNCH(KID_XFWD, st, (k_xfwd<float, float2, RHS_F><<<xgrid, 256, xsm, st>>>(xa))); break;
+    case RHS_DIV:
+      VOFP_LAUNCH(KID_XFWD_DIV, st, (k_xfwd<float, float2, RHS_DIV><<<xgrid, 256, xsm, st>>>(xa)));
+      break;
+    case RHS_DIV_STEFAN:
+      VOFP_LAUNCH(KID_XFWD_DIVSTEF, st, (k_xfwd<float, float2, RHS_DIV_STEFAN><<<xgrid, 256, xsm, st>>>(xa)));
+      break;
+    default:
+      VOFP_LAUNCH(KID_RESID, st, (k_xfwd<float, float2, RHS_RESID><<<xgrid, 256, xsm, st>>>(xa)));
+      break;
+  }
+}
+
+int mixed_solve(vofp_plan* pl, int mode, const XArgs* xin, const double* f, double* pout, cudaStream_t st,
+                vofp_info* info) {
+  if (mode == RHS_STEFAN) return VOFP_ERR_UNSUPPORTED;  // the extension passes its source as RHS_F
+  const double tol2 = pl->opts.tol * pl->opts.tol;
+  int M = pl->opts.max_refine;
+  if (M > VOFP_MAX_REFINE) M = VOFP_MAX_REFINE;
+  const size_t cells = (size_t)pl->n[0] * pl->n[1] * pl->n[2];
+  double* conv = pl->conv;
+  if (cudaMemsetAsync(conv, 0, sizeof(double) * VOFP_CONV_SLOTS, st) != cudaSuccess) return VOFP_ERR_CUDA;
+  const bool stats = info != nullptr;
+
+  // initial FP32 solve of f (kept in FP64 in pl->F)
+  XArgs xa = {};
+  if (xin) xa = *xin;
+  if (mode == RHS_F) {
+    xa.f = f;
+    xa.scale = 1.0;
+  }
+  xa.fsave = pl->F;
+  xa.sq_out = conv + 0;
+  xa.fv_out = conv + 1;
+  xa.abs_out = conv + 2;
+  xa.skip_k = -1;
+  xa.info = nullptr;
+  xfwd32(pl, mode, xa, st);
+  solve32(pl, st, -1, tol2, stats);
+  xinv32(pl, pout, 0, -1, tol2, conv + VOFP_CONV_DEL, st);
+
+  // defect-correction refinement: correction j solves for r_{j-1} and is skipped once correction j - 1
+  // converged (see launch_skipped)
+  for (int j = 1; j <= M; ++j) {
+    XArgs ra = {};
+    ra.f = pl->F;
+    ra.p = pout;
+    ra.defect_sum = pl->singular ? conv + 1 : nullptr;
+    ra.inv_volume = 1.0 / pl->volume;
+    ra.sq_out = conv + VOFP_CONV_RES + j - 1;
+    ra.skip_conv = conv;
+    ra.skip_k = j - 1;
+    ra.tol2 = tol2;
+    xfwd32(pl, RHS_RESID, ra, st);
+    solve32(pl, st, j - 1, tol2, stats);
+    xinv32(pl, pout, 1, j - 1, tol2, conv + VOFP_CONV_DEL + j, st);
+  }
+  if (info) {
+    VOFP_LAUNCH(KID_RESID, st,
+                k_resid_norm<<<grid_blocks(cells, 256), 256, 0, st>>>(
+                    grid_dev(pl), pl->F, pout, pl->singular ? conv + 1 : nullptr, 1.0 / pl->volume,
+                    conv + VOFP_CONV_FINAL, conv, -1, tol2));
+  }
+  if (pl->singular && pout != pl->P) {
+    const double scale = 1.0 / ((double)pl->n[0] * pl->n[1] * (pl->volume / (pl->n[0] * pl->dx * pl->n[1] * pl->dy)));
+    VOFP_LAUNCH(KID_RESID, st,
+                k_shift<<<grid_blocks(cells, 256), 256, 0, st>>>(pout, cells, conv + VOFP_CONV_MEAN, scale));
+  }
+  if (cudaGetLastError() != cudaSuccess) return VOFP_ERR_CUDA;
+  if (!info) return VOFP_OK;
+
+  double h[VOFP_CONV_SLOTS];
+  vofp_devinfo hi;
+  if (cudaMemcpyAsync(h, conv, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&hi, pl->info, sizeof(hi), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return VOFP_ERR_CUDA;
+  int status = VOFP_OK;
+  const double f2 = h[0];
+  auto converged = [&](int j) {
+    return h[VOFP_CONV_RES + j - 1] <= tol2 * f2 && h[VOFP_CONV_DEL + j] <= 0.01 * tol2 * h[VOFP_CONV_DEL];
+  };
+  int iters = 1;
+  while (iters < M && !converged(iters)) ++iters;
+  const bool conv_ok = converged(iters);
+  const double rr = f2 > 0 ? std::sqrt(h[VOFP_CONV_FINAL] / f2) : 0.0;
+  const double defect = pl->singular ? h[1] / pl->volume : 0.0;
+  info->compat_defect = defect;
+  info->rel_residual = rr;
+  info->refine_iters = iters;
+  if (hi.nonfinite || !std::isfinite(f2) || !std::isfinite(rr)) status = VOFP_ERR_NONFINITE;
+  if (status == VOFP_OK && !conv_ok) status = VOFP_WARN_NOT_CONVERGED;
+  if (status == VOFP_OK && pl->singular && std::fabs(defect) > 1e-12 * h[2] / pl->volume)
+    status = VOFP_WARN_INCOMPATIBLE_RHS;
+  info->status = status;
+  return status;
 }
 
 }  // namespace vofp

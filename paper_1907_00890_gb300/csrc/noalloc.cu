@@ -36,7 +36,10 @@ constexpr size_t kOffZb = kOffZa + kMaxN * sizeof(double);
 constexpr size_t kOffZc = kOffZb + kMaxN * sizeof(double);
 constexpr size_t kOffDz = kOffZc + kMaxN * sizeof(double);
 constexpr size_t kOffHz = kOffDz + kMaxN * sizeof(double);
-constexpr size_t kTableBytes = kOffHz + (kMaxN + 1) * sizeof(double) + 256;
+constexpr size_t kOffRdz = kOffHz + (kMaxN + 1) * sizeof(double);
+constexpr size_t kOffRhz = kOffRdz + kMaxN * sizeof(double);
+constexpr size_t kOffRzc = kOffRhz + (kMaxN + 1) * sizeof(double);
+constexpr size_t kTableBytes = kOffRzc + kMaxN * sizeof(double) + 256;
 constexpr size_t kScratchBytes = kSpecBytes + ((kTableBytes + 255) / 256) * 256;
 
 }  // namespace
@@ -59,6 +62,9 @@ __global__ void k_noalloc_tables(int nx, int ny, int nz, double dx, double dy, i
   double* zb = (double*)(tab + kOffZb);
   double* zc = (double*)(tab + kOffZc);
   double* hz = (double*)(tab + kOffHz);
+  double* rdz = (double*)(tab + kOffRdz);
+  double* rhz = (double*)(tab + kOffRhz);
+  double* rzc = (double*)(tab + kOffRzc);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   for (int a = 0; a < 2; ++a) {
     const int n = nn[a];
@@ -89,6 +95,7 @@ __global__ void k_noalloc_tables(int nx, int ny, int nz, double dx, double dy, i
     else
       h = 0.5 * (dz[t - 1] + dz[t]);
     hz[t] = h;
+    rhz[t] = 1.0 / h;
   }
   if (t < nz) {
     const double hlo = t == 0 ? (zper ? 0.5 * (dz[nz - 1] + dz[0]) : dz[0]) : 0.5 * (dz[t - 1] + dz[t]);
@@ -108,6 +115,8 @@ __global__ void k_noalloc_tables(int nx, int ny, int nz, double dx, double dy, i
     za[t] = aa;
     zb[t] = b;
     zc[t] = cc;
+    rdz[t] = 1.0 / dz[t];
+    rzc[t] = 1.0 / (hlo + hhi);
   }
 }
 
@@ -189,6 +198,10 @@ extern "C" int vofp_poisson_solve_noalloc(int nx, int ny, int nz, double dx, dou
   pl.zc = (double*)(tab + kOffZc);
   pl.dz = (double*)(tab + kOffDz);
   pl.hz = (double*)(tab + kOffHz);
+  pl.rdz = (double*)(tab + kOffRdz);
+  pl.rhz = (double*)(tab + kOffRhz);
+  pl.rzc = (double*)(tab + kOffRzc);
+  pl.ztab = nullptr;
   pl.S = (double*)base;
   pl.info = nullptr;
   pl.xpb = nx >= 1024 ? 1 : (1024 / nx > 16 ? 16 : 1024 / nx);

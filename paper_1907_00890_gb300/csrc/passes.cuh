@@ -35,7 +35,15 @@ struct XArgs {
   double coef;        // RHS_STEFAN: 1/rho2 - 1/rho1
   int grad_mode;
   double* fsave;      // if non-null, the FP64 right-hand side is stored here (mixed path)
-  vofp_devinfo* info; // if non-null, accumulate sum |f| V (and ||f||^2 for RHS_RESID into res2)
+  vofp_devinfo* info; // if non-null, accumulate sum |f| V into info->abs_sum
+  double* sq_out;     // if non-null, accumulate sum f^2 here
+  double* fv_out;     // if non-null, accumulate sum f V here
+  double* abs_out;    // if non-null, accumulate sum |f| V here
+  const double* skip_conv;  // mixed refinement: skip when conv[3 + skip_k] <= tol2 conv[0]
+  int skip_k;
+  double tol2;
+  const double* defect_sum; // RHS_RESID on a singular operator: subtract (*defect_sum) * inv_volume
+  double inv_volume;
   void* S;            // spectrum output
 };
 
@@ -95,6 +103,7 @@ __device__ __forceinline__ double rhs_at(const XArgs& a, int i, int j, int k) {
     f = (divergence_at(a.g, a.u, a.v, a.w, i, j, k) - s) * a.scale;
   } else {
     f = __ldg(a.f + c) - lap_at(a.g, a.p, i, j, k);
+    if (a.defect_sum) f -= *a.defect_sum * a.inv_volume;
   }
   return f;
 }
@@ -113,19 +122,20 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // x pass, forward: RHS + transform of line pairs (2p, 2p+1) of the flattened (k, j) line index.
+// Block body: `bx` is the block's index within this grid's launch (batched launches pass a local index).
 template <typename T, typename C, int MODE>
-__global__ void __launch_bounds__(256) k_xfwd(XArgs a) {
+__device__ __forceinline__ void xfwd_block(const XArgs& a, int bx, unsigned char* smem_raw, double* red) {
   typedef decltype(C::x) R;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* b0 = reinterpret_cast<C*>(smem_raw);
   const int n = a.g.nx;
   const int PB = a.pb;
   C* b1 = b0 + PB * n;
-  __shared__ double red[32];
+  if (launch_skipped(a.skip_conv, a.skip_k, a.tol2)) return;
   const long nlines = (long)a.g.ny * a.g.nz;
-  const long pair0 = (long)blockIdx.x * PB;
+  const long pair0 = (long)bx * PB;
   const int bc = a.g.bcx;
-  double acc_abs = 0, acc_sq = 0;
+  const bool stats = a.info || a.sq_out || a.fv_out || a.abs_out;
+  double acc_abs = 0, acc_sq = 0, acc_fv = 0;
   for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
     const int pb = t / n, i = t - pb * n;
     const long l0 = 2 * (pair0 + pb), l1 = l0 + 1;
@@ -134,20 +144,22 @@ __global__ void __launch_bounds__(256) k_xfwd(XArgs a) {
       const int k = (int)(l0 / a.g.ny), j = (int)(l0 - (long)k * a.g.ny);
       fa = rhs_at<MODE>(a, i, j, k);
       if (a.fsave) a.fsave[l0 * n + i] = fa;
-      if (a.info) {
+      if (stats) {
         const double vol = a.g.dx * a.g.dy * __ldg(a.g.dz + k);
         acc_abs += fabs(fa) * vol;
         acc_sq += fa * fa;
+        acc_fv += fa * vol;
       }
     }
     if (l1 < nlines) {
       const int k = (int)(l1 / a.g.ny), j = (int)(l1 - (long)k * a.g.ny);
       fb = rhs_at<MODE>(a, i, j, k);
       if (a.fsave) a.fsave[l1 * n + i] = fb;
-      if (a.info) {
+      if (stats) {
         const double vol = a.g.dx * a.g.dy * __ldg(a.g.dz + k);
         acc_abs += fabs(fb) * vol;
         acc_sq += fb * fb;
+        acc_fv += fb * vol;
       }
     }
     int idx = i;
@@ -158,13 +170,20 @@ __global__ void __launch_bounds__(256) k_xfwd(XArgs a) {
     }
     b0[pb * n + idx] = cmk<C>(sg * (R)fa, sg * (R)fb);
   }
-  if (a.info) {
+  if (a.info || a.abs_out) {
     const double s1 = block_sum(acc_abs, red);
-    if (threadIdx.x == 0 && s1 != 0) atomicAdd(&a.info->abs_sum, s1);
-    if (MODE == RHS_RESID) {
-      const double s2 = block_sum(acc_sq, red);
-      if (threadIdx.x == 0 && s2 != 0) atomicAdd(&a.info->res2, s2);
+    if (threadIdx.x == 0 && s1 != 0) {
+      if (a.info) atomicAdd(&a.info->abs_sum, s1);
+      if (a.abs_out) atomicAdd(a.abs_out, s1);
     }
+  }
+  if (a.sq_out) {
+    const double s2 = block_sum(acc_sq, red);
+    if (threadIdx.x == 0 && s2 != 0) atomicAdd(a.sq_out, s2);
+  }
+  if (a.fv_out) {
+    const double s3 = block_sum(acc_fv, red);
+    if (threadIdx.x == 0 && s3 != 0) atomicAdd(a.fv_out, s3);
   }
   __syncthreads();
   const C* Z = fft_smem<C>(b0, b1, PB, a.fd, reinterpret_cast<const C*>(a.tw));
@@ -180,6 +199,19 @@ __global__ void __launch_bounds__(256) k_xfwd(XArgs a) {
   }
 }
 
+template <typename T, typename C, int MODE>
+__global__ void __launch_bounds__(256) k_xfwd(XArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  xfwd_block<T, C, MODE>(a, blockIdx.x, smem_raw, red);
+}
+
+// Number of blocks of the x pass for one grid.
+__host__ __device__ __forceinline__ int xpass_blocks(int ny, int nz, int pb) {
+  const long npairs = ((long)ny * nz + 1) / 2;
+  return (int)((npairs + pb - 1) / pb);
+}
+
 struct YArgs {
   int nx, ny, nz, bc;
   FftDesc fd;
@@ -187,19 +219,22 @@ struct YArgs {
   const void* quart;
   int tx;  // columns per block (even)
   void* S;
+  const double* skip_conv;
+  int skip_k;
+  double tol2;
 };
 
-// y pass on a tile of `tx` columns (pairs of columns share one complex FFT) of plane k = blockIdx.y.
+// y pass on a tile of `tx` columns (pairs of columns share one complex FFT) of plane k = by.
 template <typename T, typename C, bool INV>
-__global__ void __launch_bounds__(256) k_ypass(YArgs a) {
+__device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsigned char* smem_raw) {
   typedef decltype(C::x) R;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (launch_skipped(a.skip_conv, a.skip_k, a.tol2)) return;
   const int n = a.ny;
   const int B = a.tx >> 1;
   C* b0 = reinterpret_cast<C*>(smem_raw);
   C* b1 = b0 + B * n;
-  const int i0 = blockIdx.x * a.tx;
-  const size_t base = (size_t)blockIdx.y * a.ny * a.nx;
+  const int i0 = bx * a.tx;
+  const size_t base = (size_t)by * a.ny * a.nx;
   T* S = reinterpret_cast<T*>(a.S);
   const int bc = a.bc;
   const C* quart = reinterpret_cast<const C*>(a.quart);
@@ -265,6 +300,12 @@ __global__ void __launch_bounds__(256) k_ypass(YArgs a) {
   }
 }
 
+template <typename T, typename C, bool INV>
+__global__ void __launch_bounds__(256) k_ypass(YArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ypass_block<T, C, INV>(a, blockIdx.x, blockIdx.y, smem_raw);
+}
+
 struct XInvArgs {
   int nx, ny, nz, bc;
   FftDesc fd;
@@ -274,19 +315,25 @@ struct XInvArgs {
   const void* S;
   double* p;
   int accumulate;  // 0: p = value, 1: p += value
+  const double* skip_conv;
+  int skip_k;
+  double tol2;
+  const double* dz;   // with mean_out: accumulate sum value * dz[k] (the gauge of the result)
+  double* mean_out;
+  double* d2_out;     // if non-null: accumulate sum value^2 (size of this correction)
 };
 
 // x pass, inverse: two packed lines per complex FFT, result written (or added) to the FP64 cell array p.
 template <typename T, typename C>
-__global__ void __launch_bounds__(256) k_xinv(XInvArgs a) {
+__device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned char* smem_raw, double* red) {
   typedef decltype(C::x) R;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (launch_skipped(a.skip_conv, a.skip_k, a.tol2)) return;
   const int n = a.nx;
   const int PB = a.pb;
   C* b0 = reinterpret_cast<C*>(smem_raw);
   C* b1 = b0 + PB * n;
   const long nlines = (long)a.ny * a.nz;
-  const long pair0 = (long)blockIdx.x * PB;
+  const long pair0 = (long)bx * PB;
   const T* S = reinterpret_cast<const T*>(a.S);
   const int bc = a.bc;
   const C* quart = reinterpret_cast<const C*>(a.quart);
@@ -304,6 +351,7 @@ __global__ void __launch_bounds__(256) k_xinv(XInvArgs a) {
   }
   __syncthreads();
   const C* Y = fft_smem<C>(b0, b1, PB, a.fd, reinterpret_cast<const C*>(a.tw));
+  double acc = 0, acc2 = 0;
   for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
     const int pb = t / n, i = t - pb * n;
     const long l0 = 2 * (pair0 + pb), l1 = l0 + 1;
@@ -322,7 +370,30 @@ __global__ void __launch_bounds__(256) k_xinv(XInvArgs a) {
       if (l0 < nlines) a.p[l0 * n + i] = va;
       if (l1 < nlines) a.p[l1 * n + i] = vb;
     }
+    if (a.mean_out) {
+      if (l0 < nlines) acc += va * __ldg(a.dz + l0 / a.ny);
+      if (l1 < nlines) acc += vb * __ldg(a.dz + l1 / a.ny);
+    }
+    if (a.d2_out) {
+      if (l0 < nlines) acc2 += va * va;
+      if (l1 < nlines) acc2 += vb * vb;
+    }
   }
+  if (a.mean_out) {
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0 && s != 0) atomicAdd(a.mean_out, s);
+  }
+  if (a.d2_out) {
+    const double s = block_sum(acc2, red);
+    if (threadIdx.x == 0 && s != 0) atomicAdd(a.d2_out, s);
+  }
+}
+
+template <typename T, typename C>
+__global__ void __launch_bounds__(256) k_xinv(XInvArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  xinv_block<T, C>(a, blockIdx.x, smem_raw, red);
 }
 
 }  // namespace vofp

@@ -7,6 +7,10 @@
 //   DD       : -(4/h^2) sin^2(pi (m+1) / (2n)).
 // z keeps its tridiagonal rows: a_k = 1/(dz_k h_{k-1/2}), c_k = 1/(dz_k h_{k+1/2}), b_k = -(a_k + c_k); an N
 // end folds the outer coupling into the diagonal (+), a D end subtracts it (-), a periodic axis wraps.
+//
+// Creation is split in two: plan_prepare validates and builds every table on the host (and reports the
+// device bytes the plan needs), plan_bind places the plan in device memory -- its own cudaMalloc, or a block
+// handed in by the caller (the server's arena) with asynchronous uploads on a stream.
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -59,63 +63,47 @@ void factor_radices(int n, FftDesc* fd) {
 }
 
 static std::atomic<unsigned long long> g_launches{0};
-void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
-
-}  // namespace vofp
-
-using namespace vofp;
-
-extern "C" unsigned long long vofp_launch_count(void) { return g_launches.load(); }
+// While this thread captures a graph its launches are not executions: count them apart (they are added
+// once per replay instead) and do not trace them.
+static thread_local int t_capturing = 0;
+static thread_local unsigned long long t_captured = 0;
+void note_launches(int n) {
+  if (t_capturing)
+    t_captured += (unsigned long long)n;
+  else
+    g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed);
+}
+bool capturing() { return t_capturing != 0; }
+void capture_begin() {
+  t_capturing = 1;
+  t_captured = 0;
+}
+unsigned long long capture_end() {
+  t_capturing = 0;
+  return t_captured;
+}
 
 static const double kPi = 3.14159265358979323846;
 
-extern "C" void vofp_opts_default(vofp_opts* opt) {
-  if (!opt) return;
-  opt->prec = VOFP_FP64;
-  opt->tol = 1e-10;
-  opt->max_refine = 6;
-  opt->grad_mode = 0;
-  opt->tune = 0;
-}
-
-extern "C" const char* vofp_error_string(int s) {
-  switch (s) {
-    case VOFP_OK: return "ok";
-    case VOFP_WARN_INCOMPATIBLE_RHS: return "warning: right-hand side incompatible with the singular operator (mean removed)";
-    case VOFP_WARN_NOT_CONVERGED: return "warning: mixed-precision refinement did not reach the tolerance";
-    case VOFP_ERR_INVALID_ARG: return "invalid argument";
-    case VOFP_ERR_UNSUPPORTED: return "unsupported configuration";
-    case VOFP_ERR_OOM: return "out of device memory";
-    case VOFP_ERR_CUDA: return "CUDA error";
-    case VOFP_ERR_TIMEOUT: return "timed out";
-    case VOFP_ERR_BUSY: return "busy: over the memory budget";
-    case VOFP_ERR_NONFINITE: return "non-finite values in the result";
-    case VOFP_ERR_TOO_LARGE: return "problem larger than the static scratch of the allocation-free solve";
-    default: return "unknown status";
-  }
-}
-
 static double eig_1d(int bc, int n, double h, int q) {
-  int m;
   double arg;
-  if (bc == VOFP_BC_P) {
-    m = (q + 1) / 2;
-    arg = kPi * m / n;
-  } else if (bc == VOFP_BC_NN) {
+  if (bc == VOFP_BC_P)
+    arg = kPi * ((q + 1) / 2) / n;
+  else if (bc == VOFP_BC_NN)
     arg = kPi * q / (2.0 * n);
-  } else {
+  else
     arg = kPi * (q + 1) / (2.0 * n);
-  }
   const double s = std::sin(arg);
   return -4.0 / (h * h) * s * s;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+static int zdistinct(int n, int bc) { return bc == VOFP_BC_P ? n / 2 + 1 : n; }
 
-extern "C" int vofp_plan_create(int nx, int ny, int nz, double dx, double dy, const double* dz, const int bc[3],
-                                const vofp_opts* opt, vofp_plan** out) {
-  if (!out || !dz || !bc) return VOFP_ERR_INVALID_ARG;
-  *out = nullptr;
+// Validate, fill the host-side plan and build all tables on the host.
+int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz, const int bc[3],
+                 const vofp_opts* opt, PlanPrep* pp) {
+  if (!dz || !bc) return VOFP_ERR_INVALID_ARG;
   if (nx < 1 || ny < 1 || nz < 1 || !(dx > 0) || !(dy > 0) || !std::isfinite(dx) || !std::isfinite(dy))
     return VOFP_ERR_INVALID_ARG;
   if ((long long)nx * ny * nz > (1LL << 31) - 1) return VOFP_ERR_UNSUPPORTED;
@@ -129,9 +117,9 @@ extern "C" int vofp_plan_create(int nx, int ny, int nz, double dx, double dy, co
   vofp_opts_default(&o);
   if (opt) o = *opt;
   if (o.prec != VOFP_FP64 && o.prec != VOFP_MIXED) return VOFP_ERR_INVALID_ARG;
-  if (o.prec == VOFP_MIXED) return VOFP_ERR_UNSUPPORTED;
   if (o.grad_mode != 0 && o.grad_mode != 1) return VOFP_ERR_INVALID_ARG;
   if (o.max_refine < 1) o.max_refine = 1;
+  if (o.max_refine > VOFP_MAX_REFINE) o.max_refine = VOFP_MAX_REFINE;
   if (!(o.tol > 0)) o.tol = 1e-10;
 
   vofp_plan* p = (vofp_plan*)calloc(1, sizeof(vofp_plan));
@@ -151,6 +139,8 @@ extern "C" int vofp_plan_create(int nx, int ny, int nz, double dx, double dy, co
   double lz = 0;
   for (int k = 0; k < nz; ++k) lz += dz[k];
   p->volume = nx * dx * ny * dy * lz;
+  const bool mixed = o.prec == VOFP_MIXED;
+  const bool zper = bc[2] == VOFP_BC_P;
 
   // ---- host tables ----
   const int nn[2] = {nx, ny};
@@ -178,8 +168,7 @@ extern "C" int vofp_plan_create(int nx, int ny, int nz, double dx, double dy, co
     p->ax[a].n = n;
     p->ax[a].bc = bc[a];
   }
-  std::vector<double> za(nz), zb(nz), zc(nz), hz(nz + 1);
-  const bool zper = bc[2] == VOFP_BC_P;
+  std::vector<double> za(nz), zb(nz), zc(nz), hz(nz + 1), rdz(nz), rhz(nz + 1), rzc(nz);
   const double hper = 0.5 * (dz[nz - 1] + dz[0]);
   for (int k = 0; k <= nz; ++k) {
     if (k == 0)
@@ -188,6 +177,7 @@ extern "C" int vofp_plan_create(int nx, int ny, int nz, double dx, double dy, co
       hz[k] = zper ? hper : dz[nz - 1];
     else
       hz[k] = 0.5 * (dz[k - 1] + dz[k]);
+    rhz[k] = 1.0 / hz[k];
   }
   for (int k = 0; k < nz; ++k) {
     const double a = 1.0 / (dz[k] * hz[k]);
@@ -205,116 +195,259 @@ extern "C" int vofp_plan_create(int nx, int ny, int nz, double dx, double dy, co
     za[k] = aa;
     zb[k] = b;
     zc[k] = cc;
+    rdz[k] = 1.0 / dz[k];
+    rzc[k] = 1.0 / (hz[k] + hz[k + 1]);
   }
-
-  // ---- one device block for all tables ----
-  size_t off = 0;
-  size_t o_lam[2], o_tw[2], o_q[2], o_tw32[2], o_q32[2];
-  for (int a = 0; a < 2; ++a) {
-    o_lam[a] = off;
-    off = align256(off + sizeof(double) * nn[a]);
-    o_tw[a] = off;
-    off = align256(off + sizeof(double2) * nn[a]);
-    o_q[a] = off;
-    off = align256(off + sizeof(double2) * nn[a]);
-    o_tw32[a] = off;
-    off = align256(off + sizeof(float2) * nn[a]);
-    o_q32[a] = off;
-    off = align256(off + sizeof(float2) * nn[a]);
-  }
-  const size_t o_za = off;
-  off = align256(off + sizeof(double) * nz);
-  const size_t o_zb = off;
-  off = align256(off + sizeof(double) * nz);
-  const size_t o_zc = off;
-  off = align256(off + sizeof(double) * nz);
-  const size_t o_dz = off;
-  off = align256(off + sizeof(double) * nz);
-  const size_t o_hz = off;
-  off = align256(off + sizeof(double) * (nz + 1));
-  const size_t o_info = off;
-  off = align256(off + sizeof(vofp_devinfo));
-  const size_t table_bytes = off;
-
-  std::vector<unsigned char> host(table_bytes, 0);
-  for (int a = 0; a < 2; ++a) {
-    memcpy(&host[o_lam[a]], lam[a].data(), sizeof(double) * nn[a]);
-    memcpy(&host[o_tw[a]], tw[a].data(), sizeof(double2) * nn[a]);
-    memcpy(&host[o_q[a]], quart[a].data(), sizeof(double2) * nn[a]);
-    memcpy(&host[o_tw32[a]], tw32[a].data(), sizeof(float2) * nn[a]);
-    memcpy(&host[o_q32[a]], quart32[a].data(), sizeof(float2) * nn[a]);
-  }
-  memcpy(&host[o_za], za.data(), sizeof(double) * nz);
-  memcpy(&host[o_zb], zb.data(), sizeof(double) * nz);
-  memcpy(&host[o_zc], zc.data(), sizeof(double) * nz);
-  memcpy(&host[o_dz], dz, sizeof(double) * nz);
-  memcpy(&host[o_hz], hz.data(), sizeof(double) * (nz + 1));
-
-  const size_t cells = (size_t)nx * ny * nz;
-  const bool mixed = o.prec == VOFP_MIXED;
-  size_t ws = 0;
-  const size_t o_S = ws;
-  ws = align256(ws + sizeof(double) * cells);
-  const size_t o_P = ws;
-  ws = align256(ws + sizeof(double) * cells);
-  size_t o_S32 = 0, o_F = 0, o_R = 0;
+  // mixed path: the low-eigenvalue (x, y) pairs, |lx + ly| <= 64 * (smallest positive |eigenvalue|)
+  std::vector<int2> low;
+  p->lowthr = -1.0;
   if (mixed) {
-    o_S32 = ws;
-    ws = align256(ws + sizeof(float) * cells);
-    o_F = ws;
-    ws = align256(ws + sizeof(double) * cells);
-    o_R = ws;
-    ws = align256(ws + sizeof(double) * cells);
+    double l1 = 0;
+    for (int a = 0; a < 2; ++a)
+      for (int q = 0; q < nn[a]; ++q) {
+        const double v = std::fabs(lam[a][q]);
+        if (v > 0 && (l1 == 0 || v < l1)) l1 = v;
+      }
+    p->lowthr = 64.0 * l1;
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        if (std::fabs(lam[0][i] + lam[1][j]) <= p->lowthr) low.push_back(make_int2(i, j));
   }
-  void* block = nullptr;
-  if (cudaMalloc(&block, table_bytes + ws) != cudaSuccess) {
-    cudaGetLastError();
-    free(p->dz_host);
-    free(p);
-    return VOFP_ERR_OOM;
-  }
-  if (cudaMemcpy(block, host.data(), table_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
-    cudaFree(block);
-    free(p->dz_host);
-    free(p);
-    return VOFP_ERR_CUDA;
-  }
-  unsigned char* b = (unsigned char*)block;
-  p->table_block = block;
-  p->bytes = table_bytes + ws;
-  for (int a = 0; a < 2; ++a) {
-    p->ax[a].lam = (const double*)(b + o_lam[a]);
-    p->ax[a].tw64 = (const double2*)(b + o_tw[a]);
-    p->ax[a].quart64 = (const double2*)(b + o_q[a]);
-    p->ax[a].tw32 = (const float2*)(b + o_tw32[a]);
-    p->ax[a].quart32 = (const float2*)(b + o_q32[a]);
-  }
-  p->za = (double*)(b + o_za);
-  p->zb = (double*)(b + o_zb);
-  p->zc = (double*)(b + o_zc);
-  p->dz = (double*)(b + o_dz);
-  p->hz = (double*)(b + o_hz);
-  p->info = (vofp_devinfo*)(b + o_info);
-  unsigned char* w = b + table_bytes;
-  p->S = (double*)(w + o_S);
-  p->P = (double*)(w + o_P);
-  p->S32 = mixed ? (float*)(w + o_S32) : nullptr;
-  p->F = mixed ? (double*)(w + o_F) : nullptr;
-  p->R = mixed ? (double*)(w + o_R) : nullptr;
+  p->nlow = (int)low.size();
 
-  // launch shapes (defaults; the tuner may override them)
+  // ---- layout ----
+  PlanLayout& L = pp->L;
+  size_t off = 0;
+  for (int a = 0; a < 2; ++a) {
+    L.lam[a] = off;
+    off = align256(off + sizeof(double) * nn[a]);
+    L.tw[a] = off;
+    off = align256(off + sizeof(double2) * nn[a]);
+    L.q[a] = off;
+    off = align256(off + sizeof(double2) * nn[a]);
+    L.tw32[a] = off;
+    off = align256(off + sizeof(float2) * nn[a]);
+    L.q32[a] = off;
+    off = align256(off + sizeof(float2) * nn[a]);
+  }
+  L.za = off;
+  off = align256(off + sizeof(double) * nz);
+  L.zb = off;
+  off = align256(off + sizeof(double) * nz);
+  L.zc = off;
+  off = align256(off + sizeof(double) * nz);
+  L.dz = off;
+  off = align256(off + sizeof(double) * nz);
+  L.hz = off;
+  off = align256(off + sizeof(double) * (nz + 1));
+  L.rdz = off;
+  off = align256(off + sizeof(double) * nz);
+  L.rhz = off;
+  off = align256(off + sizeof(double) * (nz + 1));
+  L.rzc = off;
+  off = align256(off + sizeof(double) * nz);
+  L.low = off;
+  off = align256(off + sizeof(int2) * low.size());
+  L.conv = off;
+  off = align256(off + sizeof(double) * VOFP_CONV_SLOTS);
+  L.info = off;
+  off = align256(off + sizeof(vofp_devinfo));
+  L.table_bytes = off;
+  // workspace: both paths keep a scratch potential; FP64 plans the FP64 spectrum and the z factor table,
+  // mixed plans the FP32 spectrum, the FP64 right-hand side and FP64 columns for the low-eigenvalue systems
+  const size_t cells = (size_t)nx * ny * nz;
+  const int Ux = zdistinct(nx, bc[0]), Uy = zdistinct(ny, bc[1]);
+  L.P = off;
+  off = align256(off + sizeof(double) * cells);
+  L.S = L.T = L.S32 = L.F = L.lowscr = 0;
+  if (!mixed) {
+    L.S = off;
+    off = align256(off + sizeof(double) * cells);
+    if (!zper) {
+      L.T = off;
+      off = align256(off + sizeof(double2) * (size_t)Ux * Uy * nz);
+    }
+  } else {
+    L.S32 = off;
+    off = align256(off + sizeof(float) * cells);
+    L.F = off;
+    off = align256(off + sizeof(double) * cells);
+    L.lowscr = off;
+    off = align256(off + sizeof(double) * 3 * (size_t)nz * low.size());
+  }
+  L.total = off;
+  p->Ux = Ux;
+  p->Uy = Uy;
+
+  std::vector<unsigned char>& host = pp->host;
+  host.assign(L.table_bytes, 0);
+  for (int a = 0; a < 2; ++a) {
+    memcpy(&host[L.lam[a]], lam[a].data(), sizeof(double) * nn[a]);
+    memcpy(&host[L.tw[a]], tw[a].data(), sizeof(double2) * nn[a]);
+    memcpy(&host[L.q[a]], quart[a].data(), sizeof(double2) * nn[a]);
+    memcpy(&host[L.tw32[a]], tw32[a].data(), sizeof(float2) * nn[a]);
+    memcpy(&host[L.q32[a]], quart32[a].data(), sizeof(float2) * nn[a]);
+  }
+  memcpy(&host[L.za], za.data(), sizeof(double) * nz);
+  memcpy(&host[L.zb], zb.data(), sizeof(double) * nz);
+  memcpy(&host[L.zc], zc.data(), sizeof(double) * nz);
+  memcpy(&host[L.dz], dz, sizeof(double) * nz);
+  memcpy(&host[L.hz], hz.data(), sizeof(double) * (nz + 1));
+  memcpy(&host[L.rdz], rdz.data(), sizeof(double) * nz);
+  memcpy(&host[L.rhz], rhz.data(), sizeof(double) * (nz + 1));
+  memcpy(&host[L.rzc], rzc.data(), sizeof(double) * nz);
+  if (!low.empty()) memcpy(&host[L.low], low.data(), sizeof(int2) * low.size());
+
+  // launch shapes
   p->xpb = nx >= 1024 ? 1 : (1024 / nx > 16 ? 16 : 1024 / nx);
   if (p->xpb < 1) p->xpb = 1;
   int tx = 16;
   while (tx > 2 && (size_t)16 * tx * ny > 96 * 1024) tx -= 2;
   p->ytx = tx;
+  tx = 16;
+  while (tx > 2 && (size_t)8 * tx * ny > 96 * 1024) tx -= 2;
+  p->ytx32 = tx;
   const int nvec = zper ? 3 : 2;
   int ti = 32;
   while (ti > 1 && (size_t)nvec * ti * nz * sizeof(double) > 96 * 1024) ti /= 2;
   p->zti = ti;
+  ti = 32;
+  while (ti > 1 && (size_t)nvec * ti * nz * sizeof(float) > 96 * 1024) ti /= 2;
+  p->zti32 = ti;
+  pp->p = p;
+  return VOFP_OK;
+}
+
+// Place a prepared plan in device memory.  `block` NULL: the plan allocates (and later frees) its own
+// block and uploads synchronously.  Otherwise `block` (L.total bytes, owned by the caller) receives the
+// tables by an asynchronous copy on `st` from `stage` (pinned host memory of L.table_bytes bytes that must
+// stay valid until the copy has run).
+int plan_bind(PlanPrep* pp, void* block, cudaStream_t st, unsigned char* stage) {
+  vofp_plan* p = pp->p;
+  const PlanLayout& L = pp->L;
+  const bool own = block == nullptr;
+  if (own) {
+    if (cudaMalloc(&block, L.total) != cudaSuccess) {
+      cudaGetLastError();
+      return VOFP_ERR_OOM;
+    }
+    if (cudaMemcpy(block, pp->host.data(), L.table_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(block);
+      return VOFP_ERR_CUDA;
+    }
+    p->table_block = block;
+  } else {
+    memcpy(stage, pp->host.data(), L.table_bytes);
+    if (cudaMemcpyAsync(block, stage, L.table_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return VOFP_ERR_CUDA;
+    p->table_block = nullptr;  // not owned
+  }
+  unsigned char* b = (unsigned char*)block;
+  p->bytes = L.total;
+  for (int a = 0; a < 2; ++a) {
+    p->ax[a].lam = (const double*)(b + L.lam[a]);
+    p->ax[a].tw64 = (const double2*)(b + L.tw[a]);
+    p->ax[a].quart64 = (const double2*)(b + L.q[a]);
+    p->ax[a].tw32 = (const float2*)(b + L.tw32[a]);
+    p->ax[a].quart32 = (const float2*)(b + L.q32[a]);
+  }
+  p->za = (double*)(b + L.za);
+  p->zb = (double*)(b + L.zb);
+  p->zc = (double*)(b + L.zc);
+  p->dz = (double*)(b + L.dz);
+  p->hz = (double*)(b + L.hz);
+  p->rdz = (double*)(b + L.rdz);
+  p->rhz = (double*)(b + L.rhz);
+  p->rzc = (double*)(b + L.rzc);
+  p->conv = (double*)(b + L.conv);
+  p->info = (vofp_devinfo*)(b + L.info);
+  p->lowmodes = p->nlow ? (int2*)(b + L.low) : nullptr;
+  p->P = (double*)(b + L.P);
+  const bool mixed = p->opts.prec == VOFP_MIXED;
+  p->S = mixed ? nullptr : (double*)(b + L.S);
+  p->ztab = (!mixed && L.T) ? (double2*)(b + L.T) : nullptr;
+  p->S32 = mixed ? (float*)(b + L.S32) : nullptr;
+  p->F = mixed ? (double*)(b + L.F) : nullptr;
+  p->lowscratch = (mixed && p->nlow) ? (double*)(b + L.lowscr) : nullptr;
+  p->R = nullptr;
+  p->G = nullptr;  // interface geometry: allocated on first use (extension / Stefan source)
   init_kernel_attributes_fp64();
   init_kernel_attributes_mixed();
-  *out = p;
+  if (p->ztab) {
+    const int s = build_z_factors(p, st, own);
+    if (s) return s;
+  }
+  return VOFP_OK;
+}
+
+size_t plan_prep_device_bytes(const PlanPrep* pp) { return pp->L.total; }
+size_t plan_prep_stage_bytes(const PlanPrep* pp) { return pp->L.table_bytes; }
+
+void plan_free_host(vofp_plan* p) {
+  if (!p) return;
+  free(p->dz_host);
+  free(p);
+}
+
+int ensure_geometry(vofp_plan* p) {
+  if (p->G) return VOFP_OK;
+  const size_t cells = (size_t)p->n[0] * p->n[1] * p->n[2];
+  void* m = nullptr;
+  if (cudaMalloc(&m, 4 * sizeof(double) * cells) != cudaSuccess) {
+    cudaGetLastError();
+    return VOFP_ERR_OOM;
+  }
+  p->G = (double*)m;
+  p->bytes += 4 * sizeof(double) * cells;
+  return VOFP_OK;
+}
+
+}  // namespace vofp
+
+using namespace vofp;
+
+extern "C" unsigned long long vofp_launch_count(void) { return g_launches.load(); }
+
+extern "C" void vofp_opts_default(vofp_opts* opt) {
+  if (!opt) return;
+  opt->prec = VOFP_FP64;
+  opt->tol = 1e-10;
+  opt->max_refine = 6;
+  opt->grad_mode = 0;
+  opt->tune = 0;
+}
+
+extern "C" const char* vofp_error_string(int s) {
+  switch (s) {
+    case VOFP_OK: return "ok";
+    case VOFP_WARN_INCOMPATIBLE_RHS: return "warning: right-hand side incompatible with the singular operator (mean removed)";
+    case VOFP_WARN_NOT_CONVERGED: return "warning: mixed-precision refinement did not reach the tolerance";
+    case VOFP_ERR_INVALID_ARG: return "invalid argument";
+    case VOFP_ERR_UNSUPPORTED: return "unsupported configuration";
+    case VOFP_ERR_OOM: return "out of device memory";
+    case VOFP_ERR_CUDA: return "CUDA error";
+    case VOFP_ERR_TIMEOUT: return "timed out";
+    case VOFP_ERR_BUSY: return "busy: over the memory budget";
+    case VOFP_ERR_NONFINITE: return "non-finite values in the result";
+    case VOFP_ERR_TOO_LARGE: return "problem larger than the static scratch of the allocation-free solve";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int vofp_plan_create(int nx, int ny, int nz, double dx, double dy, const double* dz, const int bc[3],
+                                const vofp_opts* opt, vofp_plan** out) {
+  if (!out) return VOFP_ERR_INVALID_ARG;
+  *out = nullptr;
+  PlanPrep pp;
+  int s = plan_prepare(nx, ny, nz, dx, dy, dz, bc, opt, &pp);
+  if (s) return s;
+  s = plan_bind(&pp, nullptr, nullptr, nullptr);
+  if (s) {
+    vofp_plan_destroy(pp.p);
+    return s;
+  }
+  if (pp.p->opts.tune) vofp_plan_tune(pp.p);
+  *out = pp.p;
   return VOFP_OK;
 }
 
@@ -324,10 +457,10 @@ extern "C" void vofp_plan_destroy(vofp_plan* p) {
   cudaGetDevice(&cur);
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
-  cudaFree(p->table_block);
+  if (p->table_block) cudaFree(p->table_block);
+  if (p->G) cudaFree(p->G);
   cudaSetDevice(cur);
-  free(p->dz_host);
-  free(p);
+  plan_free_host(p);
 }
 
 extern "C" size_t vofp_plan_workspace_bytes(const vofp_plan* p) { return p ? p->bytes : 0; }

@@ -1,5 +1,6 @@
 // Host orchestration of the FP64 path and the public entry points
-// vofp_poisson_solve / vofp_project / vofp_extend_liquid_velocity.
+// vofp_poisson_solve / vofp_project / vofp_project_stefan / vofp_stefan_source /
+// vofp_extend_liquid_velocity / vofp_project_extend.
 //
 // One solve = x pass (right-hand side fused) -> y pass -> z tridiagonal pass -> inverse y -> inverse x,
 // then the face epilogue (§3.2 projection, §3.6 extension).  Every launch goes to the caller's stream.
@@ -25,8 +26,13 @@ GridDev grid_dev(const vofp_plan* pl) {
   g.bcz = pl->bc[2];
   g.dx = pl->dx;
   g.dy = pl->dy;
+  g.rdx = 1.0 / pl->dx;
+  g.rdy = 1.0 / pl->dy;
   g.dz = pl->dz;
   g.hz = pl->hz;
+  g.rdz = pl->rdz;
+  g.rhz = pl->rhz;
+  g.rzc = pl->rzc;
   return g;
 }
 
@@ -45,7 +51,8 @@ void init_kernel_attributes_fp64() {
   allow_smem(k_ypass<double, double2, false>);
   allow_smem(k_ypass<double, double2, true>);
   allow_smem(k_xinv<double, double2>);
-  allow_smem(k_zsolve64);
+  allow_smem(k_zsolve<double, double>);
+  allow_smem(k_zsolve64_tab);
 }
 
 int grid_blocks(size_t total, int threads) {
@@ -53,6 +60,47 @@ int grid_blocks(size_t total, int threads) {
   if (b > 152 * 16) b = 152 * 16;
   if (b < 1) b = 1;
   return (int)b;
+}
+
+ZArgs z_args(const vofp_plan* pl, bool stats) {
+  ZArgs za;
+  za.nx = pl->n[0];
+  za.ny = pl->n[1];
+  za.nz = pl->n[2];
+  za.bcz = pl->bc[2];
+  za.ti = pl->zti;
+  za.singular = pl->singular;
+  // the forward x pass (always run) and y pass (run when ny > 1) each return twice the transform
+  za.scale = 1.0 / ((double)pl->n[0] * pl->n[1] * 2.0 * (pl->n[1] > 1 ? 2.0 : 1.0));
+  za.lz = pl->volume / (pl->n[0] * pl->dx * pl->n[1] * pl->dy);
+  za.lamx = pl->ax[0].lam;
+  za.lamy = pl->ax[1].lam;
+  za.za = pl->za;
+  za.zb = pl->zb;
+  za.zc = pl->zc;
+  za.dz = pl->dz;
+  za.info = stats ? pl->info : nullptr;
+  za.S = pl->S;
+  za.lowthr = -1.0;
+  za.skip_conv = nullptr;
+  za.skip_k = -1;
+  za.tol2 = 0.0;
+  return za;
+}
+
+int build_z_factors(vofp_plan* pl, cudaStream_t st, bool sync) {
+  ZArgs za = z_args(pl, false);
+  ZTabArgs zt;
+  zt.Ux = pl->Ux;
+  zt.Uy = pl->Uy;
+  zt.bcx = pl->bc[0];
+  zt.bcy = pl->bc[1];
+  zt.tab = pl->ztab;
+  const int n = pl->Ux * pl->Uy;
+  k_zfactor64<<<(n + 127) / 128, 128, 0, st>>>(za, zt, pl->ztab);
+  if (cudaGetLastError() != cudaSuccess) return VOFP_ERR_CUDA;
+  if (sync && cudaStreamSynchronize(st) != cudaSuccess) return VOFP_ERR_CUDA;
+  return VOFP_OK;
 }
 
 // x forward + y forward + z solve + y inverse + x inverse into `pout`.
@@ -70,7 +118,9 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
   const size_t xsm = 2 * (size_t)xa.pb * nx * sizeof(double2);
   switch (mode) {
     case RHS_F: VOFP_LAUNCH(KID_XFWD, st, k_xfwd<double, double2, RHS_F><<<xgrid, 256, xsm, st>>>(xa)); break;
-    case RHS_DIV: VOFP_LAUNCH(KID_XFWD_DIV, st, k_xfwd<double, double2, RHS_DIV><<<xgrid, 256, xsm, st>>>(xa)); break;
+    case RHS_DIV:
+      VOFP_LAUNCH(KID_XFWD_DIV, st, k_xfwd<double, double2, RHS_DIV><<<xgrid, 256, xsm, st>>>(xa));
+      break;
     case RHS_STEFAN:
       VOFP_LAUNCH(KID_XFWD_STEFAN, st, k_xfwd<double, double2, RHS_STEFAN><<<xgrid, 256, xsm, st>>>(xa));
       break;
@@ -79,7 +129,8 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
       break;
     default: return VOFP_ERR_INVALID_ARG;
   }
-  YArgs ya;
+  YArgs ya = {};
+  ya.skip_k = -1;
   ya.nx = nx;
   ya.ny = ny;
   ya.nz = nz;
@@ -92,29 +143,25 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
   const dim3 ygrid((nx + ya.tx - 1) / ya.tx, nz);
   const size_t ysm = 2 * (size_t)(ya.tx / 2) * ny * sizeof(double2);
   if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, k_ypass<double, double2, false><<<ygrid, 256, ysm, st>>>(ya));
-  ZArgs za;
-  za.nx = nx;
-  za.ny = ny;
-  za.nz = nz;
-  za.bcz = pl->bc[2];
-  za.ti = pl->zti;
-  za.singular = pl->singular;
-  za.scale = 1.0 / ((double)nx * ny);
-  za.lz = pl->volume / (nx * pl->dx * ny * pl->dy);
-  za.lamx = pl->ax[0].lam;
-  za.lamy = pl->ax[1].lam;
-  za.za = pl->za;
-  za.zb = pl->zb;
-  za.zc = pl->zc;
-  za.dz = pl->dz;
-  za.info = stats ? pl->info : nullptr;
-  za.S = pl->S;
-  const int nvec = pl->bc[2] == VOFP_BC_P ? 3 : 2;
+  ZArgs za = z_args(pl, stats);
   const dim3 zgrid((nx + za.ti - 1) / za.ti, ny);
-  const size_t zsm = (size_t)nvec * za.ti * nz * sizeof(double);
-  VOFP_LAUNCH(KID_ZSOLVE, st, k_zsolve64<<<zgrid, 128, zsm, st>>>(za));
+  if (pl->ztab) {
+    ZTabArgs zt;
+    zt.Ux = pl->Ux;
+    zt.Uy = pl->Uy;
+    zt.bcx = pl->bc[0];
+    zt.bcy = pl->bc[1];
+    zt.tab = pl->ztab;
+    const size_t zsm = (size_t)za.ti * nz * (sizeof(double) + sizeof(double2));
+    VOFP_LAUNCH(KID_ZSOLVE, st, k_zsolve64_tab<<<zgrid, 128, zsm, st>>>(za, zt));
+  } else {
+    const int nvec = pl->bc[2] == VOFP_BC_P ? 3 : 2;
+    const size_t zsm = (size_t)nvec * za.ti * nz * sizeof(double);
+    VOFP_LAUNCH(KID_ZSOLVE, st, (k_zsolve<double, double><<<zgrid, 128, zsm, st>>>(za)));
+  }
   if (ny > 1) VOFP_LAUNCH(KID_YINV, st, k_ypass<double, double2, true><<<ygrid, 256, ysm, st>>>(ya));
-  XInvArgs xi;
+  XInvArgs xi = {};
+  xi.skip_k = -1;
   xi.nx = nx;
   xi.ny = ny;
   xi.nz = nz;
@@ -156,17 +203,108 @@ int finish_info(vofp_plan* pl, cudaStream_t st, vofp_info* info, int status) {
   return status;
 }
 
+// Interface geometry into the plan's workspace: s (and n unless `with_n` is false).
+static int launch_geometry(vofp_plan* pl, const double* C, const double* mdot, double coef, bool with_n,
+                           double* s_out, cudaStream_t st) {
+  if ((!s_out || with_n) && ensure_geometry(pl)) return VOFP_ERR_OOM;
+  const GridDev g = grid_dev(pl);
+  const size_t cells = (size_t)g.nx * g.ny * g.nz;
+  double* G = pl->G;
+  VOFP_LAUNCH(KID_STEFAN, st,
+              k_geometry<<<grid_blocks(cells, 256), 256, 0, st>>>(
+                  g, C, mdot, coef, pl->opts.grad_mode, s_out ? s_out : G, with_n ? G + cells : nullptr,
+                  with_n ? G + 2 * cells : nullptr, with_n ? G + 3 * cells : nullptr));
+  return cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
+}
+
+// Pressure projection given the right-hand-side mode and inputs in `xa`; runs the correction epilogue.
+static int project_common(vofp_plan* pl, int mode, XArgs& xa, double* u, double* v, double* w, double dt_over_rho0,
+                          double* p, cudaStream_t st, vofp_info* info) {
+  int s = begin_info(pl, st, info);
+  if (s) return s;
+  double* pout = p ? p : pl->P;
+  if (pl->opts.prec == VOFP_MIXED) {
+    s = mixed_solve(pl, mode, &xa, nullptr, pout, st, info);
+    if (s < 0) return s;
+  } else {
+    s = fp64_solve(pl, mode, xa, pout, st, info != nullptr);
+    if (s) return s;
+  }
+  const GridDev g = grid_dev(pl);
+  const size_t total = total_faces(g);
+  VOFP_LAUNCH(KID_GRAD, st,
+              k_grad_update<<<grid_blocks(total, 256), 256, 0, st>>>(g, pout, u, v, w, dt_over_rho0));
+  const int ls = cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
+  if (pl->opts.prec == VOFP_MIXED) {
+    if (ls) return ls;
+    if (info) {
+      if (cudaStreamSynchronize(st) != cudaSuccess) return VOFP_ERR_CUDA;
+      info->status = s;
+    }
+    return s;
+  }
+  return finish_info(pl, st, info, ls);
+}
+
+// Extension solve on the source already in G[0:cells], normals in G[cells:4 cells]; runs the epilogue.
+static int extend_common(vofp_plan* pl, const double* u, const double* v, const double* w, const double* mdot,
+                         double rho1, double* ue, double* ve, double* we, double* ug, double* vg, double* wg,
+                         double* phi, cudaStream_t st, vofp_info* info) {
+  int s = begin_info(pl, st, info);
+  if (s) return s;
+  double* pout = phi ? phi : pl->P;
+  const size_t cells = (size_t)pl->n[0] * pl->n[1] * pl->n[2];
+  XArgs xa = {};
+  xa.f = pl->G;
+  xa.scale = 1.0;
+  if (pl->opts.prec == VOFP_MIXED) {
+    s = mixed_solve(pl, RHS_F, nullptr, pl->G, pout, st, info);
+    if (s < 0) return s;
+  } else {
+    s = fp64_solve(pl, RHS_F, xa, pout, st, info != nullptr);
+    if (s) return s;
+  }
+  ExtArgs ea;
+  ea.g = grid_dev(pl);
+  ea.phi = pout;
+  ea.u = u;
+  ea.v = v;
+  ea.w = w;
+  ea.mdot = mdot;
+  ea.n[0] = pl->G + cells;
+  ea.n[1] = pl->G + 2 * cells;
+  ea.n[2] = pl->G + 3 * cells;
+  ea.quarter_inv_rho1 = 0.25 / rho1;
+  ea.ue = ue;
+  ea.ve = ve;
+  ea.we = we;
+  ea.ug = ug;
+  ea.vg = vg;
+  ea.wg = wg;
+  const size_t total = total_faces(ea.g);
+  VOFP_LAUNCH(KID_EXTEND_EPI, st, k_extend_epi<<<grid_blocks(total, 256), 256, 0, st>>>(ea));
+  const int ls = cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
+  if (pl->opts.prec == VOFP_MIXED) {
+    if (ls) return ls;
+    if (info) {
+      if (cudaStreamSynchronize(st) != cudaSuccess) return VOFP_ERR_CUDA;
+      info->status = s;
+    }
+    return s;
+  }
+  return finish_info(pl, st, info, ls);
+}
+
 }  // namespace vofp
+
+static bool good_density(double r) { return r > 0 && std::isfinite(r); }
 
 extern "C" int vofp_poisson_solve(vofp_plan* pl, const double* f, double* p, void* stream, vofp_info* info) {
   if (!pl || !f || !p) return VOFP_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   int s = begin_info(pl, st, info);
   if (s) return s;
-  if (pl->opts.prec == VOFP_MIXED) {
-    s = mixed_solve(pl, RHS_F, nullptr, f, p, st, info);
-    return s;
-  }
+  if (pl->opts.prec == VOFP_MIXED) return mixed_solve(pl, RHS_F, nullptr, f, p, st, info);
   XArgs xa = {};
   xa.f = f;
   xa.scale = 1.0;
@@ -174,32 +312,12 @@ extern "C" int vofp_poisson_solve(vofp_plan* pl, const double* f, double* p, voi
   return finish_info(pl, st, info, s);
 }
 
-__global__ void k_stefan_source(GridDev g, const double* __restrict__ C, const double* __restrict__ mdot,
-                                double coef, int mode, double* s) {
-  const size_t total = (size_t)g.nx * g.ny * g.nz;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t % g.nx);
-    const size_t r = t / g.nx;
-    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-    const double3 gc = grad_c_at(g, C, i, j, k, mode);
-    s[t] = __ldg(mdot + t) * coef * sqrt(gc.x * gc.x + gc.y * gc.y + gc.z * gc.z);
-  }
-}
-
 extern "C" int vofp_stefan_source(vofp_plan* pl, const double* C, const double* mdot, double rho1, double rho2,
                                   double* s, void* stream) {
-  if (!pl || !C || !mdot || !s || !(rho1 > 0) || !(rho2 > 0) || !std::isfinite(rho1) || !std::isfinite(rho2))
-    return VOFP_ERR_INVALID_ARG;
-  const GridDev g = grid_dev(pl);
+  if (!pl || !C || !mdot || !s || !good_density(rho1) || !good_density(rho2)) return VOFP_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  VOFP_LAUNCH(KID_STEFAN, st,
-              k_stefan_source<<<grid_blocks((size_t)g.nx * g.ny * g.nz, 256), 256, 0, st>>>(
-                  g, C, mdot, 1.0 / rho2 - 1.0 / rho1, pl->opts.grad_mode, s));
-  return cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
+  return launch_geometry(pl, C, mdot, 1.0 / rho2 - 1.0 / rho1, false, s, st);
 }
-
-static int project_common(vofp_plan* pl, int mode, XArgs& xa, double* u, double* v, double* w, double dt_over_rho0,
-                          double* p, cudaStream_t st, vofp_info* info);
 
 extern "C" int vofp_project(vofp_plan* pl, double* u, double* v, double* w, const double* src, double dt_over_rho0,
                             double* p, void* stream, vofp_info* info) {
@@ -218,7 +336,7 @@ extern "C" int vofp_project_stefan(vofp_plan* pl, double* u, double* v, double* 
                                    void* stream, vofp_info* info) {
   if (!pl || !u || !v || !w || !C || !mdot || !(dt_over_rho0 > 0) || !std::isfinite(dt_over_rho0))
     return VOFP_ERR_INVALID_ARG;
-  if (!(rho1 > 0) || !(rho2 > 0) || !std::isfinite(rho1) || !std::isfinite(rho2)) return VOFP_ERR_INVALID_ARG;
+  if (!good_density(rho1) || !good_density(rho2)) return VOFP_ERR_INVALID_ARG;
   XArgs xa = {};
   xa.u = u;
   xa.v = v;
@@ -231,86 +349,49 @@ extern "C" int vofp_project_stefan(vofp_plan* pl, double* u, double* v, double* 
   return project_common(pl, RHS_DIV_STEFAN, xa, u, v, w, dt_over_rho0, p, (cudaStream_t)stream, info);
 }
 
-static int project_common(vofp_plan* pl, int mode, XArgs& xa, double* u, double* v, double* w, double dt_over_rho0,
-                          double* p, cudaStream_t st, vofp_info* info) {
-  int s = begin_info(pl, st, info);
-  if (s) return s;
-  double* pout = p ? p : pl->P;
-  if (pl->opts.prec == VOFP_MIXED) {
-    s = mixed_solve(pl, mode, &xa, nullptr, pout, st, info);
-    if (s < 0) return s;
-  } else {
-    s = fp64_solve(pl, mode, xa, pout, st, info != nullptr);
-    if (s) return s;
-  }
-  const GridDev g = grid_dev(pl);
-  const size_t total = (size_t)nface(g.nx, g.bcx) * g.ny * g.nz + (size_t)g.nx * nface(g.ny, g.bcy) * g.nz +
-                       (size_t)g.nx * g.ny * nface(g.nz, g.bcz);
-  VOFP_LAUNCH(KID_GRAD, st, k_grad_update<<<grid_blocks(total, 256), 256, 0, st>>>(g, pout, u, v, w, dt_over_rho0));
-  const int ls = cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
-  if (pl->opts.prec == VOFP_MIXED) {
-    if (ls) return ls;
-    if (info) {
-      if (cudaStreamSynchronize(st) != cudaSuccess) return VOFP_ERR_CUDA;
-      info->status = s;
-    }
-    return s;
-  }
-  return finish_info(pl, st, info, ls);
-}
-
 extern "C" int vofp_extend_liquid_velocity(vofp_plan* pl, const double* u, const double* v, const double* w,
                                            const double* C, const double* mdot, double rho1, double rho2,
                                            double* ue, double* ve, double* we, double* ug, double* vg, double* wg,
                                            double* phi, void* stream, vofp_info* info) {
   if (!pl || !u || !v || !w || !C || !mdot || !ue || !ve || !we) return VOFP_ERR_INVALID_ARG;
-  if (!(rho1 > 0) || !(rho2 > 0) || !std::isfinite(rho1) || !std::isfinite(rho2)) return VOFP_ERR_INVALID_ARG;
+  if (!good_density(rho1) || !good_density(rho2)) return VOFP_ERR_INVALID_ARG;
   const int nug = (ug != nullptr) + (vg != nullptr) + (wg != nullptr);
   if (nug != 0 && nug != 3) return VOFP_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  int s = begin_info(pl, st, info);
-  if (s) return s;
-  double* pout = phi ? phi : pl->P;
+  const int gs = launch_geometry(pl, C, mdot, 1.0 / rho2 - 1.0 / rho1, ug != nullptr, nullptr, st);
+  if (gs) return gs;
+  return extend_common(pl, u, v, w, mdot, rho1, ue, ve, we, ug, vg, wg, phi, st, info);
+}
+
+extern "C" int vofp_project_extend(vofp_plan* pl, double* u, double* v, double* w, const double* C,
+                                   const double* mdot, double rho1, double rho2, double dt_over_rho0, double* p,
+                                   double* ue, double* ve, double* we, double* ug, double* vg, double* wg,
+                                   double* phi, void* stream, vofp_info* info) {
+  if (!pl || !u || !v || !w || !C || !mdot || !ue || !ve || !we) return VOFP_ERR_INVALID_ARG;
+  if (!(dt_over_rho0 > 0) || !std::isfinite(dt_over_rho0) || !good_density(rho1) || !good_density(rho2))
+    return VOFP_ERR_INVALID_ARG;
+  const int nug = (ug != nullptr) + (vg != nullptr) + (wg != nullptr);
+  if (nug != 0 && nug != 3) return VOFP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int gs = launch_geometry(pl, C, mdot, 1.0 / rho2 - 1.0 / rho1, ug != nullptr, nullptr, st);
+  if (gs) return gs;
   XArgs xa = {};
-  xa.C = C;
-  xa.mdot = mdot;
-  xa.coef = 1.0 / rho2 - 1.0 / rho1;
-  xa.grad_mode = pl->opts.grad_mode;
-  if (pl->opts.prec == VOFP_MIXED) {
-    s = mixed_solve(pl, RHS_STEFAN, &xa, nullptr, pout, st, info);
-    if (s < 0) return s;
-  } else {
-    s = fp64_solve(pl, RHS_STEFAN, xa, pout, st, info != nullptr);
-    if (s) return s;
+  xa.u = u;
+  xa.v = v;
+  xa.w = w;
+  xa.src = pl->G;
+  xa.scale = 1.0 / dt_over_rho0;
+  vofp_info i1;
+  int s1 = project_common(pl, RHS_DIV, xa, u, v, w, dt_over_rho0, p, st, info ? &i1 : nullptr);
+  if (s1 < 0) return s1;
+  int s2 = extend_common(pl, u, v, w, mdot, rho1, ue, ve, we, ug, vg, wg, phi, st, info);
+  if (s2 < 0) return s2;
+  if (info) {
+    // report the projection's defect and the worse of the two statuses
+    info->compat_defect = i1.compat_defect;
+    if (i1.rel_residual > info->rel_residual) info->rel_residual = i1.rel_residual;
+    info->refine_iters += i1.refine_iters;
+    info->status = s1 > s2 ? s1 : s2;
   }
-  ExtArgs ea;
-  ea.g = grid_dev(pl);
-  ea.phi = pout;
-  ea.u = u;
-  ea.v = v;
-  ea.w = w;
-  ea.C = C;
-  ea.mdot = mdot;
-  ea.inv_rho1 = 1.0 / rho1;
-  ea.grad_mode = pl->opts.grad_mode;
-  ea.ue = ue;
-  ea.ve = ve;
-  ea.we = we;
-  ea.ug = ug;
-  ea.vg = vg;
-  ea.wg = wg;
-  const GridDev& g = ea.g;
-  const size_t total = (size_t)nface(g.nx, g.bcx) * g.ny * g.nz + (size_t)g.nx * nface(g.ny, g.bcy) * g.nz +
-                       (size_t)g.nx * g.ny * nface(g.nz, g.bcz);
-  VOFP_LAUNCH(KID_EXTEND_EPI, st, k_extend_epi<<<grid_blocks(total, 256), 256, 0, st>>>(ea));
-  const int ls = cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
-  if (pl->opts.prec == VOFP_MIXED) {
-    if (ls) return ls;
-    if (info) {
-      if (cudaStreamSynchronize(st) != cudaSuccess) return VOFP_ERR_CUDA;
-      info->status = s;
-    }
-    return s;
-  }
-  return finish_info(pl, st, info, ls);
+  return s1 > s2 ? s1 : s2;
 }

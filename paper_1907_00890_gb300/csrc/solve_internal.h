@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "vofp_internal.cuh"
 
 namespace vofp {
@@ -37,6 +39,10 @@ void trace_end(TraceTok* tok, cudaStream_t st);
 
 // Count `n` kernel launches (read by vofp_launch_count).
 void note_launches(int n);
+// Graph capture on this thread: launches are counted apart and not traced; capture_end returns their number.
+bool capturing();
+void capture_begin();
+unsigned long long capture_end();
 
 // Launch a kernel with launch counting and optional tracing: VOFP_LAUNCH(kid, stream, kernel<<<...>>>(...)).
 #define VOFP_LAUNCH(kid, st, ...)         \
@@ -48,18 +54,46 @@ void note_launches(int n);
     ::vofp::note_launches(1);             \
   } while (0)
 
+// ---- plan construction in two phases (see plan.cu) ----
+struct PlanLayout {
+  size_t lam[2], tw[2], q[2], tw32[2], q32[2];
+  size_t za, zb, zc, dz, hz, rdz, rhz, rzc, conv, info, low;
+  size_t table_bytes;  // host-built part, uploaded as one copy
+  size_t P, S, T, S32, F, lowscr;
+  size_t total;
+};
+struct PlanPrep {
+  vofp_plan* p;
+  std::vector<unsigned char> host;
+  PlanLayout L;
+};
+int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz, const int bc[3],
+                 const vofp_opts* opt, PlanPrep* pp);
+int plan_bind(PlanPrep* pp, void* block, cudaStream_t st, unsigned char* stage);
+size_t plan_prep_device_bytes(const PlanPrep* pp);
+size_t plan_prep_stage_bytes(const PlanPrep* pp);
+void plan_free_host(vofp_plan* p);
+// Allocate the interface-geometry workspace (s, n) on first use.
+int ensure_geometry(vofp_plan* p);
+
 struct XArgs;
 struct GridDev;
+struct ZArgs;
 GridDev grid_dev(const vofp_plan* pl);
+ZArgs z_args(const vofp_plan* pl, bool stats);
 int grid_blocks(size_t total, int threads);
 void init_kernel_attributes_fp64();
 void init_kernel_attributes_mixed();
 int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st, bool stats);
 // Mixed-precision solve: FP32 transforms with FP64 defect correction.  `xa` carries the right-hand-side
-// inputs for RHS_DIV / RHS_STEFAN (NULL for RHS_F, which reads `f`).  Fills `info` (if non-NULL) and
+// inputs for RHS_DIV / RHS_DIV_STEFAN (NULL for RHS_F, which reads `f`).  Fills `info` (if non-NULL) and
 // synchronises the stream in that case.
 int mixed_solve(vofp_plan* pl, int mode, const XArgs* xa, const double* f, double* pout, cudaStream_t st,
                 vofp_info* info);
 int begin_info(vofp_plan* pl, cudaStream_t st, vofp_info* info);
+// Thomas factor tables for a bounded z axis (FP64 plans), built on `st`; `sync` waits for them.
+int build_z_factors(vofp_plan* pl, cudaStream_t st, bool sync);
 int finish_info(vofp_plan* pl, cudaStream_t st, vofp_info* info, int status);
 }  // namespace vofp
+
+extern "C" int vofp_plan_tune(vofp_plan* plan);

@@ -7,6 +7,8 @@
 // -2 p_{n-1} / w_{n-1} high end).  |grad C| and n (§3.2 regularised delta, §3.6 Eq. int_vel): central or
 // Youngs corner-averaged differences with C copied into ghost cells at bounded ends and wrapped at periodic
 // ends; n = -grad C / |grad C|, zero where min(C, 1 - C) < 1e-8 or |grad C| = 0.
+// FP64 divisions are replaced by multiplications with reciprocal tables built once per plan (the FP64 pipe
+// of the GB300 is narrow; a division costs about ten multiply-adds).
 #pragma once
 
 #include "vofp_internal.cuh"
@@ -17,8 +19,12 @@ struct GridDev {
   int nx, ny, nz;
   int bcx, bcy, bcz;
   double dx, dy;
-  const double* dz;  // nz
-  const double* hz;  // nz + 1 centre distances across z faces (ghost distances at the ends)
+  double rdx, rdy;    // 1/dx, 1/dy
+  const double* dz;   // nz widths
+  const double* hz;   // nz + 1 centre distances across z faces (ghost distances at the ends)
+  const double* rdz;  // 1/dz
+  const double* rhz;  // 1/hz
+  const double* rzc;  // 1/(hz[k] + hz[k+1]): central difference in z
 };
 
 __host__ __device__ __forceinline__ int nface(int n, int bc) { return n + (bc != VOFP_BC_P); }
@@ -44,7 +50,7 @@ __device__ __forceinline__ double divergence_at(const GridDev& g, const double* 
   const int kp = (g.bcz == VOFP_BC_P && k + 1 == g.nz) ? 0 : k + 1;
   const size_t wb = (size_t)j * g.nx + i;
   const double dw = __ldg(w + wb + kp * plane) - __ldg(w + wb + k * plane);
-  return du / g.dx + dv / g.dy + dw / __ldg(g.dz + k);
+  return fma(du, g.rdx, fma(dv, g.rdy, dw * __ldg(g.rdz + k)));
 }
 
 __device__ __forceinline__ double cval(const GridDev& g, const double* __restrict__ C, int i, int j, int k) {
@@ -59,9 +65,9 @@ __device__ __forceinline__ double3 grad_c_at(const GridDev& g, const double* __r
                                              int mode) {
   double3 r;
   if (mode == 0) {
-    r.x = (cval(g, C, i + 1, j, k) - cval(g, C, i - 1, j, k)) / (2.0 * g.dx);
-    r.y = (cval(g, C, i, j + 1, k) - cval(g, C, i, j - 1, k)) / (2.0 * g.dy);
-    r.z = (cval(g, C, i, j, k + 1) - cval(g, C, i, j, k - 1)) / (__ldg(g.hz + k) + __ldg(g.hz + k + 1));
+    r.x = (cval(g, C, i + 1, j, k) - cval(g, C, i - 1, j, k)) * (0.5 * g.rdx);
+    r.y = (cval(g, C, i, j + 1, k) - cval(g, C, i, j - 1, k)) * (0.5 * g.rdy);
+    r.z = (cval(g, C, i, j, k + 1) - cval(g, C, i, j, k - 1)) * __ldg(g.rzc + k);
     return r;
   }
   const double wt[3] = {0.25, 0.5, 0.25};
@@ -76,9 +82,9 @@ __device__ __forceinline__ double3 grad_c_at(const GridDev& g, const double* __r
         az += wab * (cval(g, C, i + a, j + b, k + s) - cval(g, C, i + a, j + b, k + s - 1));
       }
     }
-    gx += ax / g.dx;
-    gy += ay / g.dy;
-    gz += az / __ldg(g.hz + k + s);
+    gx += ax * g.rdx;
+    gy += ay * g.rdy;
+    gz += az * __ldg(g.rhz + k + s);
   }
   r.x = 0.5 * gx;
   r.y = 0.5 * gy;
@@ -86,18 +92,27 @@ __device__ __forceinline__ double3 grad_c_at(const GridDev& g, const double* __r
   return r;
 }
 
+// |grad C| and the unit normal n = -grad C / |grad C| (zero where clipped) at one cell.
+__device__ __forceinline__ double geometry_at(const GridDev& g, const double* __restrict__ C, int i, int j, int k,
+                                              int mode, double3& n) {
+  const double3 gc = grad_c_at(g, C, i, j, k, mode);
+  const double m2 = fma(gc.x, gc.x, fma(gc.y, gc.y, gc.z * gc.z));
+  n = make_double3(0.0, 0.0, 0.0);
+  if (m2 == 0.0) return 0.0;
+  const double r = rsqrt(m2);
+  const double c = __ldg(C + ((size_t)k * g.ny + j) * g.nx + i);
+  if (fmin(c, 1.0 - c) >= 1e-8) {
+    n.x = -gc.x * r;
+    n.y = -gc.y * r;
+    n.z = -gc.z * r;
+  }
+  return m2 * r;
+}
+
 __device__ __forceinline__ double3 normal_at(const GridDev& g, const double* __restrict__ C, int i, int j, int k,
                                              int mode) {
-  const double c = __ldg(C + ((size_t)k * g.ny + j) * g.nx + i);
-  double3 n = make_double3(0.0, 0.0, 0.0);
-  if (fmin(c, 1.0 - c) < 1e-8) return n;
-  const double3 gc = grad_c_at(g, C, i, j, k, mode);
-  const double m = sqrt(gc.x * gc.x + gc.y * gc.y + gc.z * gc.z);
-  if (m > 0) {
-    n.x = -gc.x / m;
-    n.y = -gc.y / m;
-    n.z = -gc.z / m;
-  }
+  double3 n;
+  geometry_at(g, C, i, j, k, mode, n);
   return n;
 }
 

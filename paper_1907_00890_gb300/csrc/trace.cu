@@ -37,7 +37,7 @@ static cudaEvent_t get_event() {
 
 void trace_begin(int kid, cudaStream_t st, TraceTok* tok) {
   tok->active = 0;
-  if (!g_on.load(std::memory_order_relaxed)) return;
+  if (!g_on.load(std::memory_order_relaxed) || capturing()) return;
   std::lock_guard<std::mutex> lk(g_mu);
   tok->active = 1;
   tok->kid = kid;

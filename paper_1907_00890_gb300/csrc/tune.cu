@@ -1,0 +1,160 @@
+// Launch-shape autotuner.
+//
+// For one plan it times whole Poisson solves (CUDA events on a private stream, after a warm-up) while
+// walking each tile knob in turn -- line pairs per block of the x passes, columns per block of the y
+// passes, systems per block of the z pass -- and keeps the fastest value of each (coordinate descent over
+// the candidates that fit in shared memory).  Results are cached per process and, when the environment
+// variable VOFP_TUNE_CACHE names a file, in that file (one line per grid/precision/GPU key), so a serving
+// process or a batch pays the search once per shape.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "solve_internal.h"
+
+namespace {
+
+struct Shape {
+  int xpb, ytx, zti;
+};
+
+std::mutex g_mu;
+std::map<std::string, Shape> g_cache;
+bool g_file_loaded = false;
+
+std::string key_of(const vofp_plan* p) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, p->device);
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s|%d|%d|%d|%d|%d|%d|%d", prop.name, p->n[0], p->n[1], p->n[2], p->bc[0], p->bc[1],
+           p->bc[2], p->opts.prec);
+  for (char* c = buf; *c; ++c)
+    if (*c == ' ') *c = '_';
+  return buf;
+}
+
+void load_file() {
+  if (g_file_loaded) return;
+  g_file_loaded = true;
+  const char* path = getenv("VOFP_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char k[256];
+  Shape s;
+  while (fscanf(f, "%255s %d %d %d", k, &s.xpb, &s.ytx, &s.zti) == 4) g_cache[k] = s;
+  fclose(f);
+}
+
+void save_entry(const std::string& k, const Shape& s) {
+  const char* path = getenv("VOFP_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d %d %d\n", k.c_str(), s.xpb, s.ytx, s.zti);
+  fclose(f);
+}
+
+bool mixed(const vofp_plan* p) { return p->opts.prec == VOFP_MIXED; }
+
+void apply(vofp_plan* p, const Shape& s) {
+  p->xpb = s.xpb;
+  if (mixed(p)) {
+    p->ytx32 = s.ytx;
+    p->zti32 = s.zti;
+  } else {
+    p->ytx = s.ytx;
+    p->zti = s.zti;
+  }
+}
+
+Shape current(const vofp_plan* p) {
+  return Shape{p->xpb, mixed(p) ? p->ytx32 : p->ytx, mixed(p) ? p->zti32 : p->zti};
+}
+
+bool fits(const vofp_plan* p, const Shape& s) {
+  const size_t c = mixed(p) ? sizeof(float2) : sizeof(double2);
+  const size_t r = mixed(p) ? sizeof(float) : sizeof(double);
+  const int nvec = p->bc[2] == VOFP_BC_P ? 3 : 2;
+  const size_t lim = 160 * 1024;
+  if (2 * (size_t)s.xpb * p->n[0] * c > lim) return false;
+  if (2 * (size_t)(s.ytx / 2) * p->n[1] * c > lim) return false;
+  size_t zs = (size_t)nvec * s.zti * p->n[2] * r;
+  if (!mixed(p) && p->ztab) zs = (size_t)s.zti * p->n[2] * (sizeof(double) + sizeof(double2));
+  if (zs > lim) return false;
+  if (s.zti > 128) return false;  // the z pass runs 128 threads per block, one system each
+  return true;
+}
+
+// Average milliseconds of a Poisson solve of the plan's scratch potential (in place).
+float time_solve(vofp_plan* p, cudaStream_t st) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int reps = 4;
+  vofp_poisson_solve(p, p->P, p->P, st, nullptr);
+  cudaEventRecord(a, st);
+  for (int r = 0; r < reps; ++r) vofp_poisson_solve(p, p->P, p->P, st, nullptr);
+  cudaEventRecord(b, st);
+  cudaEventSynchronize(b);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / reps;
+}
+
+}  // namespace
+
+extern "C" int vofp_plan_tune(vofp_plan* p) {
+  if (!p) return VOFP_ERR_INVALID_ARG;
+  const std::string k = key_of(p);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_file();
+    auto it = g_cache.find(k);
+    if (it != g_cache.end()) {
+      if (fits(p, it->second)) apply(p, it->second);
+      return VOFP_OK;
+    }
+  }
+  cudaStream_t st;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return VOFP_ERR_CUDA;
+  // a bounded, deterministic right-hand side: zeros (the kernels' cost does not depend on the values)
+  cudaMemsetAsync(p->P, 0, sizeof(double) * (size_t)p->n[0] * p->n[1] * p->n[2], st);
+  Shape best = current(p);
+  float tbest = time_solve(p, st);
+  const int xs[] = {1, 2, 4, 8, 16, 32};
+  const int ys[] = {2, 4, 8, 16, 32};
+  const int zs[] = {4, 8, 16, 32, 64, 128};
+  for (int knob = 0; knob < 3; ++knob) {
+    const int* cand = knob == 0 ? xs : (knob == 1 ? ys : zs);
+    const int nc = knob == 0 ? 6 : (knob == 1 ? 5 : 6);
+    for (int c = 0; c < nc; ++c) {
+      Shape s = best;
+      if (knob == 0) s.xpb = cand[c];
+      if (knob == 1) s.ytx = cand[c];
+      if (knob == 2) s.zti = cand[c];
+      if (!fits(p, s)) continue;
+      apply(p, s);
+      const float t = time_solve(p, st);
+      if (t < tbest) {
+        tbest = t;
+        best = s;
+      }
+    }
+    apply(p, best);
+  }
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  if (cudaGetLastError() != cudaSuccess) return VOFP_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_cache[k] = best;
+  save_entry(k, best);
+  return VOFP_OK;
+}

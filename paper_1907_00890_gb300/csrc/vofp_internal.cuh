@@ -18,6 +18,7 @@
 #include "vofp.h"
 
 #define VOFP_MAX_STAGES 24
+#define VOFP_CONV_SLOTS 32
 
 namespace vofp {
 
@@ -57,6 +58,29 @@ __device__ __forceinline__ C cmul(C a, C b) {
 template <typename C>
 __device__ __forceinline__ C cmi(C a) {
   return cmk<C>(a.y, -a.x);
+}
+
+// ---- mixed-precision refinement: device-side convergence test ---------------------------------------
+// Slots: conv[0] = ||f||^2, conv[1] = sum f V, conv[2] = sum |f| V,
+//        conv[VOFP_CONV_RES + j] = ||r_j||^2, r_j = f - fbar - L p_j the residual after j corrections,
+//        conv[VOFP_CONV_DEL + j] = ||delta_j||^2 (delta_0 = the initial FP32 solve, delta_j the j-th
+//        correction), conv[VOFP_CONV_MEAN] = sum of delta dz over all of them (the gauge of p),
+//        conv[VOFP_CONV_FINAL] = ||r||^2 of the returned p (reporting pass).
+// Correction j + 1 is skipped once correction j (j >= 1) left BOTH a small residual before it and a small
+// step:  ||r_{j-1}||^2 <= tol^2 ||f||^2  and  ||delta_j||^2 <= (tol/10)^2 ||delta_0||^2.  (A residual test
+// alone is blind to errors in the smoothest modes, whose residual is smaller by their eigenvalue.)
+#define VOFP_CONV_RES 3
+#define VOFP_CONV_DEL 16
+#define VOFP_CONV_MEAN 30
+#define VOFP_CONV_FINAL 31
+#define VOFP_MAX_REFINE 12
+// j = -1 or 0: never skipped; j <= -2: always skipped (a correction beyond an instance's own limit in a
+// batch); j >= 1: skipped when correction j converged.  Every block reads the same values.
+__device__ __forceinline__ bool launch_skipped(const double* conv, int j, double tol2) {
+  if (j <= -2) return true;
+  if (!conv || j <= 0) return false;
+  return conv[VOFP_CONV_RES + j - 1] <= tol2 * conv[0] &&
+         conv[VOFP_CONV_DEL + j] <= 0.01 * tol2 * conv[VOFP_CONV_DEL];
 }
 
 // ---- FFT descriptor ----------------------------------------------------------------------------------
@@ -245,24 +269,30 @@ __device__ __forceinline__ void split_two(const C* Z, int n, int m, C& A, C& B) 
   B = cmk<C>((R)0.5 * (P.y + Q.y), (R)-0.5 * (P.x - Q.x));
 }
 
-// Forward post-processing: spectral output q of both lines from the FFT result Z.
+// Forward post-processing: spectral output q of both lines from the FFT result Z, returned TWICE the
+// transform (2A, 2B of split_two without the halving; the z pass folds the factor into its scale).
 template <typename C>
 __device__ __forceinline__ void fwd_post(const C* Z, int n, int bc, int q, const C* __restrict__ quart,
                                          decltype(C::x)& oa, decltype(C::x)& ob) {
   if (bc == VOFP_BC_P) {
     const int m = (q + 1) >> 1;
-    C A, B;
-    split_two(Z, n, m, A, B);
-    const bool re = (q == 0) || (q & 1);
-    oa = re ? A.x : A.y;
-    ob = re ? B.x : B.y;
+    const C P = Z[m];
+    const C Q = Z[m == 0 ? 0 : n - m];
+    if ((q == 0) || (q & 1)) {  // real parts
+      oa = P.x + Q.x;
+      ob = P.y + Q.y;
+    } else {  // imaginary parts
+      oa = P.y - Q.y;
+      ob = Q.x - P.x;
+    }
   } else {
     const int m = (bc == VOFP_BC_DD) ? (n - 1 - q) : q;
-    C A, B;
-    split_two(Z, n, m, A, B);
+    const C P = Z[m];
+    const C Q = Z[m == 0 ? 0 : n - m];
     const C w = quart[m];
-    oa = w.x * A.x - w.y * A.y;
-    ob = w.x * B.x - w.y * B.y;
+    // Re(w * 2A) and Re(w * 2B)
+    oa = w.x * (P.x + Q.x) - w.y * (P.y - Q.y);
+    ob = w.x * (P.y + Q.y) - w.y * (Q.x - P.x);
   }
 }
 
@@ -346,6 +376,20 @@ struct vofp_plan {
   double* zc;  // coefficient of p_{k+1}
   double* dz;  // widths
   double* hz;  // centre distance across face k (k = 0..nz; ghost distances at the ends)
+  double* rdz;   // 1/dz
+  double* rhz;   // 1/hz
+  double* rzc;   // 1/(hz[k] + hz[k+1])
+  double* conv;  // mixed path: FP64 reduction slots (norms, means) per solve
+  double* G;     // interface geometry: s, n_x, n_y, n_z (4 * cells)
+  double2* ztab; // bounded z: Thomas factors per distinct eigenvalue pair (NULL: periodic z)
+  int Ux, Uy;    // distinct eigenvalue counts in x, y
+  // mixed path
+  double lowthr;       // |lx + ly| at or below which a z system is solved in FP64
+  int nlow;            // number of such systems
+  int2* lowmodes;      // their (x, y) spectral indices
+  double* lowscratch;  // FP64 columns for them (3 nz each)
+  void* low_block;     // allocation holding lowmodes and lowscratch
+  int ytx32, zti32;    // launch shapes of the FP32 y and z passes
   // workspace
   double* S;   // spectrum, nx*ny*nz (FP64 path)
   double* P;   // potential scratch when the caller passes none

@@ -72,6 +72,146 @@ EXPORTED = ["vofp_opts_default", "vofp_plan_create", "vofp_plan_destroy", "vofp_
             "vofp_trace_collect", "vofp_trace_kernel_classes", "vofp_trace_name"]
 
 
+_lib.vofp_project_extend.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                     ctypes.POINTER(vofp_info)]
+_lib.vofp_project_extend.restype = _I
+EXPORTED.append("vofp_project_extend")
+
+
+def vofp_project_extend(plan, u, v, w, C, mdot, rho1, rho2, dt_over_rho0, p, ue, ve, we, ug=None, vg=None,
+                        wg=None, phi=None, stream=None, info=False):
+    inf = vofp_info() if info else None
+    s = _check(_lib.vofp_project_extend(
+        plan, _ptr(u, name="u"), _ptr(v, name="v"), _ptr(w, name="w"), _ptr(C, name="C"), _ptr(mdot, name="mdot"),
+        float(rho1), float(rho2), float(dt_over_rho0), _ptr(p, name="p"), _ptr(ue, name="ue"), _ptr(ve, name="ve"),
+        _ptr(we, name="we"), _ptr(ug, name="ug"), _ptr(vg, name="vg"), _ptr(wg, name="wg"), _ptr(phi, name="phi"),
+        _stream(stream), ctypes.byref(inf) if info else None), "vofp_project_extend")
+    return (s, _info_dict(inf)) if info else s
+
+
+class vofp_request(ctypes.Structure):
+    _fields_ = [("n", _I * 3), ("dx", _D), ("dy", _D), ("dz", ctypes.POINTER(_D)), ("bc", _I * 3),
+                ("u", _P), ("v", _P), ("w", _P), ("src", _P), ("dt_over_rho0", _D), ("p", _P)]
+
+
+_ULL = ctypes.c_ulonglong
+_lib.vofp_server_create.argtypes = [ctypes.c_size_t, _I, ctypes.POINTER(vofp_opts), ctypes.POINTER(_P)]
+_lib.vofp_server_create.restype = _I
+_lib.vofp_server_submit.argtypes = [_P, ctypes.POINTER(vofp_request), ctypes.POINTER(_ULL)]
+_lib.vofp_server_submit.restype = _I
+_lib.vofp_server_poll.argtypes = [_P, _ULL, ctypes.POINTER(vofp_info), ctypes.POINTER(_D)]
+_lib.vofp_server_poll.restype = _I
+_lib.vofp_server_wait.argtypes = [_P, _ULL, _D, ctypes.POINTER(vofp_info), ctypes.POINTER(_D)]
+_lib.vofp_server_wait.restype = _I
+_lib.vofp_server_stats.argtypes = [_P, ctypes.POINTER(_D), _I, _I]
+_lib.vofp_server_stats.restype = _I
+_lib.vofp_server_destroy.argtypes = [_P]
+_lib.vofp_server_destroy.restype = None
+EXPORTED += ["vofp_server_create", "vofp_server_submit", "vofp_server_poll", "vofp_server_wait",
+             "vofp_server_stats", "vofp_server_destroy"]
+
+
+def vofp_server_create(mem_budget_bytes=0, max_inflight=16, opts=None):
+    h = _P()
+    _check(_lib.vofp_server_create(int(mem_budget_bytes), int(max_inflight),
+                                   ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)),
+           "vofp_server_create")
+    return h.value
+
+
+def vofp_server_submit(server, n, dx, dy, dz, bc, u, v, w, src=None, dt_over_rho0=1.0, p=None):
+    """Submit a projection request; returns its ticket.  The fields must stay valid until it completes."""
+    dzh = np.ascontiguousarray(np.broadcast_to(np.asarray(dz, dtype=np.float64), (int(n[2]),)))
+    r = vofp_request()
+    r.n[:] = [int(x) for x in n]
+    r.dx, r.dy = float(dx), float(dy)
+    r.dz = dzh.ctypes.data_as(ctypes.POINTER(_D))
+    r.bc[:] = [BC[b] if isinstance(b, str) else int(b) for b in bc]
+    r.u, r.v, r.w = _ptr(u, name="u"), _ptr(v, name="v"), _ptr(w, name="w")
+    r.src = _ptr(src, name="src")
+    r.dt_over_rho0 = float(dt_over_rho0)
+    r.p = _ptr(p, name="p")
+    t = _ULL()
+    _check(_lib.vofp_server_submit(server, ctypes.byref(r), ctypes.byref(t)), "vofp_server_submit")
+    return t.value
+
+
+def vofp_server_poll(server, ticket):
+    """(status, latency_s): status 1 = pending, 0 = done; an error raises."""
+    lat = _D()
+    s = _lib.vofp_server_poll(server, _ULL(ticket), None, ctypes.byref(lat))
+    _check(s, "vofp_server_poll")
+    return s, lat.value
+
+
+def vofp_server_wait(server, ticket, timeout_s=60.0):
+    lat = _D()
+    _check(_lib.vofp_server_wait(server, _ULL(ticket), float(timeout_s), None, ctypes.byref(lat)),
+           "vofp_server_wait")
+    return lat.value
+
+
+def vofp_server_stats(server, reset=False):
+    out = (_D * 10)()
+    _check(_lib.vofp_server_stats(server, out, 10, 1 if reset else 0), "vofp_server_stats")
+    keys = ["completed", "admitted", "rejected", "pending", "arena_in_use", "arena_bytes", "p50_s", "p99_s",
+            "cells", "seconds"]
+    return dict(zip(keys, list(out)))
+
+
+def vofp_server_destroy(server):
+    _lib.vofp_server_destroy(server)
+
+
+_lib.vofp_plan_tune.argtypes = [_P]
+_lib.vofp_plan_tune.restype = _I
+EXPORTED.append("vofp_plan_tune")
+
+
+def vofp_plan_tune(plan):
+    return _check(_lib.vofp_plan_tune(plan), "vofp_plan_tune")
+
+
+_lib.vofp_batch_create.argtypes = [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]
+_lib.vofp_batch_create.restype = _I
+_lib.vofp_batch_project.argtypes = [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                    ctypes.POINTER(_P), ctypes.POINTER(_D), ctypes.POINTER(_P), _P]
+_lib.vofp_batch_project.restype = _I
+_lib.vofp_batch_size.argtypes = [_P]
+_lib.vofp_batch_size.restype = _I
+_lib.vofp_batch_destroy.argtypes = [_P]
+_lib.vofp_batch_destroy.restype = None
+EXPORTED += ["vofp_batch_create", "vofp_batch_project", "vofp_batch_size", "vofp_batch_destroy"]
+
+
+def vofp_batch_create(plans):
+    arr = (_P * len(plans))(*plans)
+    h = _P()
+    _check(_lib.vofp_batch_create(arr, len(plans), ctypes.byref(h)), "vofp_batch_create")
+    return h.value
+
+
+def _ptr_array(ts, name):
+    return (_P * len(ts))(*[_ptr(t, name=name) for t in ts])
+
+
+def vofp_batch_project(batch, u, v, w, src, dt_over_rho0, p, stream=None):
+    n = len(u)
+    s = _ptr_array(src, "src") if src is not None else None
+    pp = _ptr_array(p, "p") if p is not None else None
+    dts = (_D * n)(*[float(x) for x in dt_over_rho0])
+    return _check(_lib.vofp_batch_project(batch, _ptr_array(u, "u"), _ptr_array(v, "v"), _ptr_array(w, "w"), s,
+                                          dts, pp, _stream(stream)), "vofp_batch_project")
+
+
+def vofp_batch_size(batch):
+    return int(_lib.vofp_batch_size(batch))
+
+
+def vofp_batch_destroy(batch):
+    _lib.vofp_batch_destroy(batch)
+
+
 _lib.vofp_poisson_solve_noalloc.argtypes = [_I, _I, _I, _D, _D, ctypes.POINTER(_D), ctypes.POINTER(_I), _P, _P,
                                             _P]
 _lib.vofp_poisson_solve_noalloc.restype = _I

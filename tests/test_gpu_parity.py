@@ -203,3 +203,34 @@ def test_invalid_arguments_rejected_before_launch(vp):
     assert vp._lib.vofp_poisson_solve(plan.handle, None, None, None, None) == -1
     assert vp._lib.vofp_project(plan.handle, None, None, None, None, 1.0, None, None, None) == -1
     plan.close()
+
+
+@pytest.mark.parametrize("n,bc,mode", [((128, 128, 128), ("P", "P", "NN"), 0), ((36, 30, 28), ("NN", "DD", "DN"), 1),
+                                       ((33, 20, 24), ("P", "P", "P"), 0)])
+def test_project_extend_step(vp, n, bc, mode):
+    """vofp_project_extend (both solves of one step, shared geometry) against the oracle's two solves."""
+    import torch
+    dz = synth.stretched_dz(n[2]) if bc[2] != "P" else synth.uniform_dz(n[2])
+    g = oracle.Grid(*n, 1.0 / n[0], 1.0 / n[1], dz, bc)
+    C, centre = synth.droplet(n, bc, 12, dz=dz)
+    mdot = 1.0 + 0.2 * synth.rng(13).standard_normal(g.shape)
+    u0 = synth.swirl_velocity(n, bc, centre, 14)
+    s = oracle.stefan_source(g, C, mdot, 100.0, 1.0, mode)
+    dt = 0.01
+    ou = oracle.project(g, *u0, src=s, dt_over_rho0=dt)
+    oe = oracle.extend_liquid_velocity(g, *ou[:3], C, mdot, 100.0, 1.0, mode=mode)
+    plan = vp.Plan(n, g.widths[0][0], g.widths[1][0], dz, bc, grad_mode=mode)
+    u = [dev(a) for a in u0]
+    p = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+    ue = [torch.empty_like(a) for a in u]
+    ug = [torch.empty_like(a) for a in u]
+    phi = torch.empty_like(p)
+    st, info = vp.vofp_project_extend(plan.handle, *u, dev(C), dev(mdot), 100.0, 1.0, dt, p, *ue, *ug, phi, info=True)
+    assert rel(host(p), ou[3]) < TOL
+    for a in range(3):
+        assert rel(host(u[a]), ou[a]) < TOL
+        assert rel(host(ue[a]), oe[a]) < TOL
+        assert rel(host(ug[a]), oe[3 + a]) < TOL
+    assert rel(host(phi), oe[6]) < TOL
+    assert abs(info["compat_defect"] - ou[4]["compat_defect"]) < 1e-10 * max(1.0, abs(ou[4]["compat_defect"]))
+    plan.close()
