@@ -41,7 +41,197 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="arithmetic of the main step (the 128^3 droplet step is specified in FP64)")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
     return ap.parse_args()
+
+
+def bench_mixed_step(vofp, c, u0, C, md, st, flush, args):
+    """The same droplet step through a mixed-precision plan (FP32 transforms + FP64 refinement)."""
+    import torch
+    plan = vofp.Plan(c["n"], c["dx"], c["dy"], c["dz"], c["bc"], prec=vofp.MIXED)
+    u = [x.clone() for x in u0]
+    p = torch.empty(plan.cell_shape, dtype=torch.float64, device=u0[0].device)
+    phi = torch.empty_like(p)
+    ue = [torch.empty_like(x) for x in u]
+    ug = [torch.empty_like(x) for x in u]
+
+    def step():
+        vofp.vofp_project_extend(plan.handle, u[0], u[1], u[2], C, md, c["rho1"], c["rho2"], c["dt_over_rho0"], p,
+                                 ue[0], ue[1], ue[2], ug[0], ug[1], ug[2], phi)
+
+    def prep():
+        for a, b in zip(u, u0):
+            a.copy_(b)
+        flush.zero_()
+
+    for _ in range(args.warmup):
+        prep()
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    vofp.vofp_trace_collect()
+    vofp.vofp_trace_enable(True)
+    for i in range(args.steps):
+        prep()
+        ev[i][0].record(st)
+        step()
+        ev[i][1].record(st)
+    torch.cuda.synchronize()
+    vofp.vofp_trace_enable(False)
+    trace = vofp.vofp_trace_collect()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    # one more step with info for the refinement statistics
+    prep()
+    _, info = vofp.vofp_project_extend(plan.handle, u[0], u[1], u[2], C, md, c["rho1"], c["rho2"],
+                                       c["dt_over_rho0"], p, ue[0], ue[1], ue[2], ug[0], ug[1], ug[2], phi,
+                                       info=True)
+    cells = int(np.prod(c["n"]))
+    out = {"value": cells * 2 / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms, "dtype": "f32+f64",
+           "refine_iters_both_solves": info["refine_iters"], "rel_residual": info["rel_residual"],
+           "per_kernel_ms": {k: round(v[0] / v[1], 5) for k, v in trace.items()},
+           "roofline": roofline_mixed(trace, c["n"])}
+    # outputs compared with the oracle's step (ue, ug, phi in the oracle's order) by the caller
+    out["_outputs"] = [x.cpu().numpy() for x in ue] + [x.cpu().numpy() for x in ug] + [phi.cpu().numpy()]
+    plan.close()
+    return out
+
+
+def roofline_mixed(trace, n):
+    """HBM roofline of the dominant kernel of the mixed step (FP32 spectrum, FP64 fields)."""
+    if not trace:
+        return None
+    name = max(trace, key=lambda k: trace[k][0])
+    tot, cnt = trace[name]
+    nx, ny, nz = n
+    cells = nx * ny * nz
+    per = {"x_forward_div": 24 + 8 + 4, "x_forward": 8 + 8 + 4, "residual_update": 8 + 8 + 4, "y_forward": 8,
+           "y_inverse": 8, "z_tridiag": 8, "x_inverse": 4 + 16, "grad_update": 56, "extend_epilogue": 96,
+           "stefan_source": 48}
+    by = per.get(name, 0) * cells
+    hbm, how = peaks()
+    gbs = by / (tot / cnt / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": name, "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+            "launches": cnt, "avg_launch_ms": tot / cnt, "peak_source": how}
+
+
+def bench_batched(vofp, args):
+    """64 independent instances, per-axis sizes from {32,48,64,96,128,160}, one graph replay per step."""
+    import torch
+    from paper_1907_00890_gb300 import synth
+    sizes = synth.batch_sizes(64)
+    bc = ("P", "P", "NN")
+    plans, us = [], []
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.BASE_SEED + 4)
+    for n in sizes:
+        plans.append(vofp.Plan(n, 1.0 / n[0], 1.0 / n[1], synth.uniform_dz(n[2]), bc, prec=vofp.MIXED))
+        us.append([torch.randn(s, generator=gen, dtype=torch.float64, device="cuda")
+                   for s in synth.face_shapes(n, bc)])
+        for a in us[-1][2:]:
+            a[0].zero_()
+            a[-1].zero_()
+    u0 = [[x.clone() for x in u] for u in us]
+    b = vofp.vofp_batch_create([p.handle for p in plans])
+    dts = [1.0] * len(plans)
+    cells = sum(int(np.prod(n)) for n in sizes)
+
+    def prep():
+        for u, v in zip(us, u0):
+            for a, bb in zip(u, v):
+                a.copy_(bb)
+
+    for _ in range(max(2, args.warmup)):
+        prep()
+        vofp.vofp_batch_project(b, [u[0] for u in us], [u[1] for u in us], [u[2] for u in us], None, dts, None)
+    torch.cuda.synchronize()
+    reps = max(3, min(args.steps, 10))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    st = torch.cuda.current_stream()
+    for i in range(reps):
+        prep()
+        ev[i][0].record(st)
+        vofp.vofp_batch_project(b, [u[0] for u in us], [u[1] for u in us], [u[2] for u in us], None, dts, None)
+        ev[i][1].record(st)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(bb) for a, bb in ev]))
+    vofp.vofp_batch_destroy(b)
+    for p in plans:
+        p.close()
+    return {"value": cells / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_batch": ms, "instances": len(sizes),
+            "cells": cells, "solves_per_s": len(sizes) / (ms / 1e3), "dtype": "f32+f64",
+            "workload": "64 projection instances, sizes per axis from {32,48,64,96,128,160}, P,P,NN, mixed, "
+                        "one CUDA-graph replay per batch"}
+
+
+def bench_served(vofp, args):
+    """Poisson arrivals of projection requests with log-uniform sizes 48..256 per axis, served with
+    continuous batching: mixed precision, then the same stream through the plain FP64 path."""
+    import torch
+    from paper_1907_00890_gb300 import synth
+    rate = args.serve_rate
+    warm = 1.0
+    dur = args.serve_seconds
+    rng = synth.rng(synth.BASE_SEED + 5)
+    nreq = int((warm + dur) * rate * 1.2) + 16
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+    arrivals = arrivals[arrivals < warm + dur]
+    sizes = synth.serve_sizes(len(arrivals))
+    bc = ("P", "P", "NN")
+    # pool of field buffers at the largest shape; each request views a contiguous prefix of one slot
+    pool = 48
+    maxc = 257 * 256 * 256
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.BASE_SEED + 6)
+    bufs = [[torch.randn(maxc, generator=gen, dtype=torch.float64, device="cuda") for _ in range(3)]
+            for _ in range(pool)]
+    out = {}
+    for name, prec in (("mixed", vofp.MIXED), ("fp64", vofp.FP64)):
+        o = vofp.vofp_opts_default()
+        o.prec = prec
+        s = vofp.vofp_server_create(0, 32, o)
+        free = list(range(pool))
+        busy = {}
+        t0 = time.perf_counter()
+        reset_done = False
+        i = 0
+        late = 0
+        while i < len(arrivals) or busy:
+            now = time.perf_counter() - t0
+            if not reset_done and now >= warm:
+                vofp.vofp_server_stats(s, reset=True)
+                reset_done = True
+            # retire completed requests
+            for t in list(busy):
+                st_, _ = vofp.vofp_server_poll(s, t)
+                if st_ == 0:
+                    free.append(busy.pop(t))
+            while i < len(arrivals) and arrivals[i] <= now and free:
+                n = sizes[i]
+                k = free.pop()
+                fs = synth.face_shapes(n, bc)
+                views = [bufs[k][a][:int(np.prod(fs[a]))].view(fs[a]) for a in range(3)]
+                t = vofp.vofp_server_submit(s, n, 1.0 / n[0], 1.0 / n[1], synth.uniform_dz(n[2]), bc, *views)
+                busy[t] = k
+                if now - arrivals[i] > 0.01:
+                    late += 1
+                i += 1
+            if now > warm + dur + 60.0:
+                break
+            time.sleep(0.0001)
+        st = vofp.vofp_server_stats(s)
+        vofp.vofp_server_destroy(s)
+        out[name] = {"p50_ms": st["p50_s"] * 1e3, "p99_ms": st["p99_s"] * 1e3,
+                     "solves_per_s": st["completed"] / st["seconds"],
+                     "value": st["cells"] / st["seconds"] / 1e6, "unit": UNIT, "completed": int(st["completed"]),
+                     "rejected": int(st["rejected"]), "late_submissions": late,
+                     "dtype": "f32+f64" if prec == vofp.MIXED else "f64"}
+    out["workload"] = ("Poisson arrivals at %.0f req/s for %.0f s after %.0f s warm-up, per-axis sizes "
+                       "log-uniform in [48, 256], P,P,NN, N(0,1) fields, 32 in flight" % (rate, dur, warm))
+    return out
 
 
 class ClockSampler:
@@ -193,7 +383,8 @@ def run_ours(args):
     c = synth.config_droplet(args.n, seed_offset=rank)
     n = c["n"]
     cells = int(np.prod(n))
-    plan = vofp.Plan(n, c["dx"], c["dy"], c["dz"], c["bc"])
+    mixed = args.precision == "mixed"
+    plan = vofp.Plan(n, c["dx"], c["dy"], c["dz"], c["bc"], prec=vofp.MIXED if mixed else vofp.FP64)
     st = torch.cuda.current_stream()
 
     def T(a):
@@ -279,14 +470,25 @@ def run_ours(args):
     e2e_value = world * cells * 2 / (float(e2e_t.item()) / 1e3) / 1e6
 
     # ---- roofline of the dominant kernel (its launches timed with events on the launching stream) ----
-    roof = roofline_from_trace(trace, n)
+    roof = roofline_mixed(trace, n) if mixed else roofline_from_trace(trace, n)
+
+    # ---- the other forms of the same path: mixed precision, batched ensemble, served stream ----
+    variants = {}
+    if not args.no_variants:
+        variants["mixed_step"] = bench_mixed_step(vofp, c, u0, C, md, st, flush, args)
+        torch.cuda.empty_cache()
+        variants["batched"] = bench_batched(vofp, args)
+        torch.cuda.empty_cache()
+        variants["served"] = bench_served(vofp, args)
+        torch.cuda.empty_cache()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
                 "config": {"workload": "droplet step %d^3 (project with Stefan source + liquid-velocity extension), "
-                                       "P,P,NN, FP64" % args.n, "grid": list(n), "solves_per_step": 2,
+                                       "P,P,NN, %s" % (args.n, "mixed precision" if mixed else "FP64"),
+                           "grid": list(n), "solves_per_step": 2,
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed between steps (256 MiB write, outside the events)"},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -298,6 +500,17 @@ def run_ours(args):
             line["cpu_baseline"] = {"value": cells * 2 / sec / 1e6, "unit": UNIT, "cores": cpu_threads(),
                                     "kind": "oracle",
                                     "sample": "%d oracle steps (median) of the same %d^3 droplet workload" % (nsteps, args.n)}
+            if "mixed_step" in variants:
+                # accuracy of the mixed-precision step against the oracle (one step, same inputs)
+                import oracle
+                g = oracle.Grid(*c["n"], c["dx"], c["dy"], c["dz"], c["bc"])
+                ref = oracle_step(c, g)
+                got = variants["mixed_step"].pop("_outputs")
+                errs = [float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)) for a, b in zip(got, ref[:7])]
+                variants["mixed_step"]["max_rel_err_vs_oracle"] = max(errs)
+        if variants:
+            variants.get("mixed_step", {}).pop("_outputs", None)
+            line["variants"] = variants
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:

@@ -1,0 +1,105 @@
+"""GPU tests of the serving loop (continuous batching with memory-based admission).
+
+* requests of uneven sizes submitted back to back with more requests than slots and an arena that holds
+  only a few plans at once: every request completes, matches the oracle (mixed: rel-L2 <= 1e-10) and
+  matches the same request served alone (to 1e-12: the same kernels run, only FP64 reduction order may
+  differ);
+* a request whose plan alone exceeds the arena completes with VOFP_ERR_BUSY;
+* the latency statistics are filled.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_00890_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def vp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_00890_gb300 import build
+    build.build()
+    from paper_1907_00890_gb300 import vofp
+    return vofp
+
+
+def dev(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def rel(a, b):
+    nb = np.linalg.norm(np.ravel(b))
+    return float(np.linalg.norm(np.ravel(a - b)) / nb) if nb > 0 else float(np.linalg.norm(np.ravel(a)))
+
+
+def requests(count):
+    sizes = synth.serve_sizes(count, lo=16, hi=72)
+    out = []
+    for i, n in enumerate(sizes):
+        bc = ("P", "P", "NN") if i % 3 else ("NN", "DD", "DN")
+        dz = synth.stretched_dz(n[2]) if bc[2] != "P" else synth.uniform_dz(n[2])
+        out.append(dict(n=n, bc=bc, dz=dz, dx=1.0 / n[0], dy=1.0 / n[1], u0=synth.random_velocity(n, bc, 700 + i),
+                        dt=0.5 + 0.1 * i))
+    return out
+
+
+def serve(vp, reqs, budget, inflight):
+    import torch
+    o = vp.vofp_opts_default()
+    o.prec = vp.MIXED
+    s = vp.vofp_server_create(budget, inflight, o)
+    fields, tickets = [], []
+    for r in reqs:
+        u = [dev(a) for a in r["u0"]]
+        p = torch.empty((r["n"][2], r["n"][1], r["n"][0]), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        tickets.append(vp.vofp_server_submit(s, r["n"], r["dx"], r["dy"], r["dz"], r["bc"], *u,
+                                             dt_over_rho0=r["dt"], p=p))
+        fields.append((u, p))
+    lats = [vp.vofp_server_wait(s, t, 120.0) for t in tickets]
+    stats = vp.vofp_server_stats(s)
+    vp.vofp_server_destroy(s)
+    return fields, lats, stats
+
+
+def test_served_results_match_oracle_and_alone(vp):
+    reqs = requests(12)
+    # arena for about three mid-size plans: admission must wait for completions
+    budget = 3 * 48 ** 3 * 8 * 4
+    fields, lats, stats = serve(vp, reqs, budget, 4)
+    assert stats["completed"] == len(reqs) and stats["rejected"] == 0
+    assert stats["p99_s"] >= stats["p50_s"] > 0
+    assert all(l > 0 for l in lats)
+    for r, (u, p) in zip(reqs, fields):
+        g = oracle.Grid(*r["n"], r["dx"], r["dy"], r["dz"], r["bc"])
+        ou = oracle.project(g, *r["u0"], dt_over_rho0=r["dt"])
+        assert rel(p.cpu().numpy(), ou[3]) < TOL
+        for a in range(3):
+            assert rel(u[a].cpu().numpy(), ou[a]) < TOL
+    # the same requests served one at a time
+    for idx in (0, 5, 11):
+        alone, _, _ = serve(vp, [reqs[idx]], budget, 1)
+        assert rel(alone[0][1].cpu().numpy(), fields[idx][1].cpu().numpy()) < 1e-12
+        for a in range(3):
+            assert rel(alone[0][0][a].cpu().numpy(), fields[idx][0][a].cpu().numpy()) < 1e-12
+
+
+def test_oversize_request_is_rejected_busy(vp):
+    import torch
+    o = vp.vofp_opts_default()
+    o.prec = vp.MIXED
+    s = vp.vofp_server_create(1 << 20, 2, o)   # 1 MiB arena
+    n = (64, 64, 64)
+    u = [dev(a) for a in synth.random_velocity(n, ("P", "P", "NN"), 3)]
+    t = vp.vofp_server_submit(s, n, 1 / 64, 1 / 64, synth.uniform_dz(64), ("P", "P", "NN"), *u)
+    with pytest.raises(vp.VofpError) as e:
+        vp.vofp_server_wait(s, t, 60.0)
+    assert e.value.status == -6
+    vp.vofp_server_destroy(s)
