@@ -49,10 +49,12 @@ def parse():
     return ap.parse_args()
 
 
-def bench_mixed_step(vofp, c, u0, C, md, st, flush, args):
-    """The same droplet step through a mixed-precision plan (FP32 transforms + FP64 refinement)."""
+def bench_mixed_step(vofp, c, u0, C, md, st, flush, args, prec=None, max_refine=6):
+    """The same droplet step through a reduced-precision plan (FP32 or FP32-pair transforms + FP64
+    refinement)."""
     import torch
-    plan = vofp.Plan(c["n"], c["dx"], c["dy"], c["dz"], c["bc"], prec=vofp.MIXED)
+    plan = vofp.Plan(c["n"], c["dx"], c["dy"], c["dz"], c["bc"], prec=vofp.MIXED if prec is None else prec,
+                     max_refine=max_refine)
     u = [x.clone() for x in u0]
     p = torch.empty(plan.cell_shape, dtype=torch.float64, device=u0[0].device)
     phi = torch.empty_like(p)
@@ -90,7 +92,8 @@ def bench_mixed_step(vofp, c, u0, C, md, st, flush, args):
                                        c["dt_over_rho0"], p, ue[0], ue[1], ue[2], ug[0], ug[1], ug[2], phi,
                                        info=True)
     cells = int(np.prod(c["n"]))
-    out = {"value": cells * 2 / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms, "dtype": "f32+f64",
+    out = {"value": cells * 2 / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+           "dtype": "f32+f64" if prec in (None, vofp.MIXED) else "f32x2+f64", "max_refine": max_refine,
            "refine_iters_both_solves": info["refine_iters"], "rel_residual": info["rel_residual"],
            "per_kernel_ms": {k: round(v[0] / v[1], 5) for k, v in trace.items()},
            "roofline": roofline_mixed(trace, c["n"])}
@@ -182,17 +185,17 @@ def bench_served(vofp, args):
     sizes = synth.serve_sizes(len(arrivals))
     bc = ("P", "P", "NN")
     # pool of field buffers at the largest shape; each request views a contiguous prefix of one slot
-    pool = 48
+    pool = 128
     maxc = 257 * 256 * 256
     gen = torch.Generator(device="cuda")
     gen.manual_seed(synth.BASE_SEED + 6)
     bufs = [[torch.randn(maxc, generator=gen, dtype=torch.float64, device="cuda") for _ in range(3)]
             for _ in range(pool)]
     out = {}
-    for name, prec in (("mixed", vofp.MIXED), ("fp64", vofp.FP64)):
+    for name, prec in (("mixed", vofp.MIXED), ("ff", vofp.FF), ("fp64", vofp.FP64)):
         o = vofp.vofp_opts_default()
         o.prec = prec
-        s = vofp.vofp_server_create(0, 32, o)
+        s = vofp.vofp_server_create(0, 64, o)
         free = list(range(pool))
         busy = {}
         t0 = time.perf_counter()
@@ -228,9 +231,9 @@ def bench_served(vofp, args):
                      "solves_per_s": st["completed"] / st["seconds"],
                      "value": st["cells"] / st["seconds"] / 1e6, "unit": UNIT, "completed": int(st["completed"]),
                      "rejected": int(st["rejected"]), "late_submissions": late,
-                     "dtype": "f32+f64" if prec == vofp.MIXED else "f64"}
+                     "dtype": {vofp.MIXED: "f32+f64", vofp.FF: "f32x2+f64"}.get(prec, "f64")}
     out["workload"] = ("Poisson arrivals at %.0f req/s for %.0f s after %.0f s warm-up, per-axis sizes "
-                       "log-uniform in [48, 256], P,P,NN, N(0,1) fields, 32 in flight" % (rate, dur, warm))
+                       "log-uniform in [48, 256], P,P,NN, N(0,1) fields, 64 in flight" % (rate, dur, warm))
     return out
 
 
@@ -476,6 +479,8 @@ def run_ours(args):
     variants = {}
     if not args.no_variants:
         variants["mixed_step"] = bench_mixed_step(vofp, c, u0, C, md, st, flush, args)
+        variants["ff_step"] = bench_mixed_step(vofp, c, u0, C, md, st, flush, args, prec=vofp.FF, max_refine=0)
+        variants["ff_step_confirmed"] = bench_mixed_step(vofp, c, u0, C, md, st, flush, args, prec=vofp.FF)
         torch.cuda.empty_cache()
         variants["batched"] = bench_batched(vofp, args)
         torch.cuda.empty_cache()
@@ -500,16 +505,20 @@ def run_ours(args):
             line["cpu_baseline"] = {"value": cells * 2 / sec / 1e6, "unit": UNIT, "cores": cpu_threads(),
                                     "kind": "oracle",
                                     "sample": "%d oracle steps (median) of the same %d^3 droplet workload" % (nsteps, args.n)}
-            if "mixed_step" in variants:
-                # accuracy of the mixed-precision step against the oracle (one step, same inputs)
-                import oracle
-                g = oracle.Grid(*c["n"], c["dx"], c["dy"], c["dz"], c["bc"])
-                ref = oracle_step(c, g)
-                got = variants["mixed_step"].pop("_outputs")
+            ref = None
+            for vk in ("mixed_step", "ff_step", "ff_step_confirmed"):
+                if vk not in variants:
+                    continue
+                # accuracy of the reduced-precision step against the oracle (one step, same inputs)
+                if ref is None:
+                    import oracle
+                    ref = oracle_step(c, oracle.Grid(*c["n"], c["dx"], c["dy"], c["dz"], c["bc"]))
+                got = variants[vk].pop("_outputs")
                 errs = [float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)) for a, b in zip(got, ref[:7])]
-                variants["mixed_step"]["max_rel_err_vs_oracle"] = max(errs)
+                variants[vk]["max_rel_err_vs_oracle"] = max(errs)
         if variants:
-            variants.get("mixed_step", {}).pop("_outputs", None)
+            for vk in ("mixed_step", "ff_step", "ff_step_confirmed"):
+                variants.get(vk, {}).pop("_outputs", None)
             line["variants"] = variants
         print(json.dumps(line), flush=True)
     plan.close()

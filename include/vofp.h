@@ -63,8 +63,11 @@ typedef enum { VOFP_BC_P = 0, VOFP_BC_NN = 1, VOFP_BC_DD = 2, VOFP_BC_ND = 3, VO
 
 /* arithmetic of the solve */
 typedef enum {
-  VOFP_FP64 = 0, /* every step in FP64                                                               */
-  VOFP_MIXED = 1 /* FP32 transforms, FP64 low modes / reductions / residual, defect-correction refinement */
+  VOFP_FP64 = 0,  /* every step in FP64                                                              */
+  VOFP_MIXED = 1, /* FP32 transforms, FP64 low modes / reductions / residual, defect-correction refinement */
+  VOFP_FF = 2     /* as VOFP_MIXED, but the transforms and z recurrences in FP32-pair (float-float)
+                     arithmetic (~1e-14 relative) on the FP32 pipe: the first solve is already within
+                     ~1e-13 and one correction confirms it; max_refine = 0 skips the confirmation        */
 } vofp_prec;
 
 typedef struct {

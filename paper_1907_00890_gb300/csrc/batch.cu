@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(128) k_zsolve_batch(const ZArgs* __restrict__ 
 struct LowArgs {
   const int2* modes;
   int nlow;
+  const double2* tab;
   double* scratch;
 };
 
@@ -74,16 +75,8 @@ __global__ void k_zlow_batch(const ZArgs* __restrict__ args, const LowArgs* __re
   const ZArgs& a = args[i];
   if (launch_skipped(a.skip_conv, a.skip_k, a.tol2)) return;
   const int q = t - __ldg(off + i);
-  const int2 m = low[i].modes[q];
-  const int nz = a.nz;
-  const size_t plane = (size_t)a.nx * a.ny;
-  float* S = reinterpret_cast<float*>(a.S);
-  const size_t col = (size_t)m.y * a.nx + m.x;
-  double* d = low[i].scratch + (size_t)q * 3 * nz;
-  for (int k = 0; k < nz; ++k) d[k] = (double)S[k * plane + col];
-  Col<double> dd = {d, 1}, cc = {d + nz, 1}, zz = {d + 2 * nz, 1};
-  solve_column<double>(a, m.x, m.y, dd, cc, zz);
-  for (int k = 0; k < nz; ++k) S[k * plane + col] = (float)d[k];
+  const LowArgs& L = low[i];
+  zlow_system<float>(a, L.modes[q], q, L.nlow, L.tab, L.scratch);
 }
 
 template <typename T, typename C>
@@ -375,6 +368,7 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
     L[i].modes = pl->lowmodes;
     L[i].nlow = pl->nlow;
     L[i].scratch = pl->lowscratch;
+    L[i].tab = pl->lowtab;
     EpiArgs e;
     e.g = grid_dev(pl);
     e.p = pout;

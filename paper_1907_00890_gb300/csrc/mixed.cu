@@ -1,13 +1,14 @@
-// Mixed-precision path: FP32 transforms and FP32 z recurrences for the bulk of the spectrum, FP64 for the
-// low-eigenvalue z systems, the right-hand side, the residual stencil, the accumulated potential and every
-// reduction; defect-correction refinement (p += S32(f - fbar - L p)) back to the accuracy of an FP64 solve.
+// Mixed-precision path: reduced-precision transforms and z recurrences for the bulk of the spectrum -- FP32
+// (VOFP_MIXED) or FP32-pair float-float (VOFP_FF) -- and FP64 for the low-eigenvalue z systems, the
+// right-hand side, the residual stencil, the accumulated potential and every reduction; defect-correction
+// refinement (p += S(f - fbar - L p)) back to the accuracy of an FP64 solve.
 //
 // The loop is fully asynchronous: the residual norm of correction k is accumulated in FP64 by the residual
-// pass itself, and every launch of correction k + 1 reads it on the device and returns at once when
-// ||r_k|| <= tol ||f|| (so there is no host round trip and the whole sequence can be replayed as a graph).
-// The singular operator's mean is removed from the residual in FP64 (the compatibility defect is the
-// FP64 volume-weighted mean of f, not the FP32 spectrum's), and the gauge of p (zero volume-weighted mean)
-// is restored in FP64 at the end from the exact sums of the corrections.
+// pass itself, and every launch of the next correction reads it on the device and returns at once when the
+// convergence test passes (so there is no host round trip and the whole sequence can be replayed as a
+// graph).  The singular operator's mean is removed from the residual in FP64 (the compatibility defect is
+// the FP64 volume-weighted mean of f, not the reduced-precision spectrum's), and the gauge of p (zero
+// volume-weighted mean) is restored in FP64 at the end from the exact sums of the corrections.
 #include <cmath>
 #include <vector>
 
@@ -24,15 +25,29 @@ static void allow_smem(K kern) {
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
 }
 
+template <typename T, typename C>
+static void allow_all() {
+  allow_smem(k_xfwd<T, C, RHS_F>);
+  allow_smem(k_xfwd<T, C, RHS_DIV>);
+  allow_smem(k_xfwd<T, C, RHS_DIV_STEFAN>);
+  allow_smem(k_xfwd<T, C, RHS_RESID>);
+  allow_smem(k_ypass<T, C, false>);
+  allow_smem(k_ypass<T, C, true>);
+  allow_smem(k_xinv<T, C>);
+  allow_smem(k_zsolve<T, T>);
+}
+
 void init_kernel_attributes_mixed() {
-  allow_smem(k_xfwd<float, float2, RHS_F>);
-  allow_smem(k_xfwd<float, float2, RHS_DIV>);
-  allow_smem(k_xfwd<float, float2, RHS_DIV_STEFAN>);
-  allow_smem(k_xfwd<float, float2, RHS_RESID>);
-  allow_smem(k_ypass<float, float2, false>);
-  allow_smem(k_ypass<float, float2, true>);
-  allow_smem(k_xinv<float, float2>);
-  allow_smem(k_zsolve<float, float>);
+  allow_all<float, float2>();
+  allow_all<ff, cff>();
+}
+
+int build_low_factors(vofp_plan* pl, cudaStream_t st, bool sync) {
+  ZArgs za = z_args(pl, false);
+  k_zfactor_low<<<(pl->nlow + 127) / 128, 128, 0, st>>>(za, pl->lowmodes, pl->nlow, pl->lowtab);
+  if (cudaGetLastError() != cudaSuccess) return VOFP_ERR_CUDA;
+  if (sync && cudaStreamSynchronize(st) != cudaSuccess) return VOFP_ERR_CUDA;
+  return VOFP_OK;
 }
 
 // p -= (*sum) * scale  (gauge restoration)
@@ -62,8 +77,26 @@ __global__ void k_resid_norm(GridDev g, const double* __restrict__ F, const doub
   if (threadIdx.x == 0 && s != 0) atomicAdd(out, s);
 }
 
-// y forward, z (FP32 bulk + FP64 low modes), y inverse on the FP32 spectrum; skipped when converged.
-static void solve32(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, bool stats) {
+// Reduced-precision element types: R (real) / C (complex) of the spectrum and its tables.
+template <typename R>
+struct Red;
+template <>
+struct Red<float> {
+  typedef float2 C;
+  static const void* tw(const AxisDev& a) { return a.tw32; }
+  static const void* quart(const AxisDev& a) { return a.quart32; }
+};
+template <>
+struct Red<ff> {
+  typedef cff C;
+  static const void* tw(const AxisDev& a) { return a.twff; }
+  static const void* quart(const AxisDev& a) { return a.quartff; }
+};
+
+// y forward, z (bulk + FP64 low modes), y inverse on the spectrum; skipped when converged.
+template <typename R>
+static void solve_red(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, bool stats) {
+  typedef typename Red<R>::C C;
   const int nx = pl->n[0], ny = pl->n[1], nz = pl->n[2];
   YArgs ya = {};
   ya.nx = nx;
@@ -71,16 +104,16 @@ static void solve32(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, boo
   ya.nz = nz;
   ya.bc = pl->bc[1];
   ya.fd = pl->ax[1].fd;
-  ya.tw = pl->ax[1].tw32;
-  ya.quart = pl->ax[1].quart32;
+  ya.tw = Red<R>::tw(pl->ax[1]);
+  ya.quart = Red<R>::quart(pl->ax[1]);
   ya.tx = pl->ytx32;
   ya.S = pl->S32;
   ya.skip_conv = pl->conv;
   ya.skip_k = skip_k;
   ya.tol2 = tol2;
   const dim3 ygrid((nx + ya.tx - 1) / ya.tx, nz);
-  const size_t ysm = 2 * (size_t)(ya.tx / 2) * ny * sizeof(float2);
-  if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, (k_ypass<float, float2, false><<<ygrid, 256, ysm, st>>>(ya)));
+  const size_t ysm = 2 * (size_t)(ya.tx / 2) * ny * sizeof(C);
+  if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, (k_ypass<R, C, false><<<ygrid, 256, ysm, st>>>(ya)));
   ZArgs za = z_args(pl, stats);
   za.S = pl->S32;
   za.ti = pl->zti32;
@@ -90,24 +123,27 @@ static void solve32(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, boo
   za.tol2 = tol2;
   const int nvec = pl->bc[2] == VOFP_BC_P ? 3 : 2;
   const dim3 zgrid((nx + za.ti - 1) / za.ti, ny);
-  const size_t zsm = (size_t)nvec * za.ti * nz * sizeof(float);
-  VOFP_LAUNCH(KID_ZSOLVE, st, (k_zsolve<float, float><<<zgrid, 128, zsm, st>>>(za)));
+  const size_t zsm = (size_t)nvec * za.ti * nz * sizeof(R);
+  VOFP_LAUNCH(KID_ZSOLVE, st, (k_zsolve<R, R><<<zgrid, 128, zsm, st>>>(za)));
   if (pl->nlow > 0)
     VOFP_LAUNCH(KID_ZSOLVE, st,
-                k_zlow64<<<(pl->nlow + 63) / 64, 64, 0, st>>>(za, pl->lowmodes, pl->nlow, pl->lowscratch));
-  if (ny > 1) VOFP_LAUNCH(KID_YINV, st, (k_ypass<float, float2, true><<<ygrid, 256, ysm, st>>>(ya)));
+                k_zlow64<R><<<(pl->nlow + 63) / 64, 64, 0, st>>>(za, pl->lowmodes, pl->nlow, pl->lowtab,
+                                                                 pl->lowscratch));
+  if (ny > 1) VOFP_LAUNCH(KID_YINV, st, (k_ypass<R, C, true><<<ygrid, 256, ysm, st>>>(ya)));
 }
 
-static void xinv32(vofp_plan* pl, double* pout, int accumulate, int skip_k, double tol2, double* d2_out,
-                   cudaStream_t st) {
+template <typename R>
+static void xinv_red(vofp_plan* pl, double* pout, int accumulate, int skip_k, double tol2, double* d2_out,
+                     cudaStream_t st) {
+  typedef typename Red<R>::C C;
   XInvArgs xi = {};
   xi.nx = pl->n[0];
   xi.ny = pl->n[1];
   xi.nz = pl->n[2];
   xi.bc = pl->bc[0];
   xi.fd = pl->ax[0].fd;
-  xi.tw = pl->ax[0].tw32;
-  xi.quart = pl->ax[0].quart32;
+  xi.tw = Red<R>::tw(pl->ax[0]);
+  xi.quart = Red<R>::quart(pl->ax[0]);
   xi.pb = pl->xpb;
   xi.S = pl->S32;
   xi.p = pout;
@@ -118,39 +154,60 @@ static void xinv32(vofp_plan* pl, double* pout, int accumulate, int skip_k, doub
   xi.dz = pl->dz;
   xi.mean_out = pl->singular ? pl->conv + VOFP_CONV_MEAN : nullptr;
   xi.d2_out = d2_out;
-  const long npairs = ((long)xi.ny * xi.nz + 1) / 2;
-  const int xgrid = (int)((npairs + xi.pb - 1) / xi.pb);
-  const size_t xsm = 2 * (size_t)xi.pb * xi.nx * sizeof(float2);
-  VOFP_LAUNCH(KID_XINV, st, (k_xinv<float, float2><<<xgrid, 256, xsm, st>>>(xi)));
+  const int xgrid = xpass_blocks(xi.ny, xi.nz, xi.pb);
+  const size_t xsm = 2 * (size_t)xi.pb * xi.nx * sizeof(C);
+  VOFP_LAUNCH(KID_XINV, st, (k_xinv<R, C><<<xgrid, 256, xsm, st>>>(xi)));
 }
 
-static void xfwd32(vofp_plan* pl, int mode, XArgs xa, cudaStream_t st) {
+template <typename R>
+static void xfwd_red(vofp_plan* pl, int mode, XArgs xa, cudaStream_t st) {
+  typedef typename Red<R>::C C;
   xa.g = grid_dev(pl);
   xa.fd = pl->ax[0].fd;
-  xa.tw = pl->ax[0].tw32;
-  xa.quart = pl->ax[0].quart32;
+  xa.tw = Red<R>::tw(pl->ax[0]);
+  xa.quart = Red<R>::quart(pl->ax[0]);
   xa.pb = pl->xpb;
   xa.S = pl->S32;
-  const long npairs = ((long)pl->n[1] * pl->n[2] + 1) / 2;
-  const int xgrid = (int)((npairs + xa.pb - 1) / xa.pb);
-  const size_t xsm = 2 * (size_t)xa.pb * pl->n[0] * sizeof(float2);
+  const int xgrid = xpass_blocks(pl->n[1], pl->n[2], xa.pb);
+  const size_t xsm = 2 * (size_t)xa.pb * pl->n[0] * sizeof(C);
   switch (mode) {
-    case RHS_F: VOFP_LAUNCH(KID_XFWD, st, (k_xfwd<float, float2, RHS_F><<<xgrid, 256, xsm, st>>>(xa))); break;
-    case RHS_DIV:
-      VOFP_LAUNCH(KID_XFWD_DIV, st, (k_xfwd<float, float2, RHS_DIV><<<xgrid, 256, xsm, st>>>(xa)));
-      break;
+    case RHS_F: VOFP_LAUNCH(KID_XFWD, st, (k_xfwd<R, C, RHS_F><<<xgrid, 256, xsm, st>>>(xa))); break;
+    case RHS_DIV: VOFP_LAUNCH(KID_XFWD_DIV, st, (k_xfwd<R, C, RHS_DIV><<<xgrid, 256, xsm, st>>>(xa))); break;
     case RHS_DIV_STEFAN:
-      VOFP_LAUNCH(KID_XFWD_DIVSTEF, st, (k_xfwd<float, float2, RHS_DIV_STEFAN><<<xgrid, 256, xsm, st>>>(xa)));
+      VOFP_LAUNCH(KID_XFWD_DIVSTEF, st, (k_xfwd<R, C, RHS_DIV_STEFAN><<<xgrid, 256, xsm, st>>>(xa)));
       break;
-    default:
-      VOFP_LAUNCH(KID_RESID, st, (k_xfwd<float, float2, RHS_RESID><<<xgrid, 256, xsm, st>>>(xa)));
-      break;
+    default: VOFP_LAUNCH(KID_RESID, st, (k_xfwd<R, C, RHS_RESID><<<xgrid, 256, xsm, st>>>(xa))); break;
+  }
+}
+
+template <typename R>
+static void refine_sequence(vofp_plan* pl, int mode, XArgs xa, double* pout, int M, double tol2, bool stats,
+                            cudaStream_t st) {
+  double* conv = pl->conv;
+  xfwd_red<R>(pl, mode, xa, st);
+  solve_red<R>(pl, st, -1, tol2, stats);
+  xinv_red<R>(pl, pout, 0, -1, tol2, conv + VOFP_CONV_DEL, st);
+  // correction j solves for r_{j-1} and is skipped once correction j - 1 converged (see launch_skipped)
+  for (int j = 1; j <= M; ++j) {
+    XArgs ra = {};
+    ra.f = pl->F;
+    ra.p = pout;
+    ra.defect_sum = pl->singular ? conv + 1 : nullptr;
+    ra.inv_volume = 1.0 / pl->volume;
+    ra.sq_out = conv + VOFP_CONV_RES + j - 1;
+    ra.skip_conv = conv;
+    ra.skip_k = j - 1;
+    ra.tol2 = tol2;
+    xfwd_red<R>(pl, RHS_RESID, ra, st);
+    solve_red<R>(pl, st, j - 1, tol2, stats);
+    xinv_red<R>(pl, pout, 1, j - 1, tol2, conv + VOFP_CONV_DEL + j, st);
   }
 }
 
 int mixed_solve(vofp_plan* pl, int mode, const XArgs* xin, const double* f, double* pout, cudaStream_t st,
                 vofp_info* info) {
   if (mode == RHS_STEFAN) return VOFP_ERR_UNSUPPORTED;  // the extension passes its source as RHS_F
+  if (!pl->S32 || !pl->F) return VOFP_ERR_INVALID_ARG;  // an FP64 plan has no reduced-precision workspace
   const double tol2 = pl->opts.tol * pl->opts.tol;
   int M = pl->opts.max_refine;
   if (M > VOFP_MAX_REFINE) M = VOFP_MAX_REFINE;
@@ -159,7 +216,7 @@ int mixed_solve(vofp_plan* pl, int mode, const XArgs* xin, const double* f, doub
   if (cudaMemsetAsync(conv, 0, sizeof(double) * VOFP_CONV_SLOTS, st) != cudaSuccess) return VOFP_ERR_CUDA;
   const bool stats = info != nullptr;
 
-  // initial FP32 solve of f (kept in FP64 in pl->F)
+  // initial solve of f (kept in FP64 in pl->F), then the corrections
   XArgs xa = {};
   if (xin) xa = *xin;
   if (mode == RHS_F) {
@@ -172,26 +229,10 @@ int mixed_solve(vofp_plan* pl, int mode, const XArgs* xin, const double* f, doub
   xa.abs_out = conv + 2;
   xa.skip_k = -1;
   xa.info = nullptr;
-  xfwd32(pl, mode, xa, st);
-  solve32(pl, st, -1, tol2, stats);
-  xinv32(pl, pout, 0, -1, tol2, conv + VOFP_CONV_DEL, st);
-
-  // defect-correction refinement: correction j solves for r_{j-1} and is skipped once correction j - 1
-  // converged (see launch_skipped)
-  for (int j = 1; j <= M; ++j) {
-    XArgs ra = {};
-    ra.f = pl->F;
-    ra.p = pout;
-    ra.defect_sum = pl->singular ? conv + 1 : nullptr;
-    ra.inv_volume = 1.0 / pl->volume;
-    ra.sq_out = conv + VOFP_CONV_RES + j - 1;
-    ra.skip_conv = conv;
-    ra.skip_k = j - 1;
-    ra.tol2 = tol2;
-    xfwd32(pl, RHS_RESID, ra, st);
-    solve32(pl, st, j - 1, tol2, stats);
-    xinv32(pl, pout, 1, j - 1, tol2, conv + VOFP_CONV_DEL + j, st);
-  }
+  if (pl->opts.prec == VOFP_FF)
+    refine_sequence<ff>(pl, mode, xa, pout, M, tol2, stats, st);
+  else
+    refine_sequence<float>(pl, mode, xa, pout, M, tol2, stats, st);
   if (info) {
     VOFP_LAUNCH(KID_RESID, st,
                 k_resid_norm<<<grid_blocks(cells, 256), 256, 0, st>>>(
@@ -217,10 +258,16 @@ int mixed_solve(vofp_plan* pl, int mode, const XArgs* xin, const double* f, doub
   auto converged = [&](int j) {
     return h[VOFP_CONV_RES + j - 1] <= tol2 * f2 && h[VOFP_CONV_DEL + j] <= 0.01 * tol2 * h[VOFP_CONV_DEL];
   };
-  int iters = 1;
-  while (iters < M && !converged(iters)) ++iters;
-  const bool conv_ok = converged(iters);
   const double rr = f2 > 0 ? std::sqrt(h[VOFP_CONV_FINAL] / f2) : 0.0;
+  int iters = 0;
+  bool conv_ok;
+  if (M == 0) {
+    conv_ok = rr <= pl->opts.tol;  // no correction requested: judge the direct solve by its residual
+  } else {
+    iters = 1;
+    while (iters < M && !converged(iters)) ++iters;
+    conv_ok = converged(iters);
+  }
   const double defect = pl->singular ? h[1] / pl->volume : 0.0;
   info->compat_defect = defect;
   info->rel_residual = rr;

@@ -47,20 +47,19 @@ struct XArgs {
   void* S;            // spectrum output
 };
 
-// 7-point L p at a cell with the ghost rules of the MAC operator (FP64).
+// 7-point L p at a cell with the ghost rules of the MAC operator (FP64, reciprocal spacings: no divisions).
 __device__ __forceinline__ double lap_at(const GridDev& g, const double* __restrict__ p, int i, int j, int k) {
   const size_t plane = (size_t)g.nx * g.ny;
   const size_t c = k * plane + (size_t)j * g.nx + i;
   const double pc = __ldg(p + c);
-  double r = 0;
-  // x
+  double xs, ys;
   {
     double lo, hi;
     if (i > 0) lo = __ldg(p + c - 1);
     else lo = g.bcx == VOFP_BC_P ? __ldg(p + c + g.nx - 1) : (g.bcx == VOFP_BC_DD ? -pc : pc);
     if (i < g.nx - 1) hi = __ldg(p + c + 1);
     else hi = g.bcx == VOFP_BC_P ? __ldg(p + c - (g.nx - 1)) : (g.bcx == VOFP_BC_DD ? -pc : pc);
-    r += (hi - 2.0 * pc + lo) / (g.dx * g.dx);
+    xs = hi + lo;
   }
   {
     double lo, hi;
@@ -68,8 +67,9 @@ __device__ __forceinline__ double lap_at(const GridDev& g, const double* __restr
     else lo = g.bcy == VOFP_BC_P ? __ldg(p + c + (size_t)(g.ny - 1) * g.nx) : (g.bcy == VOFP_BC_DD ? -pc : pc);
     if (j < g.ny - 1) hi = __ldg(p + c + g.nx);
     else hi = g.bcy == VOFP_BC_P ? __ldg(p + c - (size_t)(g.ny - 1) * g.nx) : (g.bcy == VOFP_BC_DD ? -pc : pc);
-    r += (hi - 2.0 * pc + lo) / (g.dy * g.dy);
+    ys = hi + lo;
   }
+  double r = fma(xs, g.rdx2, fma(ys, g.rdy2, -2.0 * (g.rdx2 + g.rdy2) * pc));
   {
     double lo, hi;
     const bool lowN = g.bcz == VOFP_BC_NN || g.bcz == VOFP_BC_ND;
@@ -78,8 +78,7 @@ __device__ __forceinline__ double lap_at(const GridDev& g, const double* __restr
     else lo = g.bcz == VOFP_BC_P ? __ldg(p + c + (size_t)(g.nz - 1) * plane) : (lowN ? pc : -pc);
     if (k < g.nz - 1) hi = __ldg(p + c + plane);
     else hi = g.bcz == VOFP_BC_P ? __ldg(p + c - (size_t)(g.nz - 1) * plane) : (highN ? pc : -pc);
-    const double dzk = __ldg(g.dz + k);
-    r += ((hi - pc) / __ldg(g.hz + k + 1) - (pc - lo) / __ldg(g.hz + k)) / dzk;
+    r = fma(((hi - pc) * __ldg(g.rhz + k + 1) - (pc - lo) * __ldg(g.rhz + k)), __ldg(g.rdz + k), r);
   }
   return r;
 }

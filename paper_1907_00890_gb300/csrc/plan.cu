@@ -116,9 +116,9 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   vofp_opts o;
   vofp_opts_default(&o);
   if (opt) o = *opt;
-  if (o.prec != VOFP_FP64 && o.prec != VOFP_MIXED) return VOFP_ERR_INVALID_ARG;
+  if (o.prec != VOFP_FP64 && o.prec != VOFP_MIXED && o.prec != VOFP_FF) return VOFP_ERR_INVALID_ARG;
   if (o.grad_mode != 0 && o.grad_mode != 1) return VOFP_ERR_INVALID_ARG;
-  if (o.max_refine < 1) o.max_refine = 1;
+  if (o.max_refine < 1) o.max_refine = o.prec == VOFP_FF ? 0 : 1;  // FP32-pair solves may skip confirmation
   if (o.max_refine > VOFP_MAX_REFINE) o.max_refine = VOFP_MAX_REFINE;
   if (!(o.tol > 0)) o.tol = 1e-10;
 
@@ -139,7 +139,9 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   double lz = 0;
   for (int k = 0; k < nz; ++k) lz += dz[k];
   p->volume = nx * dx * ny * dy * lz;
-  const bool mixed = o.prec == VOFP_MIXED;
+  const bool mixed = o.prec != VOFP_FP64;  // the refinement path (FP32 or FP32-pair spectrum)
+  const bool ffp = o.prec == VOFP_FF;
+  const size_t rs = ffp ? sizeof(ff) : sizeof(float);  // bytes per real of the reduced-precision spectrum
   const bool zper = bc[2] == VOFP_BC_P;
 
   // ---- host tables ----
@@ -148,6 +150,13 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   std::vector<double> lam[2];
   std::vector<double2> tw[2], quart[2];
   std::vector<float2> tw32[2], quart32[2];
+  std::vector<cff> twff[2], quartff[2];
+  auto to_cff = [](double2 z) {
+    cff c;
+    c.x = ff(z.x);
+    c.y = ff(z.y);
+    return c;
+  };
   for (int a = 0; a < 2; ++a) {
     const int n = nn[a];
     lam[a].resize(n);
@@ -155,6 +164,8 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
     quart[a].resize(n);
     tw32[a].resize(n);
     quart32[a].resize(n);
+    twff[a].resize(n);
+    quartff[a].resize(n);
     for (int q = 0; q < n; ++q) {
       lam[a][q] = eig_1d(bc[a], n, hh[a], q);
       const double t = -2.0 * kPi * q / n;
@@ -163,6 +174,8 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
       quart[a][q] = make_double2(std::cos(u), std::sin(u));
       tw32[a][q] = make_float2((float)tw[a][q].x, (float)tw[a][q].y);
       quart32[a][q] = make_float2((float)quart[a][q].x, (float)quart[a][q].y);
+      twff[a][q] = to_cff(tw[a][q]);
+      quartff[a][q] = to_cff(quart[a][q]);
     }
     factor_radices(n, &p->ax[a].fd);
     p->ax[a].n = n;
@@ -229,6 +242,10 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
     off = align256(off + sizeof(float2) * nn[a]);
     L.q32[a] = off;
     off = align256(off + sizeof(float2) * nn[a]);
+    L.twff[a] = off;
+    off = align256(off + sizeof(cff) * nn[a]);
+    L.qff[a] = off;
+    off = align256(off + sizeof(cff) * nn[a]);
   }
   L.za = off;
   off = align256(off + sizeof(double) * nz);
@@ -259,7 +276,7 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   const int Ux = zdistinct(nx, bc[0]), Uy = zdistinct(ny, bc[1]);
   L.P = off;
   off = align256(off + sizeof(double) * cells);
-  L.S = L.T = L.S32 = L.F = L.lowscr = 0;
+  L.S = L.T = L.S32 = L.F = L.lowscr = L.lowtab = 0;
   if (!mixed) {
     L.S = off;
     off = align256(off + sizeof(double) * cells);
@@ -268,12 +285,16 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
       off = align256(off + sizeof(double2) * (size_t)Ux * Uy * nz);
     }
   } else {
-    L.S32 = off;
-    off = align256(off + sizeof(float) * cells);
+    L.S32 = off;  // FP32 or FP32-pair spectrum
+    off = align256(off + rs * cells);
     L.F = off;
     off = align256(off + sizeof(double) * cells);
     L.lowscr = off;
     off = align256(off + sizeof(double) * 3 * (size_t)nz * low.size());
+    if (!zper && !low.empty()) {
+      L.lowtab = off;
+      off = align256(off + sizeof(double2) * (size_t)nz * low.size());
+    }
   }
   L.total = off;
   p->Ux = Ux;
@@ -287,6 +308,8 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
     memcpy(&host[L.q[a]], quart[a].data(), sizeof(double2) * nn[a]);
     memcpy(&host[L.tw32[a]], tw32[a].data(), sizeof(float2) * nn[a]);
     memcpy(&host[L.q32[a]], quart32[a].data(), sizeof(float2) * nn[a]);
+    memcpy(&host[L.twff[a]], twff[a].data(), sizeof(cff) * nn[a]);
+    memcpy(&host[L.qff[a]], quartff[a].data(), sizeof(cff) * nn[a]);
   }
   memcpy(&host[L.za], za.data(), sizeof(double) * nz);
   memcpy(&host[L.zb], zb.data(), sizeof(double) * nz);
@@ -304,15 +327,16 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   int tx = 16;
   while (tx > 2 && (size_t)16 * tx * ny > 96 * 1024) tx -= 2;
   p->ytx = tx;
+  // the reduced-precision path's shapes, sized by its element (FP32 or FP32-pair)
   tx = 16;
-  while (tx > 2 && (size_t)8 * tx * ny > 96 * 1024) tx -= 2;
+  while (tx > 2 && (size_t)(4 * rs) * tx * ny > 96 * 1024) tx -= 2;
   p->ytx32 = tx;
   const int nvec = zper ? 3 : 2;
   int ti = 32;
   while (ti > 1 && (size_t)nvec * ti * nz * sizeof(double) > 96 * 1024) ti /= 2;
   p->zti = ti;
   ti = 32;
-  while (ti > 1 && (size_t)nvec * ti * nz * sizeof(float) > 96 * 1024) ti /= 2;
+  while (ti > 1 && (size_t)nvec * ti * nz * rs > 96 * 1024) ti /= 2;
   p->zti32 = ti;
   pp->p = p;
   return VOFP_OK;
@@ -350,6 +374,8 @@ int plan_bind(PlanPrep* pp, void* block, cudaStream_t st, unsigned char* stage) 
     p->ax[a].quart64 = (const double2*)(b + L.q[a]);
     p->ax[a].tw32 = (const float2*)(b + L.tw32[a]);
     p->ax[a].quart32 = (const float2*)(b + L.q32[a]);
+    p->ax[a].twff = (const cff*)(b + L.twff[a]);
+    p->ax[a].quartff = (const cff*)(b + L.qff[a]);
   }
   p->za = (double*)(b + L.za);
   p->zb = (double*)(b + L.zb);
@@ -363,18 +389,23 @@ int plan_bind(PlanPrep* pp, void* block, cudaStream_t st, unsigned char* stage) 
   p->info = (vofp_devinfo*)(b + L.info);
   p->lowmodes = p->nlow ? (int2*)(b + L.low) : nullptr;
   p->P = (double*)(b + L.P);
-  const bool mixed = p->opts.prec == VOFP_MIXED;
+  const bool mixed = p->opts.prec != VOFP_FP64;
   p->S = mixed ? nullptr : (double*)(b + L.S);
   p->ztab = (!mixed && L.T) ? (double2*)(b + L.T) : nullptr;
   p->S32 = mixed ? (float*)(b + L.S32) : nullptr;
   p->F = mixed ? (double*)(b + L.F) : nullptr;
   p->lowscratch = (mixed && p->nlow) ? (double*)(b + L.lowscr) : nullptr;
+  p->lowtab = (mixed && L.lowtab) ? (double2*)(b + L.lowtab) : nullptr;
   p->R = nullptr;
   p->G = nullptr;  // interface geometry: allocated on first use (extension / Stefan source)
   init_kernel_attributes_fp64();
   init_kernel_attributes_mixed();
   if (p->ztab) {
     const int s = build_z_factors(p, st, own);
+    if (s) return s;
+  }
+  if (p->lowtab) {
+    const int s = build_low_factors(p, st, own);
     if (s) return s;
   }
   return VOFP_OK;

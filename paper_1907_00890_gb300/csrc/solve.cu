@@ -28,6 +28,8 @@ GridDev grid_dev(const vofp_plan* pl) {
   g.dy = pl->dy;
   g.rdx = 1.0 / pl->dx;
   g.rdy = 1.0 / pl->dy;
+  g.rdx2 = g.rdx * g.rdx;
+  g.rdy2 = g.rdy * g.rdy;
   g.dz = pl->dz;
   g.hz = pl->hz;
   g.rdz = pl->rdz;
@@ -105,6 +107,7 @@ int build_z_factors(vofp_plan* pl, cudaStream_t st, bool sync) {
 
 // x forward + y forward + z solve + y inverse + x inverse into `pout`.
 int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st, bool stats) {
+  if (!pl->S) return VOFP_ERR_INVALID_ARG;  // a refinement plan has no FP64 spectrum
   const int nx = pl->n[0], ny = pl->n[1], nz = pl->n[2];
   xa.g = grid_dev(pl);
   xa.fd = pl->ax[0].fd;
@@ -223,7 +226,7 @@ static int project_common(vofp_plan* pl, int mode, XArgs& xa, double* u, double*
   int s = begin_info(pl, st, info);
   if (s) return s;
   double* pout = p ? p : pl->P;
-  if (pl->opts.prec == VOFP_MIXED) {
+  if (pl->opts.prec != VOFP_FP64) {
     s = mixed_solve(pl, mode, &xa, nullptr, pout, st, info);
     if (s < 0) return s;
   } else {
@@ -235,7 +238,7 @@ static int project_common(vofp_plan* pl, int mode, XArgs& xa, double* u, double*
   VOFP_LAUNCH(KID_GRAD, st,
               k_grad_update<<<grid_blocks(total, 256), 256, 0, st>>>(g, pout, u, v, w, dt_over_rho0));
   const int ls = cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
-  if (pl->opts.prec == VOFP_MIXED) {
+  if (pl->opts.prec != VOFP_FP64) {
     if (ls) return ls;
     if (info) {
       if (cudaStreamSynchronize(st) != cudaSuccess) return VOFP_ERR_CUDA;
@@ -257,7 +260,7 @@ static int extend_common(vofp_plan* pl, const double* u, const double* v, const 
   XArgs xa = {};
   xa.f = pl->G;
   xa.scale = 1.0;
-  if (pl->opts.prec == VOFP_MIXED) {
+  if (pl->opts.prec != VOFP_FP64) {
     s = mixed_solve(pl, RHS_F, nullptr, pl->G, pout, st, info);
     if (s < 0) return s;
   } else {
@@ -284,7 +287,7 @@ static int extend_common(vofp_plan* pl, const double* u, const double* v, const 
   const size_t total = total_faces(ea.g);
   VOFP_LAUNCH(KID_EXTEND_EPI, st, k_extend_epi<<<grid_blocks(total, 256), 256, 0, st>>>(ea));
   const int ls = cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
-  if (pl->opts.prec == VOFP_MIXED) {
+  if (pl->opts.prec != VOFP_FP64) {
     if (ls) return ls;
     if (info) {
       if (cudaStreamSynchronize(st) != cudaSuccess) return VOFP_ERR_CUDA;
@@ -304,7 +307,7 @@ extern "C" int vofp_poisson_solve(vofp_plan* pl, const double* f, double* p, voi
   cudaStream_t st = (cudaStream_t)stream;
   int s = begin_info(pl, st, info);
   if (s) return s;
-  if (pl->opts.prec == VOFP_MIXED) return mixed_solve(pl, RHS_F, nullptr, f, p, st, info);
+  if (pl->opts.prec != VOFP_FP64) return mixed_solve(pl, RHS_F, nullptr, f, p, st, info);
   XArgs xa = {};
   xa.f = f;
   xa.scale = 1.0;

@@ -56,10 +56,10 @@ unsigned long long capture_end();
 
 // ---- plan construction in two phases (see plan.cu) ----
 struct PlanLayout {
-  size_t lam[2], tw[2], q[2], tw32[2], q32[2];
+  size_t lam[2], tw[2], q[2], tw32[2], q32[2], twff[2], qff[2];
   size_t za, zb, zc, dz, hz, rdz, rhz, rzc, conv, info, low;
   size_t table_bytes;  // host-built part, uploaded as one copy
-  size_t P, S, T, S32, F, lowscr;
+  size_t P, S, T, S32, F, lowscr, lowtab;
   size_t total;
 };
 struct PlanPrep {
@@ -93,6 +93,8 @@ int mixed_solve(vofp_plan* pl, int mode, const XArgs* xa, const double* f, doubl
 int begin_info(vofp_plan* pl, cudaStream_t st, vofp_info* info);
 // Thomas factor tables for a bounded z axis (FP64 plans), built on `st`; `sync` waits for them.
 int build_z_factors(vofp_plan* pl, cudaStream_t st, bool sync);
+// The same for the low-eigenvalue systems of a mixed plan.
+int build_low_factors(vofp_plan* pl, cudaStream_t st, bool sync);
 int finish_info(vofp_plan* pl, cudaStream_t st, vofp_info* info, int status);
 }  // namespace vofp
 

@@ -20,6 +20,7 @@ struct GridDev {
   int bcx, bcy, bcz;
   double dx, dy;
   double rdx, rdy;    // 1/dx, 1/dy
+  double rdx2, rdy2;  // 1/dx^2, 1/dy^2
   const double* dz;   // nz widths
   const double* hz;   // nz + 1 centre distances across z faces (ghost distances at the ends)
   const double* rdz;  // 1/dz

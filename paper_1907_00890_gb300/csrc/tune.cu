@@ -60,7 +60,8 @@ void save_entry(const std::string& k, const Shape& s) {
   fclose(f);
 }
 
-bool mixed(const vofp_plan* p) { return p->opts.prec == VOFP_MIXED; }
+// the reduced-precision (refinement) paths keep their shapes in ytx32 / zti32
+bool mixed(const vofp_plan* p) { return p->opts.prec != VOFP_FP64; }
 
 void apply(vofp_plan* p, const Shape& s) {
   p->xpb = s.xpb;
@@ -78,8 +79,8 @@ Shape current(const vofp_plan* p) {
 }
 
 bool fits(const vofp_plan* p, const Shape& s) {
-  const size_t c = mixed(p) ? sizeof(float2) : sizeof(double2);
-  const size_t r = mixed(p) ? sizeof(float) : sizeof(double);
+  const size_t c = p->opts.prec == VOFP_MIXED ? sizeof(float2) : sizeof(double2);
+  const size_t r = p->opts.prec == VOFP_MIXED ? sizeof(float) : sizeof(double);
   const int nvec = p->bc[2] == VOFP_BC_P ? 3 : 2;
   const size_t lim = 160 * 1024;
   if (2 * (size_t)s.xpb * p->n[0] * c > lim) return false;

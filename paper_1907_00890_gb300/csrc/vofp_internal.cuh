@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ffloat.cuh"
 #include "vofp.h"
 
 #define VOFP_MAX_STAGES 24
@@ -100,6 +101,8 @@ struct AxisDev {
   const double2* quart64; // e^{-i pi k / (2 n)}, k < n
   const float2* tw32;
   const float2* quart32;
+  const cff* twff;     // float-float twiddles (FP32-pair precision)
+  const cff* quartff;
   const double* lam; // eigenvalue of packed spectral index q, q < n
 };
 
@@ -388,6 +391,7 @@ struct vofp_plan {
   int nlow;            // number of such systems
   int2* lowmodes;      // their (x, y) spectral indices
   double* lowscratch;  // FP64 columns for them (3 nz each)
+  double2* lowtab;     // bounded z: their Thomas factors (k-major), NULL for periodic z
   void* low_block;     // allocation holding lowmodes and lowscratch
   int ytx32, zti32;    // launch shapes of the FP32 y and z passes
   // workspace

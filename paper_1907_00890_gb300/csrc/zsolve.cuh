@@ -171,22 +171,84 @@ __global__ void __launch_bounds__(128) k_zsolve(ZArgs a) {
   zsolve_block<TS, TA>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
-// Mixed path: the low-eigenvalue systems (listed at plan time) solved in FP64 on their FP32 spectrum,
-// with FP64 scratch columns in global memory (three per system, contiguous in k).
-static __global__ void k_zlow64(ZArgs a, const int2* __restrict__ modes, int nlow, double* scratch) {
+// Mixed path: the low-eigenvalue systems (listed at plan time) solved in FP64 on their reduced-precision
+// spectrum.  Bounded z: plan-time Thomas factors (lowtab[k * nlow + t] = (c'_k, 1/den_k), the singular mean
+// mode pinned), so the recurrence has no division; scratch columns are k-major so that consecutive systems
+// touch consecutive addresses.  Periodic z: the general column solver on three scratch columns per system.
+static __global__ void k_zfactor_low(ZArgs a, const int2* __restrict__ modes, int nlow, double2* tab) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nlow) return;
+  const int2 md = modes[t];
+  const double lam = a.lamx[md.x] + a.lamy[md.y];
+  const bool sing = a.singular && md.x == 0 && md.y == 0;
+  const int k0 = sing ? 1 : 0;
+  if (sing) tab[t] = make_double2(0.0, 0.0);
+  double cprev = 0.0;
+  for (int k = k0; k < a.nz; ++k) {
+    const double den = a.zb[k] + lam - (k > k0 ? a.za[k] * cprev : 0.0);
+    const double m = 1.0 / den;
+    const double c = (k < a.nz - 1 ? a.zc[k] : 0.0) * m;
+    tab[(size_t)k * nlow + t] = make_double2(c, m);
+    cprev = c;
+  }
+}
+
+template <typename TS>
+__device__ __forceinline__ void zlow_system(const ZArgs& a, int2 md, int t, int nlow, const double2* __restrict__ tab,
+                                            double* __restrict__ scratch) {
+  const int nz = a.nz;
+  const size_t plane = (size_t)a.nx * a.ny;
+  TS* S = reinterpret_cast<TS*>(a.S);
+  const size_t col = (size_t)md.y * a.nx + md.x;
+  if (!tab) {
+    double* d = scratch + (size_t)t * 3 * nz;
+    for (int k = 0; k < nz; ++k) d[k] = (double)S[k * plane + col];
+    Col<double> dd = {d, 1}, cc = {d + nz, 1}, zz = {d + 2 * nz, 1};
+    solve_column<double>(a, md.x, md.y, dd, cc, zz);
+    for (int k = 0; k < nz; ++k) S[k * plane + col] = (TS)d[k];
+    return;
+  }
+  Col<double> d = {scratch + t, nlow};
+  const double sc = a.scale;
+  for (int k = 0; k < nz; ++k) d[k] = (double)S[k * plane + col] * sc;
+  int k0 = 0;
+  if (a.singular && md.x == 0 && md.y == 0) {
+    double s = 0;
+    for (int k = 0; k < nz; ++k) s += __ldg(a.dz + k) * d[k];
+    const double defect = s / a.lz;
+    if (a.info) a.info->compat_defect = defect;
+    for (int k = 0; k < nz; ++k) d[k] -= defect;
+    d[0] = 0.0;
+    k0 = 1;
+  }
+  double dprev = 0.0;
+  for (int k = k0; k < nz; ++k) {
+    const double2 f = __ldg(tab + (size_t)k * nlow + t);
+    dprev = (d[k] - (k > k0 ? __ldg(a.za + k) * dprev : 0.0)) * f.y;
+    d[k] = dprev;
+  }
+  double x = dprev;
+  for (int k = nz - 2; k >= k0; --k) {
+    const double2 f = __ldg(tab + (size_t)k * nlow + t);
+    x = fma(-f.x, x, d[k]);
+    d[k] = x;
+  }
+  if (k0 == 1) {
+    double mean = 0;
+    for (int k = 0; k < nz; ++k) mean += __ldg(a.dz + k) * d[k];
+    mean /= a.lz;
+    for (int k = 0; k < nz; ++k) d[k] -= mean;
+  }
+  for (int k = 0; k < nz; ++k) S[k * plane + col] = (TS)d[k];
+}
+
+template <typename TS>
+__global__ void k_zlow64(ZArgs a, const int2* __restrict__ modes, int nlow, const double2* __restrict__ tab,
+                         double* scratch) {
   if (launch_skipped(a.skip_conv, a.skip_k, a.tol2)) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nlow) return;
-  const int2 m = modes[t];
-  const int nz = a.nz;
-  const size_t plane = (size_t)a.nx * a.ny;
-  float* S = reinterpret_cast<float*>(a.S);
-  const size_t col = (size_t)m.y * a.nx + m.x;
-  double* d = scratch + (size_t)t * 3 * nz;
-  for (int k = 0; k < nz; ++k) d[k] = (double)S[k * plane + col];
-  Col<double> dd = {d, 1}, cc = {d + nz, 1}, zz = {d + 2 * nz, 1};
-  solve_column<double>(a, m.x, m.y, dd, cc, zz);
-  for (int k = 0; k < nz; ++k) S[k * plane + col] = (float)d[k];
+  zlow_system<TS>(a, modes[t], t, nlow, tab, scratch);
 }
 
 // ---- factorisation tables (bounded z, FP64 path) -------------------------------------------------------

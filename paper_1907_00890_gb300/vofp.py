@@ -13,7 +13,7 @@ import numpy as np
 from .build import LIB
 
 BC = {"P": 0, "NN": 1, "DD": 2, "ND": 3, "DN": 4}
-FP64, MIXED = 0, 1
+FP64, MIXED, FF = 0, 1, 2
 
 if not os.path.exists(LIB):
     raise ImportError("vofp library not built: %s is missing (run paper_1907_00890_gb300.build.build())" % LIB)

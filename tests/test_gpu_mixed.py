@@ -122,3 +122,45 @@ def test_mixed_manufactured_512_stretched(vp):
     assert np.linalg.norm(res) / np.linalg.norm(f) < TOL
     assert info["rel_residual"] <= TOL
     plan.close()
+
+
+@pytest.mark.parametrize("bcx,bcy,bcz", [("P", "P", "NN"), ("NN", "DD", "DN"), ("DD", "P", "P"), ("P", "NN", "ND")])
+@pytest.mark.parametrize("max_refine", [0, 6])
+def test_ff_poisson(vp, bcx, bcy, bcz, max_refine):
+    """FP32-pair transforms: the direct solve alone is within 1e-10; with its confirming correction too."""
+    n = (40, 28, 36)
+    bc = (bcx, bcy, bcz)
+    dz = synth.stretched_dz(n[2]) if bcz != "P" else synth.uniform_dz(n[2])
+    g = oracle.Grid(*n, 1.0 / n[0], 0.8 / n[1], dz, bc)
+    f = synth.rng(41).standard_normal(g.shape)
+    ref, _ = oracle.poisson_solve(g, f)
+    plan = vp.Plan(n, g.widths[0][0], g.widths[1][0], dz, bc, prec=vp.FF, max_refine=max_refine)
+    p, info = plan.poisson_solve(dev(f), info=True)
+    assert rel(host(p), ref) < TOL, info
+    assert info["rel_residual"] <= TOL and info["refine_iters"] <= max(max_refine, 0)
+    plan.close()
+
+
+def test_ff_project_extend_128(vp):
+    c = synth.config_droplet(128)
+    g = oracle.Grid(*c["n"], c["dx"], c["dy"], c["dz"], c["bc"])
+    s = oracle.stefan_source(g, c["C"], c["mdot"], c["rho1"], c["rho2"])
+    ou = oracle.project(g, c["u"], c["v"], c["w"], src=s, dt_over_rho0=c["dt_over_rho0"])
+    oe = oracle.extend_liquid_velocity(g, *ou[:3], c["C"], c["mdot"], c["rho1"], c["rho2"])
+    import torch
+    for mr in (0, 6):
+        plan = vp.Plan(c["n"], c["dx"], c["dy"], c["dz"], c["bc"], prec=vp.FF, max_refine=mr)
+        u = [dev(a) for a in (c["u"], c["v"], c["w"])]
+        p = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+        ue = [torch.empty_like(a) for a in u]
+        ug = [torch.empty_like(a) for a in u]
+        phi = torch.empty_like(p)
+        vp.vofp_project_extend(plan.handle, *u, dev(c["C"]), dev(c["mdot"]), c["rho1"], c["rho2"],
+                               c["dt_over_rho0"], p, *ue, *ug, phi)
+        assert rel(host(p), ou[3]) < TOL
+        for a in range(3):
+            assert rel(host(u[a]), ou[a]) < TOL
+            assert rel(host(ue[a]), oe[a]) < TOL
+            assert rel(host(ug[a]), oe[3 + a]) < TOL
+        assert rel(host(phi), oe[6]) < TOL
+        plan.close()
