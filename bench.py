@@ -51,10 +51,10 @@ def parse():
 
 def bench_mixed_step(vofp, c, u0, C, md, st, flush, args, prec=None, max_refine=6):
     """The same droplet step through a reduced-precision plan (FP32 or FP32-pair transforms + FP64
-    refinement)."""
+    low modes, reductions and refinement)."""
     import torch
-    plan = vofp.Plan(c["n"], c["dx"], c["dy"], c["dz"], c["bc"], prec=vofp.MIXED if prec is None else prec,
-                     max_refine=max_refine)
+    prec = vofp.MIXED if prec is None else prec
+    plan = vofp.Plan(c["n"], c["dx"], c["dy"], c["dz"], c["bc"], prec=prec, max_refine=max_refine)
     u = [x.clone() for x in u0]
     p = torch.empty(plan.cell_shape, dtype=torch.float64, device=u0[0].device)
     phi = torch.empty_like(p)
@@ -92,33 +92,114 @@ def bench_mixed_step(vofp, c, u0, C, md, st, flush, args, prec=None, max_refine=
                                        c["dt_over_rho0"], p, ue[0], ue[1], ue[2], ug[0], ug[1], ug[2], phi,
                                        info=True)
     cells = int(np.prod(c["n"]))
+    rs = 8 if prec == vofp.FF else 4
     out = {"value": cells * 2 / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
-           "dtype": "f32+f64" if prec in (None, vofp.MIXED) else "f32x2+f64", "max_refine": max_refine,
+           "dtype": "f32+f64" if prec == vofp.MIXED else "f32x2+f64", "max_refine": max_refine,
            "refine_iters_both_solves": info["refine_iters"], "rel_residual": info["rel_residual"],
            "per_kernel_ms": {k: round(v[0] / v[1], 5) for k, v in trace.items()},
-           "roofline": roofline_mixed(trace, c["n"])}
+           "per_step_ms": {k: round(v[0] / args.steps, 5) for k, v in trace.items()},
+           "roofline": roofline_mixed(trace, c["n"], rs)}
     # outputs compared with the oracle's step (ue, ug, phi in the oracle's order) by the caller
     out["_outputs"] = [x.cpu().numpy() for x in ue] + [x.cpu().numpy() for x in ug] + [phi.cpu().numpy()]
     plan.close()
     return out
 
 
-def roofline_mixed(trace, n):
-    """HBM roofline of the dominant kernel of the mixed step (FP32 spectrum, FP64 fields)."""
-    if not trace:
+def mixed_bytes_per_cell(rs):
+    """Algorithmic HBM bytes per cell of each kernel class of the refinement path (rs: bytes per spectrum
+    value, 4 for FP32, 8 for FP32 pairs; fields FP64)."""
+    return {"x_forward_div": 24 + 8 + rs, "x_forward": 8 + 8 + rs, "residual_update": 8 + 8 + rs,
+            "y_forward": 2 * rs, "y_inverse": 2 * rs, "z_tridiag": 2 * rs, "x_inverse": rs + 16,
+            "grad_update": 56, "extend_epilogue": 96, "stefan_source": 48}
+
+
+def roofline_mixed(trace, n, rs=4):
+    """HBM roofline of the dominant kernel of the refinement path (among the kernel classes that touch every
+    cell; the low-mode, gauge and reporting kernels touch a few columns or run once)."""
+    per = mixed_bytes_per_cell(rs)
+    cand = {k: v for k, v in trace.items() if k in per}
+    if not cand:
         return None
-    name = max(trace, key=lambda k: trace[k][0])
-    tot, cnt = trace[name]
-    nx, ny, nz = n
-    cells = nx * ny * nz
-    per = {"x_forward_div": 24 + 8 + 4, "x_forward": 8 + 8 + 4, "residual_update": 8 + 8 + 4, "y_forward": 8,
-           "y_inverse": 8, "z_tridiag": 8, "x_inverse": 4 + 16, "grad_update": 56, "extend_epilogue": 96,
-           "stefan_source": 48}
-    by = per.get(name, 0) * cells
+    name = max(cand, key=lambda k: cand[k][0])
+    tot, cnt = cand[name]
+    cells = int(np.prod(n))
+    by = per[name] * cells
     hbm, how = peaks()
     gbs = by / (tot / cnt / 1e3) / 1e9
     return {"bound": "hbm", "kernel": name, "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-            "launches": cnt, "avg_launch_ms": tot / cnt, "peak_source": how}
+            "launches": cnt, "avg_launch_ms": tot / cnt, "bytes_per_cell": per[name], "peak_source": how,
+            "note": "averages include launches that returned at once after convergence"}
+
+
+def bench_large(vofp, args):
+    """512^3 pressure projection, stretched z (tanh clustering, ratio 1.05), P,P,NN, random face velocities:
+    refinement path (FP32 transforms + FP64 low modes / reductions / defect correction), FP32-pair direct
+    solve, and the plain FP64 path.  Error stated against the FP64 GPU path (parity-tested against the oracle
+    at sizes the oracle finishes) and as the FP64 residual of the returned p."""
+    import torch
+    from paper_1907_00890_gb300 import synth
+    n = (512, 512, 512)
+    bc = ("P", "P", "NN")
+    dz = synth.stretched_dz(n[2])
+    dx = dy = 1.0 / n[0]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.BASE_SEED + 7)
+    fs = synth.face_shapes(n, bc)
+    u0 = [torch.randn(s, generator=gen, dtype=torch.float64, device="cuda") for s in fs]
+    u0[2][0].zero_()
+    u0[2][-1].zero_()
+    u = [x.clone() for x in u0]
+    p = torch.empty(n[::-1], dtype=torch.float64, device="cuda")
+    ref = None
+    out = {"workload": "pressure projection 512^3, stretched z (tanh, ratio 1.05), P,P,NN, N(0,1) face velocities; "
+                       "one solve per call, inputs > L2"}
+    reps = max(3, min(args.steps, 8))
+    for name, prec, mr in (("fp64", vofp.FP64, 1), ("mixed", vofp.MIXED, 6), ("ff", vofp.FF, 0)):
+        plan = vofp.Plan(n, dx, dy, dz, bc, prec=prec, max_refine=mr)
+        st = torch.cuda.current_stream()
+
+        def call(info=False):
+            return vofp.vofp_project(plan.handle, u[0], u[1], u[2], None, 1.0, p, info=info)
+
+        for _ in range(2):
+            for a, b in zip(u, u0):
+                a.copy_(b)
+            call()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        vofp.vofp_trace_collect()
+        vofp.vofp_trace_enable(True)
+        for i in range(reps):
+            for a, b in zip(u, u0):
+                a.copy_(b)
+            ev[i][0].record(st)
+            call()
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+        vofp.vofp_trace_enable(False)
+        trace = vofp.vofp_trace_collect()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        for a, b in zip(u, u0):
+            a.copy_(b)
+        _, info = call(info=True)
+        cells = int(np.prod(n))
+        r = {"value": cells / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_solve": ms, "solves_per_s": 1e3 / ms,
+             "rel_residual": info["rel_residual"], "refine_iters": info["refine_iters"],
+             "per_step_ms": {k: round(v[0] / reps, 4) for k, v in trace.items()}}
+        if prec == vofp.FP64:
+            ref = p.clone()
+            r["dtype"] = "f64"
+            r["roofline"] = roofline_from_trace(trace, n)
+        else:
+            r["dtype"] = "f32+f64" if prec == vofp.MIXED else "f32x2+f64"
+            r["rel_err_vs_fp64"] = float(torch.linalg.vector_norm(p - ref) / torch.linalg.vector_norm(ref))
+            r["roofline"] = roofline_mixed(trace, n, 8 if prec == vofp.FF else 4)
+        out[name] = r
+        plan.close()
+        torch.cuda.empty_cache()
+    del u, u0, p, ref
+    torch.cuda.empty_cache()
+    return out
 
 
 def bench_batched(vofp, args):
@@ -482,6 +563,8 @@ def run_ours(args):
         variants["ff_step"] = bench_mixed_step(vofp, c, u0, C, md, st, flush, args, prec=vofp.FF, max_refine=0)
         variants["ff_step_confirmed"] = bench_mixed_step(vofp, c, u0, C, md, st, flush, args, prec=vofp.FF)
         torch.cuda.empty_cache()
+        variants["large_512"] = bench_large(vofp, args)
+        torch.cuda.empty_cache()
         variants["batched"] = bench_batched(vofp, args)
         torch.cuda.empty_cache()
         variants["served"] = bench_served(vofp, args)
@@ -542,8 +625,9 @@ def algorithmic(kname, n):
     """Algorithmic HBM bytes and FP64 flops of one launch of kernel class ``kname`` on an n-grid.
 
     Bytes: each compulsory array read or written once (8 B per FP64 value).  Flops: a real-to-real transform
-    of length m counts 2.5 m log2 m per line (half the 5 m log2 m of a complex FFT); the z recurrence 8 per
-    point (plus one division); stencils their adds and multiplies.
+    of length m counts 2.5 m log2 m per line (half the 5 m log2 m of a complex FFT); the z recurrence with
+    plan-time factors 6 per point (forward multiply-add and multiply, back multiply-add, output scale);
+    stencils their adds and multiplies.
     """
     nx, ny, nz = n
     cells = nx * ny * nz
@@ -558,7 +642,7 @@ def algorithmic(kname, n):
         "x_forward_div_stefan": (48, 26 + 2.5 * lg(nx)),
         "y_forward": (16, 2.5 * lg(ny)),
         "y_inverse": (16, 2.5 * lg(ny)),
-        "z_tridiag": (16, 8),
+        "z_tridiag": (16, 6),
         "x_inverse": (16, 2.5 * lg(nx)),
         "grad_update": (56, 12),
         "extend_epilogue": (96, 60),

@@ -59,14 +59,17 @@ __global__ void __launch_bounds__(128) k_zsolve_batch(const ZArgs* __restrict__ 
   zsolve_block<float, float>(a, l % gx, l / gx, smem_raw);
 }
 
+// Per-instance z records: the low-eigenvalue systems and (bounded z) the factor-table arguments.
 struct LowArgs {
   const int2* modes;
   int nlow;
   const double2* tab;
   double* scratch;
+  ZTabArgs zt;
+  int smem_d;  // factor-table kernel: forward values in shared memory
 };
 
-// low-eigenvalue systems of all instances: thread t of the flattened list
+// low-eigenvalue systems of all instances, periodic z: thread t of the flattened list
 __global__ void k_zlow_batch(const ZArgs* __restrict__ args, const LowArgs* __restrict__ low,
                              const int* __restrict__ off, int n, int total) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -77,6 +80,32 @@ __global__ void k_zlow_batch(const ZArgs* __restrict__ args, const LowArgs* __re
   const int q = t - __ldg(off + i);
   const LowArgs& L = low[i];
   zlow_system<float>(a, L.modes[q], q, L.nlow, L.tab, L.scratch);
+}
+
+// Bounded z: factor-table systems of all instances, 128 per block (one per thread).
+__global__ void __launch_bounds__(128) k_ztab_batch(const ZArgs* __restrict__ args, const LowArgs* __restrict__ inst,
+                                                    const int* __restrict__ off, int n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int i = find_instance(off, n, blockIdx.x);
+  const ZArgs& a = args[i];
+  const LowArgs& L = inst[i];
+  const int l = blockIdx.x - __ldg(off + i);
+  const int gx = (a.nx + 127) / 128;
+  ztab_block<float, float2>(a, L.zt, L.smem_d, l % gx, l / gx, smem_raw);
+}
+
+// Bounded z: low-eigenvalue systems of all instances, one warp each.
+__global__ void __launch_bounds__(128) k_zlow_scan_batch(const ZArgs* __restrict__ args,
+                                                         const LowArgs* __restrict__ low, const int* __restrict__ off,
+                                                         int n, int total) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= total) return;  // uniform per warp
+  const int i = find_instance(off, n, w);
+  const ZArgs& a = args[i];
+  if (launch_skipped(a.skip_conv, a.skip_k, a.tol2)) return;
+  const int q = w - __ldg(off + i);
+  const LowArgs& L = low[i];
+  zlow_scan_system<float>(a, L.modes[q], q, L.nlow, L.tab, L.scratch, threadIdx.x & 31);
 }
 
 template <typename T, typename C>
@@ -159,6 +188,7 @@ struct vofp_batch {
   size_t o_x, o_yf, o_yi, o_z, o_xi, o_low, o_epi;  // per-solve stride arrays start offsets
   size_t o_offx, o_offy, o_offz, o_offlow, o_offepi;
   int tot_x, tot_y, tot_z, tot_low, tot_epi;
+  bool ztab;  // every instance has a bounded z axis: factor-table z kernels
   size_t sm_x, sm_y, sm_z;
   cudaGraphExec_t exec;
   cudaStream_t captured_on;
@@ -237,20 +267,24 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
   int* offe = (int*)(b->hstage + b->o_offepi);
   offx[0] = offy[0] = offz[0] = offl[0] = offe[0] = 0;
   b->sm_x = b->sm_y = b->sm_z = 0;
+  b->ztab = true;
+  for (int i = 0; i < n; ++i)
+    if (!plans[i]->ztab) b->ztab = false;
   for (int i = 0; i < n; ++i) {
     const vofp_plan* p = plans[i];
     const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
     offx[i + 1] = offx[i] + xpass_blocks(ny, nz, p->xpb);
     offy[i + 1] = offy[i] + (ny > 1 ? ((nx + p->ytx32 - 1) / p->ytx32) * nz : 0);
-    offz[i + 1] = offz[i] + ((nx + p->zti32 - 1) / p->zti32) * ny;
+    offz[i + 1] = offz[i] + (b->ztab ? (nx + 127) / 128 : (nx + p->zti32 - 1) / p->zti32) * ny;
     offl[i + 1] = offl[i] + p->nlow;
     const size_t faces = total_faces(grid_dev(p));
     int eb = (int)((faces + 255) / 256);
     if (eb > 512) eb = 512;
     offe[i + 1] = offe[i] + eb;
     const size_t sx = 2 * (size_t)p->xpb * nx * sizeof(float2);
-    const size_t sy = 2 * (size_t)(p->ytx32 / 2) * ny * sizeof(float2);
-    const size_t sz = (size_t)(p->bc[2] == VOFP_BC_P ? 3 : 2) * p->zti32 * nz * sizeof(float);
+    const size_t sy = 2 * (size_t)(p->ytx32 / 2) * y_ld(ny) * sizeof(float2);
+    const ZTabShape zs = ztab_shape(128, nz, sizeof(float));
+    const size_t sz = b->ztab ? zs.smem : (size_t)(p->bc[2] == VOFP_BC_P ? 3 : 2) * p->zti32 * nz * sizeof(float);
     if (sx > b->sm_x) b->sm_x = sx;
     if (sy > b->sm_y) b->sm_y = sy;
     if (sz > b->sm_z) b->sm_z = sz;
@@ -265,6 +299,7 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
   allow_smem(k_ypass_batch<float, float2, false>);
   allow_smem(k_ypass_batch<float, float2, true>);
   allow_smem(k_zsolve_batch);
+  allow_smem(k_ztab_batch);
   allow_smem(k_xinv_batch<float, float2>);
   *out = b;
   return VOFP_OK;
@@ -356,6 +391,7 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
       xi.skip_k = ya.skip_k;
       xi.tol2 = tol2;
       xi.dz = pl->dz;
+      xi.dzff = pl->dzff;
       xi.mean_out = pl->singular ? conv + VOFP_CONV_MEAN : nullptr;
       xi.d2_out = conv + VOFP_CONV_DEL + s;
       if (off) xa.skip_k = ya.skip_k = za.skip_k = xi.skip_k = -2;  // beyond this instance's own limit
@@ -369,6 +405,8 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
     L[i].nlow = pl->nlow;
     L[i].scratch = pl->lowscratch;
     L[i].tab = pl->lowtab;
+    L[i].zt = ztab_args(pl);
+    L[i].smem_d = ztab_shape(128, pl->n[2], sizeof(float)).smem_d;
     EpiArgs e;
     e.g = grid_dev(pl);
     e.p = pout;
@@ -406,14 +444,21 @@ static void launch_sequence(vofp_batch* b, cudaStream_t st) {
       VOFP_LAUNCH(KID_RESID, st, (k_xfwd_batch<float, float2, RHS_RESID><<<b->tot_x, 256, b->sm_x, st>>>(X, offx, n)));
     if (b->tot_y > 0)
       VOFP_LAUNCH(KID_YFWD, st, (k_ypass_batch<float, float2, false><<<b->tot_y, 256, b->sm_y, st>>>(YF, offy, n)));
-    VOFP_LAUNCH(KID_ZSOLVE, st, k_zsolve_batch<<<b->tot_z, 128, b->sm_z, st>>>(Z, offz, n));
-    if (b->tot_low > 0)
-      VOFP_LAUNCH(KID_ZSOLVE, st, k_zlow_batch<<<(b->tot_low + 63) / 64, 64, 0, st>>>(Z, L, offl, n, b->tot_low));
+    if (b->ztab) {
+      VOFP_LAUNCH(KID_ZSOLVE, st, k_ztab_batch<<<b->tot_z, 128, b->sm_z, st>>>(Z, L, offz, n));
+      if (b->tot_low > 0)
+        VOFP_LAUNCH(KID_ZLOW, st,
+                    k_zlow_scan_batch<<<(b->tot_low + 3) / 4, 128, 0, st>>>(Z, L, offl, n, b->tot_low));
+    } else {
+      VOFP_LAUNCH(KID_ZSOLVE, st, k_zsolve_batch<<<b->tot_z, 128, b->sm_z, st>>>(Z, offz, n));
+      if (b->tot_low > 0)
+        VOFP_LAUNCH(KID_ZLOW, st, k_zlow_batch<<<(b->tot_low + 63) / 64, 64, 0, st>>>(Z, L, offl, n, b->tot_low));
+    }
     if (b->tot_y > 0)
       VOFP_LAUNCH(KID_YINV, st, (k_ypass_batch<float, float2, true><<<b->tot_y, 256, b->sm_y, st>>>(YI, offy, n)));
     VOFP_LAUNCH(KID_XINV, st, (k_xinv_batch<float, float2><<<b->tot_x, 256, b->sm_x, st>>>(XI, offx, n)));
   }
-  VOFP_LAUNCH(KID_BATCHED, st, k_shift_batch<<<b->tot_epi, 256, 0, st>>>(E, offe, n));
+  VOFP_LAUNCH(KID_GAUGE, st, k_shift_batch<<<b->tot_epi, 256, 0, st>>>(E, offe, n));
   VOFP_LAUNCH(KID_GRAD, st, k_grad_batch<<<b->tot_epi, 256, 0, st>>>(E, offe, n));
 }
 

@@ -83,4 +83,12 @@ __device__ __forceinline__ ff& operator/=(ff& a, ff b) {
   return a;
 }
 
+// Exact widening of a reduced-precision value to a pair, and its leading FP32 part.
+__host__ __device__ __forceinline__ ff ff_of(float x) { return ff(x, 0.0f); }
+__host__ __device__ __forceinline__ ff ff_of(ff x) { return x; }
+__host__ __device__ __forceinline__ float lead(float x) { return x; }
+__host__ __device__ __forceinline__ float lead(ff x) { return x.hi; }
+__host__ __device__ __forceinline__ ff ff_of(double x) { return ff(x); }
+__host__ __device__ __forceinline__ float lead(double x) { return (float)x; }
+
 }  // namespace vofp

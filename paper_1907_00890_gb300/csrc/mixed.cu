@@ -10,6 +10,7 @@
 // the FP64 volume-weighted mean of f, not the reduced-precision spectrum's), and the gauge of p (zero
 // volume-weighted mean) is restored in FP64 at the end from the exact sums of the corrections.
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "passes.cuh"
@@ -25,7 +26,7 @@ static void allow_smem(K kern) {
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
 }
 
-template <typename T, typename C>
+template <typename T, typename C, typename TT>
 static void allow_all() {
   allow_smem(k_xfwd<T, C, RHS_F>);
   allow_smem(k_xfwd<T, C, RHS_DIV>);
@@ -35,11 +36,13 @@ static void allow_all() {
   allow_smem(k_ypass<T, C, true>);
   allow_smem(k_xinv<T, C>);
   allow_smem(k_zsolve<T, T>);
+  allow_smem(k_ztab<T, TT>);
+  allow_smem(k_ztab_staged<T, TT>);
 }
 
 void init_kernel_attributes_mixed() {
-  allow_all<float, float2>();
-  allow_all<ff, cff>();
+  allow_all<float, float2, float2>();
+  allow_all<ff, cff, cff>();
 }
 
 int build_low_factors(vofp_plan* pl, cudaStream_t st, bool sync) {
@@ -83,12 +86,14 @@ struct Red;
 template <>
 struct Red<float> {
   typedef float2 C;
+  typedef float2 TT;  // z factor pair
   static const void* tw(const AxisDev& a) { return a.tw32; }
   static const void* quart(const AxisDev& a) { return a.quart32; }
 };
 template <>
 struct Red<ff> {
   typedef cff C;
+  typedef cff TT;
   static const void* tw(const AxisDev& a) { return a.twff; }
   static const void* quart(const AxisDev& a) { return a.quartff; }
 };
@@ -112,7 +117,7 @@ static void solve_red(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, b
   ya.skip_k = skip_k;
   ya.tol2 = tol2;
   const dim3 ygrid((nx + ya.tx - 1) / ya.tx, nz);
-  const size_t ysm = 2 * (size_t)(ya.tx / 2) * ny * sizeof(C);
+  const size_t ysm = 2 * (size_t)(ya.tx / 2) * y_ld(ny) * sizeof(C);
   if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, (k_ypass<R, C, false><<<ygrid, 256, ysm, st>>>(ya)));
   ZArgs za = z_args(pl, stats);
   za.S = pl->S32;
@@ -121,14 +126,35 @@ static void solve_red(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, b
   za.skip_conv = pl->conv;
   za.skip_k = skip_k;
   za.tol2 = tol2;
-  const int nvec = pl->bc[2] == VOFP_BC_P ? 3 : 2;
-  const dim3 zgrid((nx + za.ti - 1) / za.ti, ny);
-  const size_t zsm = (size_t)nvec * za.ti * nz * sizeof(R);
-  VOFP_LAUNCH(KID_ZSOLVE, st, (k_zsolve<R, R><<<zgrid, 128, zsm, st>>>(za)));
-  if (pl->nlow > 0)
-    VOFP_LAUNCH(KID_ZSOLVE, st,
-                k_zlow64<R><<<(pl->nlow + 63) / 64, 64, 0, st>>>(za, pl->lowmodes, pl->nlow, pl->lowtab,
-                                                                 pl->lowscratch));
+  if (pl->ztab) {
+    // bulk systems from the factor table; the low-eigenvalue ones (a prefix of each row) by one warp each.
+    // FP32-pair recurrences on small grids: the shared-memory staged kernel (FP32 latency needs no staging)
+    if (!std::is_same<R, float>::value && ztab_use_staged(nx, ny, nz, sizeof(R))) {
+      const dim3 tgrid((nx + kZStagedTI - 1) / kZStagedTI, ny);
+      VOFP_LAUNCH(KID_ZSOLVE, st,
+                  (k_ztab_staged<R, typename Red<R>::TT><<<tgrid, 128, ztab_staged_smem(nz, sizeof(R)), st>>>(
+                      za, ztab_args(pl))));
+    } else {
+      const ZTabShape zs = ztab_shape(pl->zti32, nz, sizeof(R));
+      const dim3 tgrid((nx + zs.threads - 1) / zs.threads, ny);
+      VOFP_LAUNCH(KID_ZSOLVE, st,
+                  (k_ztab<R, typename Red<R>::TT><<<tgrid, zs.threads, zs.smem, st>>>(za, ztab_args(pl),
+                                                                                     zs.smem_d)));
+    }
+    if (pl->nlow > 0)
+      VOFP_LAUNCH(KID_ZLOW, st,
+                  k_zlow_scan<R><<<(pl->nlow + 3) / 4, 128, 0, st>>>(za, pl->lowmodes, pl->nlow, pl->lowtab,
+                                                                     pl->lowscratch));
+  } else {
+    const int nvec = pl->bc[2] == VOFP_BC_P ? 3 : 2;
+    const dim3 zgrid((nx + za.ti - 1) / za.ti, ny);
+    const size_t zsm = (size_t)nvec * za.ti * nz * sizeof(R);
+    VOFP_LAUNCH(KID_ZSOLVE, st, (k_zsolve<R, R><<<zgrid, 128, zsm, st>>>(za)));
+    if (pl->nlow > 0)
+      VOFP_LAUNCH(KID_ZLOW, st,
+                  k_zlow64<R><<<(pl->nlow + 63) / 64, 64, 0, st>>>(za, pl->lowmodes, pl->nlow, nullptr,
+                                                                   pl->lowscratch));
+  }
   if (ny > 1) VOFP_LAUNCH(KID_YINV, st, (k_ypass<R, C, true><<<ygrid, 256, ysm, st>>>(ya)));
 }
 
@@ -152,6 +178,7 @@ static void xinv_red(vofp_plan* pl, double* pout, int accumulate, int skip_k, do
   xi.skip_k = skip_k;
   xi.tol2 = tol2;
   xi.dz = pl->dz;
+  xi.dzff = pl->dzff;
   xi.mean_out = pl->singular ? pl->conv + VOFP_CONV_MEAN : nullptr;
   xi.d2_out = d2_out;
   const int xgrid = xpass_blocks(xi.ny, xi.nz, xi.pb);
@@ -234,14 +261,14 @@ int mixed_solve(vofp_plan* pl, int mode, const XArgs* xin, const double* f, doub
   else
     refine_sequence<float>(pl, mode, xa, pout, M, tol2, stats, st);
   if (info) {
-    VOFP_LAUNCH(KID_RESID, st,
+    VOFP_LAUNCH(KID_RESNORM, st,
                 k_resid_norm<<<grid_blocks(cells, 256), 256, 0, st>>>(
                     grid_dev(pl), pl->F, pout, pl->singular ? conv + 1 : nullptr, 1.0 / pl->volume,
                     conv + VOFP_CONV_FINAL, conv, -1, tol2));
   }
   if (pl->singular && pout != pl->P) {
     const double scale = 1.0 / ((double)pl->n[0] * pl->n[1] * (pl->volume / (pl->n[0] * pl->dx * pl->n[1] * pl->dy)));
-    VOFP_LAUNCH(KID_RESID, st,
+    VOFP_LAUNCH(KID_GAUGE, st,
                 k_shift<<<grid_blocks(cells, 256), 256, 0, st>>>(pout, cells, conv + VOFP_CONV_MEAN, scale));
   }
   if (cudaGetLastError() != cudaSuccess) return VOFP_ERR_CUDA;

@@ -206,7 +206,7 @@ extern "C" int vofp_poisson_solve_noalloc(int nx, int ny, int nz, double dx, dou
   pl.info = nullptr;
   pl.xpb = nx >= 1024 ? 1 : (1024 / nx > 16 ? 16 : 1024 / nx);
   int tx = 16;
-  while (tx > 2 && (size_t)16 * tx * ny > 96 * 1024) tx -= 2;
+  while (tx > 2 && (size_t)16 * tx * y_ld(ny) > 96 * 1024) tx -= 2;
   pl.ytx = tx;
   const int nvec = bc[2] == VOFP_BC_P ? 3 : 2;
   int ti = 32;

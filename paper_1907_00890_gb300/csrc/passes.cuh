@@ -9,6 +9,8 @@
 // The spectrum S is stored [z][y][x] like the fields, one real number per cell.
 #pragma once
 
+#include <type_traits>
+
 #include "stencil.cuh"
 #include "vofp_internal.cuh"
 
@@ -47,44 +49,44 @@ struct XArgs {
   void* S;            // spectrum output
 };
 
-// 7-point L p at a cell with the ghost rules of the MAC operator (FP64, reciprocal spacings: no divisions).
+// 7-point L p at a cell with the ghost rules of the MAC operator, as a weighted sum of the neighbours with
+// per-plane coefficients (rdx2, rdy2, czp, czm, and czc for the centre): two additions and five
+// multiply(-add)s in FP64.
 __device__ __forceinline__ double lap_at(const GridDev& g, const double* __restrict__ p, int i, int j, int k) {
   const size_t plane = (size_t)g.nx * g.ny;
   const size_t c = k * plane + (size_t)j * g.nx + i;
   const double pc = __ldg(p + c);
-  double xs, ys;
+  double xs, ys, zlo, zhi;
   {
     double lo, hi;
     if (i > 0) lo = __ldg(p + c - 1);
-    else lo = g.bcx == VOFP_BC_P ? __ldg(p + c + g.nx - 1) : (g.bcx == VOFP_BC_DD ? -pc : pc);
+    else lo = g.bcx == VOFP_BC_P ? __ldg(p + c + g.nx - 1) : neg_if(pc, g.bcx == VOFP_BC_DD);
     if (i < g.nx - 1) hi = __ldg(p + c + 1);
-    else hi = g.bcx == VOFP_BC_P ? __ldg(p + c - (g.nx - 1)) : (g.bcx == VOFP_BC_DD ? -pc : pc);
+    else hi = g.bcx == VOFP_BC_P ? __ldg(p + c - (g.nx - 1)) : neg_if(pc, g.bcx == VOFP_BC_DD);
     xs = hi + lo;
   }
   {
     double lo, hi;
     if (j > 0) lo = __ldg(p + c - g.nx);
-    else lo = g.bcy == VOFP_BC_P ? __ldg(p + c + (size_t)(g.ny - 1) * g.nx) : (g.bcy == VOFP_BC_DD ? -pc : pc);
+    else lo = g.bcy == VOFP_BC_P ? __ldg(p + c + (size_t)(g.ny - 1) * g.nx) : neg_if(pc, g.bcy == VOFP_BC_DD);
     if (j < g.ny - 1) hi = __ldg(p + c + g.nx);
-    else hi = g.bcy == VOFP_BC_P ? __ldg(p + c - (size_t)(g.ny - 1) * g.nx) : (g.bcy == VOFP_BC_DD ? -pc : pc);
+    else hi = g.bcy == VOFP_BC_P ? __ldg(p + c - (size_t)(g.ny - 1) * g.nx) : neg_if(pc, g.bcy == VOFP_BC_DD);
     ys = hi + lo;
   }
-  double r = fma(xs, g.rdx2, fma(ys, g.rdy2, -2.0 * (g.rdx2 + g.rdy2) * pc));
   {
-    double lo, hi;
     const bool lowN = g.bcz == VOFP_BC_NN || g.bcz == VOFP_BC_ND;
     const bool highN = g.bcz == VOFP_BC_NN || g.bcz == VOFP_BC_DN;
-    if (k > 0) lo = __ldg(p + c - plane);
-    else lo = g.bcz == VOFP_BC_P ? __ldg(p + c + (size_t)(g.nz - 1) * plane) : (lowN ? pc : -pc);
-    if (k < g.nz - 1) hi = __ldg(p + c + plane);
-    else hi = g.bcz == VOFP_BC_P ? __ldg(p + c - (size_t)(g.nz - 1) * plane) : (highN ? pc : -pc);
-    r = fma(((hi - pc) * __ldg(g.rhz + k + 1) - (pc - lo) * __ldg(g.rhz + k)), __ldg(g.rdz + k), r);
+    if (k > 0) zlo = __ldg(p + c - plane);
+    else zlo = g.bcz == VOFP_BC_P ? __ldg(p + c + (size_t)(g.nz - 1) * plane) : neg_if(pc, !lowN);
+    if (k < g.nz - 1) zhi = __ldg(p + c + plane);
+    else zhi = g.bcz == VOFP_BC_P ? __ldg(p + c - (size_t)(g.nz - 1) * plane) : neg_if(pc, !highN);
   }
-  return r;
+  return fma(xs, g.rdx2,
+             fma(ys, g.rdy2, fma(__ldg(g.czc + k), pc, fma(__ldg(g.czp + k), zhi, __ldg(g.czm + k) * zlo))));
 }
 
 template <int MODE>
-__device__ __forceinline__ double rhs_at(const XArgs& a, int i, int j, int k) {
+__device__ __forceinline__ double rhs_at(const XArgs& a, int i, int j, int k, double fbar) {
   const size_t c = ((size_t)k * a.g.ny + j) * a.g.nx + i;
   double f;
   if (MODE == RHS_F) {
@@ -101,8 +103,7 @@ __device__ __forceinline__ double rhs_at(const XArgs& a, int i, int j, int k) {
     const double s = __ldg(a.mdot + c) * a.coef * sqrt(gc.x * gc.x + gc.y * gc.y + gc.z * gc.z);
     f = (divergence_at(a.g, a.u, a.v, a.w, i, j, k) - s) * a.scale;
   } else {
-    f = __ldg(a.f + c) - lap_at(a.g, a.p, i, j, k);
-    if (a.defect_sum) f -= *a.defect_sum * a.inv_volume;
+    f = (__ldg(a.f + c) - fbar) - lap_at(a.g, a.p, i, j, k);
   }
   return f;
 }
@@ -134,40 +135,53 @@ __device__ __forceinline__ void xfwd_block(const XArgs& a, int bx, unsigned char
   const long pair0 = (long)bx * PB;
   const int bc = a.g.bcx;
   const bool stats = a.info || a.sq_out || a.fv_out || a.abs_out;
+  // FP64 plans keep every sum in FP64; reduced-precision plans keep only sum f V (the compatibility defect)
+  // in FP64 and accumulate the norms, which feed thresholds only, in FP32
+  constexpr bool f64 = std::is_same<T, double>::value;
+  const double fbar = (MODE == RHS_RESID && a.defect_sum) ? *a.defect_sum * a.inv_volume : 0.0;
   double acc_abs = 0, acc_sq = 0, acc_fv = 0;
+  float accf_abs = 0.0f, accf_sq = 0.0f;
   for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
     const int pb = t / n, i = t - pb * n;
     const long l0 = 2 * (pair0 + pb), l1 = l0 + 1;
     double fa = 0, fb = 0;
-    if (l0 < nlines) {
-      const int k = (int)(l0 / a.g.ny), j = (int)(l0 - (long)k * a.g.ny);
-      fa = rhs_at<MODE>(a, i, j, k);
-      if (a.fsave) a.fsave[l0 * n + i] = fa;
-      if (stats) {
-        const double vol = a.g.dx * a.g.dy * __ldg(a.g.dz + k);
-        acc_abs += fabs(fa) * vol;
-        acc_sq += fa * fa;
-        acc_fv += fa * vol;
-      }
-    }
-    if (l1 < nlines) {
-      const int k = (int)(l1 / a.g.ny), j = (int)(l1 - (long)k * a.g.ny);
-      fb = rhs_at<MODE>(a, i, j, k);
-      if (a.fsave) a.fsave[l1 * n + i] = fb;
-      if (stats) {
-        const double vol = a.g.dx * a.g.dy * __ldg(a.g.dz + k);
-        acc_abs += fabs(fb) * vol;
-        acc_sq += fb * fb;
-        acc_fv += fb * vol;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long l = h ? l1 : l0;
+      if (l < nlines) {
+        const int k = (int)(l / a.g.ny), j = (int)(l - (long)k * a.g.ny);
+        const double f = rhs_at<MODE>(a, i, j, k, fbar);
+        if (a.fsave) a.fsave[l * n + i] = f;
+        if (stats) {
+          if (f64) {
+            const double vol = __ldg(a.g.vol + k);
+            acc_abs = fma(fabs(f), vol, acc_abs);
+            acc_sq = fma(f, f, acc_sq);
+            acc_fv = fma(f, vol, acc_fv);
+          } else {
+            const float fs = (float)f;
+            accf_abs = fmaf(fabsf(fs), __ldg(a.g.volf + k), accf_abs);
+            accf_sq = fmaf(fs, fs, accf_sq);
+            if (a.fv_out) acc_fv = fma(f, __ldg(a.g.vol + k), acc_fv);
+          }
+        }
+        if (h)
+          fb = f;
+        else
+          fa = f;
       }
     }
     int idx = i;
-    R sg = 1;
+    bool fl = false;
     if (bc != VOFP_BC_P) {
       idx = dct_perm(i, n);
-      if (bc == VOFP_BC_DD && (i & 1)) sg = -1;
+      fl = bc == VOFP_BC_DD && (i & 1);
     }
-    b0[pb * n + idx] = cmk<C>(sg * (R)fa, sg * (R)fb);
+    b0[pb * n + idx] = cmk<C>(neg_if((R)fa, fl), neg_if((R)fb, fl));
+  }
+  if (!f64) {
+    acc_abs = accf_abs;
+    acc_sq = accf_sq;
   }
   if (a.info || a.abs_out) {
     const double s1 = block_sum(acc_abs, red);
@@ -185,7 +199,7 @@ __device__ __forceinline__ void xfwd_block(const XArgs& a, int bx, unsigned char
     if (threadIdx.x == 0 && s3 != 0) atomicAdd(a.fv_out, s3);
   }
   __syncthreads();
-  const C* Z = fft_smem<C>(b0, b1, PB, a.fd, reinterpret_cast<const C*>(a.tw));
+  const C* Z = fft_smem<C>(b0, b1, PB, a.fd, reinterpret_cast<const C*>(a.tw), n);
   const C* quart = reinterpret_cast<const C*>(a.quart);
   T* S = reinterpret_cast<T*>(a.S);
   for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
@@ -231,7 +245,8 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
   const int n = a.ny;
   const int B = a.tx >> 1;
   C* b0 = reinterpret_cast<C*>(smem_raw);
-  C* b1 = b0 + B * n;
+  const int ld = y_ld(n);
+  C* b1 = b0 + B * ld;
   const int i0 = bx * a.tx;
   const size_t base = (size_t)by * a.ny * a.nx;
   T* S = reinterpret_cast<T*>(a.S);
@@ -245,20 +260,20 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
       const R va = i < a.nx ? (R)S[o] : (R)0;
       const R vb = i + 1 < a.nx ? (R)S[o + 1] : (R)0;
       int idx = j;
-      R sg = 1;
+      bool fl = false;
       if (bc != VOFP_BC_P) {
         idx = dct_perm(j, n);
-        if (bc == VOFP_BC_DD && (j & 1)) sg = -1;
+        fl = bc == VOFP_BC_DD && (j & 1);
       }
-      b0[c * n + idx] = cmk<C>(sg * va, sg * vb);
+      b0[c * ld + idx] = cmk<C>(neg_if(va, fl), neg_if(vb, fl));
     }
     __syncthreads();
-    const C* Z = fft_smem<C>(b0, b1, B, a.fd, reinterpret_cast<const C*>(a.tw));
+    const C* Z = fft_smem<C>(b0, b1, B, a.fd, reinterpret_cast<const C*>(a.tw), ld);
     for (int t = threadIdx.x; t < B * n; t += blockDim.x) {
       const int c = t % B, q = t / B;
       const int i = i0 + 2 * c;
       R oa, ob;
-      fwd_post<C>(Z + c * n, n, bc, q, quart, oa, ob);
+      fwd_post<C>(Z + c * ld, n, bc, q, quart, oa, ob);
       const size_t o = base + (size_t)q * a.nx + i;
       if (i < a.nx) S[o] = (T)oa;
       if (i + 1 < a.nx) S[o + 1] = (T)ob;
@@ -278,23 +293,23 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
       const int c = t / n, m = t - c * n;
       const R* ra = st + (2 * c) * n;
       const R* rb = st + (2 * c + 1) * n;
-      b0[c * n + m] = inv_pre<C>([&](int q) { return ra[q]; }, [&](int q) { return rb[q]; }, n, bc, m, quart);
+      b0[c * ld + m] = inv_pre<C>([&](int q) { return ra[q]; }, [&](int q) { return rb[q]; }, n, bc, m, quart);
     }
     __syncthreads();
-    const C* Y = fft_smem<C>(b0, b1, B, a.fd, reinterpret_cast<const C*>(a.tw));
+    const C* Y = fft_smem<C>(b0, b1, B, a.fd, reinterpret_cast<const C*>(a.tw), ld);
     for (int t = threadIdx.x; t < B * n; t += blockDim.x) {
       const int c = t % B, j = t / B;
       const int i = i0 + 2 * c;
       int idx = j;
-      R sg = 1;
+      bool fl = false;
       if (bc != VOFP_BC_P) {
         idx = dct_perm(j, n);
-        if (bc == VOFP_BC_DD && (j & 1)) sg = -1;
+        fl = bc == VOFP_BC_DD && (j & 1);
       }
-      const C y = Y[c * n + idx];
+      const C y = Y[c * ld + idx];
       const size_t o = base + (size_t)j * a.nx + i;
-      if (i < a.nx) S[o] = (T)(sg * y.x);
-      if (i + 1 < a.nx) S[o + 1] = (T)(-sg * y.y);
+      if (i < a.nx) S[o] = (T)neg_if(y.x, fl);
+      if (i + 1 < a.nx) S[o + 1] = (T)neg_if(y.y, !fl);
     }
   }
 }
@@ -320,6 +335,7 @@ struct XInvArgs {
   const double* dz;   // with mean_out: accumulate sum value * dz[k] (the gauge of the result)
   double* mean_out;
   double* d2_out;     // if non-null: accumulate sum value^2 (size of this correction)
+  const ff* dzff;     // dz as FP32 pairs (reduced-precision plans' gauge sum)
 };
 
 // x pass, inverse: two packed lines per complex FFT, result written (or added) to the FP64 cell array p.
@@ -349,19 +365,26 @@ __device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned c
     b0[pb * n + m] = inv_pre<C>([&](int q) { return ra[q]; }, [&](int q) { return rb[q]; }, n, bc, m, quart);
   }
   __syncthreads();
-  const C* Y = fft_smem<C>(b0, b1, PB, a.fd, reinterpret_cast<const C*>(a.tw));
+  const C* Y = fft_smem<C>(b0, b1, PB, a.fd, reinterpret_cast<const C*>(a.tw), n);
+  // FP64 plans sum in FP64.  Reduced-precision plans: the correction's size (a threshold) in FP32 and its
+  // gauge sum (subtracted from p at the end, so it must be exact to well below the tolerance) in FP32 pairs
+  // of FP32 products -- no FP64 arithmetic per cell beyond the addition into p.
+  constexpr bool f64 = std::is_same<T, double>::value;
   double acc = 0, acc2 = 0;
+  ff accm(0.0f, 0.0f);
+  float acc2f = 0.0f;
   for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
     const int pb = t / n, i = t - pb * n;
     const long l0 = 2 * (pair0 + pb), l1 = l0 + 1;
     int idx = i;
-    R sg = 1;
+    bool fl = false;
     if (bc != VOFP_BC_P) {
       idx = dct_perm(i, n);
-      if (bc == VOFP_BC_DD && (i & 1)) sg = -1;
+      fl = bc == VOFP_BC_DD && (i & 1);
     }
     const C y = Y[pb * n + idx];
-    const double va = (double)(sg * y.x), vb = (double)(-sg * y.y);
+    const R ya = neg_if(y.x, fl), yb = neg_if(y.y, !fl);
+    const double va = (double)ya, vb = (double)yb;
     if (a.accumulate) {
       if (l0 < nlines) a.p[l0 * n + i] += va;
       if (l1 < nlines) a.p[l1 * n + i] += vb;
@@ -369,14 +392,30 @@ __device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned c
       if (l0 < nlines) a.p[l0 * n + i] = va;
       if (l1 < nlines) a.p[l1 * n + i] = vb;
     }
-    if (a.mean_out) {
-      if (l0 < nlines) acc += va * __ldg(a.dz + l0 / a.ny);
-      if (l1 < nlines) acc += vb * __ldg(a.dz + l1 / a.ny);
+    if (f64) {
+      if (a.mean_out) {
+        if (l0 < nlines) acc = fma(va, __ldg(a.dz + l0 / a.ny), acc);
+        if (l1 < nlines) acc = fma(vb, __ldg(a.dz + l1 / a.ny), acc);
+      }
+      if (a.d2_out) {
+        if (l0 < nlines) acc2 = fma(va, va, acc2);
+        if (l1 < nlines) acc2 = fma(vb, vb, acc2);
+      }
+    } else {
+      if (a.mean_out) {
+        if (l0 < nlines) accm += ff_of(ya) * a.dzff[l0 / a.ny];
+        if (l1 < nlines) accm += ff_of(yb) * a.dzff[l1 / a.ny];
+      }
+      if (a.d2_out) {
+        const float fa = lead(ya), fb = lead(yb);
+        if (l0 < nlines) acc2f = fmaf(fa, fa, acc2f);
+        if (l1 < nlines) acc2f = fmaf(fb, fb, acc2f);
+      }
     }
-    if (a.d2_out) {
-      if (l0 < nlines) acc2 += va * va;
-      if (l1 < nlines) acc2 += vb * vb;
-    }
+  }
+  if (!f64) {
+    acc = (double)accm;
+    acc2 = acc2f;
   }
   if (a.mean_out) {
     const double s = block_sum(acc, red);

@@ -181,7 +181,7 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
     p->ax[a].n = n;
     p->ax[a].bc = bc[a];
   }
-  std::vector<double> za(nz), zb(nz), zc(nz), hz(nz + 1), rdz(nz), rhz(nz + 1), rzc(nz);
+  std::vector<double> za(nz), zb(nz), zc(nz), hz(nz + 1), rdz(nz), rhz(nz + 1), rzc(nz), kz(4 * (size_t)nz);
   const double hper = 0.5 * (dz[nz - 1] + dz[0]);
   for (int k = 0; k <= nz; ++k) {
     if (k == 0)
@@ -210,9 +210,18 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
     zc[k] = cc;
     rdz[k] = 1.0 / dz[k];
     rzc[k] = 1.0 / (hz[k] + hz[k + 1]);
+    // per-plane constants of the residual stencil and the reductions
+    const double czp = rhz[k + 1] * rdz[k], czm = rhz[k] * rdz[k];
+    kz[k] = dx * dy * dz[k];  // cell volume
+    kz[nz + k] = czp;
+    kz[2 * nz + k] = czm;
+    kz[3 * nz + k] = -2.0 * (1.0 / (dx * dx) + 1.0 / (dy * dy)) - czp - czm;
   }
-  // mixed path: the low-eigenvalue (x, y) pairs, |lx + ly| <= 64 * (smallest positive |eigenvalue|)
+  // refinement plans: the low-eigenvalue (x, y) pairs, |lx + ly| <= 64 * (smallest positive |eigenvalue|).
+  // Every eigenvalue is <= 0 and |lx_i| is non-decreasing in the packed index i for each boundary
+  // condition, so the low pairs of row j are a prefix i < lowcut[j] of it.
   std::vector<int2> low;
+  std::vector<int> lowcut(ny, 0);
   p->lowthr = -1.0;
   if (mixed) {
     double l1 = 0;
@@ -222,9 +231,12 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
         if (v > 0 && (l1 == 0 || v < l1)) l1 = v;
       }
     p->lowthr = 64.0 * l1;
-    for (int j = 0; j < ny; ++j)
-      for (int i = 0; i < nx; ++i)
-        if (std::fabs(lam[0][i] + lam[1][j]) <= p->lowthr) low.push_back(make_int2(i, j));
+    for (int j = 0; j < ny; ++j) {
+      int cut = 0;
+      while (cut < nx && std::fabs(lam[0][cut] + lam[1][j]) <= p->lowthr) ++cut;
+      lowcut[j] = cut;
+      for (int i = 0; i < cut; ++i) low.push_back(make_int2(i, j));
+    }
   }
   p->nlow = (int)low.size();
 
@@ -263,6 +275,18 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   off = align256(off + sizeof(double) * (nz + 1));
   L.rzc = off;
   off = align256(off + sizeof(double) * nz);
+  L.kz = off;
+  off = align256(off + sizeof(double) * 4 * nz);
+  L.volf = off;
+  off = align256(off + sizeof(float) * nz);
+  L.dzff = off;
+  off = align256(off + sizeof(ff) * nz);
+  L.za32 = off;
+  off = align256(off + sizeof(float) * nz);
+  L.zaff = off;
+  off = align256(off + sizeof(ff) * nz);
+  L.lowcut = off;
+  off = align256(off + sizeof(int) * ny);
   L.low = off;
   off = align256(off + sizeof(int2) * low.size());
   L.conv = off;
@@ -277,13 +301,11 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   L.P = off;
   off = align256(off + sizeof(double) * cells);
   L.S = L.T = L.S32 = L.F = L.lowscr = L.lowtab = 0;
+  // bounded z: Thomas factor table per distinct eigenvalue pair in the plan's arithmetic type
+  const size_t tsz = o.prec == VOFP_MIXED ? sizeof(float2) : (o.prec == VOFP_FF ? sizeof(cff) : sizeof(double2));
   if (!mixed) {
     L.S = off;
     off = align256(off + sizeof(double) * cells);
-    if (!zper) {
-      L.T = off;
-      off = align256(off + sizeof(double2) * (size_t)Ux * Uy * nz);
-    }
   } else {
     L.S32 = off;  // FP32 or FP32-pair spectrum
     off = align256(off + rs * cells);
@@ -295,6 +317,10 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
       L.lowtab = off;
       off = align256(off + sizeof(double2) * (size_t)nz * low.size());
     }
+  }
+  if (!zper) {
+    L.T = off;
+    off = align256(off + tsz * (size_t)Ux * Uy * nz);
   }
   L.total = off;
   p->Ux = Ux;
@@ -319,25 +345,57 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   memcpy(&host[L.rdz], rdz.data(), sizeof(double) * nz);
   memcpy(&host[L.rhz], rhz.data(), sizeof(double) * (nz + 1));
   memcpy(&host[L.rzc], rzc.data(), sizeof(double) * nz);
+  {
+    std::vector<float> z32(nz);
+    std::vector<ff> zff(nz);
+    for (int k = 0; k < nz; ++k) {
+      z32[k] = (float)za[k];
+      zff[k] = ff(za[k]);
+    }
+    memcpy(&host[L.za32], z32.data(), sizeof(float) * nz);
+    std::vector<float> vf(nz);
+    std::vector<ff> dzf(nz);
+    for (int k = 0; k < nz; ++k) {
+      vf[k] = (float)kz[k];
+      dzf[k] = ff(dz[k]);
+    }
+    memcpy(&host[L.volf], vf.data(), sizeof(float) * nz);
+    memcpy(&host[L.dzff], dzf.data(), sizeof(ff) * nz);
+    memcpy(&host[L.kz], kz.data(), sizeof(double) * 4 * nz);
+    memcpy(&host[L.zaff], zff.data(), sizeof(ff) * nz);
+  }
+  memcpy(&host[L.lowcut], lowcut.data(), sizeof(int) * ny);
   if (!low.empty()) memcpy(&host[L.low], low.data(), sizeof(int2) * low.size());
 
   // launch shapes
   p->xpb = nx >= 1024 ? 1 : (1024 / nx > 16 ? 16 : 1024 / nx);
   if (p->xpb < 1) p->xpb = 1;
   int tx = 16;
-  while (tx > 2 && (size_t)16 * tx * ny > 96 * 1024) tx -= 2;
+  while (tx > 2 && (size_t)16 * tx * y_ld(ny) > 96 * 1024) tx -= 2;
   p->ytx = tx;
   // the reduced-precision path's shapes, sized by its element (FP32 or FP32-pair)
   tx = 16;
-  while (tx > 2 && (size_t)(4 * rs) * tx * ny > 96 * 1024) tx -= 2;
+  while (tx > 2 && (size_t)(4 * rs) * tx * y_ld(ny) > 96 * 1024) tx -= 2;
   p->ytx32 = tx;
-  const int nvec = zper ? 3 : 2;
-  int ti = 32;
-  while (ti > 1 && (size_t)nvec * ti * nz * sizeof(double) > 96 * 1024) ti /= 2;
-  p->zti = ti;
-  ti = 32;
-  while (ti > 1 && (size_t)nvec * ti * nz * rs > 96 * 1024) ti /= 2;
-  p->zti32 = ti;
+  if (zper) {
+    // periodic z (general column solver): systems per 128-thread block, three columns each in shared memory
+    int ti = 32;
+    while (ti > 1 && (size_t)3 * ti * nz * sizeof(double) > 96 * 1024) ti /= 2;
+    p->zti = ti;
+    ti = 32;
+    while (ti > 1 && (size_t)3 * ti * nz * rs > 96 * 1024) ti /= 2;
+    p->zti32 = ti;
+  } else {
+    // factor-table kernel: one system per thread; forward values in shared memory when 64 or 128 threads'
+    // columns fit in 96 KB, otherwise 128 threads keep them in place in the spectrum
+    auto table_ti = [&](size_t elem) {
+      if ((size_t)128 * nz * elem <= 96 * 1024) return 128;
+      if ((size_t)64 * nz * elem <= 96 * 1024) return 64;
+      return 128;
+    };
+    p->zti = table_ti(sizeof(double));
+    p->zti32 = table_ti(rs);
+  }
   pp->p = p;
   return VOFP_OK;
 }
@@ -385,13 +443,19 @@ int plan_bind(PlanPrep* pp, void* block, cudaStream_t st, unsigned char* stage) 
   p->rdz = (double*)(b + L.rdz);
   p->rhz = (double*)(b + L.rhz);
   p->rzc = (double*)(b + L.rzc);
+  p->kz = (double*)(b + L.kz);
+  p->volf = (float*)(b + L.volf);
+  p->dzff = (ff*)(b + L.dzff);
   p->conv = (double*)(b + L.conv);
   p->info = (vofp_devinfo*)(b + L.info);
   p->lowmodes = p->nlow ? (int2*)(b + L.low) : nullptr;
   p->P = (double*)(b + L.P);
   const bool mixed = p->opts.prec != VOFP_FP64;
   p->S = mixed ? nullptr : (double*)(b + L.S);
-  p->ztab = (!mixed && L.T) ? (double2*)(b + L.T) : nullptr;
+  p->ztab = L.T ? (void*)(b + L.T) : nullptr;
+  p->zaT = p->opts.prec == VOFP_MIXED ? (const void*)(b + L.za32)
+           : (p->opts.prec == VOFP_FF ? (const void*)(b + L.zaff) : (const void*)p->za);
+  p->lowcut = mixed ? (int*)(b + L.lowcut) : nullptr;
   p->S32 = mixed ? (float*)(b + L.S32) : nullptr;
   p->F = mixed ? (double*)(b + L.F) : nullptr;
   p->lowscratch = (mixed && p->nlow) ? (double*)(b + L.lowscr) : nullptr;

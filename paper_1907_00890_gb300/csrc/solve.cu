@@ -35,6 +35,12 @@ GridDev grid_dev(const vofp_plan* pl) {
   g.rdz = pl->rdz;
   g.rhz = pl->rhz;
   g.rzc = pl->rzc;
+  g.vol = pl->kz;
+  g.czp = pl->kz ? pl->kz + pl->n[2] : nullptr;
+  g.czm = pl->kz ? pl->kz + 2 * pl->n[2] : nullptr;
+  g.czc = pl->kz ? pl->kz + 3 * pl->n[2] : nullptr;
+  g.volf = pl->volf;
+  g.dzff = pl->dzff;
   return g;
 }
 
@@ -54,7 +60,8 @@ void init_kernel_attributes_fp64() {
   allow_smem(k_ypass<double, double2, true>);
   allow_smem(k_xinv<double, double2>);
   allow_smem(k_zsolve<double, double>);
-  allow_smem(k_zsolve64_tab);
+  allow_smem(k_ztab<double, double2>);
+  allow_smem(k_ztab_staged<double, double2>);
 }
 
 int grid_blocks(size_t total, int threads) {
@@ -90,16 +97,29 @@ ZArgs z_args(const vofp_plan* pl, bool stats) {
   return za;
 }
 
-int build_z_factors(vofp_plan* pl, cudaStream_t st, bool sync) {
-  ZArgs za = z_args(pl, false);
+ZTabArgs ztab_args(const vofp_plan* pl) {
   ZTabArgs zt;
   zt.Ux = pl->Ux;
   zt.Uy = pl->Uy;
   zt.bcx = pl->bc[0];
   zt.bcy = pl->bc[1];
   zt.tab = pl->ztab;
+  zt.za = pl->zaT;
+  zt.lowcut = pl->lowcut;
+  return zt;
+}
+
+int build_z_factors(vofp_plan* pl, cudaStream_t st, bool sync) {
+  const ZArgs za = z_args(pl, false);
+  const ZTabArgs zt = ztab_args(pl);
   const int n = pl->Ux * pl->Uy;
-  k_zfactor64<<<(n + 127) / 128, 128, 0, st>>>(za, zt, pl->ztab);
+  const int nb = (n + 127) / 128;
+  if (pl->opts.prec == VOFP_MIXED)
+    k_zfactor<float2><<<nb, 128, 0, st>>>(za, zt, (float2*)pl->ztab);
+  else if (pl->opts.prec == VOFP_FF)
+    k_zfactor<cff><<<nb, 128, 0, st>>>(za, zt, (cff*)pl->ztab);
+  else
+    k_zfactor<double2><<<nb, 128, 0, st>>>(za, zt, (double2*)pl->ztab);
   if (cudaGetLastError() != cudaSuccess) return VOFP_ERR_CUDA;
   if (sync && cudaStreamSynchronize(st) != cudaSuccess) return VOFP_ERR_CUDA;
   return VOFP_OK;
@@ -144,19 +164,20 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
   ya.tx = pl->ytx;
   ya.S = pl->S;
   const dim3 ygrid((nx + ya.tx - 1) / ya.tx, nz);
-  const size_t ysm = 2 * (size_t)(ya.tx / 2) * ny * sizeof(double2);
+  const size_t ysm = 2 * (size_t)(ya.tx / 2) * y_ld(ny) * sizeof(double2);
   if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, k_ypass<double, double2, false><<<ygrid, 256, ysm, st>>>(ya));
   ZArgs za = z_args(pl, stats);
   const dim3 zgrid((nx + za.ti - 1) / za.ti, ny);
-  if (pl->ztab) {
-    ZTabArgs zt;
-    zt.Ux = pl->Ux;
-    zt.Uy = pl->Uy;
-    zt.bcx = pl->bc[0];
-    zt.bcy = pl->bc[1];
-    zt.tab = pl->ztab;
-    const size_t zsm = (size_t)za.ti * nz * (sizeof(double) + sizeof(double2));
-    VOFP_LAUNCH(KID_ZSOLVE, st, k_zsolve64_tab<<<zgrid, 128, zsm, st>>>(za, zt));
+  if (pl->ztab && ztab_use_staged(nx, ny, nz, sizeof(double))) {
+    const dim3 tgrid((nx + kZStagedTI - 1) / kZStagedTI, ny);
+    VOFP_LAUNCH(KID_ZSOLVE, st,
+                (k_ztab_staged<double, double2><<<tgrid, 128, ztab_staged_smem(nz, sizeof(double)), st>>>(
+                    za, ztab_args(pl))));
+  } else if (pl->ztab) {
+    const ZTabShape zs = ztab_shape(pl->zti, nz, sizeof(double));
+    const dim3 tgrid((nx + zs.threads - 1) / zs.threads, ny);
+    VOFP_LAUNCH(KID_ZSOLVE, st,
+                (k_ztab<double, double2><<<tgrid, zs.threads, zs.smem, st>>>(za, ztab_args(pl), zs.smem_d)));
   } else {
     const int nvec = pl->bc[2] == VOFP_BC_P ? 3 : 2;
     const size_t zsm = (size_t)nvec * za.ti * nz * sizeof(double);

@@ -26,6 +26,9 @@ enum KernelId {
   KID_FUSED_YZY,
   KID_BATCHED,
   KID_NOALLOC_TABLES,
+  KID_ZLOW,     // refinement plans: the low-eigenvalue z systems in FP64
+  KID_GAUGE,    // gauge restoration of p
+  KID_RESNORM,  // reporting residual norm
   KID_COUNT
 };
 
@@ -57,7 +60,7 @@ unsigned long long capture_end();
 // ---- plan construction in two phases (see plan.cu) ----
 struct PlanLayout {
   size_t lam[2], tw[2], q[2], tw32[2], q32[2], twff[2], qff[2];
-  size_t za, zb, zc, dz, hz, rdz, rhz, rzc, conv, info, low;
+  size_t za, zb, zc, dz, hz, rdz, rhz, rzc, conv, info, low, za32, zaff, lowcut, kz, volf, dzff;
   size_t table_bytes;  // host-built part, uploaded as one copy
   size_t P, S, T, S32, F, lowscr, lowtab;
   size_t total;
@@ -81,6 +84,8 @@ struct GridDev;
 struct ZArgs;
 GridDev grid_dev(const vofp_plan* pl);
 ZArgs z_args(const vofp_plan* pl, bool stats);
+struct ZTabArgs;
+ZTabArgs ztab_args(const vofp_plan* pl);
 int grid_blocks(size_t total, int threads);
 void init_kernel_attributes_fp64();
 void init_kernel_attributes_mixed();
@@ -91,7 +96,7 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
 int mixed_solve(vofp_plan* pl, int mode, const XArgs* xa, const double* f, double* pout, cudaStream_t st,
                 vofp_info* info);
 int begin_info(vofp_plan* pl, cudaStream_t st, vofp_info* info);
-// Thomas factor tables for a bounded z axis (FP64 plans), built on `st`; `sync` waits for them.
+// Thomas factor tables for a bounded z axis (in the plan's arithmetic type), built on `st`; `sync` waits.
 int build_z_factors(vofp_plan* pl, cudaStream_t st, bool sync);
 // The same for the low-eigenvalue systems of a mixed plan.
 int build_low_factors(vofp_plan* pl, cudaStream_t st, bool sync);

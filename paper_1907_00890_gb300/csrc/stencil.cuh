@@ -26,6 +26,12 @@ struct GridDev {
   const double* rdz;  // 1/dz
   const double* rhz;  // 1/hz
   const double* rzc;  // 1/(hz[k] + hz[k+1]): central difference in z
+  const double* vol;  // cell volume per plane (dx dy dz_k)
+  const double* czp;  // residual stencil: coefficient of p_{k+1}, rhz[k+1] / dz_k
+  const double* czm;  //   of p_{k-1}, rhz[k] / dz_k
+  const double* czc;  //   of p_k, -2 (1/dx^2 + 1/dy^2) - czp - czm
+  const float* volf;  // cell volume per plane, FP32
+  const ff* dzff;     // dz per plane, FP32 pair
 };
 
 __host__ __device__ __forceinline__ int nface(int n, int bc) { return n + (bc != VOFP_BC_P); }

@@ -79,17 +79,15 @@ Shape current(const vofp_plan* p) {
 }
 
 bool fits(const vofp_plan* p, const Shape& s) {
-  const size_t c = p->opts.prec == VOFP_MIXED ? sizeof(float2) : sizeof(double2);
-  const size_t r = p->opts.prec == VOFP_MIXED ? sizeof(float) : sizeof(double);
-  const int nvec = p->bc[2] == VOFP_BC_P ? 3 : 2;
+  const bool f32 = p->opts.prec == VOFP_MIXED;
+  const size_t c = f32 ? sizeof(float2) : sizeof(double2);
+  const size_t r = f32 ? sizeof(float) : sizeof(double);
   const size_t lim = 160 * 1024;
   if (2 * (size_t)s.xpb * p->n[0] * c > lim) return false;
-  if (2 * (size_t)(s.ytx / 2) * p->n[1] * c > lim) return false;
-  size_t zs = (size_t)nvec * s.zti * p->n[2] * r;
-  if (!mixed(p) && p->ztab) zs = (size_t)s.zti * p->n[2] * (sizeof(double) + sizeof(double2));
-  if (zs > lim) return false;
-  if (s.zti > 128) return false;  // the z pass runs 128 threads per block, one system each
-  return true;
+  if (2 * (size_t)(s.ytx / 2) * vofp::y_ld(p->n[1]) * c > lim) return false;
+  if (s.zti > 128) return false;  // at most 128 systems per block
+  if (p->ztab) return s.zti >= 32;  // factor-table kernel: one system per thread, whole warps
+  return (size_t)3 * s.zti * p->n[2] * r <= lim;
 }
 
 // Average milliseconds of a Poisson solve of the plan's scratch potential (in place).

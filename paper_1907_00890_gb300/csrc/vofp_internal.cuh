@@ -61,6 +61,15 @@ __device__ __forceinline__ C cmi(C a) {
   return cmk<C>(a.y, -a.x);
 }
 
+// Sign flip by the sign bit (integer pipe; no FP64 multiply on a narrow FP64 unit).
+__device__ __forceinline__ double neg_if(double x, bool f) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)f << 63));
+}
+__device__ __forceinline__ float neg_if(float x, bool f) {
+  return __int_as_float(__float_as_int(x) ^ ((int)f << 31));
+}
+__device__ __forceinline__ ff neg_if(ff x, bool f) { return ff(neg_if(x.hi, f), neg_if(x.lo, f)); }
+
 // ---- mixed-precision refinement: device-side convergence test ---------------------------------------
 // Slots: conv[0] = ||f||^2, conv[1] = sum f V, conv[2] = sum |f| V,
 //        conv[VOFP_CONV_RES + j] = ||r_j||^2, r_j = f - fbar - L p_j the residual after j corrections,
@@ -110,8 +119,8 @@ struct AxisDev {
 void factor_radices(int n, FftDesc* fd);
 
 // ---- shared-memory Stockham FFT ----------------------------------------------------------------------
-// Batched forward complex DFT (exponent -2 pi i / n) of `batch` contiguous sequences of length n held in
-// shared memory buffer `a`; `b` is a second buffer of the same size.  Returns the buffer that holds the
+// Batched forward complex DFT (exponent -2 pi i / n) of `batch` sequences of length n held in shared memory
+// buffer `a` with line stride `ld` >= n; `b` is a second buffer of the same size.  Returns the buffer that holds the
 // result.  All threads of the block must call it; it ends with __syncthreads().
 
 template <typename C, int RAD>
@@ -179,15 +188,15 @@ __device__ __forceinline__ void dft_small(C* v) {
 
 template <typename C, int RAD>
 __device__ __forceinline__ void fft_stage(const C* __restrict__ src, C* __restrict__ dst, int batch, int n, int Ns,
-                                          const C* __restrict__ tw) {
+                                          const C* __restrict__ tw, int ld) {
   const int NR = n / RAD;
   const int twstep = n / (Ns * RAD);
   const int total = batch * NR;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int bi = t / NR;
     const int j = t - bi * NR;
-    const C* s = src + bi * n;
-    C* d = dst + bi * n;
+    const C* s = src + bi * ld;
+    C* d = dst + bi * ld;
     const int k = j % Ns;
     C v[RAD];
 #pragma unroll
@@ -206,7 +215,7 @@ __device__ __forceinline__ void fft_stage(const C* __restrict__ src, C* __restri
 // Stage of a radix that has no hand-written butterfly: one output per thread, O(RAD) work each.
 template <typename C>
 __device__ __forceinline__ void fft_stage_generic(const C* __restrict__ src, C* __restrict__ dst, int batch, int n,
-                                                  int Ns, int RAD, const C* __restrict__ tw) {
+                                                  int Ns, int RAD, const C* __restrict__ tw, int ld) {
   typedef decltype(C::x) R;
   const int NR = n / RAD;
   const int twstep = n / (Ns * RAD);
@@ -217,7 +226,7 @@ __device__ __forceinline__ void fft_stage_generic(const C* __restrict__ src, C* 
     const int rout = rem / NR;
     const int j = rem - rout * NR;
     const int k = j % Ns;
-    const C* s = src + bi * n;
+    const C* s = src + bi * ld;
     const int e = (k * twstep + rout * NR) % n;  // exponent step per input r
     R ax = 0, ay = 0;
     int idx = 0;
@@ -229,23 +238,23 @@ __device__ __forceinline__ void fft_stage_generic(const C* __restrict__ src, C* 
       idx += e;
       if (idx >= n) idx -= n;
     }
-    dst[bi * n + (j - k) * RAD + k + rout * Ns] = cmk<C>(ax, ay);
+    dst[bi * ld + (j - k) * RAD + k + rout * Ns] = cmk<C>(ax, ay);
   }
 }
 
 template <typename C>
-__device__ C* fft_smem(C* a, C* b, int batch, const FftDesc& fd, const C* __restrict__ tw) {
+__device__ C* fft_smem(C* a, C* b, int batch, const FftDesc& fd, const C* __restrict__ tw, int ld) {
   const int n = fd.n;
   int Ns = 1;
   for (int s = 0; s < fd.nst; ++s) {
     const int R = fd.radix[s];
     switch (R) {
-      case 2: fft_stage<C, 2>(a, b, batch, n, Ns, tw); break;
-      case 3: fft_stage<C, 3>(a, b, batch, n, Ns, tw); break;
-      case 4: fft_stage<C, 4>(a, b, batch, n, Ns, tw); break;
-      case 5: fft_stage<C, 5>(a, b, batch, n, Ns, tw); break;
-      case 8: fft_stage<C, 8>(a, b, batch, n, Ns, tw); break;
-      default: fft_stage_generic<C>(a, b, batch, n, Ns, R, tw); break;
+      case 2: fft_stage<C, 2>(a, b, batch, n, Ns, tw, ld); break;
+      case 3: fft_stage<C, 3>(a, b, batch, n, Ns, tw, ld); break;
+      case 4: fft_stage<C, 4>(a, b, batch, n, Ns, tw, ld); break;
+      case 5: fft_stage<C, 5>(a, b, batch, n, Ns, tw, ld); break;
+      case 8: fft_stage<C, 8>(a, b, batch, n, Ns, tw, ld); break;
+      default: fft_stage_generic<C>(a, b, batch, n, Ns, R, tw, ld); break;
     }
     __syncthreads();
     C* t = a;
@@ -257,6 +266,10 @@ __device__ C* fft_smem(C* a, C* b, int batch, const FftDesc& fd, const C* __rest
 }
 
 // ---- pre/post-processing of the real-to-real transforms ----------------------------------------------
+
+// Shared-memory line stride of the column (y) passes: odd, so that the lines a warp touches at one sample
+// index fall in different banks.
+__host__ __device__ __forceinline__ int y_ld(int n) { return n | 1; }
 
 // Position of sample j in the reordered sequence used by DCT-II / DST-II.
 __device__ __forceinline__ int dct_perm(int j, int n) { return (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1); }
@@ -382,9 +395,16 @@ struct vofp_plan {
   double* rdz;   // 1/dz
   double* rhz;   // 1/hz
   double* rzc;   // 1/(hz[k] + hz[k+1])
+  double* kz;    // per plane k: cell volume, then the residual stencil's z coefficients czp, czm, czc
+                 // (4 arrays of nz)
+  float* volf;   // cell volume per plane, FP32
+  vofp::ff* dzff;  // dz per plane, FP32 pair
   double* conv;  // mixed path: FP64 reduction slots (norms, means) per solve
   double* G;     // interface geometry: s, n_x, n_y, n_z (4 * cells)
-  double2* ztab; // bounded z: Thomas factors per distinct eigenvalue pair (NULL: periodic z)
+  void* ztab;    // bounded z: Thomas factors per distinct eigenvalue pair in the plan's arithmetic type
+                 // (double2, float2 or cff; NULL: periodic z)
+  const void* zaT;     // z sub-diagonal a_k in the same type
+  int* lowcut;         // refinement plans: spectral x index i of row j is a low mode iff i < lowcut[j]
   int Ux, Uy;    // distinct eigenvalue counts in x, y
   // mixed path
   double lowthr;       // |lx + ly| at or below which a z system is solved in FP64
@@ -406,5 +426,5 @@ struct vofp_plan {
   // launch shapes
   int xpb;  // line pairs per block, x pass
   int ytx;  // columns per block, y pass
-  int zti;  // systems per block, z pass
+  int zti;  // systems per block, z pass (table kernel: threads per block)
 };

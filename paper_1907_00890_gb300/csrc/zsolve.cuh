@@ -251,21 +251,47 @@ __global__ void k_zlow64(ZArgs a, const int2* __restrict__ modes, int nlow, cons
   zlow_system<TS>(a, modes[t], t, nlow, tab, scratch);
 }
 
-// ---- factorisation tables (bounded z, FP64 path) -------------------------------------------------------
+// ---- factorisation tables (bounded z) -------------------------------------------------------------------
 // The z matrix of a spectral pair depends only on lx + ly, and the periodic half-complex packing gives the
 // real and imaginary parts of one Fourier mode the same eigenvalue, so the Thomas factors (c'_k, 1/den_k) are
-// computed once per distinct eigenvalue pair at plan time: table[(k * Uy + uy) * Ux + ux] = (c'_k, m_k).
-// The singular mean mode stores the factors of its pinned system (rows 1..nz-1, p_0 = 0).
+// computed once per distinct eigenvalue pair at plan time (in FP64, stored in the plan's arithmetic type):
+// table[(k * Uy + uy) * Ux + ux] = (c'_k, m_k).  The singular mean mode stores the factors of its pinned
+// system (rows 1..nz-1, p_0 = 0).
 
 __device__ __forceinline__ int distinct_index(int q, int bc) { return bc == VOFP_BC_P ? (q + 1) >> 1 : q; }
 
 struct ZTabArgs {
   int Ux, Uy;
   int bcx, bcy;
-  const double2* tab;
+  const void* tab;     // [nz][Uy][Ux] factor pairs in the plan's arithmetic type
+  const void* za;      // a_k in the same type
+  const int* lowcut;   // refinement plans: column i of row j is a low mode iff i < lowcut[j]; NULL: none
 };
 
-static __global__ void k_zfactor64(ZArgs a, ZTabArgs zt, double2* tab) {
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ ff fma_t(ff a, ff b, ff c) { return a * b + c; }
+
+template <typename TT>
+__device__ __forceinline__ TT make_factor(double c, double m);
+template <>
+__device__ __forceinline__ double2 make_factor<double2>(double c, double m) {
+  return make_double2(c, m);
+}
+template <>
+__device__ __forceinline__ float2 make_factor<float2>(double c, double m) {
+  return make_float2((float)c, (float)m);
+}
+template <>
+__device__ __forceinline__ cff make_factor<cff>(double c, double m) {
+  cff r;
+  r.x = ff(c);
+  r.y = ff(m);
+  return r;
+}
+
+template <typename TT>
+static __global__ void k_zfactor(ZArgs a, ZTabArgs zt, TT* tab) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= zt.Ux * zt.Uy) return;
   const int ux = t % zt.Ux, uy = t / zt.Ux;
@@ -275,92 +301,394 @@ static __global__ void k_zfactor64(ZArgs a, ZTabArgs zt, double2* tab) {
   const bool sing = a.singular && ux == 0 && uy == 0;
   const int k0 = sing ? 1 : 0;
   const size_t stride = (size_t)zt.Ux * zt.Uy;
-  if (sing) tab[t] = make_double2(0.0, 0.0);
+  if (sing) tab[t] = make_factor<TT>(0.0, 0.0);
   double cprev = 0.0;
   for (int k = k0; k < a.nz; ++k) {
     const double den = a.zb[k] + lam - (k > k0 ? a.za[k] * cprev : 0.0);
     const double m = 1.0 / den;
     const double c = (k < a.nz - 1 ? a.zc[k] : 0.0) * m;
-    tab[k * stride + t] = make_double2(c, m);
+    tab[k * stride + t] = make_factor<TT>(c, m);
     cprev = c;
   }
 }
 
-// Bounded-z solve with precomputed factors: forward d_k = (r_k - a_k d_{k-1}) m_k, back x_k = d_k - c'_k x_{k+1}.
-static __global__ void __launch_bounds__(128) k_zsolve64_tab(ZArgs a, ZTabArgs zt) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int TI = a.ti, nz = a.nz;
-  // the recurrences read only shared memory: factors [nz][TI] (double2) and right-hand sides [nz][TI]
-  double2* ft = reinterpret_cast<double2*>(smem_raw);
-  double* d = reinterpret_cast<double*>(ft + (size_t)nz * TI);
-  const int i0 = blockIdx.x * TI;
-  const int jq = blockIdx.y;
+// Bounded-z solve with precomputed factors, one thread per system, `blockDim.x` neighbouring x indices of one
+// y index per block: forward d_k = (r_k - a_k d_{k-1}) m_k, back x_k = d_k - c'_k x_{k+1}, x scaled on the
+// way out.  Right-hand sides are read and solutions written row by row (coalesced across the warp); the
+// forward values d_k are kept in shared memory ([nz][blockDim.x], SMEM) or in place in the spectrum.  Written
+// as d_k = alpha_k d_{k-1} + beta_k (alpha_k = -a_k m_k, beta_k = s r_k m_k, both off the chain) and
+// x_k = d_k - c'_k x_{k+1}, each recurrence has one dependent multiply-add per row (FP64 latency is some 64
+// cycles on this GPU); the loads of rows k + 1 .. k + 8 are issued before row k is used (a register ring).
+template <typename T, typename TT, bool SMEM>
+__device__ __forceinline__ bool ztab_sweep(T* __restrict__ col, T* __restrict__ dsm, size_t plane, int TI,
+                                           const TT* __restrict__ F, size_t ts, const T* __restrict__ za, int nz,
+                                           T sc, bool check) {
+  constexpr int U = 8;
+  T rb[U];
+  TT fb[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+    if (u < nz) {
+      rb[u] = col[u * plane];
+      fb[u] = F[u * ts];
+    }
+  T dprev = (T)0;
+  for (int k0 = 0; k0 < nz; k0 += U) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u;
+      if (k < nz) {
+        const T m = fb[u].y;
+        const T al = -(za[k] * m), be = (rb[u] * sc) * m;  // off the dependent chain
+        if (k + U < nz) {
+          rb[u] = col[(k + U) * plane];
+          fb[u] = F[(k + U) * ts];
+        }
+        dprev = fma_t(al, dprev, be);
+        if (SMEM)
+          dsm[k * TI] = dprev;
+        else
+          col[k * plane] = dprev;
+      }
+    }
+  }
+  bool bad = false;
+  T x = dprev;
+  col[(size_t)(nz - 1) * plane] = x;
+  if (check) bad |= !isfinite((double)x);
+  T db[U], cb[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int k = nz - 2 - u;
+    if (k >= 0) {
+      db[u] = SMEM ? dsm[k * TI] : col[k * plane];
+      cb[u] = F[k * ts].x;
+    }
+  }
+  for (int k0 = nz - 2; k0 >= 0; k0 -= U) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 - u;
+      if (k >= 0) {
+        const T d = db[u], c = cb[u];
+        if (k - U >= 0) {
+          db[u] = SMEM ? dsm[(k - U) * TI] : col[(k - U) * plane];
+          cb[u] = F[(k - U) * ts].x;
+        }
+        x = fma_t(-c, x, d);
+        col[k * plane] = x;
+        if (check) bad |= !isfinite((double)x);
+      }
+    }
+  }
+  return bad;
+}
+
+// The pinned mean mode (singular operator, q = r = 0) on its scaled right-hand side: remove the
+// volume-weighted mean (the compatibility defect), fix p_0 = 0, eliminate rows 1..nz-1, back-substitute,
+// shift to zero volume-weighted mean.  One thread; `dcol` / `ds` is its forward-value column.
+template <typename T, typename TT>
+__device__ bool ztab_singular(const ZArgs& a, T* col, T* dcol, size_t ds, size_t plane, const TT* F, size_t ts,
+                              const T* za) {
+  const int nz = a.nz;
+  const T sc = (T)a.scale;
+  T s = (T)0;
+  for (int k = 0; k < nz; ++k) s += (T)__ldg(a.dz + k) * (col[k * plane] * sc);
+  const T defect = s / (T)a.lz;
+  if (a.info) a.info->compat_defect = (double)defect;
+  T dp = (T)0;
+  for (int k = 1; k < nz; ++k) {
+    dp = (col[k * plane] * sc - defect - (k > 1 ? za[k] * dp : (T)0)) * F[k * ts].y;
+    dcol[k * ds] = dp;
+  }
+  T x = dp;
+  for (int k = nz - 2; k >= 1; --k) {
+    x = dcol[k * ds] - F[k * ts].x * x;
+    dcol[k * ds] = x;
+  }
+  dcol[0] = (T)0;
+  T mean = (T)0;
+  for (int k = 0; k < nz; ++k) mean += (T)__ldg(a.dz + k) * dcol[k * ds];
+  mean = mean / (T)a.lz;
+  bool bad = false;
+  for (int k = 0; k < nz; ++k) {
+    const T o = dcol[k * ds] - mean;
+    col[k * plane] = o;
+    bad |= !isfinite((double)o);
+  }
+  return bad;
+}
+
+template <typename T, typename TT>
+__device__ __forceinline__ void ztab_block(const ZArgs& a, const ZTabArgs& zt, int smem_d, int bx, int by,
+                                           unsigned char* smem_raw) {
+  if (launch_skipped(a.skip_conv, a.skip_k, a.tol2)) return;
+  const int TI = blockDim.x, nz = a.nz;
+  const int c = threadIdx.x;
+  const int i = bx * TI + c, j = by;
+  if (i >= a.nx) return;
+  if (zt.lowcut && i < __ldg(zt.lowcut + j)) return;  // solved in FP64 by the low-mode kernel
   const size_t plane = (size_t)a.nx * a.ny;
-  const size_t col0 = (size_t)jq * a.nx + i0;
-  const size_t stride = (size_t)zt.Ux * zt.Uy;
-  const double2* Trow = zt.tab + (size_t)distinct_index(jq, zt.bcy) * zt.Ux;
-  double* S = reinterpret_cast<double*>(a.S);
+  T* col = reinterpret_cast<T*>(a.S) + (size_t)j * a.nx + i;
+  T* dsm = reinterpret_cast<T*>(smem_raw) + c;
+  const size_t ts = (size_t)zt.Ux * zt.Uy;
+  const TT* F = reinterpret_cast<const TT*>(zt.tab) + (size_t)distinct_index(j, zt.bcy) * zt.Ux +
+                distinct_index(i, zt.bcx);
+  const T* za = reinterpret_cast<const T*>(zt.za);
+  bool bad;
+  if (a.singular && i == 0 && j == 0)
+    bad = smem_d ? ztab_singular<T, TT>(a, col, dsm, TI, plane, F, ts, za)
+                 : ztab_singular<T, TT>(a, col, col, plane, plane, F, ts, za);
+  else if (smem_d)
+    bad = ztab_sweep<T, TT, true>(col, dsm, plane, TI, F, ts, za, nz, (T)a.scale, a.info != nullptr);
+  else
+    bad = ztab_sweep<T, TT, false>(col, nullptr, plane, TI, F, ts, za, nz, (T)a.scale, a.info != nullptr);
+  if (bad && a.info) atomicOr(&a.info->nonfinite, 1u);
+}
+
+template <typename T, typename TT>
+static __global__ void __launch_bounds__(128) k_ztab(ZArgs a, ZTabArgs zt, int smem_d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ztab_block<T, TT>(a, zt, smem_d, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// Launch shape of k_ztab: threads (= systems) per block and whether the forward values fit in shared memory
+// (at most 96 KB per block, so that two blocks share an SM).
+struct ZTabShape {
+  int threads;
+  int smem_d;
+  size_t smem;
+};
+inline ZTabShape ztab_shape(int ti, int nz, size_t elem) {
+  ZTabShape s;
+  s.threads = ti < 32 ? 32 : (ti > 128 ? 128 : ti);
+  const size_t need = (size_t)s.threads * nz * elem;
+  s.smem_d = need <= 96 * 1024;
+  s.smem = s.smem_d ? need : 0;
+  return s;
+}
+
+// ---- one system per warp: affine scans ---------------------------------------------------------------
+// Both Thomas sweeps with plan-time factors are first-order affine recurrences, d_k = alpha_k d_{k-1} + beta_k
+// with alpha_k = -a_k m_k, beta_k = m_k r_k, then x_k = -c'_k x_{k+1} + d_k.  Each lane composes the affine maps
+// of a contiguous run of rows, an inclusive warp scan of the composed maps (five shuffle steps) gives every
+// lane its incoming value, and the lane then re-applies its rows from it.  Used where a system's serial chain
+// would dominate: the low-eigenvalue systems of refinement plans (FP64) and the pinned mean mode.
+__device__ __forceinline__ double shfl_up_t(double v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_down_t(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_xor_t(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ ff shfl_up_t(ff v, int o) {
+  return ff(__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o));
+}
+__device__ __forceinline__ ff shfl_down_t(ff v, int o) {
+  return ff(__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o));
+}
+__device__ __forceinline__ ff shfl_xor_t(ff v, int o) {
+  return ff(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+
+template <typename T>
+__device__ __forceinline__ void affine_scan_up(T& A, T& B, int lane) {
+  // inclusive scan over lanes 0..lane of maps x -> A x + B, later lanes applied after earlier ones
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T pa = shfl_up_t(A, o);
+    const T pb = shfl_up_t(B, o);
+    if (lane >= o) {
+      B = fma_t(A, pb, B);
+      A = A * pa;
+    }
+  }
+}
+template <typename T>
+__device__ __forceinline__ void affine_scan_down(T& A, T& B, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T pa = shfl_down_t(A, o);
+    const T pb = shfl_down_t(B, o);
+    if (lane + o < 32) {
+      B = fma_t(A, pb, B);
+      A = A * pa;
+    }
+  }
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += shfl_xor_t(v, o);
+  return v;
+}
+
+// One bounded-z system by one warp, arithmetic in T.  col: the system's column in the spectrum (stride plane,
+// storage TS); F: its factor pairs (c'_k, m_k) at stride fs; scr: nz forward values at stride ss.  sing: the
+// pinned mean mode (defect removed, p_0 = 0, zero volume-weighted mean; its factors are the pinned system's).
+template <typename T, typename TS, typename TT>
+__device__ void zscan_system(const ZArgs& a, TS* col, size_t plane, const TT* F, size_t fs, T* scr, size_t ss,
+                             const T* za, bool sing, int lane) {
+  const int nz = a.nz;
+  const T sc = (T)a.scale;
+  const int R = (nz + 31) >> 5;
+  const int k0 = lane * R < nz ? lane * R : nz;
+  const int k1 = k0 + R < nz ? k0 + R : nz;
+  T defect = (T)0;
+  if (sing) {
+    T s = (T)0;
+    for (int k = k0; k < k1; ++k) s += (T)__ldg(a.dz + k) * ((T)col[k * plane] * sc);
+    defect = warp_sum(s) / (T)a.lz;
+    if (lane == 0 && a.info) a.info->compat_defect = (double)defect;
+  }
+  const int kb = sing ? 1 : 0;  // first eliminated row (p_0 = 0 pinned in the singular mode)
+  const int ks = k0 > kb ? k0 : kb;
+  // forward: compose this lane's rows, scan, re-apply
+  T A = (T)1, B = (T)0;
+  for (int k = ks; k < k1; ++k) {
+    const TT f = F[k * fs];
+    const T al = k > kb ? -(za[k] * f.y) : (T)0;
+    const T be = ((T)col[k * plane] * sc - defect) * f.y;
+    B = fma_t(al, B, be);
+    A = al * A;
+  }
+  affine_scan_up(A, B, lane);
+  T d = shfl_up_t(B, 1);
+  if (lane == 0) d = (T)0;
+  for (int k = ks; k < k1; ++k) {
+    const TT f = F[k * fs];
+    const T al = k > kb ? -(za[k] * f.y) : (T)0;
+    const T be = ((T)col[k * plane] * sc - defect) * f.y;
+    d = fma_t(al, d, be);
+    scr[k * ss] = d;
+  }
+  // backward: x_k = -c'_k x_{k+1} + d_k from the last row down
+  A = (T)1;
+  B = (T)0;
+  for (int k = k1 - 1; k >= ks; --k) {
+    const T g = -F[k * fs].x;
+    B = fma_t(g, B, scr[k * ss]);
+    A = g * A;
+  }
+  affine_scan_down(A, B, lane);
+  T x = shfl_down_t(B, 1);
+  if (lane == 31) x = (T)0;
+  T msum = (T)0;
+  for (int k = k1 - 1; k >= ks; --k) {
+    const T g = -F[k * fs].x;
+    x = fma_t(g, x, scr[k * ss]);
+    scr[k * ss] = x;
+    if (sing) msum += (T)__ldg(a.dz + k) * x;
+  }
+  T mean = (T)0;
+  if (sing) mean = warp_sum(msum) / (T)a.lz;  // row 0 holds 0
+  bool bad = false;
+  for (int k = k0; k < k1; ++k) {
+    const T v = (k < kb ? (T)0 : scr[k * ss]) - mean;
+    col[k * plane] = (TS)v;
+    if (a.info) bad |= !isfinite((double)v);
+  }
+  if (bad) atomicOr(&a.info->nonfinite, 1u);
+}
+
+// Refinement plans: the low-eigenvalue systems (listed at plan time) in FP64, one warp each; factors k-major
+// (tab[k * nlow + t]), forward values in `scratch` ([nz][nlow]).
+template <typename TS>
+__device__ __forceinline__ void zlow_scan_system(const ZArgs& a, int2 md, int t, int nlow,
+                                                 const double2* __restrict__ tab, double* __restrict__ scratch,
+                                                 int lane) {
+  TS* col = reinterpret_cast<TS*>(a.S) + (size_t)md.y * a.nx + md.x;
+  zscan_system<double, TS, double2>(a, col, (size_t)a.nx * a.ny, tab + t, (size_t)nlow, scratch + t, (size_t)nlow,
+                                    a.za, a.singular && md.x == 0 && md.y == 0, lane);
+}
+
+template <typename TS>
+static __global__ void __launch_bounds__(128) k_zlow_scan(ZArgs a, const int2* __restrict__ modes, int nlow,
+                                                          const double2* __restrict__ tab, double* scratch) {
+  if (launch_skipped(a.skip_conv, a.skip_k, a.tol2)) return;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= nlow) return;  // uniform per warp
+  zlow_scan_system<TS>(a, modes[w], w, nlow, tab, scratch, threadIdx.x & 31);
+}
+
+// ---- small grids: systems staged in shared memory -----------------------------------------------------
+// With few systems (nx * ny small) one thread per system leaves most of each SM idle, and an FP64 recurrence
+// is then bound by its 64-cycle dependent latency.  This kernel stages a tile of 32 systems ([nz][32]) in
+// shared memory with all 128 threads, computing alpha_k, beta_k (scaled) and c'_k on the way in; warp 0 runs
+// the two one-multiply-add recurrences from shared memory; warp 1 solves the pinned mean mode (if it is in
+// the tile) by affine scans; all threads store the tile.  Shared memory: nz * 32 * 3 values + nz scratch.
+constexpr int kZStagedTI = 32;
+template <typename T>
+struct Pair {
+  T x, y;
+};
+inline size_t ztab_staged_smem(int nz, size_t elem) { return (size_t)nz * (3 * kZStagedTI + 1) * elem; }
+// Staged kernel for FP64 / FP32-pair arithmetic when the grid has fewer than 152 * 256 systems (too few to
+// hide the recurrences' latency one thread each) and the tile fits in shared memory.
+inline bool ztab_use_staged(int nx, int ny, int nz, size_t elem) {
+  return (size_t)nx * ny < (size_t)152 * 256 && ztab_staged_smem(nz, elem) <= 200 * 1024;
+}
+
+template <typename T, typename TT>
+static __global__ void __launch_bounds__(128) k_ztab_staged(ZArgs a, ZTabArgs zt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (launch_skipped(a.skip_conv, a.skip_k, a.tol2)) return;
+  constexpr int TI = kZStagedTI;
+  const int nz = a.nz;
+  const int i0 = blockIdx.x * TI, j = blockIdx.y;
+  Pair<T>* ab = reinterpret_cast<Pair<T>*>(smem_raw);  // [nz][TI] (alpha_k, beta_k), then d_k / x_k in .y
+  T* cp = reinterpret_cast<T*>(ab + (size_t)nz * TI);  // [nz][TI] c'_k
+  T* scr = cp + (size_t)nz * TI;                        // [nz] pinned-mode scratch
+  const size_t plane = (size_t)a.nx * a.ny;
+  T* S = reinterpret_cast<T*>(a.S) + (size_t)j * a.nx + i0;
+  const TT* F = reinterpret_cast<const TT*>(zt.tab) + (size_t)distinct_index(j, zt.bcy) * zt.Ux;
+  const size_t ts = (size_t)zt.Ux * zt.Uy;
+  const T* za = reinterpret_cast<const T*>(zt.za);
+  const T sc = (T)a.scale;
+  const int cut = zt.lowcut ? __ldg(zt.lowcut + j) : 0;
+  const bool sing_here = a.singular && j == 0 && i0 == 0;  // the pinned mode is column 0 of this tile
+  const int ncol = a.nx - i0 < TI ? a.nx - i0 : TI;
   for (int t = threadIdx.x; t < nz * TI; t += blockDim.x) {
     const int k = t / TI, c = t - k * TI;
-    const bool in = i0 + c < a.nx;
-    d[t] = in ? S[k * plane + col0 + c] : 0.0;
-    ft[t] = in ? __ldg(Trow + k * stride + distinct_index(i0 + c, zt.bcx)) : make_double2(0.0, 0.0);
+    const int i = i0 + c;
+    if (c < ncol && i >= cut) {
+      const TT f = F[k * ts + distinct_index(i, zt.bcx)];
+      Pair<T> v;
+      v.x = -(za[k] * f.y);
+      v.y = (S[k * plane + c] * sc) * f.y;
+      ab[t] = v;
+      cp[t] = f.x;
+    }
   }
   __syncthreads();
-  const int c = threadIdx.x;
-  if (c < TI && i0 + c < a.nx) {
-    const int iq = i0 + c;
-    const double2* T = ft + c;
-    const size_t stride = TI;  // shadows the table stride: factors are now staged [nz][TI]
-    const double sc = a.scale;
-    int k0 = 0;
-    if (a.singular && iq == 0 && jq == 0) {
-      double s = 0;
-      for (int k = 0; k < nz; ++k) s += __ldg(a.dz + k) * d[k * TI + c];
-      const double defect = s * sc / a.lz;
-      if (a.info) a.info->compat_defect = defect;
-      for (int k = 0; k < nz; ++k) d[k * TI + c] = d[k * TI + c] * sc - defect;
-      d[c] = 0.0;
-      k0 = 1;
-      double dprev = 0.0;
-      for (int k = 1; k < nz; ++k) {
-        const double2 f = T[k * stride];
-        dprev = (d[k * TI + c] - (k > 1 ? __ldg(a.za + k) * dprev : 0.0)) * f.y;
-        d[k * TI + c] = dprev;
-      }
-    } else {
-      double dprev = 0.0;
-#pragma unroll 4
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    const int c = lane, i = i0 + c;
+    if (c < ncol && i >= cut && !(sing_here && c == 0)) {
+      T d = (T)0;
       for (int k = 0; k < nz; ++k) {
-        const double2 f = T[k * stride];
-        dprev = fma(d[k * TI + c], sc, -__ldg(a.za + k) * dprev) * f.y;
-        d[k * TI + c] = dprev;
+        Pair<T>& v = ab[k * TI + c];
+        d = fma_t(v.x, d, v.y);
+        v.y = d;
+      }
+      T x = d;
+      for (int k = nz - 2; k >= 0; --k) {
+        Pair<T>& v = ab[k * TI + c];
+        x = fma_t(-cp[k * TI + c], x, v.y);
+        v.y = x;
       }
     }
-    double x = d[(nz - 1) * TI + c];
-#pragma unroll 4
-    for (int k = nz - 2; k >= k0; --k) {
-      const double2 f = T[k * stride];
-      x = fma(-f.x, x, d[k * TI + c]);
-      d[k * TI + c] = x;
-    }
-    if (k0 == 1) {
-      double mean = 0;
-      for (int k = 0; k < nz; ++k) mean += __ldg(a.dz + k) * d[k * TI + c];
-      mean /= a.lz;
-      for (int k = 0; k < nz; ++k) d[k * TI + c] -= mean;
-    }
-    if (a.info) {
-      bool bad = false;
-      for (int k = 0; k < nz; ++k) bad |= !isfinite(d[k * TI + c]);
-      if (bad) atomicOr(&a.info->nonfinite, 1u);
-    }
+  } else if (warp == 1 && sing_here && cut == 0) {
+    zscan_system<T, T, TT>(a, S, plane, F, ts, scr, 1, za, true, lane);
   }
   __syncthreads();
+  bool bad = false;
   for (int t = threadIdx.x; t < nz * TI; t += blockDim.x) {
-    const int k = t / TI, cc = t - k * TI;
-    if (i0 + cc < a.nx) S[k * plane + col0 + cc] = d[t];
+    const int k = t / TI, c = t - k * TI;
+    const int i = i0 + c;
+    if (c < ncol && i >= cut && !(sing_here && c == 0)) {
+      const T x = ab[t].y;
+      S[k * plane + c] = x;
+      if (a.info) bad |= !isfinite((double)x);
+    }
   }
+  if (bad) atomicOr(&a.info->nonfinite, 1u);
 }
 
 }  // namespace vofp
