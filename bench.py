@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "ff"],
                     help="arithmetic of the main step (the 128^3 droplet step is specified in FP64)")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
@@ -202,17 +202,19 @@ def bench_large(vofp, args):
     return out
 
 
-def bench_batched(vofp, args):
+def bench_batched(vofp, args, prec=None):
     """64 independent instances, per-axis sizes from {32,48,64,96,128,160}, one graph replay per step."""
     import torch
     from paper_1907_00890_gb300 import synth
+    prec = vofp.MIXED if prec is None else prec
     sizes = synth.batch_sizes(64)
     bc = ("P", "P", "NN")
     plans, us = [], []
     gen = torch.Generator(device="cuda")
     gen.manual_seed(synth.BASE_SEED + 4)
     for n in sizes:
-        plans.append(vofp.Plan(n, 1.0 / n[0], 1.0 / n[1], synth.uniform_dz(n[2]), bc, prec=vofp.MIXED))
+        plans.append(vofp.Plan(n, 1.0 / n[0], 1.0 / n[1], synth.uniform_dz(n[2]), bc, prec=prec,
+                               max_refine=0 if prec == vofp.FF else 6))
         us.append([torch.randn(s, generator=gen, dtype=torch.float64, device="cuda")
                    for s in synth.face_shapes(n, bc)])
         for a in us[-1][2:]:
@@ -242,13 +244,36 @@ def bench_batched(vofp, args):
         ev[i][1].record(st)
     torch.cuda.synchronize()
     ms = float(np.mean([a.elapsed_time(bb) for a, bb in ev]))
+    # accuracy: one instance against its own plan-based single solve is covered by the tests; here the
+    # divergence left in every instance (FP64 stencil on the device) relative to the input's
+    worst = 0.0
+    for p, u, v in zip(plans, us, u0):
+        worst = max(worst, _div_ratio(torch, p, u, v))
     vofp.vofp_batch_destroy(b)
     for p in plans:
         p.close()
     return {"value": cells / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_batch": ms, "instances": len(sizes),
-            "cells": cells, "solves_per_s": len(sizes) / (ms / 1e3), "dtype": "f32+f64",
-            "workload": "64 projection instances, sizes per axis from {32,48,64,96,128,160}, P,P,NN, mixed, "
-                        "one CUDA-graph replay per batch"}
+            "cells": cells, "solves_per_s": len(sizes) / (ms / 1e3),
+            "dtype": "f32+f64" if prec == vofp.MIXED else "f32x2+f64",
+            "max_rel_divergence_after": worst,
+            "workload": "64 projection instances, sizes per axis from {32,48,64,96,128,160}, P,P,NN, %s, "
+                        "one CUDA-graph replay per batch" % ("FP32 + refinement" if prec == vofp.MIXED
+                                                             else "FP32-pair transforms")}
+
+
+def _div_ratio(torch, plan, u, u0):
+    """max |D u| / max |D u0| on the device (MAC divergence, FP64; u: projected faces, u0: the input)."""
+    nx, ny, nz = plan.n
+
+    def div(f):
+        a, b, c = f
+        dx = 1.0 / nx
+        d = (a[:, :, 1:] - a[:, :, :-1]) / dx if a.shape[2] == nx + 1 else (torch.roll(a, -1, 2) - a) / dx
+        d = d + ((b[:, 1:, :] - b[:, :-1, :]) * ny if b.shape[1] == ny + 1 else (torch.roll(b, -1, 1) - b) * ny)
+        d = d + (c[1:] - c[:-1]) * nz
+        return d.abs().max().item()
+
+    return div(u) / max(div(u0), 1e-300)
 
 
 def bench_served(vofp, args):
@@ -273,9 +298,10 @@ def bench_served(vofp, args):
     bufs = [[torch.randn(maxc, generator=gen, dtype=torch.float64, device="cuda") for _ in range(3)]
             for _ in range(pool)]
     out = {}
-    for name, prec in (("mixed", vofp.MIXED), ("ff", vofp.FF), ("fp64", vofp.FP64)):
+    for name, prec, mr in (("mixed", vofp.MIXED, 6), ("ff", vofp.FF, 0), ("fp64", vofp.FP64, 1)):
         o = vofp.vofp_opts_default()
         o.prec = prec
+        o.max_refine = mr
         s = vofp.vofp_server_create(0, 64, o)
         free = list(range(pool))
         busy = {}
@@ -467,8 +493,9 @@ def run_ours(args):
     c = synth.config_droplet(args.n, seed_offset=rank)
     n = c["n"]
     cells = int(np.prod(n))
-    mixed = args.precision == "mixed"
-    plan = vofp.Plan(n, c["dx"], c["dy"], c["dz"], c["bc"], prec=vofp.MIXED if mixed else vofp.FP64)
+    mixed = args.precision != "fp64"
+    prec = {"fp64": vofp.FP64, "mixed": vofp.MIXED, "ff": vofp.FF}[args.precision]
+    plan = vofp.Plan(n, c["dx"], c["dy"], c["dz"], c["bc"], prec=prec, max_refine=0 if prec == vofp.FF else 6)
     st = torch.cuda.current_stream()
 
     def T(a):
@@ -554,7 +581,7 @@ def run_ours(args):
     e2e_value = world * cells * 2 / (float(e2e_t.item()) / 1e3) / 1e6
 
     # ---- roofline of the dominant kernel (its launches timed with events on the launching stream) ----
-    roof = roofline_mixed(trace, n) if mixed else roofline_from_trace(trace, n)
+    roof = roofline_mixed(trace, n, 8 if prec == vofp.FF else 4) if mixed else roofline_from_trace(trace, n)
 
     # ---- the other forms of the same path: mixed precision, batched ensemble, served stream ----
     variants = {}
@@ -567,15 +594,19 @@ def run_ours(args):
         torch.cuda.empty_cache()
         variants["batched"] = bench_batched(vofp, args)
         torch.cuda.empty_cache()
+        variants["batched_ff"] = bench_batched(vofp, args, prec=vofp.FF)
+        torch.cuda.empty_cache()
         variants["served"] = bench_served(vofp, args)
         torch.cuda.empty_cache()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "ff": "f32x2+f64"}[args.precision],
+                "data": "synthetic",
                 "config": {"workload": "droplet step %d^3 (project with Stefan source + liquid-velocity extension), "
-                                       "P,P,NN, %s" % (args.n, "mixed precision" if mixed else "FP64"),
+                                       "P,P,NN, %s" % (args.n, {"fp64": "FP64", "mixed": "mixed precision (FP32 + FP64 refinement)",
+                                                               "ff": "FP32-pair transforms"}[args.precision]),
                            "grid": list(n), "solves_per_step": 2,
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed between steps (256 MiB write, outside the events)"},

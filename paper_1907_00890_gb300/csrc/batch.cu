@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(256) k_ypass_batch(const YArgs* __restrict__ a
   ypass_block<T, C, INV>(a, l % gx, l / gx, smem_raw);
 }
 
+template <typename T>
 __global__ void __launch_bounds__(128) k_zsolve_batch(const ZArgs* __restrict__ args, const int* __restrict__ off,
                                                       int n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(128) k_zsolve_batch(const ZArgs* __restrict__ 
   const ZArgs& a = args[i];
   const int l = blockIdx.x - __ldg(off + i);
   const int gx = (a.nx + a.ti - 1) / a.ti;
-  zsolve_block<float, float>(a, l % gx, l / gx, smem_raw);
+  zsolve_block<T, T>(a, l % gx, l / gx, smem_raw);
 }
 
 // Per-instance z records: the low-eigenvalue systems and (bounded z) the factor-table arguments.
@@ -70,6 +71,7 @@ struct LowArgs {
 };
 
 // low-eigenvalue systems of all instances, periodic z: thread t of the flattened list
+template <typename T>
 __global__ void k_zlow_batch(const ZArgs* __restrict__ args, const LowArgs* __restrict__ low,
                              const int* __restrict__ off, int n, int total) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -79,10 +81,11 @@ __global__ void k_zlow_batch(const ZArgs* __restrict__ args, const LowArgs* __re
   if (launch_skipped(a.skip_conv, a.skip_k, a.tol2)) return;
   const int q = t - __ldg(off + i);
   const LowArgs& L = low[i];
-  zlow_system<float>(a, L.modes[q], q, L.nlow, L.tab, L.scratch);
+  zlow_system<T>(a, L.modes[q], q, L.nlow, L.tab, L.scratch);
 }
 
 // Bounded z: factor-table systems of all instances, 128 per block (one per thread).
+template <typename T, typename TT>
 __global__ void __launch_bounds__(128) k_ztab_batch(const ZArgs* __restrict__ args, const LowArgs* __restrict__ inst,
                                                     const int* __restrict__ off, int n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -91,10 +94,11 @@ __global__ void __launch_bounds__(128) k_ztab_batch(const ZArgs* __restrict__ ar
   const LowArgs& L = inst[i];
   const int l = blockIdx.x - __ldg(off + i);
   const int gx = (a.nx + 127) / 128;
-  ztab_block<float, float2>(a, L.zt, L.smem_d, l % gx, l / gx, smem_raw);
+  ztab_block<T, TT>(a, L.zt, L.smem_d, l % gx, l / gx, smem_raw);
 }
 
 // Bounded z: low-eigenvalue systems of all instances, one warp each.
+template <typename T>
 __global__ void __launch_bounds__(128) k_zlow_scan_batch(const ZArgs* __restrict__ args,
                                                          const LowArgs* __restrict__ low, const int* __restrict__ off,
                                                          int n, int total) {
@@ -105,7 +109,7 @@ __global__ void __launch_bounds__(128) k_zlow_scan_batch(const ZArgs* __restrict
   if (launch_skipped(a.skip_conv, a.skip_k, a.tol2)) return;
   const int q = w - __ldg(off + i);
   const LowArgs& L = low[i];
-  zlow_scan_system<float>(a, L.modes[q], q, L.nlow, L.tab, L.scratch, threadIdx.x & 31);
+  zlow_scan_system<T>(a, L.modes[q], q, L.nlow, L.tab, L.scratch, threadIdx.x & 31);
 }
 
 template <typename T, typename C>
@@ -170,6 +174,17 @@ static void allow_smem(K kern) {
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
 }
 
+template <typename T, typename C>
+static void allow_batch_kernels() {
+  allow_smem(k_xfwd_batch<T, C, RHS_DIV>);
+  allow_smem(k_xfwd_batch<T, C, RHS_RESID>);
+  allow_smem(k_ypass_batch<T, C, false>);
+  allow_smem(k_ypass_batch<T, C, true>);
+  allow_smem(k_zsolve_batch<T>);
+  allow_smem(k_ztab_batch<T, C>);
+  allow_smem(k_xinv_batch<T, C>);
+}
+
 }  // namespace vofp
 
 using namespace vofp;
@@ -189,6 +204,7 @@ struct vofp_batch {
   size_t o_offx, o_offy, o_offz, o_offlow, o_offepi;
   int tot_x, tot_y, tot_z, tot_low, tot_epi;
   bool ztab;  // every instance has a bounded z axis: factor-table z kernels
+  int prec;   // VOFP_MIXED (FP32 spectrum) or VOFP_FF (FP32-pair spectrum), the same for every instance
   size_t sm_x, sm_y, sm_z;
   cudaGraphExec_t exec;
   cudaStream_t captured_on;
@@ -205,7 +221,8 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
   int M = 0;
   for (int i = 0; i < n; ++i) {
     if (!plans[i]) return VOFP_ERR_INVALID_ARG;
-    if (plans[i]->opts.prec != VOFP_MIXED) return VOFP_ERR_UNSUPPORTED;
+    if (plans[i]->opts.prec != VOFP_MIXED && plans[i]->opts.prec != VOFP_FF) return VOFP_ERR_UNSUPPORTED;
+    if (plans[i]->opts.prec != plans[0]->opts.prec) return VOFP_ERR_INVALID_ARG;  // one precision per batch
     if (plans[i]->device != dev) return VOFP_ERR_INVALID_ARG;
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i]) return VOFP_ERR_INVALID_ARG;  // a plan's workspace serves one instance
@@ -220,6 +237,9 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
   b->device = dev;
   b->exec = nullptr;
   b->captured_on = nullptr;
+  b->prec = plans[0]->opts.prec;
+  const bool ffp = b->prec == VOFP_FF;
+  const size_t csz = ffp ? sizeof(cff) : sizeof(float2), rsz = ffp ? sizeof(ff) : sizeof(float);
   const int S = M + 1;
   size_t o = 0;
   b->o_x = o;
@@ -281,10 +301,10 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
     int eb = (int)((faces + 255) / 256);
     if (eb > 512) eb = 512;
     offe[i + 1] = offe[i] + eb;
-    const size_t sx = 2 * (size_t)p->xpb * nx * sizeof(float2);
-    const size_t sy = 2 * (size_t)(p->ytx32 / 2) * y_ld(ny) * sizeof(float2);
-    const ZTabShape zs = ztab_shape(128, nz, sizeof(float));
-    const size_t sz = b->ztab ? zs.smem : (size_t)(p->bc[2] == VOFP_BC_P ? 3 : 2) * p->zti32 * nz * sizeof(float);
+    const size_t sx = 2 * (size_t)p->xpb * nx * csz;
+    const size_t sy = 2 * (size_t)(p->ytx32 / 2) * y_ld(ny) * csz;
+    const ZTabShape zs = ztab_shape(128, nz, rsz);
+    const size_t sz = b->ztab ? zs.smem : (size_t)(p->bc[2] == VOFP_BC_P ? 3 : 2) * p->zti32 * nz * rsz;
     if (sx > b->sm_x) b->sm_x = sx;
     if (sy > b->sm_y) b->sm_y = sy;
     if (sz > b->sm_z) b->sm_z = sz;
@@ -294,13 +314,8 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
   b->tot_z = offz[n];
   b->tot_low = offl[n];
   b->tot_epi = offe[n];
-  allow_smem(k_xfwd_batch<float, float2, RHS_DIV>);
-  allow_smem(k_xfwd_batch<float, float2, RHS_RESID>);
-  allow_smem(k_ypass_batch<float, float2, false>);
-  allow_smem(k_ypass_batch<float, float2, true>);
-  allow_smem(k_zsolve_batch);
-  allow_smem(k_ztab_batch);
-  allow_smem(k_xinv_batch<float, float2>);
+  allow_batch_kernels<float, float2>();
+  allow_batch_kernels<ff, cff>();
   *out = b;
   return VOFP_OK;
 }
@@ -309,6 +324,7 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
 static void fill_args(vofp_batch* b, double* const* u, double* const* v, double* const* w, const double* const* src,
                       const double* dt, double* const* p) {
   const int n = b->n, S = b->M + 1;
+  const bool ffp = b->prec == VOFP_FF;
   XArgs* X = (XArgs*)(b->hstage + b->o_x);
   YArgs* YF = (YArgs*)(b->hstage + b->o_yf);
   YArgs* YI = (YArgs*)(b->hstage + b->o_yi);
@@ -328,8 +344,8 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
       XArgs xa = {};
       xa.g = grid_dev(pl);
       xa.fd = pl->ax[0].fd;
-      xa.tw = pl->ax[0].tw32;
-      xa.quart = pl->ax[0].quart32;
+      xa.tw = ffp ? (const void*)pl->ax[0].twff : (const void*)pl->ax[0].tw32;
+      xa.quart = ffp ? (const void*)pl->ax[0].quartff : (const void*)pl->ax[0].quart32;
       xa.pb = pl->xpb;
       xa.S = pl->S32;
       if (s == 0) {
@@ -361,8 +377,8 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
       ya.nz = pl->n[2];
       ya.bc = pl->bc[1];
       ya.fd = pl->ax[1].fd;
-      ya.tw = pl->ax[1].tw32;
-      ya.quart = pl->ax[1].quart32;
+      ya.tw = ffp ? (const void*)pl->ax[1].twff : (const void*)pl->ax[1].tw32;
+      ya.quart = ffp ? (const void*)pl->ax[1].quartff : (const void*)pl->ax[1].quart32;
       ya.tx = pl->ytx32;
       ya.S = pl->S32;
       ya.skip_conv = s == 0 ? nullptr : conv;
@@ -381,8 +397,8 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
       xi.nz = pl->n[2];
       xi.bc = pl->bc[0];
       xi.fd = pl->ax[0].fd;
-      xi.tw = pl->ax[0].tw32;
-      xi.quart = pl->ax[0].quart32;
+      xi.tw = ffp ? (const void*)pl->ax[0].twff : (const void*)pl->ax[0].tw32;
+      xi.quart = ffp ? (const void*)pl->ax[0].quartff : (const void*)pl->ax[0].quart32;
       xi.pb = pl->xpb;
       xi.S = pl->S32;
       xi.p = pout;
@@ -406,7 +422,7 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
     L[i].scratch = pl->lowscratch;
     L[i].tab = pl->lowtab;
     L[i].zt = ztab_args(pl);
-    L[i].smem_d = ztab_shape(128, pl->n[2], sizeof(float)).smem_d;
+    L[i].smem_d = ztab_shape(128, pl->n[2], ffp ? sizeof(ff) : sizeof(float)).smem_d;
     EpiArgs e;
     e.g = grid_dev(pl);
     e.p = pout;
@@ -421,7 +437,8 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
   }
 }
 
-static void launch_sequence(vofp_batch* b, cudaStream_t st) {
+template <typename T, typename C>
+static void launch_sequence_t(vofp_batch* b, cudaStream_t st) {
   const int n = b->n, S = b->M + 1;
   unsigned char* d = (unsigned char*)b->dmem;
   const int* offx = (const int*)(d + b->o_offx);
@@ -439,27 +456,34 @@ static void launch_sequence(vofp_batch* b, cudaStream_t st) {
     const ZArgs* Z = (const ZArgs*)(d + b->o_z) + (size_t)s * n;
     const XInvArgs* XI = (const XInvArgs*)(d + b->o_xi) + (size_t)s * n;
     if (s == 0)
-      VOFP_LAUNCH(KID_XFWD_DIV, st, (k_xfwd_batch<float, float2, RHS_DIV><<<b->tot_x, 256, b->sm_x, st>>>(X, offx, n)));
+      VOFP_LAUNCH(KID_XFWD_DIV, st, (k_xfwd_batch<T, C, RHS_DIV><<<b->tot_x, 256, b->sm_x, st>>>(X, offx, n)));
     else
-      VOFP_LAUNCH(KID_RESID, st, (k_xfwd_batch<float, float2, RHS_RESID><<<b->tot_x, 256, b->sm_x, st>>>(X, offx, n)));
+      VOFP_LAUNCH(KID_RESID, st, (k_xfwd_batch<T, C, RHS_RESID><<<b->tot_x, 256, b->sm_x, st>>>(X, offx, n)));
     if (b->tot_y > 0)
-      VOFP_LAUNCH(KID_YFWD, st, (k_ypass_batch<float, float2, false><<<b->tot_y, 256, b->sm_y, st>>>(YF, offy, n)));
+      VOFP_LAUNCH(KID_YFWD, st, (k_ypass_batch<T, C, false><<<b->tot_y, 256, b->sm_y, st>>>(YF, offy, n)));
     if (b->ztab) {
-      VOFP_LAUNCH(KID_ZSOLVE, st, k_ztab_batch<<<b->tot_z, 128, b->sm_z, st>>>(Z, L, offz, n));
+      VOFP_LAUNCH(KID_ZSOLVE, st, k_ztab_batch<T, C><<<b->tot_z, 128, b->sm_z, st>>>(Z, L, offz, n));
       if (b->tot_low > 0)
         VOFP_LAUNCH(KID_ZLOW, st,
-                    k_zlow_scan_batch<<<(b->tot_low + 3) / 4, 128, 0, st>>>(Z, L, offl, n, b->tot_low));
+                    k_zlow_scan_batch<T><<<(b->tot_low + 3) / 4, 128, 0, st>>>(Z, L, offl, n, b->tot_low));
     } else {
-      VOFP_LAUNCH(KID_ZSOLVE, st, k_zsolve_batch<<<b->tot_z, 128, b->sm_z, st>>>(Z, offz, n));
+      VOFP_LAUNCH(KID_ZSOLVE, st, k_zsolve_batch<T><<<b->tot_z, 128, b->sm_z, st>>>(Z, offz, n));
       if (b->tot_low > 0)
-        VOFP_LAUNCH(KID_ZLOW, st, k_zlow_batch<<<(b->tot_low + 63) / 64, 64, 0, st>>>(Z, L, offl, n, b->tot_low));
+        VOFP_LAUNCH(KID_ZLOW, st, k_zlow_batch<T><<<(b->tot_low + 63) / 64, 64, 0, st>>>(Z, L, offl, n, b->tot_low));
     }
     if (b->tot_y > 0)
-      VOFP_LAUNCH(KID_YINV, st, (k_ypass_batch<float, float2, true><<<b->tot_y, 256, b->sm_y, st>>>(YI, offy, n)));
-    VOFP_LAUNCH(KID_XINV, st, (k_xinv_batch<float, float2><<<b->tot_x, 256, b->sm_x, st>>>(XI, offx, n)));
+      VOFP_LAUNCH(KID_YINV, st, (k_ypass_batch<T, C, true><<<b->tot_y, 256, b->sm_y, st>>>(YI, offy, n)));
+    VOFP_LAUNCH(KID_XINV, st, (k_xinv_batch<T, C><<<b->tot_x, 256, b->sm_x, st>>>(XI, offx, n)));
   }
   VOFP_LAUNCH(KID_GAUGE, st, k_shift_batch<<<b->tot_epi, 256, 0, st>>>(E, offe, n));
   VOFP_LAUNCH(KID_GRAD, st, k_grad_batch<<<b->tot_epi, 256, 0, st>>>(E, offe, n));
+}
+
+static void launch_sequence(vofp_batch* b, cudaStream_t st) {
+  if (b->prec == VOFP_FF)
+    launch_sequence_t<ff, cff>(b, st);
+  else
+    launch_sequence_t<float, float2>(b, st);
 }
 
 extern "C" int vofp_batch_project(vofp_batch* b, double* const* u, double* const* v, double* const* w,

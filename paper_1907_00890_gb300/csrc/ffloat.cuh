@@ -91,4 +91,61 @@ __host__ __device__ __forceinline__ float lead(ff x) { return x.hi; }
 __host__ __device__ __forceinline__ ff ff_of(double x) { return ff(x); }
 __host__ __device__ __forceinline__ float lead(double x) { return (float)x; }
 
+// ---- conversions on the integer pipe ----------------------------------------------------------------------
+// On this GPU a conversion between FP64 and FP32 issues on the FP64 unit (same rate and latency as an FP64
+// multiply-add), so the reduced-precision passes split and join doubles with integer operations instead.
+// Magnitudes below the FP32 normal range are flushed to zero; above it they become infinities.
+
+// FP32 value of the 24 leading significand bits of a double (truncated, not rounded).
+__device__ __forceinline__ float f32_lead_bits(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi32 = (unsigned)(b >> 32);
+  const unsigned sign = hi32 & 0x80000000u;
+  const int e = (int)((hi32 >> 20) & 0x7ffu);
+  const int ef = e - 1023 + 127;
+  const unsigned m23 = (unsigned)(b >> 29) & 0x7fffffu;
+  unsigned r = sign | ((unsigned)ef << 23) | m23;
+  if (ef <= 0) r = sign;                                              // zero, subnormal range
+  if (ef >= 255) r = sign | 0x7f800000u | (e == 0x7ff && (b << 12) ? 1u : 0u);  // overflow, inf, nan
+  return __uint_as_float(r);
+}
+
+// Split a double into a normalised FP32 pair: hi = its 24 leading significand bits, lo = the next 24 of the
+// remaining 29 (relative error of the pair below 2^-47).
+__device__ __forceinline__ ff ff_split(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi32 = (unsigned)(b >> 32);
+  const unsigned sign = hi32 & 0x80000000u;
+  const int e = (int)((hi32 >> 20) & 0x7ffu);
+  const float hi = f32_lead_bits(d);
+  const unsigned rem = (unsigned)b & 0x1fffffffu;  // the 29 significand bits below hi
+  // rem * 2^(e - 1075): its leading one at bit p
+  const int p = 31 - __clz(rem | 1u);
+  const int elo = p + e - 1075 + 127;
+  const unsigned ml = (p >= 23 ? (rem >> (p - 23)) : (rem << (23 - p))) & 0x7fffffu;
+  unsigned lb = sign | ((unsigned)elo << 23) | ml;
+  if (rem == 0u || elo <= 0 || e - 1023 + 127 <= 0 || e - 1023 + 127 >= 255) lb = 0u;
+  return ff_fast_two_sum(hi, __uint_as_float(lb));
+}
+
+// Exact widening of a normal FP32 value to FP64 (zero and subnormals give zero; inf and nan pass).
+__device__ __forceinline__ double f64_of_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned ef = (u >> 23) & 0xffu;
+  const unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
+  unsigned long long r = sign | ((unsigned long long)(ef + 1023u - 127u) << 52) | m;
+  if (ef == 0u) r = sign;
+  if (ef == 255u) r = sign | 0x7ff0000000000000ull | m;
+  return __longlong_as_double((long long)r);
+}
+
+// Reduced-precision value <-> double with the conversions above (one FP64 addition for a pair).
+__device__ __forceinline__ float red_of(double d, float*) { return f32_lead_bits(d); }
+__device__ __forceinline__ ff red_of(double d, ff*) { return ff_split(d); }
+__device__ __forceinline__ double red_of(double d, double*) { return d; }
+__device__ __forceinline__ double wide_of(float x) { return f64_of_bits(x); }
+__device__ __forceinline__ double wide_of(ff x) { return f64_of_bits(x.hi) + f64_of_bits(x.lo); }
+__device__ __forceinline__ double wide_of(double x) { return x; }
+
 }  // namespace vofp

@@ -128,8 +128,8 @@ static void solve_red(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, b
   za.tol2 = tol2;
   if (pl->ztab) {
     // bulk systems from the factor table; the low-eigenvalue ones (a prefix of each row) by one warp each.
-    // FP32-pair recurrences on small grids: the shared-memory staged kernel (FP32 latency needs no staging)
-    if (!std::is_same<R, float>::value && ztab_use_staged(nx, ny, nz, sizeof(R))) {
+    // Small grids: the shared-memory staged kernel (too few systems to hide the row loads one thread each)
+    if (ztab_use_staged(nx, ny, nz, sizeof(R))) {
       const dim3 tgrid((nx + kZStagedTI - 1) / kZStagedTI, ny);
       VOFP_LAUNCH(KID_ZSOLVE, st,
                   (k_ztab_staged<R, typename Red<R>::TT><<<tgrid, 128, ztab_staged_smem(nz, sizeof(R)), st>>>(

@@ -144,13 +144,14 @@ __device__ __forceinline__ void xfwd_block(const XArgs& a, int bx, unsigned char
   for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
     const int pb = t / n, i = t - pb * n;
     const long l0 = 2 * (pair0 + pb), l1 = l0 + 1;
-    double fa = 0, fb = 0;
+    R fa = (R)0, fb = (R)0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const long l = h ? l1 : l0;
       if (l < nlines) {
         const int k = (int)(l / a.g.ny), j = (int)(l - (long)k * a.g.ny);
         const double f = rhs_at<MODE>(a, i, j, k, fbar);
+        const R fr = red_of(f, (R*)nullptr);  // integer-pipe conversion in reduced-precision plans
         if (a.fsave) a.fsave[l * n + i] = f;
         if (stats) {
           if (f64) {
@@ -159,16 +160,16 @@ __device__ __forceinline__ void xfwd_block(const XArgs& a, int bx, unsigned char
             acc_sq = fma(f, f, acc_sq);
             acc_fv = fma(f, vol, acc_fv);
           } else {
-            const float fs = (float)f;
+            const float fs = lead(fr);
             accf_abs = fmaf(fabsf(fs), __ldg(a.g.volf + k), accf_abs);
             accf_sq = fmaf(fs, fs, accf_sq);
             if (a.fv_out) acc_fv = fma(f, __ldg(a.g.vol + k), acc_fv);
           }
         }
         if (h)
-          fb = f;
+          fb = fr;
         else
-          fa = f;
+          fa = fr;
       }
     }
     int idx = i;
@@ -177,7 +178,7 @@ __device__ __forceinline__ void xfwd_block(const XArgs& a, int bx, unsigned char
       idx = dct_perm(i, n);
       fl = bc == VOFP_BC_DD && (i & 1);
     }
-    b0[pb * n + idx] = cmk<C>(neg_if((R)fa, fl), neg_if((R)fb, fl));
+    b0[pb * n + idx] = cmk<C>(neg_if(fa, fl), neg_if(fb, fl));
   }
   if (!f64) {
     acc_abs = accf_abs;
@@ -384,7 +385,7 @@ __device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned c
     }
     const C y = Y[pb * n + idx];
     const R ya = neg_if(y.x, fl), yb = neg_if(y.y, !fl);
-    const double va = (double)ya, vb = (double)yb;
+    const double va = wide_of(ya), vb = wide_of(yb);  // integer-pipe widening (one FP64 add for a pair)
     if (a.accumulate) {
       if (l0 < nlines) a.p[l0 * n + i] += va;
       if (l1 < nlines) a.p[l1 * n + i] += vb;

@@ -644,16 +644,31 @@ static __global__ void __launch_bounds__(128) k_ztab_staged(ZArgs a, ZTabArgs zt
   const int cut = zt.lowcut ? __ldg(zt.lowcut + j) : 0;
   const bool sing_here = a.singular && j == 0 && i0 == 0;  // the pinned mode is column 0 of this tile
   const int ncol = a.nx - i0 < TI ? a.nx - i0 : TI;
-  for (int t = threadIdx.x; t < nz * TI; t += blockDim.x) {
-    const int k = t / TI, c = t - k * TI;
-    const int i = i0 + c;
-    if (c < ncol && i >= cut) {
-      const TT f = F[k * ts + distinct_index(i, zt.bcx)];
-      Pair<T> v;
-      v.x = -(za[k] * f.y);
-      v.y = (S[k * plane + c] * sc) * f.y;
-      ab[t] = v;
-      cp[t] = f.x;
+  // tile load: eight rows per thread in flight (all loads issued before any is used)
+  constexpr int UL = 8;
+  for (int t0 = threadIdx.x; t0 < nz * TI; t0 += UL * blockDim.x) {
+    T rv[UL];
+    TT fv[UL];
+#pragma unroll
+    for (int u = 0; u < UL; ++u) {
+      const int t = t0 + u * blockDim.x;
+      const int k = t / TI, c = t - k * TI;
+      if (t < nz * TI && c < ncol && i0 + c >= cut) {
+        fv[u] = F[k * ts + distinct_index(i0 + c, zt.bcx)];
+        rv[u] = S[k * plane + c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UL; ++u) {
+      const int t = t0 + u * blockDim.x;
+      const int k = t / TI, c = t - k * TI;
+      if (t < nz * TI && c < ncol && i0 + c >= cut) {
+        Pair<T> v;
+        v.x = -(za[k] * fv[u].y);
+        v.y = (rv[u] * sc) * fv[u].y;
+        ab[t] = v;
+        cp[t] = fv[u].x;
+      }
     }
   }
   __syncthreads();

@@ -1,6 +1,7 @@
 """GPU tests of the batched projection (one launch per pass over all instances, replayed as a CUDA graph).
 
-* parity: every instance of a heterogeneous batch against the oracle (rel-L2 <= 1e-10, mixed precision);
+* parity: every instance of a heterogeneous batch against the oracle (rel-L2 <= 1e-10), for FP32 transforms
+  with refinement and for FP32-pair transforms; a batch of plans of different precisions is refused;
 * batch invariance: an instance's result alone (batch of one) and in the batch agree to 1e-12 relative (far
   inside the 1e-10 bar; they are not bitwise equal because the FP64 reductions add block partials with
   atomics, whose order varies from run to run);
@@ -44,13 +45,15 @@ CASES = [((32, 48, 40), ("P", "P", "NN")), ((48, 32, 64), ("P", "P", "NN")), ((2
          ((64, 64, 32), ("P", "P", "P")), ((33, 17, 12), ("DD", "P", "ND")), ((96, 40, 20), ("P", "NN", "DD"))]
 
 
-def make_instances(vp, cases, seed0):
+def make_instances(vp, cases, seed0, prec=None):
+    prec = vp.MIXED if prec is None else prec
     insts = []
     for idx, (n, bc) in enumerate(cases):
         dz = synth.stretched_dz(n[2]) if bc[2] != "P" else synth.uniform_dz(n[2])
         g = oracle.Grid(*n, 1.0 / n[0], 1.0 / n[1], dz, bc)
         u0 = synth.random_velocity(n, bc, seed0 + idx)
-        plan = vp.Plan(n, g.widths[0][0], g.widths[1][0], dz, bc, prec=vp.MIXED)
+        plan = vp.Plan(n, g.widths[0][0], g.widths[1][0], dz, bc, prec=prec,
+                       max_refine=0 if prec == vp.FF else 6)
         insts.append(dict(g=g, u0=u0, plan=plan))
     return insts
 
@@ -65,9 +68,10 @@ def run_batch(vp, insts, dts):
     return b, us, ps
 
 
-def test_batch_parity_invariance_and_replay(vp):
+@pytest.mark.parametrize("precision", ["mixed", "ff"])
+def test_batch_parity_invariance_and_replay(vp, precision):
     import torch
-    insts = make_instances(vp, CASES, 500)
+    insts = make_instances(vp, CASES, 500, vp.MIXED if precision == "mixed" else vp.FF)
     dts = [0.5, 1.0, 2.0, 0.25, 1.0, 0.1]
     b, us, ps = run_batch(vp, insts, dts)
     for it, u, p, dt in zip(insts, us, ps, dts):
@@ -101,11 +105,21 @@ def test_batch_parity_invariance_and_replay(vp):
         it["plan"].close()
 
 
-def test_batch_64_instance_ensemble(vp):
+def test_batch_refuses_mixed_precisions(vp):
+    a = vp.Plan((16, 16, 16), 1 / 16, 1 / 16, synth.uniform_dz(16), ("P", "P", "NN"), prec=vp.MIXED)
+    b = vp.Plan((16, 16, 16), 1 / 16, 1 / 16, synth.uniform_dz(16), ("P", "P", "NN"), prec=vp.FF)
+    with pytest.raises(vp.VofpError):
+        vp.vofp_batch_create([a.handle, b.handle])
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "ff"])
+def test_batch_64_instance_ensemble(vp, precision):
     import torch
     sizes = synth.batch_sizes(64)
     bc = ("P", "P", "NN")
-    insts = make_instances(vp, [(n, bc) for n in sizes], 900)
+    insts = make_instances(vp, [(n, bc) for n in sizes], 900, vp.MIXED if precision == "mixed" else vp.FF)
     dts = [1.0] * len(insts)
     b, us, ps = run_batch(vp, insts, dts)
     for it, u in zip(insts, us):
