@@ -28,6 +28,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the served stream runs up to 64 requests on their own streams: give them as many hardware queues as the
+# driver allows (set before the CUDA context exists)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "projection Mpts/s & p99 latency, served/mixed vs plain FP64, rel err ≤1e-10"
 UNIT = "Mpts/s"
@@ -98,7 +101,8 @@ def bench_mixed_step(vofp, c, u0, C, md, st, flush, args, prec=None, max_refine=
            "refine_iters_both_solves": info["refine_iters"], "rel_residual": info["rel_residual"],
            "per_kernel_ms": {k: round(v[0] / v[1], 5) for k, v in trace.items()},
            "per_step_ms": {k: round(v[0] / args.steps, 5) for k, v in trace.items()},
-           "roofline": roofline_mixed(trace, c["n"], rs)}
+           "roofline": roofline_mixed(trace, c["n"], rs,
+                                      "droplet%d_%s" % (c["n"][0], "mixed" if prec == vofp.MIXED else "ff"))}
     # outputs compared with the oracle's step (ue, ug, phi in the oracle's order) by the caller
     out["_outputs"] = [x.cpu().numpy() for x in ue] + [x.cpu().numpy() for x in ug] + [phi.cpu().numpy()]
     plan.close()
@@ -113,7 +117,7 @@ def mixed_bytes_per_cell(rs):
             "grad_update": 56, "extend_epilogue": 96, "stefan_source": 48}
 
 
-def roofline_mixed(trace, n, rs=4):
+def roofline_mixed(trace, n, rs=4, workload=None):
     """HBM roofline of the dominant kernel of the refinement path (among the kernel classes that touch every
     cell; the low-mode, gauge and reporting kernels touch a few columns or run once)."""
     per = mixed_bytes_per_cell(rs)
@@ -128,6 +132,7 @@ def roofline_mixed(trace, n, rs=4):
     gbs = by / (tot / cnt / 1e3) / 1e9
     return {"bound": "hbm", "kernel": name, "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
             "launches": cnt, "avg_launch_ms": tot / cnt, "bytes_per_cell": per[name], "peak_source": how,
+            "traffic": measured_traffic(workload, name) if workload else None,
             "note": "averages include launches that returned at once after convergence"}
 
 
@@ -189,11 +194,11 @@ def bench_large(vofp, args):
         if prec == vofp.FP64:
             ref = p.clone()
             r["dtype"] = "f64"
-            r["roofline"] = roofline_from_trace(trace, n)
+            r["roofline"] = roofline_from_trace(trace, n, "projection512_fp64")
         else:
             r["dtype"] = "f32+f64" if prec == vofp.MIXED else "f32x2+f64"
             r["rel_err_vs_fp64"] = float(torch.linalg.vector_norm(p - ref) / torch.linalg.vector_norm(ref))
-            r["roofline"] = roofline_mixed(trace, n, 8 if prec == vofp.FF else 4)
+            r["roofline"] = roofline_mixed(trace, n, 8 if prec == vofp.FF else 4, "projection512_" + name)
         out[name] = r
         plan.close()
         torch.cuda.empty_cache()
@@ -581,7 +586,8 @@ def run_ours(args):
     e2e_value = world * cells * 2 / (float(e2e_t.item()) / 1e3) / 1e6
 
     # ---- roofline of the dominant kernel (its launches timed with events on the launching stream) ----
-    roof = roofline_mixed(trace, n, 8 if prec == vofp.FF else 4) if mixed else roofline_from_trace(trace, n)
+    wl = "droplet%d_%s" % (args.n, args.precision)
+    roof = roofline_mixed(trace, n, 8 if prec == vofp.FF else 4, wl) if mixed else roofline_from_trace(trace, n, wl)
 
     # ---- the other forms of the same path: mixed precision, batched ensemble, served stream ----
     variants = {}
@@ -652,6 +658,32 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def source_sha():
+    """Digest of the CUDA sources: DRAM traffic recorded from an ncu capture is valid only for these kernels."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1907_00890_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload, kernel):
+    """DRAM bytes (read + write) per launch of a kernel class, from the ncu summary in profiles/traffic.json,
+    or None when that capture was taken on other kernel sources (or is missing)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+    except Exception:
+        return None
+    if t.get("source_sha") != source_sha():
+        return None
+    v = t.get("workloads", {}).get(workload, {}).get(kernel)
+    return float(v) if v is not None else None
+
+
 def algorithmic(kname, n):
     """Algorithmic HBM bytes and FP64 flops of one launch of kernel class ``kname`` on an n-grid.
 
@@ -683,7 +715,7 @@ def algorithmic(kname, n):
     return b * cells, f * cells
 
 
-def roofline_from_trace(trace, n):
+def roofline_from_trace(trace, n, workload=None):
     """Dominant kernel class (largest summed time) with its achieved rates against the peaks."""
     if not trace:
         return None
@@ -701,7 +733,8 @@ def roofline_from_trace(trace, n):
            "frac": gfl / FP64_NOMINAL_GFLOPS, "peak_source": "nominal FP64 rate of the recipe"}
     r = dict(alu if alu["frac"] >= mem["frac"] else mem)
     r.update({"kernel": name, "launches": cnt, "avg_launch_ms": tot_ms / cnt, "share_of_step": share,
-              "traffic": None, "other": mem if r["bound"] == "alu" else alu,
+              "traffic": measured_traffic(workload, name) if workload else None,
+              "other": mem if r["bound"] == "alu" else alu,
               "per_kernel_ms": {k: round(v[0] / v[1], 5) for k, v in trace.items()}})
     return r
 

@@ -181,7 +181,7 @@ static void allow_batch_kernels() {
   allow_smem(k_ypass_batch<T, C, false>);
   allow_smem(k_ypass_batch<T, C, true>);
   allow_smem(k_zsolve_batch<T>);
-  allow_smem(k_ztab_batch<T, C>);
+  allow_smem(k_ztab_batch<T, ZF<T>>);
   allow_smem(k_xinv_batch<T, C>);
 }
 
@@ -314,8 +314,10 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
   b->tot_z = offz[n];
   b->tot_low = offl[n];
   b->tot_epi = offe[n];
-  allow_batch_kernels<float, float2>();
-  allow_batch_kernels<ff, cff>();
+  if (first_use_on_device(2)) {
+    allow_batch_kernels<float, float2>();
+    allow_batch_kernels<ff, cff>();
+  }
   *out = b;
   return VOFP_OK;
 }
@@ -408,7 +410,7 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
       xi.tol2 = tol2;
       xi.dz = pl->dz;
       xi.dzff = pl->dzff;
-      xi.mean_out = pl->singular ? conv + VOFP_CONV_MEAN : nullptr;
+      xi.mean_out = (pl->singular && !ffp) ? conv + VOFP_CONV_MEAN : nullptr;  // FP32-pair: no gauge shift
       xi.d2_out = conv + VOFP_CONV_DEL + s;
       if (off) xa.skip_k = ya.skip_k = za.skip_k = xi.skip_k = -2;  // beyond this instance's own limit
       X[s * n + i] = xa;
@@ -430,7 +432,7 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
     e.v = v[i];
     e.w = w[i];
     e.s = dt[i];
-    e.mean = (pl->singular && p && p[i]) ? conv + VOFP_CONV_MEAN : nullptr;
+    e.mean = (pl->singular && !ffp && p && p[i]) ? conv + VOFP_CONV_MEAN : nullptr;
     e.mean_scale = 1.0 / ((double)pl->n[0] * pl->n[1] * (pl->volume / (pl->n[0] * pl->dx * pl->n[1] * pl->dy)));
     e.conv = conv;
     E[i] = e;
@@ -462,7 +464,7 @@ static void launch_sequence_t(vofp_batch* b, cudaStream_t st) {
     if (b->tot_y > 0)
       VOFP_LAUNCH(KID_YFWD, st, (k_ypass_batch<T, C, false><<<b->tot_y, 256, b->sm_y, st>>>(YF, offy, n)));
     if (b->ztab) {
-      VOFP_LAUNCH(KID_ZSOLVE, st, k_ztab_batch<T, C><<<b->tot_z, 128, b->sm_z, st>>>(Z, L, offz, n));
+      VOFP_LAUNCH(KID_ZSOLVE, st, k_ztab_batch<T, ZF<T>><<<b->tot_z, 128, b->sm_z, st>>>(Z, L, offz, n));
       if (b->tot_low > 0)
         VOFP_LAUNCH(KID_ZLOW, st,
                     k_zlow_scan_batch<T><<<(b->tot_low + 3) / 4, 128, 0, st>>>(Z, L, offl, n, b->tot_low));

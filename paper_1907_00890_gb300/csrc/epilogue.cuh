@@ -83,38 +83,61 @@ __host__ __device__ __forceinline__ size_t total_faces(const GridDev& g) {
          (size_t)g.nx * g.ny * nface(g.nz, g.bcz);
 }
 
-// u -= s * G p on all three face arrays (one flat index space).
-static __global__ void k_grad_update(GridDev g, const double* __restrict__ p, double* u, double* v, double* w, double s) {
-  const size_t total = total_faces(g);
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    int i, j, k;
-    size_t off;
-    const int axis = decode_face(g, t, i, j, k, off);
-    double gr;
-    if (!grad_on_face(g, p, axis, i, j, k, gr)) continue;
-    double* F = axis == 0 ? u : (axis == 1 ? v : w);
-    F[off] -= s * gr;
-  }
+// Face launch shape: blockIdx.z = axis, blockIdx.y = plane k of that face array, blockIdx.x * blockDim.x +
+// threadIdx.x = index within the plane (32-bit arithmetic; no 64-bit division per face).
+inline dim3 face_grid(const GridDev& g, int threads) {
+  const long a = (long)nface(g.nx, g.bcx) * g.ny, b = (long)g.nx * nface(g.ny, g.bcy), c = (long)g.nx * g.ny;
+  const long m = a > b ? (a > c ? a : c) : (b > c ? b : c);
+  return dim3((unsigned)((m + threads - 1) / threads), (unsigned)(g.nz + 1), 3);
+}
+__device__ __forceinline__ bool face_coord(const GridDev& g, int& axis, int& i, int& j, int& k, size_t& off) {
+  axis = blockIdx.z;
+  const int fx = axis == 0 ? nface(g.nx, g.bcx) : g.nx;
+  const int fy = axis == 1 ? nface(g.ny, g.bcy) : g.ny;
+  const int fz = axis == 2 ? nface(g.nz, g.bcz) : g.nz;
+  k = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= fz || idx >= fx * fy) return false;
+  j = idx / fx;
+  i = idx - j * fx;
+  off = ((size_t)k * fy + j) * fx + i;
+  return true;
 }
 
-// Interface geometry per cell: s = coef * mdot * |grad C| and n = -grad C / |grad C| (clipped).
-static __global__ void k_geometry(GridDev g, const double* __restrict__ C, const double* __restrict__ mdot, double coef,
-                           int mode, double* __restrict__ s, double* __restrict__ nx, double* __restrict__ ny,
-                           double* __restrict__ nz) {
-  const size_t total = (size_t)g.nx * g.ny * g.nz;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t % g.nx);
-    const size_t r = t / g.nx;
-    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-    double3 n;
-    const double m = geometry_at(g, C, i, j, k, mode, n);
-    s[t] = __ldg(mdot + t) * coef * m;
-    if (nx) {
-      nx[t] = n.x;
-      ny[t] = n.y;
-      nz[t] = n.z;
-    }
+// u -= s * G p on all three face arrays.
+static __global__ void __launch_bounds__(256) k_grad_update(GridDev g, const double* __restrict__ p, double* u,
+                                                           double* v, double* w, double s) {
+  int axis, i, j, k;
+  size_t off;
+  if (!face_coord(g, axis, i, j, k, off)) return;
+  double gr;
+  if (!grad_on_face(g, p, axis, i, j, k, gr)) return;
+  double* F = axis == 0 ? u : (axis == 1 ? v : w);
+  F[off] = fma(-s, gr, F[off]);
+}
+
+// Interface geometry per cell: s = coef * mdot * |grad C| and n = -grad C / |grad C| (clipped).  The
+// gradient stencil is a template argument (0 central, 1 Youngs) so each kernel carries only its own.
+template <int MODE>
+static __global__ void __launch_bounds__(256) k_geometry(GridDev g, const double* __restrict__ C,
+                                                        const double* __restrict__ mdot, double coef,
+                                                        double* __restrict__ s, double* __restrict__ nx,
+                                                        double* __restrict__ ny, double* __restrict__ nz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, k = blockIdx.z;
+  if (i >= g.nx) return;
+  const size_t t = ((size_t)k * g.ny + j) * g.nx + i;
+  double3 n;
+  const double m = geometry_at(g, C, i, j, k, MODE, n);
+  s[t] = __ldg(mdot + t) * coef * m;
+  if (nx) {
+    nx[t] = n.x;
+    ny[t] = n.y;
+    nz[t] = n.z;
   }
+}
+inline dim3 cell_grid(const GridDev& g, int threads) {
+  return dim3((unsigned)((g.nx + threads - 1) / threads), (unsigned)g.ny, (unsigned)g.nz);
 }
 
 // Twice the mean of a cell array over the cells adjacent to face (axis, i, j, k): the sum of the two
@@ -159,24 +182,21 @@ struct ExtArgs {
   double* wg;
 };
 
-static __global__ void k_extend_epi(ExtArgs a) {
+static __global__ void __launch_bounds__(256) k_extend_epi(ExtArgs a) {
   const GridDev& g = a.g;
-  const size_t total = total_faces(g);
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    int i, j, k;
-    size_t off;
-    const int axis = decode_face(g, t, i, j, k, off);
-    const double* U = axis == 0 ? a.u : (axis == 1 ? a.v : a.w);
-    double gr = 0;
-    grad_on_face(g, a.phi, axis, i, j, k, gr);
-    const double ue = __ldg(U + off) - gr;
-    (axis == 0 ? a.ue : (axis == 1 ? a.ve : a.we))[off] = ue;
-    if (a.ug) {
-      // (mean mdot)(mean n) / rho1 = (sum mdot)(sum n) / (4 rho1)
-      const double md = face_sum_arr(g, a.mdot, axis, i, j, k);
-      const double nf = face_sum_arr(g, a.n[axis], axis, i, j, k);
-      (axis == 0 ? a.ug : (axis == 1 ? a.vg : a.wg))[off] = fma(-a.quarter_inv_rho1 * md, nf, ue);
-    }
+  int axis, i, j, k;
+  size_t off;
+  if (!face_coord(g, axis, i, j, k, off)) return;
+  const double* U = axis == 0 ? a.u : (axis == 1 ? a.v : a.w);
+  double gr = 0;
+  grad_on_face(g, a.phi, axis, i, j, k, gr);
+  const double ue = __ldg(U + off) - gr;
+  (axis == 0 ? a.ue : (axis == 1 ? a.ve : a.we))[off] = ue;
+  if (a.ug) {
+    // (mean mdot)(mean n) / rho1 = (sum mdot)(sum n) / (4 rho1)
+    const double md = face_sum_arr(g, a.mdot, axis, i, j, k);
+    const double nf = face_sum_arr(g, a.n[axis], axis, i, j, k);
+    (axis == 0 ? a.ug : (axis == 1 ? a.vg : a.wg))[off] = fma(-a.quarter_inv_rho1 * md, nf, ue);
   }
 }
 

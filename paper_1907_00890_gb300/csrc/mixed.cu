@@ -41,8 +41,9 @@ static void allow_all() {
 }
 
 void init_kernel_attributes_mixed() {
-  allow_all<float, float2, float2>();
-  allow_all<ff, cff, cff>();
+  if (!first_use_on_device(1)) return;
+  allow_all<float, float2, ZF<float>>();
+  allow_all<ff, cff, ZF<ff>>();
 }
 
 int build_low_factors(vofp_plan* pl, cudaStream_t st, bool sync) {
@@ -86,14 +87,14 @@ struct Red;
 template <>
 struct Red<float> {
   typedef float2 C;
-  typedef float2 TT;  // z factor pair
+  typedef ZF<float> TT;  // z factor entry
   static const void* tw(const AxisDev& a) { return a.tw32; }
   static const void* quart(const AxisDev& a) { return a.quart32; }
 };
 template <>
 struct Red<ff> {
   typedef cff C;
-  typedef cff TT;
+  typedef ZF<ff> TT;
   static const void* tw(const AxisDev& a) { return a.twff; }
   static const void* quart(const AxisDev& a) { return a.quartff; }
 };
@@ -179,7 +180,9 @@ static void xinv_red(vofp_plan* pl, double* pout, int accumulate, int skip_k, do
   xi.tol2 = tol2;
   xi.dz = pl->dz;
   xi.dzff = pl->dzff;
-  xi.mean_out = pl->singular ? pl->conv + VOFP_CONV_MEAN : nullptr;
+  // gauge: the FP32 spectrum's rounding leaves p with a mean of ~1e-7 |p| that is removed in FP64 at the end;
+  // FP32-pair transforms keep the zero-mean gauge of the pinned mean mode to ~1e-14 and need no shift
+  xi.mean_out = (pl->singular && pl->opts.prec == VOFP_MIXED) ? pl->conv + VOFP_CONV_MEAN : nullptr;
   xi.d2_out = d2_out;
   const int xgrid = xpass_blocks(xi.ny, xi.nz, xi.pb);
   const size_t xsm = 2 * (size_t)xi.pb * xi.nx * sizeof(C);
@@ -266,7 +269,7 @@ int mixed_solve(vofp_plan* pl, int mode, const XArgs* xin, const double* f, doub
                     grid_dev(pl), pl->F, pout, pl->singular ? conv + 1 : nullptr, 1.0 / pl->volume,
                     conv + VOFP_CONV_FINAL, conv, -1, tol2));
   }
-  if (pl->singular && pout != pl->P) {
+  if (pl->singular && pl->opts.prec == VOFP_MIXED && pout != pl->P) {
     const double scale = 1.0 / ((double)pl->n[0] * pl->n[1] * (pl->volume / (pl->n[0] * pl->dx * pl->n[1] * pl->dy)));
     VOFP_LAUNCH(KID_GAUGE, st,
                 k_shift<<<grid_blocks(cells, 256), 256, 0, st>>>(pout, cells, conv + VOFP_CONV_MEAN, scale));

@@ -302,7 +302,7 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   off = align256(off + sizeof(double) * cells);
   L.S = L.T = L.S32 = L.F = L.lowscr = L.lowtab = 0;
   // bounded z: Thomas factor table per distinct eigenvalue pair in the plan's arithmetic type
-  const size_t tsz = o.prec == VOFP_MIXED ? sizeof(float2) : (o.prec == VOFP_FF ? sizeof(cff) : sizeof(double2));
+  const size_t tsz = o.prec == VOFP_MIXED ? 3 * sizeof(float) : (o.prec == VOFP_FF ? 3 * sizeof(ff) : 3 * sizeof(double));
   if (!mixed) {
     L.S = off;
     off = align256(off + sizeof(double) * cells);

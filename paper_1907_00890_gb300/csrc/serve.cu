@@ -4,10 +4,11 @@
 // thread admits them as in-flight slots and device memory free up: each admitted request gets a plan built
 // on the host (tables), placed in a block of the server's arena (one cudaMalloc at creation; the arena's
 // free list is the memory-based admission), uploaded and solved asynchronously on the slot's own stream,
-// so the work of requests admitted while others are on the GPU overlaps on the device.  A host callback
-// enqueued after each request's kernels stamps its completion, returns its arena block and slot and wakes
-// the worker: there is no cudaMalloc, cudaFree or device synchronisation on the serving path.  Latency is
-// measured from submission to that completion stamp.  Each request runs exactly the kernels it would run
+// so the work of requests admitted while others are on the GPU overlaps on the device.  An event recorded
+// after each request's kernels is polled by the worker (every 50 us while work is in flight), which then
+// stamps the completion and returns the arena block and slot: there is no cudaMalloc, cudaFree, host
+// callback or device synchronisation on the serving path.  Latency is measured from submission to that
+// completion stamp.  Each request runs exactly the kernels it would run
 // alone (its plan depends only on its own grid), so its result does not depend on what else is in flight.
 #include <algorithm>
 #include <chrono>
@@ -44,9 +45,11 @@ struct Req {
 
 struct Slot {
   cudaStream_t st;
+  cudaEvent_t done;  // recorded after the request's last kernel; polled by the worker
   unsigned char* stage;
   size_t stage_bytes;
   bool busy;
+  Req* req;
 };
 
 }  // namespace
@@ -69,6 +72,9 @@ struct vofp_server {
   // statistics
   std::vector<double> lat;
   unsigned long long completed, rejected, admitted;
+  long long queued;  // submitted, not yet admitted or rejected
+  double t_prepare, t_launch;  // worker seconds spent building plans and enqueuing work
+  unsigned long long loops;
   double cells_done;
   Clock::time_point t0;
 };
@@ -110,58 +116,48 @@ void arena_free(vofp_server* s, size_t off, size_t bytes) {
   }
 }
 
-struct DoneCtx {
-  vofp_server* s;
-  Req* q;
-};
-
-void CUDART_CB on_done(void* arg) {
-  DoneCtx* c = (DoneCtx*)arg;
-  vofp_server* s = c->s;
-  Req* q = c->q;
-  delete c;
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    q->t_done = Clock::now();
-    q->done = true;
-    arena_free(s, q->block_off, q->block_bytes);
-    s->slots[q->slot].busy = false;
-    plan_free_host(q->prep.p);
-    q->prep.p = nullptr;
-    q->prep.host.clear();
-    q->prep.host.shrink_to_fit();
-    s->completed++;
-    s->cells_done += (double)q->r.n[0] * q->r.n[1] * q->r.n[2];
-    s->lat.push_back(std::chrono::duration<double>(q->t_done - q->t_submit).count());
-  }
-  s->cv_work.notify_one();
-  s->cv_done.notify_all();
+// Completion of the request on slot `k` (lock held): stamp it, return its arena block and slot.
+void complete(vofp_server* s, int k, Clock::time_point t) {
+  Slot& sl = s->slots[k];
+  Req* q = sl.req;
+  q->t_done = t;
+  q->done = true;
+  arena_free(s, q->block_off, q->block_bytes);
+  sl.busy = false;
+  sl.req = nullptr;
+  s->completed++;
+  s->cells_done += (double)q->r.n[0] * q->r.n[1] * q->r.n[2];
+  s->lat.push_back(std::chrono::duration<double>(q->t_done - q->t_submit).count());
+  plan_free_host(q->prep.p);
+  q->prep.p = nullptr;
+  std::vector<unsigned char>().swap(q->prep.host);
 }
 
-// Try to admit request q (lock held).  Returns true if it was launched or rejected (removed from pending).
-bool try_admit(vofp_server* s, Req* q) {
-  if (!q->prepared) {
-    const int st = plan_prepare(q->r.n[0], q->r.n[1], q->r.n[2], q->r.dx, q->r.dy, q->dz.data(), q->r.bc, &s->opts,
-                                &q->prep);
-    if (st) {
-      q->status = st;
-      q->done = true;
-      q->t_done = Clock::now();
-      s->rejected++;
-      return true;
-    }
-    q->prepared = true;
-    q->block_bytes = plan_prep_device_bytes(&q->prep);
-    if (q->block_bytes > s->arena_bytes) {
-      q->status = VOFP_ERR_BUSY;
-      q->done = true;
-      q->t_done = Clock::now();
-      plan_free_host(q->prep.p);
-      q->prep.p = nullptr;
-      s->rejected++;
-      return true;
-    }
-  }
+// Host part of admission (no lock): build the plan's tables.  Returns a status; < 0 rejects the request.
+int prepare_request(vofp_server* s, Req* q) {
+  const int st = plan_prepare(q->r.n[0], q->r.n[1], q->r.n[2], q->r.dx, q->r.dy, q->dz.data(), q->r.bc, &s->opts,
+                              &q->prep);
+  if (st) return st;
+  q->prepared = true;
+  q->block_bytes = plan_prep_device_bytes(&q->prep);
+  if (q->block_bytes > s->arena_bytes) return VOFP_ERR_BUSY;              // can never fit
+  if (plan_prep_stage_bytes(&q->prep) > (size_t)(4 << 20)) return VOFP_ERR_UNSUPPORTED;  // staging size
+  return VOFP_OK;
+}
+
+// Finish a request that will not run (lock held).
+void reject(vofp_server* s, Req* q, int status) {
+  q->status = status;
+  q->done = true;
+  q->t_done = Clock::now();
+  if (q->prep.p) plan_free_host(q->prep.p);
+  q->prep.p = nullptr;
+  s->rejected++;
+  s->queued--;
+}
+
+// Reserve a slot and an arena block for a prepared request (lock held).  False: not now.
+bool reserve(vofp_server* s, Req* q) {
   int slot = -1;
   for (size_t i = 0; i < s->slots.size(); ++i)
     if (!s->slots[i].busy) {
@@ -171,65 +167,104 @@ bool try_admit(vofp_server* s, Req* q) {
   if (slot < 0) return false;
   size_t off;
   if (!arena_alloc(s, q->block_bytes, &off)) return false;
-  Slot& sl = s->slots[slot];
-  if (plan_prep_stage_bytes(&q->prep) > sl.stage_bytes) {
-    // (the staging buffers are sized at creation for axes up to 4096 cells; no pinned allocation here,
-    // which could wait on the device while the lock is held)
-    arena_free(s, off, q->block_bytes);
-    q->status = VOFP_ERR_UNSUPPORTED;
-    q->done = true;
-    q->t_done = Clock::now();
-    plan_free_host(q->prep.p);
-    q->prep.p = nullptr;
-    s->rejected++;
-    return true;
-  }
-  sl.busy = true;
+  s->slots[slot].busy = true;
   q->slot = slot;
   q->block_off = off;
-  int st = plan_bind(&q->prep, s->arena + off, sl.st, sl.stage);
-  if (!st) {
-    st = vofp_project(q->prep.p, q->r.u, q->r.v, q->r.w, q->r.src, q->r.dt_over_rho0, q->r.p, sl.st, nullptr);
-  }
-  q->status = st;
   s->admitted++;
-  DoneCtx* c = new DoneCtx{s, q};
-  if (cudaLaunchHostFunc(sl.st, on_done, c) != cudaSuccess) {
-    // could not enqueue the completion: finish synchronously
-    delete c;
-    cudaStreamSynchronize(sl.st);
-    q->t_done = Clock::now();
-    q->done = true;
-    arena_free(s, off, q->block_bytes);
-    sl.busy = false;
-    q->status = VOFP_ERR_CUDA;
-  }
+  s->queued--;
   return true;
 }
 
+// Upload the tables, enqueue the projection and record the slot's completion event (no lock).
+void launch_request(vofp_server* s, Req* q) {
+  Slot& sl = s->slots[q->slot];
+  int st = plan_bind(&q->prep, s->arena + q->block_off, sl.st, sl.stage);
+  if (!st) st = vofp_project(q->prep.p, q->r.u, q->r.v, q->r.w, q->r.src, q->r.dt_over_rho0, q->r.p, sl.st, nullptr);
+  if (cudaEventRecord(sl.done, sl.st) != cudaSuccess) {
+    cudaStreamSynchronize(sl.st);  // the worker's next poll then finds the event complete or in error
+    st = VOFP_ERR_CUDA;
+  }
+  q->status = st;
+}
+
+// The worker takes submitted requests into its own queue, builds their plans without holding the lock,
+// admits them oldest first as slots and arena memory allow (a large request does not block smaller ones),
+// launches each outside the lock, and retires finished ones by polling their slots' events -- no host
+// callbacks in the streams, which would stall the hardware queues the streams share.
 void worker_loop(vofp_server* s) {
   cudaSetDevice(s->device);
+  std::deque<Req*> local;
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
-    s->cv_work.wait(lk, [&] { return s->stop || !s->pending.empty(); });
-    if (s->stop && s->pending.empty()) break;
-    // admit every pending request that fits now, oldest first (a large request does not block smaller ones)
-    bool progress = false;
-    int scanned = 0;
-    for (auto it = s->pending.begin(); it != s->pending.end() && scanned < 256; ++scanned) {
+    s->loops++;
+    int inflight = 0;
+    for (const Slot& sl : s->slots) inflight += sl.busy;
+    if (local.empty() && inflight == 0) {
+      s->cv_work.wait(lk, [&] { return s->stop || !s->pending.empty(); });
+      if (s->stop && s->pending.empty()) break;
+    }
+    // retire finished requests
+    bool retired = false;
+    const Clock::time_point now = Clock::now();
+    for (size_t k = 0; k < s->slots.size(); ++k) {
+      if (!s->slots[k].busy || !s->slots[k].req) continue;
+      const cudaError_t e = cudaEventQuery(s->slots[k].done);
+      if (e == cudaErrorNotReady) continue;
+      if (e != cudaSuccess) s->slots[k].req->status = VOFP_ERR_CUDA;
+      complete(s, (int)k, now);
+      retired = true;
+    }
+    if (retired) s->cv_done.notify_all();
+    while (!s->pending.empty()) {
+      local.push_back(s->pending.front());
+      s->pending.pop_front();
+    }
+    // host tables for the new requests
+    std::vector<std::pair<Req*, int>> built;
+    for (Req* q : local)
+      if (!q->prepared && !q->done) built.emplace_back(q, 0);
+    if (!built.empty()) {
+      lk.unlock();
+      const Clock::time_point a = Clock::now();
+      for (auto& b : built) b.second = prepare_request(s, b.first);
+      const double dt = std::chrono::duration<double>(Clock::now() - a).count();
+      lk.lock();
+      s->t_prepare += dt;
+      for (auto& b : built)
+        if (b.second) {
+          reject(s, b.first, b.second);
+          s->cv_done.notify_all();
+        }
+    }
+    bool progress = retired;
+    for (auto it = local.begin(); it != local.end();) {
       Req* q = *it;
-      if (try_admit(s, q)) {
-        it = s->pending.erase(it);
+      if (q->done) {  // rejected above
+        it = local.erase(it);
         progress = true;
-        if (q->done) s->cv_done.notify_all();
-      } else {
-        ++it;
+        continue;
       }
+      if (!reserve(s, q)) {
+        ++it;
+        continue;
+      }
+      s->slots[q->slot].req = q;
+      it = local.erase(it);
+      lk.unlock();
+      const Clock::time_point a = Clock::now();
+      launch_request(s, q);
+      const double dt = std::chrono::duration<double>(Clock::now() - a).count();
+      lk.lock();
+      s->t_launch += dt;
+      progress = true;
     }
-    if (!progress && !s->pending.empty()) {
-      // nothing fits: wait for a completion (on_done notifies cv_work)
-      s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+    if (s->stop && s->pending.empty() && local.empty()) {
+      bool any = false;
+      for (const Slot& sl : s->slots) any |= sl.busy;
+      if (!any) break;
     }
+    // poll again shortly while work is on the GPU; a submission wakes the worker at once
+    if (!progress) s->cv_work.wait_for(lk, std::chrono::microseconds(50));
   }
 }
 
@@ -262,6 +297,8 @@ extern "C" int vofp_server_create(size_t mem_budget_bytes, int max_inflight, con
   s->slots.resize(max_inflight);
   for (auto& sl : s->slots) {
     cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    sl.req = nullptr;
     sl.stage_bytes = 4 << 20;
     if (cudaMallocHost((void**)&sl.stage, sl.stage_bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -273,6 +310,9 @@ extern "C" int vofp_server_create(size_t mem_budget_bytes, int max_inflight, con
   s->next_id = 1;
   s->stop = false;
   s->completed = s->rejected = s->admitted = 0;
+  s->queued = 0;
+  s->t_prepare = s->t_launch = 0;
+  s->loops = 0;
   s->cells_done = 0;
   s->t0 = Clock::now();
   init_kernel_attributes_fp64();
@@ -300,6 +340,7 @@ extern "C" int vofp_server_submit(vofp_server* s, const vofp_request* r, unsigne
     q->id = s->next_id++;
     s->all[q->id] = q;
     s->pending.push_back(q);
+    s->queued++;
     *ticket = q->id;
   }
   s->cv_work.notify_one();
@@ -339,8 +380,9 @@ extern "C" int vofp_server_wait(vofp_server* s, unsigned long long ticket, doubl
   return finish_ticket(s, q, info, latency_s);
 }
 
-// out[0] completed, [1] admitted, [2] rejected, [3] pending, [4] arena bytes in use, [5] arena bytes,
-// [6] p50 latency s, [7] p99 latency s, [8] cells solved (sum), [9] seconds since creation or reset.
+// out[0] completed, [1] admitted, [2] rejected, [3] queued, [4] arena bytes in use, [5] arena bytes,
+// [6] p50 latency s, [7] p99 latency s, [8] cells solved (sum), [9] seconds since creation or reset,
+// [10] worker seconds building plans, [11] worker seconds enqueuing work, [12] worker loop iterations.
 extern "C" int vofp_server_stats(vofp_server* s, double* out, int n, int reset) {
   if (!s || !out || n < 1) return VOFP_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(s->mu);
@@ -351,14 +393,17 @@ extern "C" int vofp_server_stats(vofp_server* s, double* out, int n, int reset) 
     size_t i = (size_t)(q * (l.size() - 1) + 0.5);
     return l[std::min(i, l.size() - 1)];
   };
-  double v[10] = {(double)s->completed, (double)s->admitted, (double)s->rejected, (double)s->pending.size(),
+  double v[13] = {(double)s->completed, (double)s->admitted, (double)s->rejected, (double)s->queued,
                   (double)s->in_use,    (double)s->arena_bytes, pct(0.50), pct(0.99), s->cells_done,
-                  std::chrono::duration<double>(Clock::now() - s->t0).count()};
-  for (int i = 0; i < n && i < 10; ++i) out[i] = v[i];
+                  std::chrono::duration<double>(Clock::now() - s->t0).count(), s->t_prepare, s->t_launch,
+                  (double)s->loops};
+  for (int i = 0; i < n && i < 13; ++i) out[i] = v[i];
   if (reset) {
     s->lat.clear();
     s->completed = s->admitted = s->rejected = 0;
     s->cells_done = 0;
+    s->t_prepare = s->t_launch = 0;
+    s->loops = 0;
     s->t0 = Clock::now();
   }
   return VOFP_OK;
@@ -379,6 +424,7 @@ extern "C" void vofp_server_destroy(vofp_server* s) {
   }
   for (auto& sl : s->slots) {
     cudaStreamDestroy(sl.st);
+    cudaEventDestroy(sl.done);
     if (sl.stage) cudaFreeHost(sl.stage);
   }
   cudaFree(s->arena);

@@ -5,6 +5,8 @@
 // One solve = x pass (right-hand side fused) -> y pass -> z tridiagonal pass -> inverse y -> inverse x,
 // then the face epilogue (§3.2 projection, §3.6 extension).  Every launch goes to the caller's stream.
 #include <cmath>
+#include <mutex>
+#include <set>
 #include <cstdio>
 
 #include "epilogue.cuh"
@@ -51,7 +53,17 @@ static void allow_smem(K kern) {
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
 }
 
+bool first_use_on_device(int which) {
+  static std::mutex mu;
+  static std::set<std::pair<int, int>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  return done.insert(std::make_pair(dev, which)).second;
+}
+
 void init_kernel_attributes_fp64() {
+  if (!first_use_on_device(0)) return;
   allow_smem(k_xfwd<double, double2, RHS_F>);
   allow_smem(k_xfwd<double, double2, RHS_DIV>);
   allow_smem(k_xfwd<double, double2, RHS_STEFAN>);
@@ -60,8 +72,8 @@ void init_kernel_attributes_fp64() {
   allow_smem(k_ypass<double, double2, true>);
   allow_smem(k_xinv<double, double2>);
   allow_smem(k_zsolve<double, double>);
-  allow_smem(k_ztab<double, double2>);
-  allow_smem(k_ztab_staged<double, double2>);
+  allow_smem(k_ztab<double, ZF<double>>);
+  allow_smem(k_ztab_staged<double, ZF<double>>);
 }
 
 int grid_blocks(size_t total, int threads) {
@@ -115,11 +127,11 @@ int build_z_factors(vofp_plan* pl, cudaStream_t st, bool sync) {
   const int n = pl->Ux * pl->Uy;
   const int nb = (n + 127) / 128;
   if (pl->opts.prec == VOFP_MIXED)
-    k_zfactor<float2><<<nb, 128, 0, st>>>(za, zt, (float2*)pl->ztab);
+    k_zfactor<ZF<float>><<<nb, 128, 0, st>>>(za, zt, (ZF<float>*)pl->ztab);
   else if (pl->opts.prec == VOFP_FF)
-    k_zfactor<cff><<<nb, 128, 0, st>>>(za, zt, (cff*)pl->ztab);
+    k_zfactor<ZF<ff>><<<nb, 128, 0, st>>>(za, zt, (ZF<ff>*)pl->ztab);
   else
-    k_zfactor<double2><<<nb, 128, 0, st>>>(za, zt, (double2*)pl->ztab);
+    k_zfactor<ZF<double>><<<nb, 128, 0, st>>>(za, zt, (ZF<double>*)pl->ztab);
   if (cudaGetLastError() != cudaSuccess) return VOFP_ERR_CUDA;
   if (sync && cudaStreamSynchronize(st) != cudaSuccess) return VOFP_ERR_CUDA;
   return VOFP_OK;
@@ -171,13 +183,13 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
   if (pl->ztab && ztab_use_staged(nx, ny, nz, sizeof(double))) {
     const dim3 tgrid((nx + kZStagedTI - 1) / kZStagedTI, ny);
     VOFP_LAUNCH(KID_ZSOLVE, st,
-                (k_ztab_staged<double, double2><<<tgrid, 128, ztab_staged_smem(nz, sizeof(double)), st>>>(
+                (k_ztab_staged<double, ZF<double>><<<tgrid, 128, ztab_staged_smem(nz, sizeof(double)), st>>>(
                     za, ztab_args(pl))));
   } else if (pl->ztab) {
     const ZTabShape zs = ztab_shape(pl->zti, nz, sizeof(double));
     const dim3 tgrid((nx + zs.threads - 1) / zs.threads, ny);
     VOFP_LAUNCH(KID_ZSOLVE, st,
-                (k_ztab<double, double2><<<tgrid, zs.threads, zs.smem, st>>>(za, ztab_args(pl), zs.smem_d)));
+                (k_ztab<double, ZF<double>><<<tgrid, zs.threads, zs.smem, st>>>(za, ztab_args(pl), zs.smem_d)));
   } else {
     const int nvec = pl->bc[2] == VOFP_BC_P ? 3 : 2;
     const size_t zsm = (size_t)nvec * za.ti * nz * sizeof(double);
@@ -234,10 +246,16 @@ static int launch_geometry(vofp_plan* pl, const double* C, const double* mdot, d
   const GridDev g = grid_dev(pl);
   const size_t cells = (size_t)g.nx * g.ny * g.nz;
   double* G = pl->G;
-  VOFP_LAUNCH(KID_STEFAN, st,
-              k_geometry<<<grid_blocks(cells, 256), 256, 0, st>>>(
-                  g, C, mdot, coef, pl->opts.grad_mode, s_out ? s_out : G, with_n ? G + cells : nullptr,
-                  with_n ? G + 2 * cells : nullptr, with_n ? G + 3 * cells : nullptr));
+  const int mode = pl->opts.grad_mode;
+  double* sp = s_out ? s_out : G;
+  double* n0 = with_n ? G + cells : nullptr;
+  double* n1 = with_n ? G + 2 * cells : nullptr;
+  double* n2 = with_n ? G + 3 * cells : nullptr;
+  const int th = g.nx >= 128 ? 128 : 64;
+  if (mode == 1)
+    VOFP_LAUNCH(KID_STEFAN, st, k_geometry<1><<<cell_grid(g, th), th, 0, st>>>(g, C, mdot, coef, sp, n0, n1, n2));
+  else
+    VOFP_LAUNCH(KID_STEFAN, st, k_geometry<0><<<cell_grid(g, th), th, 0, st>>>(g, C, mdot, coef, sp, n0, n1, n2));
   return cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
 }
 
@@ -255,9 +273,8 @@ static int project_common(vofp_plan* pl, int mode, XArgs& xa, double* u, double*
     if (s) return s;
   }
   const GridDev g = grid_dev(pl);
-  const size_t total = total_faces(g);
   VOFP_LAUNCH(KID_GRAD, st,
-              k_grad_update<<<grid_blocks(total, 256), 256, 0, st>>>(g, pout, u, v, w, dt_over_rho0));
+              k_grad_update<<<face_grid(g, 256), 256, 0, st>>>(g, pout, u, v, w, dt_over_rho0));
   const int ls = cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
   if (pl->opts.prec != VOFP_FP64) {
     if (ls) return ls;
@@ -305,8 +322,7 @@ static int extend_common(vofp_plan* pl, const double* u, const double* v, const 
   ea.ug = ug;
   ea.vg = vg;
   ea.wg = wg;
-  const size_t total = total_faces(ea.g);
-  VOFP_LAUNCH(KID_EXTEND_EPI, st, k_extend_epi<<<grid_blocks(total, 256), 256, 0, st>>>(ea));
+  VOFP_LAUNCH(KID_EXTEND_EPI, st, k_extend_epi<<<face_grid(ea.g, 256), 256, 0, st>>>(ea));
   const int ls = cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
   if (pl->opts.prec != VOFP_FP64) {
     if (ls) return ls;

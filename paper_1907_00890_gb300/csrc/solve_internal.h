@@ -89,6 +89,9 @@ ZTabArgs ztab_args(const vofp_plan* pl);
 int grid_blocks(size_t total, int threads);
 void init_kernel_attributes_fp64();
 void init_kernel_attributes_mixed();
+// True the first time it is called for the current device (each kernel's shared-memory attribute is set
+// once per device and process, not on every plan).
+bool first_use_on_device(int which);
 int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st, bool stats);
 // Mixed-precision solve: FP32 transforms with FP64 defect correction.  `xa` carries the right-hand-side
 // inputs for RHS_DIV / RHS_DIV_STEFAN (NULL for RHS_F, which reads `f`).  Fills `info` (if non-NULL) and

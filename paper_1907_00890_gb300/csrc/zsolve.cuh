@@ -272,22 +272,20 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return f
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ ff fma_t(ff a, ff b, ff c) { return a * b + c; }
 
-template <typename TT>
-__device__ __forceinline__ TT make_factor(double c, double m);
-template <>
-__device__ __forceinline__ double2 make_factor<double2>(double c, double m) {
-  return make_double2(c, m);
+// Factor-table element: c' = c'_k (back substitution), ms = s m_k (forward, with the transform scale s of the
+// z pass folded in), al = alpha_k = -a_k m_k (0 on the first eliminated row).  Forward: d_k = al d_{k-1} +
+// ms r_k; back: x_k = d_k - c' x_{k+1}; x is the scaled solution.
+template <typename T>
+struct ZF {
+  T c, ms, al;
+};
+
+__device__ __forceinline__ ZF<double> make_factor(double c, double ms, double al, ZF<double>*) { return {c, ms, al}; }
+__device__ __forceinline__ ZF<float> make_factor(double c, double ms, double al, ZF<float>*) {
+  return {(float)c, (float)ms, (float)al};
 }
-template <>
-__device__ __forceinline__ float2 make_factor<float2>(double c, double m) {
-  return make_float2((float)c, (float)m);
-}
-template <>
-__device__ __forceinline__ cff make_factor<cff>(double c, double m) {
-  cff r;
-  r.x = ff(c);
-  r.y = ff(m);
-  return r;
+__device__ __forceinline__ ZF<ff> make_factor(double c, double ms, double al, ZF<ff>*) {
+  return {ff(c), ff(ms), ff(al)};
 }
 
 template <typename TT>
@@ -301,13 +299,13 @@ static __global__ void k_zfactor(ZArgs a, ZTabArgs zt, TT* tab) {
   const bool sing = a.singular && ux == 0 && uy == 0;
   const int k0 = sing ? 1 : 0;
   const size_t stride = (size_t)zt.Ux * zt.Uy;
-  if (sing) tab[t] = make_factor<TT>(0.0, 0.0);
+  if (sing) tab[t] = make_factor(0.0, 0.0, 0.0, (TT*)nullptr);
   double cprev = 0.0;
   for (int k = k0; k < a.nz; ++k) {
     const double den = a.zb[k] + lam - (k > k0 ? a.za[k] * cprev : 0.0);
     const double m = 1.0 / den;
     const double c = (k < a.nz - 1 ? a.zc[k] : 0.0) * m;
-    tab[k * stride + t] = make_factor<TT>(c, m);
+    tab[k * stride + t] = make_factor(c, a.scale * m, k > k0 ? -a.za[k] * m : 0.0, (TT*)nullptr);
     cprev = c;
   }
 }
@@ -325,7 +323,7 @@ __device__ __forceinline__ bool ztab_sweep(T* __restrict__ col, T* __restrict__ 
                                            T sc, bool check) {
   constexpr int U = 8;
   T rb[U];
-  TT fb[U];
+  TT fb[U];  // ZF<T>
 #pragma unroll
   for (int u = 0; u < U; ++u)
     if (u < nz) {
@@ -338,8 +336,7 @@ __device__ __forceinline__ bool ztab_sweep(T* __restrict__ col, T* __restrict__ 
     for (int u = 0; u < U; ++u) {
       const int k = k0 + u;
       if (k < nz) {
-        const T m = fb[u].y;
-        const T al = -(za[k] * m), be = (rb[u] * sc) * m;  // off the dependent chain
+        const T al = fb[u].al, be = rb[u] * fb[u].ms;  // off the dependent chain
         if (k + U < nz) {
           rb[u] = col[(k + U) * plane];
           fb[u] = F[(k + U) * ts];
@@ -362,7 +359,7 @@ __device__ __forceinline__ bool ztab_sweep(T* __restrict__ col, T* __restrict__ 
     const int k = nz - 2 - u;
     if (k >= 0) {
       db[u] = SMEM ? dsm[k * TI] : col[k * plane];
-      cb[u] = F[k * ts].x;
+      cb[u] = F[k * ts].c;
     }
   }
   for (int k0 = nz - 2; k0 >= 0; k0 -= U) {
@@ -373,7 +370,7 @@ __device__ __forceinline__ bool ztab_sweep(T* __restrict__ col, T* __restrict__ 
         const T d = db[u], c = cb[u];
         if (k - U >= 0) {
           db[u] = SMEM ? dsm[(k - U) * TI] : col[(k - U) * plane];
-          cb[u] = F[(k - U) * ts].x;
+          cb[u] = F[(k - U) * ts].c;
         }
         x = fma_t(-c, x, d);
         col[k * plane] = x;
@@ -384,26 +381,26 @@ __device__ __forceinline__ bool ztab_sweep(T* __restrict__ col, T* __restrict__ 
   return bad;
 }
 
-// The pinned mean mode (singular operator, q = r = 0) on its scaled right-hand side: remove the
-// volume-weighted mean (the compatibility defect), fix p_0 = 0, eliminate rows 1..nz-1, back-substitute,
-// shift to zero volume-weighted mean.  One thread; `dcol` / `ds` is its forward-value column.
+// The pinned mean mode (singular operator, q = r = 0): remove the volume-weighted mean of its right-hand
+// side (the compatibility defect), fix p_0 = 0, eliminate rows 1..nz-1 (the table holds the pinned system's
+// factors), back-substitute, shift to zero volume-weighted mean.  One thread; `dcol` / `ds` is its
+// forward-value column.
 template <typename T, typename TT>
-__device__ bool ztab_singular(const ZArgs& a, T* col, T* dcol, size_t ds, size_t plane, const TT* F, size_t ts,
-                              const T* za) {
+__device__ bool ztab_singular(const ZArgs& a, T* col, T* dcol, size_t ds, size_t plane, const TT* F, size_t ts) {
   const int nz = a.nz;
-  const T sc = (T)a.scale;
   T s = (T)0;
-  for (int k = 0; k < nz; ++k) s += (T)__ldg(a.dz + k) * (col[k * plane] * sc);
-  const T defect = s / (T)a.lz;
-  if (a.info) a.info->compat_defect = (double)defect;
+  for (int k = 0; k < nz; ++k) s += (T)__ldg(a.dz + k) * col[k * plane];
+  const T defect = s / (T)a.lz;  // of the unscaled right-hand side
+  if (a.info) a.info->compat_defect = (double)defect * a.scale;
   T dp = (T)0;
   for (int k = 1; k < nz; ++k) {
-    dp = (col[k * plane] * sc - defect - (k > 1 ? za[k] * dp : (T)0)) * F[k * ts].y;
+    const TT f = F[k * ts];
+    dp = fma_t(f.al, dp, (col[k * plane] - defect) * f.ms);
     dcol[k * ds] = dp;
   }
   T x = dp;
   for (int k = nz - 2; k >= 1; --k) {
-    x = dcol[k * ds] - F[k * ts].x * x;
+    x = dcol[k * ds] - F[k * ts].c * x;
     dcol[k * ds] = x;
   }
   dcol[0] = (T)0;
@@ -437,8 +434,8 @@ __device__ __forceinline__ void ztab_block(const ZArgs& a, const ZTabArgs& zt, i
   const T* za = reinterpret_cast<const T*>(zt.za);
   bool bad;
   if (a.singular && i == 0 && j == 0)
-    bad = smem_d ? ztab_singular<T, TT>(a, col, dsm, TI, plane, F, ts, za)
-                 : ztab_singular<T, TT>(a, col, col, plane, plane, F, ts, za);
+    bad = smem_d ? ztab_singular<T, TT>(a, col, dsm, TI, plane, F, ts)
+                 : ztab_singular<T, TT>(a, col, col, plane, plane, F, ts);
   else if (smem_d)
     bad = ztab_sweep<T, TT, true>(col, dsm, plane, TI, F, ts, za, nz, (T)a.scale, a.info != nullptr);
   else
@@ -519,6 +516,15 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Uniform view of a factor entry: plan tables hold ZF already; the low-mode tables hold (c'_k, m_k).
+__device__ __forceinline__ ZF<double> fac_view(const double2& f, double za_k, double sc) {
+  return {f.x, sc * f.y, -za_k * f.y};
+}
+template <typename T>
+__device__ __forceinline__ ZF<T> fac_view(const ZF<T>& f, T, T) {
+  return f;
+}
+
 // One bounded-z system by one warp, arithmetic in T.  col: the system's column in the spectrum (stride plane,
 // storage TS); F: its factor pairs (c'_k, m_k) at stride fs; scr: nz forward values at stride ss.  sing: the
 // pinned mean mode (defect removed, p_0 = 0, zero volume-weighted mean; its factors are the pinned system's).
@@ -530,21 +536,21 @@ __device__ void zscan_system(const ZArgs& a, TS* col, size_t plane, const TT* F,
   const int R = (nz + 31) >> 5;
   const int k0 = lane * R < nz ? lane * R : nz;
   const int k1 = k0 + R < nz ? k0 + R : nz;
-  T defect = (T)0;
+  T defect = (T)0;  // of the unscaled right-hand side
   if (sing) {
     T s = (T)0;
-    for (int k = k0; k < k1; ++k) s += (T)__ldg(a.dz + k) * ((T)col[k * plane] * sc);
+    for (int k = k0; k < k1; ++k) s += (T)__ldg(a.dz + k) * (T)col[k * plane];
     defect = warp_sum(s) / (T)a.lz;
-    if (lane == 0 && a.info) a.info->compat_defect = (double)defect;
+    if (lane == 0 && a.info) a.info->compat_defect = (double)defect * a.scale;
   }
   const int kb = sing ? 1 : 0;  // first eliminated row (p_0 = 0 pinned in the singular mode)
   const int ks = k0 > kb ? k0 : kb;
   // forward: compose this lane's rows, scan, re-apply
   T A = (T)1, B = (T)0;
   for (int k = ks; k < k1; ++k) {
-    const TT f = F[k * fs];
-    const T al = k > kb ? -(za[k] * f.y) : (T)0;
-    const T be = ((T)col[k * plane] * sc - defect) * f.y;
+    const ZF<T> f = fac_view(F[k * fs], za[k], sc);
+    const T al = k > kb ? f.al : (T)0;
+    const T be = ((T)col[k * plane] - defect) * f.ms;
     B = fma_t(al, B, be);
     A = al * A;
   }
@@ -552,9 +558,9 @@ __device__ void zscan_system(const ZArgs& a, TS* col, size_t plane, const TT* F,
   T d = shfl_up_t(B, 1);
   if (lane == 0) d = (T)0;
   for (int k = ks; k < k1; ++k) {
-    const TT f = F[k * fs];
-    const T al = k > kb ? -(za[k] * f.y) : (T)0;
-    const T be = ((T)col[k * plane] * sc - defect) * f.y;
+    const ZF<T> f = fac_view(F[k * fs], za[k], sc);
+    const T al = k > kb ? f.al : (T)0;
+    const T be = ((T)col[k * plane] - defect) * f.ms;
     d = fma_t(al, d, be);
     scr[k * ss] = d;
   }
@@ -562,7 +568,7 @@ __device__ void zscan_system(const ZArgs& a, TS* col, size_t plane, const TT* F,
   A = (T)1;
   B = (T)0;
   for (int k = k1 - 1; k >= ks; --k) {
-    const T g = -F[k * fs].x;
+    const T g = -fac_view(F[k * fs], za[k], sc).c;
     B = fma_t(g, B, scr[k * ss]);
     A = g * A;
   }
@@ -571,7 +577,7 @@ __device__ void zscan_system(const ZArgs& a, TS* col, size_t plane, const TT* F,
   if (lane == 31) x = (T)0;
   T msum = (T)0;
   for (int k = k1 - 1; k >= ks; --k) {
-    const T g = -F[k * fs].x;
+    const T g = -fac_view(F[k * fs], za[k], sc).c;
     x = fma_t(g, x, scr[k * ss]);
     scr[k * ss] = x;
     if (sing) msum += (T)__ldg(a.dz + k) * x;
@@ -664,10 +670,10 @@ static __global__ void __launch_bounds__(128) k_ztab_staged(ZArgs a, ZTabArgs zt
       const int k = t / TI, c = t - k * TI;
       if (t < nz * TI && c < ncol && i0 + c >= cut) {
         Pair<T> v;
-        v.x = -(za[k] * fv[u].y);
-        v.y = (rv[u] * sc) * fv[u].y;
+        v.x = fv[u].al;
+        v.y = rv[u] * fv[u].ms;
         ab[t] = v;
-        cp[t] = fv[u].x;
+        cp[t] = fv[u].c;
       }
     }
   }

@@ -124,6 +124,32 @@ def test_mixed_manufactured_512_stretched(vp):
     plan.close()
 
 
+def test_refined_512_stretched_projection_vs_oracle(vp):
+    """The 512^3 stretched-z projection of random face velocities, element by element against the oracle
+    (itself corrected to the discrete solution): FP32 + refinement and FP32 pairs + one confirming
+    correction both within 1e-10 for p and u.  (A direct FP64 solve of this system, the GPU's or the oracle's
+    without its correction step, is off by eps * cond ~ 2e-10 in p, in the smoothest modes.)"""
+    import torch
+    n = (512, 512, 512)
+    bc = ("P", "P", "NN")
+    dz = synth.stretched_dz(n[2])
+    g = oracle.Grid(*n, 1.0 / n[0], 1.0 / n[1], dz, bc)
+    u0 = synth.random_velocity(n, bc, 2024)
+    ref = oracle.project(g, *u0, dt_over_rho0=1.0)
+    for prec in (vp.MIXED, vp.FF):
+        plan = vp.Plan(n, g.widths[0][0], g.widths[1][0], dz, bc, prec=prec, max_refine=6)
+        u = [dev(a) for a in u0]
+        p = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+        _, info = vp.vofp_project(plan.handle, *u, None, 1.0, p, info=True)
+        assert rel(host(p), ref[3]) < TOL, (prec, info)
+        for a in range(3):
+            assert rel(host(u[a]), ref[a]) < TOL
+        assert info["rel_residual"] <= TOL
+        plan.close()
+        del u, p
+        torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("bcx,bcy,bcz", [("P", "P", "NN"), ("NN", "DD", "DN"), ("DD", "P", "P"), ("P", "NN", "ND")])
 @pytest.mark.parametrize("max_refine", [0, 6])
 def test_ff_poisson(vp, bcx, bcy, bcz, max_refine):
