@@ -301,8 +301,8 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
     int eb = (int)((faces + 255) / 256);
     if (eb > 512) eb = 512;
     offe[i + 1] = offe[i] + eb;
-    const size_t sx = 2 * (size_t)p->xpb * nx * csz;
-    const size_t sy = 2 * (size_t)(p->ytx32 / 2) * y_ld(ny) * csz;
+    const size_t sx = 2 * (size_t)p->xpb * fft_span(p->ax[0].fd, p->ax[0].blu64) * csz;
+    const size_t sy = 2 * (size_t)(p->ytx32 / 2) * y_ld(fft_span(p->ax[1].fd, p->ax[1].blu64)) * csz;
     const ZTabShape zs = ztab_shape(128, nz, rsz);
     const size_t sz = b->ztab ? zs.smem : (size_t)(p->bc[2] == VOFP_BC_P ? 3 : 2) * p->zti32 * nz * rsz;
     if (sx > b->sm_x) b->sm_x = sx;
@@ -348,6 +348,7 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
       xa.fd = pl->ax[0].fd;
       xa.tw = ffp ? (const void*)pl->ax[0].twff : (const void*)pl->ax[0].tw32;
       xa.quart = ffp ? (const void*)pl->ax[0].quartff : (const void*)pl->ax[0].quart32;
+      xa.blu = ffp ? (const void*)pl->ax[0].bluff : (const void*)pl->ax[0].blu32;
       xa.pb = pl->xpb;
       xa.S = pl->S32;
       if (s == 0) {
@@ -381,6 +382,7 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
       ya.fd = pl->ax[1].fd;
       ya.tw = ffp ? (const void*)pl->ax[1].twff : (const void*)pl->ax[1].tw32;
       ya.quart = ffp ? (const void*)pl->ax[1].quartff : (const void*)pl->ax[1].quart32;
+      ya.blu = ffp ? (const void*)pl->ax[1].bluff : (const void*)pl->ax[1].blu32;
       ya.tx = pl->ytx32;
       ya.S = pl->S32;
       ya.skip_conv = s == 0 ? nullptr : conv;
@@ -401,6 +403,7 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
       xi.fd = pl->ax[0].fd;
       xi.tw = ffp ? (const void*)pl->ax[0].twff : (const void*)pl->ax[0].tw32;
       xi.quart = ffp ? (const void*)pl->ax[0].quartff : (const void*)pl->ax[0].quart32;
+      xi.blu = ffp ? (const void*)pl->ax[0].bluff : (const void*)pl->ax[0].blu32;
       xi.pb = pl->xpb;
       xi.S = pl->S32;
       xi.p = pout;

@@ -90,6 +90,7 @@ struct Red<float> {
   typedef ZF<float> TT;  // z factor entry
   static const void* tw(const AxisDev& a) { return a.tw32; }
   static const void* quart(const AxisDev& a) { return a.quart32; }
+  static const void* blu(const AxisDev& a) { return a.blu32; }
 };
 template <>
 struct Red<ff> {
@@ -97,6 +98,7 @@ struct Red<ff> {
   typedef ZF<ff> TT;
   static const void* tw(const AxisDev& a) { return a.twff; }
   static const void* quart(const AxisDev& a) { return a.quartff; }
+  static const void* blu(const AxisDev& a) { return a.bluff; }
 };
 
 // y forward, z (bulk + FP64 low modes), y inverse on the spectrum; skipped when converged.
@@ -112,13 +114,14 @@ static void solve_red(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, b
   ya.fd = pl->ax[1].fd;
   ya.tw = Red<R>::tw(pl->ax[1]);
   ya.quart = Red<R>::quart(pl->ax[1]);
+  ya.blu = Red<R>::blu(pl->ax[1]);
   ya.tx = pl->ytx32;
   ya.S = pl->S32;
   ya.skip_conv = pl->conv;
   ya.skip_k = skip_k;
   ya.tol2 = tol2;
   const dim3 ygrid((nx + ya.tx - 1) / ya.tx, nz);
-  const size_t ysm = 2 * (size_t)(ya.tx / 2) * y_ld(ny) * sizeof(C);
+  const size_t ysm = 2 * (size_t)(ya.tx / 2) * y_ld(fft_span(ya.fd, ya.blu)) * sizeof(C);
   if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, (k_ypass<R, C, false><<<ygrid, 256, ysm, st>>>(ya)));
   ZArgs za = z_args(pl, stats);
   za.S = pl->S32;
@@ -171,6 +174,7 @@ static void xinv_red(vofp_plan* pl, double* pout, int accumulate, int skip_k, do
   xi.fd = pl->ax[0].fd;
   xi.tw = Red<R>::tw(pl->ax[0]);
   xi.quart = Red<R>::quart(pl->ax[0]);
+  xi.blu = Red<R>::blu(pl->ax[0]);
   xi.pb = pl->xpb;
   xi.S = pl->S32;
   xi.p = pout;
@@ -185,7 +189,7 @@ static void xinv_red(vofp_plan* pl, double* pout, int accumulate, int skip_k, do
   xi.mean_out = (pl->singular && pl->opts.prec == VOFP_MIXED) ? pl->conv + VOFP_CONV_MEAN : nullptr;
   xi.d2_out = d2_out;
   const int xgrid = xpass_blocks(xi.ny, xi.nz, xi.pb);
-  const size_t xsm = 2 * (size_t)xi.pb * xi.nx * sizeof(C);
+  const size_t xsm = 2 * (size_t)xi.pb * fft_span(xi.fd, xi.blu) * sizeof(C);
   VOFP_LAUNCH(KID_XINV, st, (k_xinv<R, C><<<xgrid, 256, xsm, st>>>(xi)));
 }
 
@@ -196,10 +200,11 @@ static void xfwd_red(vofp_plan* pl, int mode, XArgs xa, cudaStream_t st) {
   xa.fd = pl->ax[0].fd;
   xa.tw = Red<R>::tw(pl->ax[0]);
   xa.quart = Red<R>::quart(pl->ax[0]);
+  xa.blu = Red<R>::blu(pl->ax[0]);
   xa.pb = pl->xpb;
   xa.S = pl->S32;
   const int xgrid = xpass_blocks(pl->n[1], pl->n[2], xa.pb);
-  const size_t xsm = 2 * (size_t)xa.pb * pl->n[0] * sizeof(C);
+  const size_t xsm = 2 * (size_t)xa.pb * fft_span(xa.fd, xa.blu) * sizeof(C);
   switch (mode) {
     case RHS_F: VOFP_LAUNCH(KID_XFWD, st, (k_xfwd<R, C, RHS_F><<<xgrid, 256, xsm, st>>>(xa))); break;
     case RHS_DIV: VOFP_LAUNCH(KID_XFWD_DIV, st, (k_xfwd<R, C, RHS_DIV><<<xgrid, 256, xsm, st>>>(xa))); break;

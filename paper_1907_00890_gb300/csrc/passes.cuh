@@ -22,7 +22,8 @@ struct XArgs {
   GridDev g;
   FftDesc fd;
   const void* tw;     // complex twiddles of the compute precision
-  const void* quart;  // quarter-wave twiddles
+  const void* quart;
+  const void* blu;  // Bluestein tables of the x axis (NULL: direct stages)  // quarter-wave twiddles
   int pb;             // line pairs per block
   // right-hand side inputs
   const double* f;    // RHS_F: f;  RHS_RESID: f (FP64)
@@ -129,7 +130,8 @@ __device__ __forceinline__ void xfwd_block(const XArgs& a, int bx, unsigned char
   C* b0 = reinterpret_cast<C*>(smem_raw);
   const int n = a.g.nx;
   const int PB = a.pb;
-  C* b1 = b0 + PB * n;
+  const int ld = fft_span(a.fd, a.blu);
+  C* b1 = b0 + PB * ld;
   if (launch_skipped(a.skip_conv, a.skip_k, a.tol2)) return;
   const long nlines = (long)a.g.ny * a.g.nz;
   const long pair0 = (long)bx * PB;
@@ -178,7 +180,7 @@ __device__ __forceinline__ void xfwd_block(const XArgs& a, int bx, unsigned char
       idx = dct_perm(i, n);
       fl = bc == VOFP_BC_DD && (i & 1);
     }
-    b0[pb * n + idx] = cmk<C>(neg_if(fa, fl), neg_if(fb, fl));
+    b0[pb * ld + idx] = cmk<C>(neg_if(fa, fl), neg_if(fb, fl));
   }
   if (!f64) {
     acc_abs = accf_abs;
@@ -200,14 +202,15 @@ __device__ __forceinline__ void xfwd_block(const XArgs& a, int bx, unsigned char
     if (threadIdx.x == 0 && s3 != 0) atomicAdd(a.fv_out, s3);
   }
   __syncthreads();
-  const C* Z = fft_smem<C>(b0, b1, PB, a.fd, reinterpret_cast<const C*>(a.tw), n);
+  const C* Z = fft_smem<C>(b0, b1, PB, a.fd, reinterpret_cast<const C*>(a.tw), ld,
+                           reinterpret_cast<const C*>(a.blu));
   const C* quart = reinterpret_cast<const C*>(a.quart);
   T* S = reinterpret_cast<T*>(a.S);
   for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
     const int pb = t / n, q = t - pb * n;
     const long l0 = 2 * (pair0 + pb), l1 = l0 + 1;
     R oa, ob;
-    fwd_post<C>(Z + pb * n, n, bc, q, quart, oa, ob);
+    fwd_post<C>(Z + pb * ld, n, bc, q, quart, oa, ob);
     if (l0 < nlines) S[l0 * n + q] = (T)oa;
     if (l1 < nlines) S[l1 * n + q] = (T)ob;
   }
@@ -231,6 +234,7 @@ struct YArgs {
   FftDesc fd;
   const void* tw;
   const void* quart;
+  const void* blu;
   int tx;  // columns per block (even)
   void* S;
   const double* skip_conv;
@@ -246,7 +250,7 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
   const int n = a.ny;
   const int B = a.tx >> 1;
   C* b0 = reinterpret_cast<C*>(smem_raw);
-  const int ld = y_ld(n);
+  const int ld = y_ld(fft_span(a.fd, a.blu));
   C* b1 = b0 + B * ld;
   const int i0 = bx * a.tx;
   const size_t base = (size_t)by * a.ny * a.nx;
@@ -269,7 +273,8 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
       b0[c * ld + idx] = cmk<C>(neg_if(va, fl), neg_if(vb, fl));
     }
     __syncthreads();
-    const C* Z = fft_smem<C>(b0, b1, B, a.fd, reinterpret_cast<const C*>(a.tw), ld);
+    const C* Z = fft_smem<C>(b0, b1, B, a.fd, reinterpret_cast<const C*>(a.tw), ld,
+                             reinterpret_cast<const C*>(a.blu));
     for (int t = threadIdx.x; t < B * n; t += blockDim.x) {
       const int c = t % B, q = t / B;
       const int i = i0 + 2 * c;
@@ -297,7 +302,8 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
       b0[c * ld + m] = inv_pre<C>([&](int q) { return ra[q]; }, [&](int q) { return rb[q]; }, n, bc, m, quart);
     }
     __syncthreads();
-    const C* Y = fft_smem<C>(b0, b1, B, a.fd, reinterpret_cast<const C*>(a.tw), ld);
+    const C* Y = fft_smem<C>(b0, b1, B, a.fd, reinterpret_cast<const C*>(a.tw), ld,
+                             reinterpret_cast<const C*>(a.blu));
     for (int t = threadIdx.x; t < B * n; t += blockDim.x) {
       const int c = t % B, j = t / B;
       const int i = i0 + 2 * c;
@@ -326,6 +332,7 @@ struct XInvArgs {
   FftDesc fd;
   const void* tw;
   const void* quart;
+  const void* blu;
   int pb;
   const void* S;
   double* p;
@@ -346,8 +353,9 @@ __device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned c
   if (launch_skipped(a.skip_conv, a.skip_k, a.tol2)) return;
   const int n = a.nx;
   const int PB = a.pb;
+  const int ld = fft_span(a.fd, a.blu);
   C* b0 = reinterpret_cast<C*>(smem_raw);
-  C* b1 = b0 + PB * n;
+  C* b1 = b0 + PB * ld;
   const long nlines = (long)a.ny * a.nz;
   const long pair0 = (long)bx * PB;
   const T* S = reinterpret_cast<const T*>(a.S);
@@ -363,10 +371,11 @@ __device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned c
     const int pb = t / n, m = t - pb * n;
     const R* ra = st + (2 * pb) * n;
     const R* rb = st + (2 * pb + 1) * n;
-    b0[pb * n + m] = inv_pre<C>([&](int q) { return ra[q]; }, [&](int q) { return rb[q]; }, n, bc, m, quart);
+    b0[pb * ld + m] = inv_pre<C>([&](int q) { return ra[q]; }, [&](int q) { return rb[q]; }, n, bc, m, quart);
   }
   __syncthreads();
-  const C* Y = fft_smem<C>(b0, b1, PB, a.fd, reinterpret_cast<const C*>(a.tw), n);
+  const C* Y = fft_smem<C>(b0, b1, PB, a.fd, reinterpret_cast<const C*>(a.tw), ld,
+                           reinterpret_cast<const C*>(a.blu));
   // FP64 plans sum in FP64.  Reduced-precision plans: the correction's size (a threshold) in FP32 and its
   // gauge sum (subtracted from p at the end, so it must be exact to well below the tolerance) in FP32 pairs
   // of FP32 products -- no FP64 arithmetic per cell beyond the addition into p.
@@ -383,7 +392,7 @@ __device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned c
       idx = dct_perm(i, n);
       fl = bc == VOFP_BC_DD && (i & 1);
     }
-    const C y = Y[pb * n + idx];
+    const C y = Y[pb * ld + idx];
     const R ya = neg_if(y.x, fl), yb = neg_if(y.y, !fl);
     const double va = wide_of(ya), vb = wide_of(yb);  // integer-pipe widening (one FP64 add for a pair)
     if (a.accumulate) {

@@ -13,6 +13,7 @@
 // handed in by the caller (the server's arena) with asynchronous uploads on a stream.
 #include <atomic>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -60,6 +61,75 @@ void factor_radices(int n, FftDesc* fd) {
       m = 1;
     }
   }
+  // a prime factor above 7 makes a stage cost O(p) per point: such lengths also get the Bluestein form
+  int maxp = 1;
+  for (int s = 0; s < fd->nst; ++s)
+    if (fd->radix[s] > maxp && fd->radix[s] != 8 && fd->radix[s] != 4) maxp = fd->radix[s];
+  fd->bm = 0;
+  fd->bst = 0;
+  if (maxp > 7 && 2 * n - 1 <= 4096) {  // (longer lines would not fit in shared memory twice over)
+    int M = 1, e2 = 0;
+    while (M < 2 * n - 1) {
+      M *= 2;
+      ++e2;
+    }
+    fd->bm = M;
+    int b8 = e2 / 3, br = e2 % 3;
+    if (br == 1 && b8 > 0) {
+      --b8;
+      fd->bradix[fd->bst++] = 4;
+      fd->bradix[fd->bst++] = 4;
+    } else if (br == 1) {
+      fd->bradix[fd->bst++] = 2;
+    } else if (br == 2) {
+      fd->bradix[fd->bst++] = 4;
+    }
+    for (int i = 0; i < b8; ++i) fd->bradix[fd->bst++] = 8;
+  }
+}
+
+// In-place forward DFT of length M (a power of two) in FP64 on the host (iterative radix 2), for the
+// Bluestein kernel spectrum.
+static void host_fft_pow2(std::vector<std::complex<double>>& x) {
+  const size_t M = x.size();
+  for (size_t i = 1, j = 0; i < M; ++i) {
+    size_t bit = M >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(x[i], x[j]);
+  }
+  for (size_t len = 2; len <= M; len <<= 1) {
+    const double ang = -2.0 * 3.14159265358979323846 / (double)len;
+    for (size_t i = 0; i < M; i += len)
+      for (size_t k = 0; k < len / 2; ++k) {
+        const std::complex<double> w(std::cos(ang * (double)k), std::sin(ang * (double)k));
+        const std::complex<double> u = x[i + k], v = x[i + k + len / 2] * w;
+        x[i + k] = u + v;
+        x[i + k + len / 2] = u - v;
+      }
+  }
+}
+
+// Bluestein tables of an axis (see fft_smem): chirp (n), kernel spectrum / M (M), M-point twiddles (M).
+static std::vector<double2> bluestein_tables(const FftDesc& fd) {
+  const int n = fd.n, M = fd.bm;
+  std::vector<double2> t((size_t)n + 2 * (size_t)M);
+  std::vector<std::complex<double>> h(M, std::complex<double>(0.0, 0.0));
+  for (int j = 0; j < n; ++j) {
+    const long long r = ((long long)j * j) % (2LL * n);  // exact reduction of j^2 modulo 2n
+    const double ang = -3.14159265358979323846 * (double)r / (double)n;
+    t[j] = make_double2(std::cos(ang), std::sin(ang));
+    const std::complex<double> c(std::cos(ang), -std::sin(ang));  // conj(w_j)
+    h[j] = c;
+    if (j > 0) h[M - j] = c;
+  }
+  host_fft_pow2(h);
+  for (int k = 0; k < M; ++k) t[n + k] = make_double2(h[k].real() / M, h[k].imag() / M);
+  for (int q = 0; q < M; ++q) {
+    const double ang = -2.0 * 3.14159265358979323846 * q / M;
+    t[n + M + q] = make_double2(std::cos(ang), std::sin(ang));
+  }
+  return t;
 }
 
 static std::atomic<unsigned long long> g_launches{0};
@@ -151,6 +221,7 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   std::vector<double2> tw[2], quart[2];
   std::vector<float2> tw32[2], quart32[2];
   std::vector<cff> twff[2], quartff[2];
+  std::vector<double2> blu[2];  // Bluestein tables (empty when the axis needs none)
   auto to_cff = [](double2 z) {
     cff c;
     c.x = ff(z.x);
@@ -180,6 +251,7 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
     factor_radices(n, &p->ax[a].fd);
     p->ax[a].n = n;
     p->ax[a].bc = bc[a];
+    if (p->ax[a].fd.bm) blu[a] = bluestein_tables(p->ax[a].fd);
   }
   std::vector<double> za(nz), zb(nz), zc(nz), hz(nz + 1), rdz(nz), rhz(nz + 1), rzc(nz), kz(4 * (size_t)nz);
   const double hper = 0.5 * (dz[nz - 1] + dz[0]);
@@ -258,6 +330,15 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
     off = align256(off + sizeof(cff) * nn[a]);
     L.qff[a] = off;
     off = align256(off + sizeof(cff) * nn[a]);
+    L.blu64[a] = L.blu32[a] = L.bluff[a] = 0;
+    if (!blu[a].empty()) {
+      L.blu64[a] = off;
+      off = align256(off + sizeof(double2) * blu[a].size());
+      L.blu32[a] = off;
+      off = align256(off + sizeof(float2) * blu[a].size());
+      L.bluff[a] = off;
+      off = align256(off + sizeof(cff) * blu[a].size());
+    }
   }
   L.za = off;
   off = align256(off + sizeof(double) * nz);
@@ -336,6 +417,16 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
     memcpy(&host[L.q32[a]], quart32[a].data(), sizeof(float2) * nn[a]);
     memcpy(&host[L.twff[a]], twff[a].data(), sizeof(cff) * nn[a]);
     memcpy(&host[L.qff[a]], quartff[a].data(), sizeof(cff) * nn[a]);
+    if (!blu[a].empty()) {
+      const size_t m = blu[a].size();
+      memcpy(&host[L.blu64[a]], blu[a].data(), sizeof(double2) * m);
+      float2* f2 = (float2*)&host[L.blu32[a]];
+      cff* fc = (cff*)&host[L.bluff[a]];
+      for (size_t q = 0; q < m; ++q) {
+        f2[q] = make_float2((float)blu[a][q].x, (float)blu[a][q].y);
+        fc[q] = to_cff(blu[a][q]);
+      }
+    }
   }
   memcpy(&host[L.za], za.data(), sizeof(double) * nz);
   memcpy(&host[L.zb], zb.data(), sizeof(double) * nz);
@@ -368,14 +459,16 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   if (!low.empty()) memcpy(&host[L.low], low.data(), sizeof(int2) * low.size());
 
   // launch shapes
-  p->xpb = nx >= 1024 ? 1 : (1024 / nx > 16 ? 16 : 1024 / nx);
+  // shared-memory line lengths (the Bluestein length where an axis uses it)
+  const int sx = p->ax[0].fd.bm ? p->ax[0].fd.bm : nx, sy = p->ax[1].fd.bm ? p->ax[1].fd.bm : ny;
+  p->xpb = sx >= 1024 ? 1 : (1024 / sx > 16 ? 16 : 1024 / sx);
   if (p->xpb < 1) p->xpb = 1;
   int tx = 16;
-  while (tx > 2 && (size_t)16 * tx * y_ld(ny) > 96 * 1024) tx -= 2;
+  while (tx > 2 && (size_t)16 * tx * y_ld(sy) > 96 * 1024) tx -= 2;
   p->ytx = tx;
   // the reduced-precision path's shapes, sized by its element (FP32 or FP32-pair)
   tx = 16;
-  while (tx > 2 && (size_t)(4 * rs) * tx * y_ld(ny) > 96 * 1024) tx -= 2;
+  while (tx > 2 && (size_t)(4 * rs) * tx * y_ld(sy) > 96 * 1024) tx -= 2;
   p->ytx32 = tx;
   if (zper) {
     // periodic z (general column solver): systems per 128-thread block, three columns each in shared memory
@@ -434,6 +527,9 @@ int plan_bind(PlanPrep* pp, void* block, cudaStream_t st, unsigned char* stage) 
     p->ax[a].quart32 = (const float2*)(b + L.q32[a]);
     p->ax[a].twff = (const cff*)(b + L.twff[a]);
     p->ax[a].quartff = (const cff*)(b + L.qff[a]);
+    p->ax[a].blu64 = L.blu64[a] ? (const double2*)(b + L.blu64[a]) : nullptr;
+    p->ax[a].blu32 = L.blu32[a] ? (const float2*)(b + L.blu32[a]) : nullptr;
+    p->ax[a].bluff = L.bluff[a] ? (const cff*)(b + L.bluff[a]) : nullptr;
   }
   p->za = (double*)(b + L.za);
   p->zb = (double*)(b + L.zb);

@@ -145,12 +145,13 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
   xa.fd = pl->ax[0].fd;
   xa.tw = pl->ax[0].tw64;
   xa.quart = pl->ax[0].quart64;
+  xa.blu = pl->ax[0].blu64;
   xa.pb = pl->xpb;
   xa.S = pl->S;
   xa.info = stats ? pl->info : nullptr;
   const long npairs = ((long)ny * nz + 1) / 2;
   const int xgrid = (int)((npairs + xa.pb - 1) / xa.pb);
-  const size_t xsm = 2 * (size_t)xa.pb * nx * sizeof(double2);
+  const size_t xsm = 2 * (size_t)xa.pb * fft_span(xa.fd, xa.blu) * sizeof(double2);
   switch (mode) {
     case RHS_F: VOFP_LAUNCH(KID_XFWD, st, k_xfwd<double, double2, RHS_F><<<xgrid, 256, xsm, st>>>(xa)); break;
     case RHS_DIV:
@@ -173,10 +174,11 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
   ya.fd = pl->ax[1].fd;
   ya.tw = pl->ax[1].tw64;
   ya.quart = pl->ax[1].quart64;
+  ya.blu = pl->ax[1].blu64;
   ya.tx = pl->ytx;
   ya.S = pl->S;
   const dim3 ygrid((nx + ya.tx - 1) / ya.tx, nz);
-  const size_t ysm = 2 * (size_t)(ya.tx / 2) * y_ld(ny) * sizeof(double2);
+  const size_t ysm = 2 * (size_t)(ya.tx / 2) * y_ld(fft_span(ya.fd, ya.blu)) * sizeof(double2);
   if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, k_ypass<double, double2, false><<<ygrid, 256, ysm, st>>>(ya));
   ZArgs za = z_args(pl, stats);
   const dim3 zgrid((nx + za.ti - 1) / za.ti, ny);
@@ -205,6 +207,7 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
   xi.fd = pl->ax[0].fd;
   xi.tw = pl->ax[0].tw64;
   xi.quart = pl->ax[0].quart64;
+  xi.blu = pl->ax[0].blu64;
   xi.pb = pl->xpb;
   xi.S = pl->S;
   xi.p = pout;

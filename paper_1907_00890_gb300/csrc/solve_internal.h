@@ -59,7 +59,7 @@ unsigned long long capture_end();
 
 // ---- plan construction in two phases (see plan.cu) ----
 struct PlanLayout {
-  size_t lam[2], tw[2], q[2], tw32[2], q32[2], twff[2], qff[2];
+  size_t lam[2], tw[2], q[2], tw32[2], q32[2], twff[2], qff[2], blu64[2], blu32[2], bluff[2];
   size_t za, zb, zc, dz, hz, rdz, rhz, rzc, conv, info, low, za32, zaff, lowcut, kz, volf, dzff;
   size_t table_bytes;  // host-built part, uploaded as one copy
   size_t P, S, T, S32, F, lowscr, lowtab;

@@ -83,8 +83,9 @@ bool fits(const vofp_plan* p, const Shape& s) {
   const size_t c = f32 ? sizeof(float2) : sizeof(double2);
   const size_t r = f32 ? sizeof(float) : sizeof(double);
   const size_t lim = 160 * 1024;
-  if (2 * (size_t)s.xpb * p->n[0] * c > lim) return false;
-  if (2 * (size_t)(s.ytx / 2) * vofp::y_ld(p->n[1]) * c > lim) return false;
+  const int sx = vofp::fft_span(p->ax[0].fd, p->ax[0].blu64), sy = vofp::fft_span(p->ax[1].fd, p->ax[1].blu64);
+  if (2 * (size_t)s.xpb * sx * c > lim) return false;
+  if (2 * (size_t)(s.ytx / 2) * vofp::y_ld(sy) * c > lim) return false;
   if (s.zti > 128) return false;  // at most 128 systems per block
   if (p->ztab) return s.zti >= 32;  // factor-table kernel: one system per thread, whole warps
   return (size_t)3 * s.zti * p->n[2] * r <= lim;

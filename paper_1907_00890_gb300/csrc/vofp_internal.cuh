@@ -99,7 +99,17 @@ struct FftDesc {
   int n;
   int nst;
   int radix[VOFP_MAX_STAGES];
+  // Bluestein (chirp-z) form, used when n has a prime factor above 7 and the plan supplies its tables: the
+  // length-n DFT as a cyclic convolution of length bm (a power of two >= 2n - 1) done with bm-point FFTs.
+  int bm;  // 0: n's own stages only
+  int bst;
+  int bradix[VOFP_MAX_STAGES];
 };
+
+// Points per shared-memory line of a transform: n, or bm when the Bluestein form runs (tables present).
+__host__ __device__ __forceinline__ int fft_span(const FftDesc& fd, const void* blu) {
+  return (blu && fd.bm) ? fd.bm : fd.n;
+}
 
 // Per-axis tables on the device.
 struct AxisDev {
@@ -112,6 +122,9 @@ struct AxisDev {
   const float2* quart32;
   const cff* twff;     // float-float twiddles (FP32-pair precision)
   const cff* quartff;
+  const double2* blu64;  // Bluestein tables (see fft_smem), NULL when n needs none
+  const float2* blu32;
+  const cff* bluff;
   const double* lam; // eigenvalue of packed spectral index q, q < n
 };
 
@@ -243,11 +256,10 @@ __device__ __forceinline__ void fft_stage_generic(const C* __restrict__ src, C* 
 }
 
 template <typename C>
-__device__ C* fft_smem(C* a, C* b, int batch, const FftDesc& fd, const C* __restrict__ tw, int ld) {
-  const int n = fd.n;
+__device__ C* fft_stages(C* a, C* b, int batch, int n, int nst, const int* radix, const C* __restrict__ tw, int ld) {
   int Ns = 1;
-  for (int s = 0; s < fd.nst; ++s) {
-    const int R = fd.radix[s];
+  for (int s = 0; s < nst; ++s) {
+    const int R = radix[s];
     switch (R) {
       case 2: fft_stage<C, 2>(a, b, batch, n, Ns, tw, ld); break;
       case 3: fft_stage<C, 3>(a, b, batch, n, Ns, tw, ld); break;
@@ -263,6 +275,48 @@ __device__ C* fft_smem(C* a, C* b, int batch, const FftDesc& fd, const C* __rest
     Ns *= R;
   }
   return a;
+}
+
+// Complex conjugate.
+template <typename C>
+__device__ __forceinline__ C cconj(C a) {
+  return cmk<C>(a.x, -a.y);
+}
+
+// `blu`: the plan's Bluestein tables for this axis in the precision of C -- chirp w_j = e^{-i pi j^2 / n}
+// (n entries), then Bh = FFT_bm(h) / bm with h_m = conj(w_|m|) placed cyclically (bm entries), then the
+// bm-point twiddles (bm entries) -- or NULL.  With them, X_k = w_k * y_k, y = the cyclic convolution of
+// (x_j w_j) with h, computed as conj(FFT(conj(FFT(x w) * Bh))).  Lines need a stride ld >= bm then.
+template <typename C>
+__device__ C* fft_smem(C* a, C* b, int batch, const FftDesc& fd, const C* __restrict__ tw, int ld,
+                       const C* __restrict__ blu) {
+  if (!blu || fd.bm == 0) return fft_stages(a, b, batch, fd.n, fd.nst, fd.radix, tw, ld);
+  const int n = fd.n, M = fd.bm;
+  const C* __restrict__ w = blu;
+  const C* __restrict__ Bh = blu + n;
+  const C* __restrict__ twM = blu + n + M;
+  for (int t = threadIdx.x; t < batch * M; t += blockDim.x) {
+    const int bi = t / M, j = t - bi * M;
+    C* p = a + bi * ld + j;
+    *p = j < n ? cmul(*p, w[j]) : cmk<C>((decltype(C::x))0, (decltype(C::x))0);
+  }
+  __syncthreads();
+  C* r = fft_stages(a, b, batch, M, fd.bst, fd.bradix, twM, ld);
+  C* o = r == a ? b : a;
+  for (int t = threadIdx.x; t < batch * M; t += blockDim.x) {
+    const int bi = t / M, j = t - bi * M;
+    C* p = r + bi * ld + j;
+    *p = cconj(cmul(*p, Bh[j]));
+  }
+  __syncthreads();
+  C* r2 = fft_stages(r, o, batch, M, fd.bst, fd.bradix, twM, ld);
+  for (int t = threadIdx.x; t < batch * n; t += blockDim.x) {
+    const int bi = t / n, k = t - bi * n;
+    C* p = r2 + bi * ld + k;
+    *p = cmul(cconj(*p), w[k]);
+  }
+  __syncthreads();
+  return r2;
 }
 
 // ---- pre/post-processing of the real-to-real transforms ----------------------------------------------

@@ -83,6 +83,26 @@ def test_poisson_sizes(vp, n, bc):
     plan.close()
 
 
+# lengths with a prime factor above 7 run the Bluestein (chirp-z) form: primes, 4 * 31, 2 * 3 * 41, 251,
+# and 2039 (prime, Bluestein length 4096, the longest that takes it) on each transformed axis
+BLUESTEIN = [(11, 4, 3), (37, 13, 5), (124, 6, 4), (246, 17, 3), (251, 5, 2), (6, 97, 3), (4, 251, 3),
+             (2039, 2, 2), (3, 2039, 2)]
+
+
+@pytest.mark.parametrize("n", BLUESTEIN)
+@pytest.mark.parametrize("bc", [("P", "P", "NN"), ("NN", "DD", "P"), ("DD", "NN", "DN")])
+@pytest.mark.parametrize("precision", ["fp64", "ff"])
+def test_poisson_bluestein_lengths(vp, n, bc, precision):
+    g, dz = make(n, bc, stretched=bc[2] != "P")
+    f = synth.rng(sum(n) + 7).standard_normal(g.shape)
+    ref, _ = oracle.poisson_solve(g, f)
+    prec = vp.FP64 if precision == "fp64" else vp.FF
+    plan = vp.Plan(n, g.widths[0][0], g.widths[1][0], dz, bc, prec=prec, max_refine=0 if prec == vp.FF else 6)
+    p = plan.poisson_solve(dev(f))
+    assert rel(host(p), ref) < (TOL if prec == vp.FP64 else 1e-10), (n, bc)
+    plan.close()
+
+
 def test_poisson_in_place_and_side_stream(vp):
     import torch
     n = (33, 17, 12)
