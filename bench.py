@@ -9,7 +9,9 @@ interface velocity.  Metric: projection Mpts/s = cells x solves / s.
 
 Timed region per step: CUDA events on the launching stream around the two library calls, inputs resident
 in HBM; L2 is flushed (256 MiB write) and u* restored from a pristine copy before each step, outside the
-events.  ``e2e`` repeats the measurement through the same C-ABI calls with pinned host buffers: the H2D copy
+events.  The roofline's per-kernel launch durations come from a second pass of the same K steps in which
+every library launch is bracketed by CUDA events on its own stream (kept out of the first pass, whose
+timing the extra events would perturb).  ``e2e`` repeats the measurement through the same C-ABI calls with pinned host buffers: the H2D copy
 of the step's inputs and the D2H copy of its results are inside the timed region.  Under torchrun each rank
 runs its own droplet instance (ensemble members are independent: weak scaling, no collective on the data
 path); rank 0 prints one JSON line with the max-over-ranks time.  ``--impl reference`` times the CPU oracle
@@ -47,12 +49,41 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "ff"],
                     help="arithmetic of the main step (the 128^3 droplet step is specified in FP64)")
+    ap.add_argument("--only", choices=["large", "batched", "batched_ff", "served"], default=None,
+                    help="run one variant alone and print its JSON (for profiling captures)")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     return ap.parse_args()
 
 
-def bench_mixed_step(vofp, c, u0, C, md, st, flush, args, prec=None, max_refine=6):
+def timed_steps(vofp, st, prep, step, steps, trace=True):
+    """Mean ms of `steps` steps (CUDA events on stream `st` around each step, `prep` outside them), untraced;
+    then, if `trace`, the same steps again with every library launch bracketed by CUDA events on its stream
+    (the per-kernel durations of the roofline; kept out of the first pass, whose timing they would perturb).
+    Returns (mean ms, per-step ms list, {kernel class: (total ms, launches)} or None)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        prep()
+        ev[i][0].record(st)
+        step()
+        ev[i][1].record(st)
+    torch.cuda.synchronize()
+    per = [a.elapsed_time(b) for a, b in ev]
+    tr = None
+    if trace:
+        vofp.vofp_trace_collect()
+        vofp.vofp_trace_enable(True)
+        for i in range(steps):
+            prep()
+            step()
+        torch.cuda.synchronize()
+        vofp.vofp_trace_enable(False)
+        tr = vofp.vofp_trace_collect()
+    return float(np.mean(per)), per, tr
+
+
+def bench_mixed_step(vofp, c, u0, C, md, st, flush, args, prec=None, max_refine=3):
     """The same droplet step through a reduced-precision plan (FP32 or FP32-pair transforms + FP64
     low modes, reductions and refinement)."""
     import torch
@@ -77,18 +108,7 @@ def bench_mixed_step(vofp, c, u0, C, md, st, flush, args, prec=None, max_refine=
         prep()
         step()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    vofp.vofp_trace_collect()
-    vofp.vofp_trace_enable(True)
-    for i in range(args.steps):
-        prep()
-        ev[i][0].record(st)
-        step()
-        ev[i][1].record(st)
-    torch.cuda.synchronize()
-    vofp.vofp_trace_enable(False)
-    trace = vofp.vofp_trace_collect()
-    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    ms, _, trace = timed_steps(vofp, st, prep, step, args.steps)
     # one more step with info for the refinement statistics
     prep()
     _, info = vofp.vofp_project_extend(plan.handle, u[0], u[1], u[2], C, md, c["rho1"], c["rho2"],
@@ -159,7 +179,7 @@ def bench_large(vofp, args):
     out = {"workload": "pressure projection 512^3, stretched z (tanh, ratio 1.05), P,P,NN, N(0,1) face velocities; "
                        "one solve per call, inputs > L2"}
     reps = max(3, min(args.steps, 8))
-    for name, prec, mr in (("fp64", vofp.FP64, 1), ("mixed", vofp.MIXED, 6), ("ff", vofp.FF, 0)):
+    for name, prec, mr in (("fp64", vofp.FP64, 1), ("mixed", vofp.MIXED, 3), ("ff", vofp.FF, 0)):
         plan = vofp.Plan(n, dx, dy, dz, bc, prec=prec, max_refine=mr)
         st = torch.cuda.current_stream()
 
@@ -171,19 +191,12 @@ def bench_large(vofp, args):
                 a.copy_(b)
             call()
         torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-        vofp.vofp_trace_collect()
-        vofp.vofp_trace_enable(True)
-        for i in range(reps):
+
+        def prep():
             for a, b in zip(u, u0):
                 a.copy_(b)
-            ev[i][0].record(st)
-            call()
-            ev[i][1].record(st)
-        torch.cuda.synchronize()
-        vofp.vofp_trace_enable(False)
-        trace = vofp.vofp_trace_collect()
-        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+        ms, _, trace = timed_steps(vofp, st, prep, call, reps)
         for a, b in zip(u, u0):
             a.copy_(b)
         _, info = call(info=True)
@@ -219,7 +232,7 @@ def bench_batched(vofp, args, prec=None):
     gen.manual_seed(synth.BASE_SEED + 4)
     for n in sizes:
         plans.append(vofp.Plan(n, 1.0 / n[0], 1.0 / n[1], synth.uniform_dz(n[2]), bc, prec=prec,
-                               max_refine=0 if prec == vofp.FF else 6))
+                               max_refine=0 if prec == vofp.FF else 3))
         us.append([torch.randn(s, generator=gen, dtype=torch.float64, device="cuda")
                    for s in synth.face_shapes(n, bc)])
         for a in us[-1][2:]:
@@ -303,7 +316,7 @@ def bench_served(vofp, args):
     bufs = [[torch.randn(maxc, generator=gen, dtype=torch.float64, device="cuda") for _ in range(3)]
             for _ in range(pool)]
     out = {}
-    for name, prec, mr in (("mixed", vofp.MIXED, 6), ("ff", vofp.FF, 0), ("fp64", vofp.FP64, 1)):
+    for name, prec, mr in (("mixed", vofp.MIXED, 3), ("ff", vofp.FF, 0), ("fp64", vofp.FP64, 1)):
         o = vofp.vofp_opts_default()
         o.prec = prec
         o.max_refine = mr
@@ -500,7 +513,7 @@ def run_ours(args):
     cells = int(np.prod(n))
     mixed = args.precision != "fp64"
     prec = {"fp64": vofp.FP64, "mixed": vofp.MIXED, "ff": vofp.FF}[args.precision]
-    plan = vofp.Plan(n, c["dx"], c["dy"], c["dz"], c["bc"], prec=prec, max_refine=0 if prec == vofp.FF else 6)
+    plan = vofp.Plan(n, c["dx"], c["dy"], c["dz"], c["bc"], prec=prec, max_refine=0 if prec == vofp.FF else 3)
     st = torch.cuda.current_stream()
 
     def T(a):
@@ -535,8 +548,6 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     l0 = vofp.vofp_launch_count()
-    vofp.vofp_trace_collect()
-    vofp.vofp_trace_enable(True)
     with ClockSampler(torch.cuda.current_device()) as clk:
         for i in range(args.steps):
             prep()
@@ -544,9 +555,9 @@ def run_ours(args):
             step()
             ev[i][1].record(st)
         torch.cuda.synchronize()
-    vofp.vofp_trace_enable(False)
-    trace = vofp.vofp_trace_collect()
     launches = vofp.vofp_launch_count() - l0
+    # the same steps once more with per-launch events: kernel durations for the roofline
+    _, _, trace = timed_steps(vofp, st, prep, step, args.steps)
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -739,8 +750,26 @@ def roofline_from_trace(trace, n, workload=None):
     return r
 
 
+def run_only(args):
+    from paper_1907_00890_gb300 import build
+    build.build()
+    from paper_1907_00890_gb300 import vofp
+    if args.only == "large":
+        r = bench_large(vofp, args)
+    elif args.only == "batched":
+        r = bench_batched(vofp, args)
+    elif args.only == "batched_ff":
+        r = bench_batched(vofp, args, prec=vofp.FF)
+    else:
+        r = bench_served(vofp, args)
+    print(json.dumps({"only": args.only, "result": r}))
+
+
 def main():
     args = parse()
+    if args.only:
+        run_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -73,7 +73,7 @@ typedef enum {
 typedef struct {
   int prec;       /* vofp_prec                                                                  */
   double tol;     /* mixed: stop when ||f - L p|| / ||f|| <= tol (default 1e-10)                   */
-  int max_refine; /* mixed: maximum defect-correction iterations (default 6)                       */
+  int max_refine; /* mixed: maximum defect-correction iterations (default 3)                       */
   int grad_mode;  /* |grad C| and n: 0 = central differences (default), 1 = Youngs corner average    */
   int tune;       /* 0 = default launch shapes, 1 = autotuned (cached per shape)                    */
 } vofp_opts;
@@ -87,7 +87,7 @@ typedef struct {
 
 typedef struct vofp_plan vofp_plan;
 
-/* Fill `opt` with the defaults (FP64, tol 1e-10, max_refine 6, central gradients, no tuning). */
+/* Fill `opt` with the defaults (FP64, tol 1e-10, max_refine 3, central gradients, no tuning). */
 void vofp_opts_default(vofp_opts* opt);
 
 /*

@@ -214,6 +214,15 @@ struct vofp_batch {
 
 static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Systems per block of the general z kernel (used when some instance of the batch has a periodic z axis):
+// as many as fit two or three columns each in 96 KB of shared memory, at most 32.
+static int generic_ti(const vofp_plan* p, size_t rsz) {
+  const int nvec = p->bc[2] == VOFP_BC_P ? 3 : 2;
+  int ti = 32;
+  while (ti > 1 && (size_t)nvec * ti * p->n[2] * rsz > 96 * 1024) ti /= 2;
+  return ti;
+}
+
 extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** out) {
   if (!plans || n < 1 || !out) return VOFP_ERR_INVALID_ARG;
   *out = nullptr;
@@ -295,7 +304,8 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
     const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
     offx[i + 1] = offx[i] + xpass_blocks(ny, nz, p->xpb);
     offy[i + 1] = offy[i] + (ny > 1 ? ((nx + p->ytx32 - 1) / p->ytx32) * nz : 0);
-    offz[i + 1] = offz[i] + (b->ztab ? (nx + 127) / 128 : (nx + p->zti32 - 1) / p->zti32) * ny;
+    const int gti = generic_ti(p, rsz);
+    offz[i + 1] = offz[i] + (b->ztab ? (nx + 127) / 128 : (nx + gti - 1) / gti) * ny;
     offl[i + 1] = offl[i] + p->nlow;
     const size_t faces = total_faces(grid_dev(p));
     int eb = (int)((faces + 255) / 256);
@@ -304,7 +314,7 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
     const size_t sx = 2 * (size_t)p->xpb * fft_span(p->ax[0].fd, p->ax[0].blu64) * csz;
     const size_t sy = 2 * (size_t)(p->ytx32 / 2) * y_ld(fft_span(p->ax[1].fd, p->ax[1].blu64)) * csz;
     const ZTabShape zs = ztab_shape(128, nz, rsz);
-    const size_t sz = b->ztab ? zs.smem : (size_t)(p->bc[2] == VOFP_BC_P ? 3 : 2) * p->zti32 * nz * rsz;
+    const size_t sz = b->ztab ? zs.smem : (size_t)(p->bc[2] == VOFP_BC_P ? 3 : 2) * gti * nz * rsz;
     if (sx > b->sm_x) b->sm_x = sx;
     if (sy > b->sm_y) b->sm_y = sy;
     if (sz > b->sm_z) b->sm_z = sz;
@@ -369,7 +379,7 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
         xa.inv_volume = 1.0 / pl->volume;
         xa.sq_out = conv + VOFP_CONV_RES + k;
         xa.skip_conv = conv;
-        xa.skip_k = k;  // correction s = k + 1 is skipped once correction k converged
+        xa.skip_k = k;  // residual pass of correction s = k + 1: skipped when F_k
         xa.tol2 = tol2;
       }
       // corrections beyond this instance's own max_refine never run
@@ -386,11 +396,11 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
       ya.tx = pl->ytx32;
       ya.S = pl->S32;
       ya.skip_conv = s == 0 ? nullptr : conv;
-      ya.skip_k = s == 0 ? -1 : k;
+      ya.skip_k = s == 0 ? -1 : s;  // solve and inverse pass of correction s: skipped when F_s
       ya.tol2 = tol2;
       ZArgs za = z_args(pl, false);
       za.S = pl->S32;
-      za.ti = pl->zti32;
+      za.ti = generic_ti(pl, ffp ? sizeof(ff) : sizeof(float));  // general kernel only (bounded: 128)
       za.lowthr = pl->lowthr;
       za.skip_conv = ya.skip_conv;
       za.skip_k = ya.skip_k;

@@ -136,6 +136,43 @@ static __global__ void __launch_bounds__(256) k_geometry(GridDev g, const double
     nz[t] = n.z;
   }
 }
+// The same geometry for reduced-precision plans (central differences): the C differences are taken in FP64,
+// everything after them -- scaling, |grad C|^2, the reciprocal square root (FP32 seed and one FP32-pair
+// Newton step), s and n -- in FP32 pairs, with integer-pipe conversions; FP64 work per cell drops from some
+// 25 operations to 9.  Results agree with the FP64 kernel to about 1e-14 relative.
+static __global__ void __launch_bounds__(256) k_geometry_ff(GridDev g, const double* __restrict__ C,
+                                                           const double* __restrict__ mdot, double coef,
+                                                           double* __restrict__ s, double* __restrict__ nx,
+                                                           double* __restrict__ ny, double* __restrict__ nz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, k = blockIdx.z;
+  if (i >= g.nx) return;
+  const size_t t = ((size_t)k * g.ny + j) * g.nx + i;
+  const ff gx = ff_split(cval(g, C, i + 1, j, k) - cval(g, C, i - 1, j, k)) * ff_split(0.5 * g.rdx);
+  const ff gy = ff_split(cval(g, C, i, j + 1, k) - cval(g, C, i, j - 1, k)) * ff_split(0.5 * g.rdy);
+  const ff gz = ff_split(cval(g, C, i, j, k + 1) - cval(g, C, i, j, k - 1)) * ff_split(__ldg(g.rzc + k));
+  const ff m2 = gx * gx + gy * gy + gz * gz;
+  double sv = 0.0, n0 = 0.0, n1 = 0.0, n2 = 0.0;
+  if (m2.hi > 0.0f) {
+    const float y0 = rsqrtf(m2.hi);
+    const ff y(y0, 0.0f);
+    const ff r = y * (ff(1.5f, 0.0f) - ff(0.5f, 0.0f) * (m2 * y * y));  // one Newton step for 1/sqrt(m2)
+    sv = wide_of(ff_split(__ldg(mdot + t) * coef) * (m2 * r));
+    const double c = __ldg(C + t);
+    if (fmin(c, 1.0 - c) >= 1e-8) {
+      n0 = wide_of(-(gx * r));
+      n1 = wide_of(-(gy * r));
+      n2 = wide_of(-(gz * r));
+    }
+  }
+  s[t] = sv;
+  if (nx) {
+    nx[t] = n0;
+    ny[t] = n1;
+    nz[t] = n2;
+  }
+}
+
 inline dim3 cell_grid(const GridDev& g, int threads) {
   return dim3((unsigned)((g.nx + threads - 1) / threads), (unsigned)g.ny, (unsigned)g.nz);
 }

@@ -133,7 +133,7 @@ static void solve_red(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, b
   if (pl->ztab) {
     // bulk systems from the factor table; the low-eigenvalue ones (a prefix of each row) by one warp each.
     // Small grids: the shared-memory staged kernel (too few systems to hide the row loads one thread each)
-    if (ztab_use_staged(nx, ny, nz, sizeof(R))) {
+    if (pl->zti32 == 0) {
       const dim3 tgrid((nx + kZStagedTI - 1) / kZStagedTI, ny);
       VOFP_LAUNCH(KID_ZSOLVE, st,
                   (k_ztab_staged<R, typename Red<R>::TT><<<tgrid, 128, ztab_staged_smem(nz, sizeof(R)), st>>>(
@@ -221,8 +221,8 @@ static void refine_sequence(vofp_plan* pl, int mode, XArgs xa, double* pout, int
   double* conv = pl->conv;
   xfwd_red<R>(pl, mode, xa, st);
   solve_red<R>(pl, st, -1, tol2, stats);
-  xinv_red<R>(pl, pout, 0, -1, tol2, conv + VOFP_CONV_DEL, st);
-  // correction j solves for r_{j-1} and is skipped once correction j - 1 converged (see launch_skipped)
+  xinv_red<R>(pl, pout, 0, -1, tol2, M > 0 ? conv + VOFP_CONV_DEL : nullptr, st);
+  // correction j: residual pass R_j (skipped when F_{j-1}), solve S_j and inverse pass X_j (skipped when F_j)
   for (int j = 1; j <= M; ++j) {
     XArgs ra = {};
     ra.f = pl->F;
@@ -234,8 +234,8 @@ static void refine_sequence(vofp_plan* pl, int mode, XArgs xa, double* pout, int
     ra.skip_k = j - 1;
     ra.tol2 = tol2;
     xfwd_red<R>(pl, RHS_RESID, ra, st);
-    solve_red<R>(pl, st, j - 1, tol2, stats);
-    xinv_red<R>(pl, pout, 1, j - 1, tol2, conv + VOFP_CONV_DEL + j, st);
+    solve_red<R>(pl, st, j, tol2, stats);
+    xinv_red<R>(pl, pout, 1, j, tol2, conv + VOFP_CONV_DEL + j, st);
   }
 }
 
@@ -258,10 +258,13 @@ int mixed_solve(vofp_plan* pl, int mode, const XArgs* xin, const double* f, doub
     xa.f = f;
     xa.scale = 1.0;
   }
-  xa.fsave = pl->F;
-  xa.sq_out = conv + 0;
-  xa.fv_out = conv + 1;
-  xa.abs_out = conv + 2;
+  // a direct solve without statistics (no correction, no info) needs neither the FP64 right-hand side nor
+  // the norms: its x pass then does no FP64 arithmetic beyond the right-hand side itself
+  const bool need = M > 0 || info != nullptr;
+  xa.fsave = need ? pl->F : nullptr;
+  xa.sq_out = need ? conv + 0 : nullptr;
+  xa.fv_out = need ? conv + 1 : nullptr;
+  xa.abs_out = need ? conv + 2 : nullptr;
   xa.skip_k = -1;
   xa.info = nullptr;
   if (pl->opts.prec == VOFP_FF)
@@ -290,18 +293,16 @@ int mixed_solve(vofp_plan* pl, int mode, const XArgs* xin, const double* f, doub
     return VOFP_ERR_CUDA;
   int status = VOFP_OK;
   const double f2 = h[0];
-  auto converged = [&](int j) {
-    return h[VOFP_CONV_RES + j - 1] <= tol2 * f2 && h[VOFP_CONV_DEL + j] <= 0.01 * tol2 * h[VOFP_CONV_DEL];
-  };
   const double rr = f2 > 0 ? std::sqrt(h[VOFP_CONV_FINAL] / f2) : 0.0;
   int iters = 0;
   bool conv_ok;
   if (M == 0) {
     conv_ok = rr <= pl->opts.tol;  // no correction requested: judge the direct solve by its residual
   } else {
+    // corrections that ran: up to the first m whose successor's solve was skipped (F_{m+1})
     iters = 1;
-    while (iters < M && !converged(iters)) ++iters;
-    conv_ok = converged(iters);
+    while (iters < M && !refine_done(h, iters + 1, tol2)) ++iters;
+    conv_ok = iters < M || (rr <= pl->opts.tol && refine_err_ok(h, M, tol2));
   }
   const double defect = pl->singular ? h[1] / pl->volume : 0.0;
   info->compat_defect = defect;

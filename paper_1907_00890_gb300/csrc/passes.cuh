@@ -91,7 +91,8 @@ __device__ __forceinline__ double rhs_at(const XArgs& a, int i, int j, int k, do
   const size_t c = ((size_t)k * a.g.ny + j) * a.g.nx + i;
   double f;
   if (MODE == RHS_F) {
-    f = __ldg(a.f + c) * a.scale;
+    f = __ldg(a.f + c);
+    if (a.scale != 1.0) f *= a.scale;
   } else if (MODE == RHS_DIV) {
     f = divergence_at(a.g, a.u, a.v, a.w, i, j, k);
     if (a.src) f -= __ldg(a.src + c);

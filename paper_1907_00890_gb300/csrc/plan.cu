@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "solve_internal.h"
+#include "zsolve.cuh"
 #include "vofp_internal.cuh"
 
 namespace vofp {
@@ -481,7 +482,11 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   } else {
     // factor-table kernel: one system per thread; forward values in shared memory when 64 or 128 threads'
     // columns fit in 96 KB, otherwise 128 threads keep them in place in the spectrum
+    // factor-table kernels: 0 = the shared-memory staged kernel (grids with few systems), otherwise the
+    // streaming kernel's threads per block (forward values in shared memory when 64 or 128 threads'
+    // columns fit in 96 KB, else kept in place in the spectrum)
     auto table_ti = [&](size_t elem) {
+      if (ztab_use_staged(nx, ny, nz, elem)) return 0;
       if ((size_t)128 * nz * elem <= 96 * 1024) return 128;
       if ((size_t)64 * nz * elem <= 96 * 1024) return 64;
       return 128;
@@ -603,7 +608,7 @@ extern "C" void vofp_opts_default(vofp_opts* opt) {
   if (!opt) return;
   opt->prec = VOFP_FP64;
   opt->tol = 1e-10;
-  opt->max_refine = 6;
+  opt->max_refine = 3;
   opt->grad_mode = 0;
   opt->tune = 0;
 }

@@ -181,8 +181,7 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
   const size_t ysm = 2 * (size_t)(ya.tx / 2) * y_ld(fft_span(ya.fd, ya.blu)) * sizeof(double2);
   if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, k_ypass<double, double2, false><<<ygrid, 256, ysm, st>>>(ya));
   ZArgs za = z_args(pl, stats);
-  const dim3 zgrid((nx + za.ti - 1) / za.ti, ny);
-  if (pl->ztab && ztab_use_staged(nx, ny, nz, sizeof(double))) {
+  if (pl->ztab && pl->zti == 0) {
     const dim3 tgrid((nx + kZStagedTI - 1) / kZStagedTI, ny);
     VOFP_LAUNCH(KID_ZSOLVE, st,
                 (k_ztab_staged<double, ZF<double>><<<tgrid, 128, ztab_staged_smem(nz, sizeof(double)), st>>>(
@@ -195,6 +194,7 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
   } else {
     const int nvec = pl->bc[2] == VOFP_BC_P ? 3 : 2;
     const size_t zsm = (size_t)nvec * za.ti * nz * sizeof(double);
+    const dim3 zgrid((nx + za.ti - 1) / za.ti, ny);
     VOFP_LAUNCH(KID_ZSOLVE, st, (k_zsolve<double, double><<<zgrid, 128, zsm, st>>>(za)));
   }
   if (ny > 1) VOFP_LAUNCH(KID_YINV, st, k_ypass<double, double2, true><<<ygrid, 256, ysm, st>>>(ya));
@@ -255,7 +255,9 @@ static int launch_geometry(vofp_plan* pl, const double* C, const double* mdot, d
   double* n1 = with_n ? G + 2 * cells : nullptr;
   double* n2 = with_n ? G + 3 * cells : nullptr;
   const int th = g.nx >= 128 ? 128 : 64;
-  if (mode == 1)
+  if (mode == 0 && pl->opts.prec != VOFP_FP64)  // reduced-precision plans: FP32-pair geometry
+    VOFP_LAUNCH(KID_STEFAN, st, k_geometry_ff<<<cell_grid(g, th), th, 0, st>>>(g, C, mdot, coef, sp, n0, n1, n2));
+  else if (mode == 1)
     VOFP_LAUNCH(KID_STEFAN, st, k_geometry<1><<<cell_grid(g, th), th, 0, st>>>(g, C, mdot, coef, sp, n0, n1, n2));
   else
     VOFP_LAUNCH(KID_STEFAN, st, k_geometry<0><<<cell_grid(g, th), th, 0, st>>>(g, C, mdot, coef, sp, n0, n1, n2));

@@ -76,21 +76,36 @@ __device__ __forceinline__ ff neg_if(ff x, bool f) { return ff(neg_if(x.hi, f), 
 //        conv[VOFP_CONV_DEL + j] = ||delta_j||^2 (delta_0 = the initial FP32 solve, delta_j the j-th
 //        correction), conv[VOFP_CONV_MEAN] = sum of delta dz over all of them (the gauge of p),
 //        conv[VOFP_CONV_FINAL] = ||r||^2 of the returned p (reporting pass).
-// Correction j + 1 is skipped once correction j (j >= 1) left BOTH a small residual before it and a small
-// step:  ||r_{j-1}||^2 <= tol^2 ||f||^2  and  ||delta_j||^2 <= (tol/10)^2 ||delta_0||^2.  (A residual test
-// alone is blind to errors in the smoothest modes, whose residual is smaller by their eigenvalue.)
+// Correction m (m >= 1) is a residual pass R_m (r_{m-1} = f - fbar - L p_{m-1}, its squared norm into
+// conv[VOFP_CONV_RES + m - 1]), a reduced-precision solve S_m and the inverse pass X_m (p_m = p_{m-1} +
+// delta_m, ||delta_m||^2 into conv[VOFP_CONV_DEL + m]).  F_k ("done after correction k - 1"): the residual
+// after it is small, ||r_{k-1}||^2 <= tol^2 ||f||^2, AND the error left after it is estimated small, from the
+// correction itself: ||delta_{k-1}|| <= (tol/10) ||delta_0||, or -- the corrections contracting by rho =
+// ||delta_{k-1}|| / ||delta_{k-2}|| <= 1/4 -- rho ||delta_{k-1}|| <= (tol/10) ||delta_0||.  (A residual test
+// alone is blind to errors in the smoothest modes, whose residual is smaller by their eigenvalue.)  R_m is
+// skipped when F_{m-1} holds, S_m and X_m when F_m holds, so the refinement stops right after the residual
+// pass that shows convergence.
 #define VOFP_CONV_RES 3
 #define VOFP_CONV_DEL 16
 #define VOFP_CONV_MEAN 30
 #define VOFP_CONV_FINAL 31
 #define VOFP_MAX_REFINE 12
-// j = -1 or 0: never skipped; j <= -2: always skipped (a correction beyond an instance's own limit in a
-// batch); j >= 1: skipped when correction j converged.  Every block reads the same values.
+__host__ __device__ __forceinline__ bool refine_err_ok(const double* c, int j, double tol2) {
+  if (j < 1) return false;  // no estimate from the first solve alone
+  const double d0 = c[VOFP_CONV_DEL], dj = c[VOFP_CONV_DEL + j], dp = c[VOFP_CONV_DEL + j - 1];
+  if (dj <= 0.01 * tol2 * d0) return true;
+  return dj <= 0.0625 * dp && dj * dj <= 0.01 * tol2 * d0 * dp;
+}
+__host__ __device__ __forceinline__ bool refine_done(const double* c, int k, double tol2) {
+  if (k < 1) return false;
+  return c[VOFP_CONV_RES + k - 1] <= tol2 * c[0] && refine_err_ok(c, k - 1, tol2);
+}
+// j <= -2: always skipped (a correction beyond an instance's own limit in a batch); j <= 0: never; j >= 1:
+// skipped when F_j holds.  Every block reads the same values.
 __device__ __forceinline__ bool launch_skipped(const double* conv, int j, double tol2) {
   if (j <= -2) return true;
   if (!conv || j <= 0) return false;
-  return conv[VOFP_CONV_RES + j - 1] <= tol2 * conv[0] &&
-         conv[VOFP_CONV_DEL + j] <= 0.01 * tol2 * conv[VOFP_CONV_DEL];
+  return refine_done(conv, j, tol2);
 }
 
 // ---- FFT descriptor ----------------------------------------------------------------------------------

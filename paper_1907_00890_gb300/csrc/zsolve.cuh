@@ -682,17 +682,50 @@ static __global__ void __launch_bounds__(128) k_ztab_staged(ZArgs a, ZTabArgs zt
   if (warp == 0) {
     const int c = lane, i = i0 + c;
     if (c < ncol && i >= cut && !(sing_here && c == 0)) {
+      // the shared-memory operands of rows k + 1 .. k + 8 are read before row k is used (a register ring),
+      // so each row costs one dependent multiply-add and no load latency
+      constexpr int U = 8;
+      Pair<T> rb[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (u < nz) rb[u] = ab[u * TI + c];
       T d = (T)0;
-      for (int k = 0; k < nz; ++k) {
-        Pair<T>& v = ab[k * TI + c];
-        d = fma_t(v.x, d, v.y);
-        v.y = d;
+      for (int k0 = 0; k0 < nz; k0 += U) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int k = k0 + u;
+          if (k < nz) {
+            const Pair<T> v = rb[u];
+            if (k + U < nz) rb[u] = ab[(k + U) * TI + c];
+            d = fma_t(v.x, d, v.y);
+            ab[k * TI + c].y = d;
+          }
+        }
       }
       T x = d;
-      for (int k = nz - 2; k >= 0; --k) {
-        Pair<T>& v = ab[k * TI + c];
-        x = fma_t(-cp[k * TI + c], x, v.y);
-        v.y = x;
+      T db[U], cb[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = nz - 2 - u;
+        if (k >= 0) {
+          db[u] = ab[k * TI + c].y;
+          cb[u] = cp[k * TI + c];
+        }
+      }
+      for (int k0 = nz - 2; k0 >= 0; k0 -= U) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int k = k0 - u;
+          if (k >= 0) {
+            const T dk = db[u], ck = cb[u];
+            if (k - U >= 0) {
+              db[u] = ab[(k - U) * TI + c].y;
+              cb[u] = cp[(k - U) * TI + c];
+            }
+            x = fma_t(-ck, x, dk);
+            ab[k * TI + c].y = x;
+          }
+        }
       }
     }
   } else if (warp == 1 && sing_here && cut == 0) {

@@ -369,7 +369,7 @@ def face_shapes(n, bc):
 class Plan:
     """Owns a plan handle; convenience wrappers that allocate outputs with torch (marshalling only)."""
 
-    def __init__(self, n, dx, dy, dz, bc, prec=FP64, tol=1e-10, max_refine=6, grad_mode=0, tune=0):
+    def __init__(self, n, dx, dy, dz, bc, prec=FP64, tol=1e-10, max_refine=3, grad_mode=0, tune=0):
         o = vofp_opts_default()
         o.prec, o.tol, o.max_refine, o.grad_mode, o.tune = prec, tol, max_refine, grad_mode, tune
         self.n = tuple(int(x) for x in n)
