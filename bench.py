@@ -295,8 +295,10 @@ def _div_ratio(torch, plan, u, u0):
 
 
 def bench_served(vofp, args):
-    """Poisson arrivals of projection requests with log-uniform sizes 48..256 per axis, served with
-    continuous batching: mixed precision, then the same stream through the plain FP64 path."""
+    """Poisson arrivals of projection requests from an ensemble of 64 droplet runs, each run with its own grid
+    (per-axis sizes log-uniform in 48..256, drawn once per run), every request from a run drawn at random;
+    served with continuous batching and resident plans: FP32 + refinement, FP32 pairs, and the plain FP64
+    path."""
     import torch
     from paper_1907_00890_gb300 import synth
     rate = args.serve_rate
@@ -306,7 +308,9 @@ def bench_served(vofp, args):
     nreq = int((warm + dur) * rate * 1.2) + 16
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
     arrivals = arrivals[arrivals < warm + dur]
-    sizes = synth.serve_sizes(len(arrivals))
+    runs = synth.serve_sizes(64)
+    pick = rng.integers(0, len(runs), size=len(arrivals))
+    sizes = [runs[k] for k in pick]
     bc = ("P", "P", "NN")
     # pool of field buffers at the largest shape; each request views a contiguous prefix of one slot
     pool = 128
@@ -354,11 +358,14 @@ def bench_served(vofp, args):
         vofp.vofp_server_destroy(s)
         out[name] = {"p50_ms": st["p50_s"] * 1e3, "p99_ms": st["p99_s"] * 1e3,
                      "solves_per_s": st["completed"] / st["seconds"],
+                     "plan_hits": int(st["plan_hits"]), "plan_misses": int(st["plan_misses"]),
+                     "resident_plans": int(st["resident_plans"]),
                      "value": st["cells"] / st["seconds"] / 1e6, "unit": UNIT, "completed": int(st["completed"]),
                      "rejected": int(st["rejected"]), "late_submissions": late,
                      "dtype": {vofp.MIXED: "f32+f64", vofp.FF: "f32x2+f64"}.get(prec, "f64")}
-    out["workload"] = ("Poisson arrivals at %.0f req/s for %.0f s after %.0f s warm-up, per-axis sizes "
-                       "log-uniform in [48, 256], P,P,NN, N(0,1) fields, 64 in flight" % (rate, dur, warm))
+    out["workload"] = ("Poisson arrivals at %.0f req/s for %.0f s after %.0f s warm-up from an ensemble of 64 runs "
+                       "(per-axis sizes log-uniform in [48, 256], drawn once per run), P,P,NN, N(0,1) fields, "
+                       "64 in flight, resident plans" % (rate, dur, warm))
     return out
 
 

@@ -215,10 +215,13 @@ void vofp_batch_destroy(vofp_batch* b);
  * plan alone exceeds the arena completes with VOFP_ERR_BUSY.
  * vofp_server_poll: 0 = done (the ticket is consumed; *latency_s = completion - submission), 1 = pending,
  * < 0 = the request's error (also consumes the ticket).  vofp_server_wait: the same, blocking up to
- * timeout_s (VOFP_ERR_TIMEOUT, ticket kept).  vofp_server_stats: out[0..12] (the first n are written) =
+ * timeout_s (VOFP_ERR_TIMEOUT, ticket kept).  vofp_server_stats: out[0..16] (the first n are written) =
  * completed, admitted, rejected, queued (submitted, not yet admitted), arena bytes in use, arena bytes, p50
  * and p99 latency (s), cells solved, seconds since creation or the last reset, worker seconds spent building
- * plans, worker seconds spent enqueuing work, worker loop iterations (reset != 0 clears the counters).
+ * plans, worker seconds spent enqueuing work, worker loop iterations, requests served by a resident plan,
+ * requests that needed a new plan, plans evicted, resident plans (reset != 0 clears the counters).  Plans
+ * stay resident in the arena after their request and serve later requests of the same grid, spacings and
+ * boundary conditions; idle ones are evicted, least recently used first, when a new plan needs the space.
  * vofp_server_destroy waits for in-flight work.
  */
 typedef struct {

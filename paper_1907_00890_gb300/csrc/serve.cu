@@ -1,21 +1,26 @@
 // Serving loop: continuous batching of projection requests from an ensemble of independent droplet runs.
 //
 // Requests of any grid size arrive at any time (vofp_server_submit returns at once with a ticket).  A worker
-// thread admits them as in-flight slots and device memory free up: each admitted request gets a plan built
-// on the host (tables), placed in a block of the server's arena (one cudaMalloc at creation; the arena's
-// free list is the memory-based admission), uploaded and solved asynchronously on the slot's own stream,
+// thread admits them as in-flight slots and device memory free up.  Plans stay resident: each plan (tables,
+// factor tables and workspace, one block of the server's arena -- one cudaMalloc at creation, a first-fit
+// free list being the memory-based admission) is kept after its request completes and is reused by the
+// next request with the same grid, boundary conditions and options; a request that finds no idle plan of
+// its shape gets a new one (host tables built without holding the lock, uploaded asynchronously), evicting
+// the least recently used idle plans when the arena is full.  Each request runs on its slot's own stream,
 // so the work of requests admitted while others are on the GPU overlaps on the device.  An event recorded
 // after each request's kernels is polled by the worker (every 50 us while work is in flight), which then
-// stamps the completion and returns the arena block and slot: there is no cudaMalloc, cudaFree, host
-// callback or device synchronisation on the serving path.  Latency is measured from submission to that
-// completion stamp.  Each request runs exactly the kernels it would run
-// alone (its plan depends only on its own grid), so its result does not depend on what else is in flight.
+// stamps the completion and frees the slot and the plan: there is no cudaMalloc, cudaFree, host callback
+// or device synchronisation on the serving path.  Latency is measured from submission to that completion
+// stamp.  Each request runs exactly the kernels it would run alone (its plan depends only on its own grid),
+// so its result does not depend on what else is in flight.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <list>
 #include <map>
+#include <string>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -28,18 +33,27 @@ using Clock = std::chrono::steady_clock;
 
 namespace {
 
+// A resident plan: placed in the arena, reused by every request of its shape while idle.
+struct CachedPlan {
+  std::string key;
+  PlanPrep prep;  // prep.p is the bound plan
+  size_t block_off, block_bytes;
+  bool busy;
+  bool bound;
+  Clock::time_point last;
+};
+
 struct Req {
   unsigned long long id;
   vofp_request r;
   std::vector<double> dz;
+  std::string key;    // grid, spacing, boundary conditions: requests with equal keys share plans
+  CachedPlan* plan;   // while admitted
   Clock::time_point t_submit;
   Clock::time_point t_done;
   int status;
   bool done;
-  // in flight
-  PlanPrep prep;
-  bool prepared;
-  size_t block_off, block_bytes;
+  bool prepared;  // plan->prep holds tables built for this request
   int slot;
 };
 
@@ -77,6 +91,9 @@ struct vofp_server {
   unsigned long long loops;
   double cells_done;
   Clock::time_point t0;
+  // resident plans
+  std::list<CachedPlan*> plans;  // least recently used first
+  unsigned long long plan_hits, plan_misses, plan_evictions;
 };
 
 namespace {
@@ -116,32 +133,69 @@ void arena_free(vofp_server* s, size_t off, size_t bytes) {
   }
 }
 
-// Completion of the request on slot `k` (lock held): stamp it, return its arena block and slot.
+// Completion of the request on slot `k` (lock held): stamp it, free its slot and plan (which stays resident).
 void complete(vofp_server* s, int k, Clock::time_point t) {
   Slot& sl = s->slots[k];
   Req* q = sl.req;
   q->t_done = t;
   q->done = true;
-  arena_free(s, q->block_off, q->block_bytes);
   sl.busy = false;
   sl.req = nullptr;
+  CachedPlan* cp = q->plan;
+  cp->busy = false;
+  cp->last = t;
+  s->plans.remove(cp);
+  s->plans.push_back(cp);  // most recently used last
+  q->plan = nullptr;
   s->completed++;
   s->cells_done += (double)q->r.n[0] * q->r.n[1] * q->r.n[2];
   s->lat.push_back(std::chrono::duration<double>(q->t_done - q->t_submit).count());
-  plan_free_host(q->prep.p);
-  q->prep.p = nullptr;
-  std::vector<unsigned char>().swap(q->prep.host);
 }
 
-// Host part of admission (no lock): build the plan's tables.  Returns a status; < 0 rejects the request.
+// An idle resident plan for `key` (lock held), or NULL.
+CachedPlan* find_idle(vofp_server* s, const std::string& key) {
+  for (CachedPlan* cp : s->plans)
+    if (!cp->busy && cp->bound && cp->key == key) return cp;
+  return nullptr;
+}
+
+// Arena block for a new plan (lock held), evicting least recently used idle plans as needed.
+bool alloc_plan_block(vofp_server* s, size_t bytes, size_t* off) {
+  while (!arena_alloc(s, bytes, off)) {
+    CachedPlan* victim = nullptr;
+    for (CachedPlan* cp : s->plans)
+      if (!cp->busy) {
+        victim = cp;
+        break;
+      }
+    if (!victim) return false;
+    s->plans.remove(victim);
+    arena_free(s, victim->block_off, victim->block_bytes);
+    plan_free_host(victim->prep.p);
+    delete victim;
+    s->plan_evictions++;
+  }
+  return true;
+}
+
+// Host part of admission (no lock): build a new plan's tables into a resident-plan record for q.
+// Returns a status; < 0 rejects the request.
 int prepare_request(vofp_server* s, Req* q) {
+  CachedPlan* cp = new CachedPlan();
+  cp->key = q->key;
+  cp->busy = false;
+  cp->bound = false;
   const int st = plan_prepare(q->r.n[0], q->r.n[1], q->r.n[2], q->r.dx, q->r.dy, q->dz.data(), q->r.bc, &s->opts,
-                              &q->prep);
-  if (st) return st;
+                              &cp->prep);
+  if (st) {
+    delete cp;
+    return st;
+  }
+  cp->block_bytes = plan_prep_device_bytes(&cp->prep);
+  q->plan = cp;
   q->prepared = true;
-  q->block_bytes = plan_prep_device_bytes(&q->prep);
-  if (q->block_bytes > s->arena_bytes) return VOFP_ERR_BUSY;              // can never fit
-  if (plan_prep_stage_bytes(&q->prep) > (size_t)(4 << 20)) return VOFP_ERR_UNSUPPORTED;  // staging size
+  if (cp->block_bytes > s->arena_bytes) return VOFP_ERR_BUSY;                            // can never fit
+  if (plan_prep_stage_bytes(&cp->prep) > (size_t)(4 << 20)) return VOFP_ERR_UNSUPPORTED;  // staging size
   return VOFP_OK;
 }
 
@@ -150,13 +204,17 @@ void reject(vofp_server* s, Req* q, int status) {
   q->status = status;
   q->done = true;
   q->t_done = Clock::now();
-  if (q->prep.p) plan_free_host(q->prep.p);
-  q->prep.p = nullptr;
+  if (q->plan && !q->plan->bound) {  // a prepared plan that never got a block
+    plan_free_host(q->plan->prep.p);
+    delete q->plan;
+  }
+  q->plan = nullptr;
   s->rejected++;
   s->queued--;
 }
 
-// Reserve a slot and an arena block for a prepared request (lock held).  False: not now.
+// Reserve a slot and a plan for q (lock held): an idle resident plan of q's shape, else the plan prepared
+// for q placed in a new arena block.  False: not now (no slot, no memory, or q still needs its tables).
 bool reserve(vofp_server* s, Req* q) {
   int slot = -1;
   for (size_t i = 0; i < s->slots.size(); ++i)
@@ -165,21 +223,40 @@ bool reserve(vofp_server* s, Req* q) {
       break;
     }
   if (slot < 0) return false;
-  size_t off;
-  if (!arena_alloc(s, q->block_bytes, &off)) return false;
+  CachedPlan* cp = find_idle(s, q->key);
+  if (cp) {
+    if (q->plan && !q->plan->bound) {  // tables built speculatively, not needed
+      plan_free_host(q->plan->prep.p);
+      delete q->plan;
+    }
+    s->plan_hits++;
+  } else {
+    if (!q->prepared) return false;
+    cp = q->plan;
+    if (!alloc_plan_block(s, cp->block_bytes, &cp->block_off)) return false;
+    s->plans.push_back(cp);
+    s->plan_misses++;
+  }
+  cp->busy = true;
+  q->plan = cp;
   s->slots[slot].busy = true;
   q->slot = slot;
-  q->block_off = off;
   s->admitted++;
   s->queued--;
   return true;
 }
 
-// Upload the tables, enqueue the projection and record the slot's completion event (no lock).
+// Place a new plan (tables uploaded asynchronously), enqueue the projection and record the slot's completion
+// event (no lock).
 void launch_request(vofp_server* s, Req* q) {
   Slot& sl = s->slots[q->slot];
-  int st = plan_bind(&q->prep, s->arena + q->block_off, sl.st, sl.stage);
-  if (!st) st = vofp_project(q->prep.p, q->r.u, q->r.v, q->r.w, q->r.src, q->r.dt_over_rho0, q->r.p, sl.st, nullptr);
+  CachedPlan* cp = q->plan;
+  int st = VOFP_OK;
+  if (!cp->bound) {
+    st = plan_bind(&cp->prep, s->arena + cp->block_off, sl.st, sl.stage);
+    cp->bound = true;  // the stage buffer is free again once this stream passes the upload
+  }
+  if (!st) st = vofp_project(cp->prep.p, q->r.u, q->r.v, q->r.w, q->r.src, q->r.dt_over_rho0, q->r.p, sl.st, nullptr);
   if (cudaEventRecord(sl.done, sl.st) != cudaSuccess) {
     cudaStreamSynchronize(sl.st);  // the worker's next poll then finds the event complete or in error
     st = VOFP_ERR_CUDA;
@@ -219,10 +296,10 @@ void worker_loop(vofp_server* s) {
       local.push_back(s->pending.front());
       s->pending.pop_front();
     }
-    // host tables for the new requests
+    // host tables for new requests whose shape has no idle resident plan
     std::vector<std::pair<Req*, int>> built;
     for (Req* q : local)
-      if (!q->prepared && !q->done) built.emplace_back(q, 0);
+      if (!q->prepared && !q->done && !find_idle(s, q->key)) built.emplace_back(q, 0);
     if (!built.empty()) {
       lk.unlock();
       const Clock::time_point a = Clock::now();
@@ -311,6 +388,7 @@ extern "C" int vofp_server_create(size_t mem_budget_bytes, int max_inflight, con
   s->stop = false;
   s->completed = s->rejected = s->admitted = 0;
   s->queued = 0;
+  s->plan_hits = s->plan_misses = s->plan_evictions = 0;
   s->t_prepare = s->t_launch = 0;
   s->loops = 0;
   s->cells_done = 0;
@@ -329,11 +407,20 @@ extern "C" int vofp_server_submit(vofp_server* s, const vofp_request* r, unsigne
   q->r = *r;
   q->dz.assign(r->dz, r->dz + r->n[2]);
   q->r.dz = nullptr;
+  {
+    // plan key: grid, spacings and boundary conditions (bit patterns; the options are the server's)
+    std::string k((const char*)r->n, sizeof(r->n));
+    k.append((const char*)&r->dx, sizeof(double));
+    k.append((const char*)&r->dy, sizeof(double));
+    k.append((const char*)r->bc, sizeof(r->bc));
+    k.append((const char*)q->dz.data(), sizeof(double) * q->dz.size());
+    q->key = std::move(k);
+  }
+  q->plan = nullptr;
   q->t_submit = Clock::now();
   q->status = VOFP_OK;
   q->done = false;
   q->prepared = false;
-  q->prep.p = nullptr;
   q->slot = -1;
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -382,7 +469,9 @@ extern "C" int vofp_server_wait(vofp_server* s, unsigned long long ticket, doubl
 
 // out[0] completed, [1] admitted, [2] rejected, [3] queued, [4] arena bytes in use, [5] arena bytes,
 // [6] p50 latency s, [7] p99 latency s, [8] cells solved (sum), [9] seconds since creation or reset,
-// [10] worker seconds building plans, [11] worker seconds enqueuing work, [12] worker loop iterations.
+// [10] worker seconds building plans, [11] worker seconds enqueuing work, [12] worker loop iterations,
+// [13] requests served by a resident plan, [14] requests that needed a new plan, [15] plans evicted,
+// [16] resident plans.
 extern "C" int vofp_server_stats(vofp_server* s, double* out, int n, int reset) {
   if (!s || !out || n < 1) return VOFP_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(s->mu);
@@ -393,17 +482,19 @@ extern "C" int vofp_server_stats(vofp_server* s, double* out, int n, int reset) 
     size_t i = (size_t)(q * (l.size() - 1) + 0.5);
     return l[std::min(i, l.size() - 1)];
   };
-  double v[13] = {(double)s->completed, (double)s->admitted, (double)s->rejected, (double)s->queued,
+  double v[17] = {(double)s->completed, (double)s->admitted, (double)s->rejected, (double)s->queued,
                   (double)s->in_use,    (double)s->arena_bytes, pct(0.50), pct(0.99), s->cells_done,
                   std::chrono::duration<double>(Clock::now() - s->t0).count(), s->t_prepare, s->t_launch,
-                  (double)s->loops};
-  for (int i = 0; i < n && i < 13; ++i) out[i] = v[i];
+                  (double)s->loops, (double)s->plan_hits, (double)s->plan_misses, (double)s->plan_evictions,
+                  (double)s->plans.size()};
+  for (int i = 0; i < n && i < 17; ++i) out[i] = v[i];
   if (reset) {
     s->lat.clear();
     s->completed = s->admitted = s->rejected = 0;
     s->cells_done = 0;
     s->t_prepare = s->t_launch = 0;
     s->loops = 0;
+    s->plan_hits = s->plan_misses = s->plan_evictions = 0;
     s->t0 = Clock::now();
   }
   return VOFP_OK;
@@ -419,8 +510,16 @@ extern "C" void vofp_server_destroy(vofp_server* s) {
   s->worker.join();
   for (auto& sl : s->slots) cudaStreamSynchronize(sl.st);
   for (auto& kv : s->all) {
-    if (kv.second->prep.p) plan_free_host(kv.second->prep.p);
-    delete kv.second;
+    Req* q = kv.second;
+    if (q->plan && !q->plan->bound) {
+      plan_free_host(q->plan->prep.p);
+      delete q->plan;
+    }
+    delete q;
+  }
+  for (CachedPlan* cp : s->plans) {
+    plan_free_host(cp->prep.p);
+    delete cp;
   }
   for (auto& sl : s->slots) {
     cudaStreamDestroy(sl.st);

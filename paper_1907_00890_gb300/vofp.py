@@ -152,10 +152,11 @@ def vofp_server_wait(server, ticket, timeout_s=60.0):
 
 
 def vofp_server_stats(server, reset=False):
-    out = (_D * 13)()
-    _check(_lib.vofp_server_stats(server, out, 13, 1 if reset else 0), "vofp_server_stats")
+    out = (_D * 17)()
+    _check(_lib.vofp_server_stats(server, out, 17, 1 if reset else 0), "vofp_server_stats")
     keys = ["completed", "admitted", "rejected", "pending", "arena_in_use", "arena_bytes", "p50_s", "p99_s",
-            "cells", "seconds", "worker_prepare_s", "worker_launch_s", "worker_loops"]
+            "cells", "seconds", "worker_prepare_s", "worker_launch_s", "worker_loops", "plan_hits",
+            "plan_misses", "plan_evictions", "resident_plans"]
     return dict(zip(keys, list(out)))
 
 

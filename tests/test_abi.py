@@ -46,7 +46,7 @@ def test_error_strings_and_default_opts(lib):
     assert vofp.vofp_error_string(0) == "ok"
     assert "invalid" in vofp.vofp_error_string(-1)
     o = vofp.vofp_opts_default()
-    assert o.prec == 0 and o.tol == 1e-10 and o.max_refine == 6
+    assert o.prec == 0 and o.tol == 1e-10 and o.max_refine == 3
 
 
 def test_sm103a_only_build_flags():

@@ -103,3 +103,50 @@ def test_oversize_request_is_rejected_busy(vp):
         vp.vofp_server_wait(s, t, 60.0)
     assert e.value.status == -6
     vp.vofp_server_destroy(s)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "ff"])
+def test_resident_plans_reused_and_evicted(vp, precision):
+    """An ensemble of three runs (three grids) submitting in turn: plans stay resident and are reused (three
+    new plans for twelve requests); with an arena for about one plan at a time they are evicted instead.
+    Every result matches the oracle either way."""
+    import torch
+    shapes = [((24, 20, 16), ("P", "P", "NN")), ((30, 17, 12), ("NN", "DD", "DN")), ((16, 32, 20), ("P", "P", "NN"))]
+    reqs = []
+    for i in range(12):
+        n, bc = shapes[i % 3]
+        dz = synth.stretched_dz(n[2]) if bc[2] != "P" else synth.uniform_dz(n[2])
+        reqs.append(dict(n=n, bc=bc, dz=dz, dx=1.0 / n[0], dy=1.0 / n[1],
+                         u0=synth.random_velocity(n, bc, 900 + i), dt=1.0))
+    o = vp.vofp_opts_default()
+    o.prec = vp.MIXED if precision == "mixed" else vp.FF
+    o.max_refine = 3 if precision == "mixed" else 0
+    sizes = []
+    for n, bc in shapes:
+        dz = synth.stretched_dz(n[2]) if bc[2] != "P" else synth.uniform_dz(n[2])
+        pl = vp.Plan(n, 1.0 / n[0], 1.0 / n[1], dz, bc, prec=o.prec, max_refine=o.max_refine)
+        sizes.append(vp.vofp_plan_workspace_bytes(pl.handle) + 256)
+        pl.close()
+    tight = max(sizes) + min(sizes) // 2  # room for the largest plan, never for two
+    for budget, expect_evictions in ((1 << 30, False), (tight, True)):
+        s = vp.vofp_server_create(budget, 2, o)
+        out = []
+        for r in reqs:  # one after another, as a time-stepping ensemble would
+            u = [dev(a) for a in r["u0"]]
+            p = torch.empty((r["n"][2], r["n"][1], r["n"][0]), dtype=torch.float64, device="cuda")
+            t = vp.vofp_server_submit(s, r["n"], r["dx"], r["dy"], r["dz"], r["bc"], *u, dt_over_rho0=r["dt"], p=p)
+            vp.vofp_server_wait(s, t, 60.0)
+            out.append((u, p))
+        st = vp.vofp_server_stats(s)
+        vp.vofp_server_destroy(s)
+        assert st["completed"] == 12 and st["rejected"] == 0
+        if expect_evictions:
+            assert st["plan_evictions"] > 0
+        else:
+            assert st["plan_misses"] == 3 and st["plan_hits"] == 9 and st["plan_evictions"] == 0
+        for r, (u, p) in zip(reqs, out):
+            g = oracle.Grid(*r["n"], r["dx"], r["dy"], r["dz"], r["bc"])
+            ou = oracle.project(g, *r["u0"], dt_over_rho0=r["dt"])
+            assert rel(p.cpu().numpy(), ou[3]) < TOL
+            for a in range(3):
+                assert rel(u[a].cpu().numpy(), ou[a]) < TOL
