@@ -11,7 +11,8 @@ Timed region per step: CUDA events on the launching stream around the two librar
 in HBM; L2 is flushed (256 MiB write) and u* restored from a pristine copy before each step, outside the
 events.  The roofline's per-kernel launch durations come from a second pass of the same K steps in which
 every library launch is bracketed by CUDA events on its own stream (kept out of the first pass, whose
-timing the extra events would perturb).  ``e2e`` repeats the measurement through the same C-ABI calls with pinned host buffers: the H2D copy
+timing the extra events would perturb).  ``e2e`` repeats the measurement through the library's host-buffer call
+(vofp_project_extend_host) with pinned host buffers: the H2D copy
 of the step's inputs and the D2H copy of its results are inside the timed region.  Under torchrun each rank
 runs its own droplet instance (ensemble members are independent: weak scaling, no collective on the data
 path); rank 0 prints one JSON line with the max-over-ranks time.  ``--impl reference`` times the CPU oracle
@@ -426,6 +427,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def job_rate(ms_local, cells_per_rank, solves, world, device):
+    """Whole-job throughput of replicas: the slowest rank's time (max over ranks) and the cells all ranks
+    processed, in Mpts/s.  Returns (max ms, Mpts/s)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * cells_per_rank * solves / (ms_max / 1e3) / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -488,7 +501,7 @@ def run_reference(args):
             break
     sec = float(np.mean(ts))
     value = cells * 2 / sec / 1e6
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": len(ts),
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": len(ts),
             "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "droplet step %d^3 (project with Stefan source + liquid-velocity extension), "
@@ -569,39 +582,34 @@ def run_ours(args):
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = float(np.mean(step_ms))
-    ms_all = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_all, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_all.item())
-    value = world * cells * 2 / (ms_max / 1e3) / 1e6
+    ms_max, value = job_rate(ms, cells, 2, world, dev)
 
-    # ---- end to end through the same calls with pinned host buffers ----
+    # ---- end to end: the same step through the host-buffer call (pinned host memory in and out; the library
+    # copies in, solves and copies back, overlapping the transfers with the compute) ----
     h_in = [torch.empty(x.shape, dtype=torch.float64, pin_memory=True) for x in u0 + [C, md]]
     for h, d in zip(h_in, u0 + [C, md]):
         h.copy_(d)
     h_out = [torch.empty(x.shape, dtype=torch.float64, pin_memory=True) for x in u + [p] + ug]
-    d_in = u + [C, md]
     h2d = sum(x.numel() * 8 for x in h_in)
     d2h = sum(x.numel() * 8 for x in h_out)
     e2e_steps = max(3, min(args.steps, 20))
     ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+
+    def host_step():
+        vofp.vofp_project_extend_host(plan.handle, h_in[0], h_in[1], h_in[2], h_in[3], h_in[4], c["rho1"],
+                                      c["rho2"], c["dt_over_rho0"], h_out[0], h_out[1], h_out[2], h_out[3],
+                                      h_out[4], h_out[5], h_out[6])
+
     for i in range(e2e_steps + 1):
         flush.zero_()
         if i > 0:
             ev2[i - 1][0].record(st)
-        for d, h in zip(d_in, h_in):
-            d.copy_(h, non_blocking=True)
-        step()
-        for h, d in zip(h_out, u + [p] + ug):
-            h.copy_(d, non_blocking=True)
+        host_step()
         if i > 0:
             ev2[i - 1][1].record(st)
     torch.cuda.synchronize()
     e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in ev2]))
-    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * cells * 2 / (float(e2e_t.item()) / 1e3) / 1e6
+    _, e2e_value = job_rate(e2e_ms, cells, 2, world, dev)
 
     # ---- roofline of the dominant kernel (its launches timed with events on the launching stream) ----
     wl = "droplet%d_%s" % (args.n, args.precision)

@@ -178,6 +178,22 @@ int vofp_project_extend(vofp_plan* plan, double* u, double* v, double* w, const 
                         vofp_info* info);
 
 /*
+ * The same time step (vofp_project_extend) on HOST buffers -- the call of a host code that keeps its fields
+ * in host memory.  Inputs u, v, w (faces), C, mdot (cells) are copied to device fields owned by the plan
+ * (allocated on its first host step), results are copied back: the projected u_out, v_out, w_out, the
+ * pressure p_out and the interface velocity ug, vg, wg (layouts as on the device).  The copies run on two
+ * streams of the plan and overlap the compute on `stream`: C and mdot go first and the geometry pass starts
+ * while the velocities are still arriving; the projected fields leave while the extension solve runs.  The
+ * call is asynchronous: `stream` completes after the last result has arrived, so the host buffers must stay
+ * valid until then (pinned host memory makes the copies asynchronous; pageable memory works but serialises
+ * them).  Errors: INVALID_ARG, OOM (device fields), CUDA.
+ */
+int vofp_project_extend_host(vofp_plan* plan, const double* u, const double* v, const double* w, const double* C,
+                             const double* mdot, double rho1, double rho2, double dt_over_rho0, double* u_out,
+                             double* v_out, double* w_out, double* p_out, double* ug, double* vg, double* wg,
+                             void* stream);
+
+/*
  * Batched projection of independent instances (an ensemble of droplet runs with uneven grids; the paper's
  * solver runs one instance, so this is the data-parallel form of vofp_project).  plans[0..n-1]: distinct
  * VOFP_MIXED plans on one device (each plan's workspace serves exactly one instance).  Every pass of the

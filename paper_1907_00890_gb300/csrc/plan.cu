@@ -464,12 +464,16 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   const int sx = p->ax[0].fd.bm ? p->ax[0].fd.bm : nx, sy = p->ax[1].fd.bm ? p->ax[1].fd.bm : ny;
   p->xpb = sx >= 1024 ? 1 : (1024 / sx > 16 ? 16 : 1024 / sx);
   if (p->xpb < 1) p->xpb = 1;
+  // y pass: columns per block so that each row segment read is 128 bytes (full cache lines), shrunk while the
+  // tile (two buffers of tx/2 complex lines) exceeds its shared-memory budget: 96 KB for the FP64 pass (two
+  // blocks per SM keep its FP64 pipe busy; measured faster than full lines at 512^3), 132 KB for the
+  // reduced-precision passes
   int tx = 16;
   while (tx > 2 && (size_t)16 * tx * y_ld(sy) > 96 * 1024) tx -= 2;
   p->ytx = tx;
   // the reduced-precision path's shapes, sized by its element (FP32 or FP32-pair)
-  tx = 16;
-  while (tx > 2 && (size_t)(4 * rs) * tx * y_ld(sy) > 96 * 1024) tx -= 2;
+  tx = (int)(128 / rs);
+  while (tx > 2 && (size_t)(4 * rs) * tx * y_ld(sy) > 132 * 1024) tx -= 2;
   p->ytx32 = tx;
   if (zper) {
     // periodic z (general column solver): systems per 128-thread block, three columns each in shared memory
@@ -655,6 +659,7 @@ extern "C" void vofp_plan_destroy(vofp_plan* p) {
   cudaDeviceSynchronize();
   if (p->table_block) cudaFree(p->table_block);
   if (p->G) cudaFree(p->G);
+  free_host_step(p);
   cudaSetDevice(cur);
   plan_free_host(p);
 }

@@ -440,3 +440,129 @@ extern "C" int vofp_project_extend(vofp_plan* pl, double* u, double* v, double* 
   }
   return s1 > s2 ? s1 : s2;
 }
+
+// ---- the droplet step on host buffers, transfers overlapped with compute ------------------------------------
+
+namespace vofp {
+
+struct HostStep {
+  double* buf;  // one allocation: u, v, w, ue, ve, we, ug, vg, wg (faces), C, mdot, p, phi (cells)
+  double *u, *v, *w, *ue, *ve, *we, *ug, *vg, *wg, *C, *mdot, *p, *phi;
+  size_t nu, nv, nw, cells;
+  cudaStream_t sin, sout;
+  cudaEvent_t start, in_cm, in_uvw, proj, ext, out;
+};
+
+static int ensure_host_step(vofp_plan* pl, HostStep** out) {
+  if (pl->hstep) {
+    *out = (HostStep*)pl->hstep;
+    return VOFP_OK;
+  }
+  HostStep* h = new HostStep();
+  const int nx = pl->n[0], ny = pl->n[1], nz = pl->n[2];
+  h->nu = (size_t)nface(nx, pl->bc[0]) * ny * nz;
+  h->nv = (size_t)nx * nface(ny, pl->bc[1]) * nz;
+  h->nw = (size_t)nx * ny * nface(nz, pl->bc[2]);
+  h->cells = (size_t)nx * ny * nz;
+  const size_t faces = h->nu + h->nv + h->nw;
+  if (cudaMalloc((void**)&h->buf, sizeof(double) * (3 * faces + 4 * h->cells)) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return VOFP_ERR_OOM;
+  }
+  double* q = h->buf;
+  double** f3[3][3] = {{&h->u, &h->v, &h->w}, {&h->ue, &h->ve, &h->we}, {&h->ug, &h->vg, &h->wg}};
+  for (int s = 0; s < 3; ++s) {
+    *f3[s][0] = q;
+    q += h->nu;
+    *f3[s][1] = q;
+    q += h->nv;
+    *f3[s][2] = q;
+    q += h->nw;
+  }
+  h->C = q;
+  h->mdot = q + h->cells;
+  h->p = q + 2 * h->cells;
+  h->phi = q + 3 * h->cells;
+  cudaStreamCreateWithFlags(&h->sin, cudaStreamNonBlocking);
+  cudaStreamCreateWithFlags(&h->sout, cudaStreamNonBlocking);
+  cudaEvent_t* evs[6] = {&h->start, &h->in_cm, &h->in_uvw, &h->proj, &h->ext, &h->out};
+  for (cudaEvent_t* e : evs) cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+  pl->bytes += sizeof(double) * (3 * faces + 4 * h->cells);
+  pl->hstep = h;
+  *out = h;
+  return VOFP_OK;
+}
+
+void free_host_step(vofp_plan* pl) {
+  HostStep* h = (HostStep*)pl->hstep;
+  if (!h) return;
+  cudaFree(h->buf);
+  cudaStreamDestroy(h->sin);
+  cudaStreamDestroy(h->sout);
+  cudaEvent_t evs[6] = {h->start, h->in_cm, h->in_uvw, h->proj, h->ext, h->out};
+  for (cudaEvent_t e : evs) cudaEventDestroy(e);
+  delete h;
+  pl->hstep = nullptr;
+}
+
+}  // namespace vofp
+
+static int h2d(double* d, const double* h, size_t n, cudaStream_t s) {
+  return cudaMemcpyAsync(d, h, sizeof(double) * n, cudaMemcpyHostToDevice, s) == cudaSuccess ? 0 : 1;
+}
+static int d2h(double* h, const double* d, size_t n, cudaStream_t s) {
+  return cudaMemcpyAsync(h, d, sizeof(double) * n, cudaMemcpyDeviceToHost, s) == cudaSuccess ? 0 : 1;
+}
+
+extern "C" int vofp_project_extend_host(vofp_plan* pl, const double* u, const double* v, const double* w,
+                                        const double* C, const double* mdot, double rho1, double rho2,
+                                        double dt_over_rho0, double* u_out, double* v_out, double* w_out,
+                                        double* p_out, double* ug, double* vg, double* wg, void* stream) {
+  if (!pl || !u || !v || !w || !C || !mdot || !u_out || !v_out || !w_out || !p_out || !ug || !vg || !wg)
+    return VOFP_ERR_INVALID_ARG;
+  if (!(dt_over_rho0 > 0) || !std::isfinite(dt_over_rho0) || !good_density(rho1) || !good_density(rho2))
+    return VOFP_ERR_INVALID_ARG;
+  HostStep* h;
+  int s = ensure_host_step(pl, &h);
+  if (s) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  // inputs on the copy-in stream, after whatever the caller queued before: C and mdot first (the geometry
+  // pass needs only them), then the velocities
+  int e = cudaEventRecord(h->start, st) != cudaSuccess;
+  e |= cudaStreamWaitEvent(h->sin, h->start, 0) != cudaSuccess;
+  e |= h2d(h->C, C, h->cells, h->sin) | h2d(h->mdot, mdot, h->cells, h->sin);
+  e |= cudaEventRecord(h->in_cm, h->sin) != cudaSuccess;
+  e |= h2d(h->u, u, h->nu, h->sin) | h2d(h->v, v, h->nv, h->sin) | h2d(h->w, w, h->nw, h->sin);
+  e |= cudaEventRecord(h->in_uvw, h->sin) != cudaSuccess;
+  if (e) return VOFP_ERR_CUDA;
+  // compute on the caller's stream: geometry while the velocities arrive, then the projection
+  e |= cudaStreamWaitEvent(st, h->in_cm, 0) != cudaSuccess;
+  const int gs = launch_geometry(pl, h->C, h->mdot, 1.0 / rho2 - 1.0 / rho1, true, nullptr, st);
+  if (gs) return gs;
+  e |= cudaStreamWaitEvent(st, h->in_uvw, 0) != cudaSuccess;
+  XArgs xa = {};
+  xa.u = h->u;
+  xa.v = h->v;
+  xa.w = h->w;
+  xa.src = pl->G;
+  xa.scale = 1.0 / dt_over_rho0;
+  const int s1 = project_common(pl, RHS_DIV, xa, h->u, h->v, h->w, dt_over_rho0, h->p, st, nullptr);
+  if (s1 < 0) return s1;
+  // the projected velocities and p leave on the copy-out stream while the extension solve runs
+  e |= cudaEventRecord(h->proj, st) != cudaSuccess;
+  e |= cudaStreamWaitEvent(h->sout, h->proj, 0) != cudaSuccess;
+  e |= d2h(u_out, h->u, h->nu, h->sout) | d2h(v_out, h->v, h->nv, h->sout) | d2h(w_out, h->w, h->nw, h->sout);
+  e |= d2h(p_out, h->p, h->cells, h->sout);
+  const int s2 = extend_common(pl, h->u, h->v, h->w, h->mdot, rho1, h->ue, h->ve, h->we, h->ug, h->vg, h->wg,
+                               h->phi, st, nullptr);
+  if (s2 < 0) return s2;
+  e |= cudaEventRecord(h->ext, st) != cudaSuccess;
+  e |= cudaStreamWaitEvent(h->sout, h->ext, 0) != cudaSuccess;
+  e |= d2h(ug, h->ug, h->nu, h->sout) | d2h(vg, h->vg, h->nv, h->sout) | d2h(wg, h->wg, h->nw, h->sout);
+  // the caller's stream completes only after the results have arrived
+  e |= cudaEventRecord(h->out, h->sout) != cudaSuccess;
+  e |= cudaStreamWaitEvent(st, h->out, 0) != cudaSuccess;
+  if (e) return VOFP_ERR_CUDA;
+  return s1 > s2 ? s1 : s2;
+}

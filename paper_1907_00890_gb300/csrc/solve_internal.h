@@ -78,6 +78,8 @@ size_t plan_prep_stage_bytes(const PlanPrep* pp);
 void plan_free_host(vofp_plan* p);
 // Allocate the interface-geometry workspace (s, n) on first use.
 int ensure_geometry(vofp_plan* p);
+// Release the host-buffer step's device fields, streams and events (plan destruction).
+void free_host_step(vofp_plan* p);
 
 struct XArgs;
 struct GridDev;

@@ -470,6 +470,7 @@ struct vofp_plan {
   vofp::ff* dzff;  // dz per plane, FP32 pair
   double* conv;  // mixed path: FP64 reduction slots (norms, means) per solve
   double* G;     // interface geometry: s, n_x, n_y, n_z (4 * cells)
+  void* hstep;   // device fields, streams and events of the host-buffer step (allocated on first use)
   void* ztab;    // bounded z: Thomas factors per distinct eigenvalue pair in the plan's arithmetic type
                  // (double2, float2 or cff; NULL: periodic z)
   const void* zaT;     // z sub-diagonal a_k in the same type

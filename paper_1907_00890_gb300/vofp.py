@@ -78,6 +78,25 @@ _lib.vofp_project_extend.restype = _I
 EXPORTED.append("vofp_project_extend")
 
 
+_lib.vofp_project_extend_host.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P]
+_lib.vofp_project_extend_host.restype = _I
+EXPORTED.append("vofp_project_extend_host")
+
+
+def vofp_project_extend_host(plan, u, v, w, C, mdot, rho1, rho2, dt_over_rho0, u_out, v_out, w_out, p_out,
+                             ug, vg, wg, stream=None):
+    """The droplet step on host (CPU) tensors: copies in, both solves, copies out, overlapped on the device.
+    Asynchronous on `stream` (default: the current stream); the tensors must stay alive until it completes."""
+    def hp(t, name):
+        if t is None or t.device.type != "cpu" or t.dtype.itemsize != 8 or not t.is_contiguous():
+            raise ValueError("%s: a contiguous float64 CPU tensor is required" % name)
+        return t.data_ptr()
+    return _check(_lib.vofp_project_extend_host(
+        plan, hp(u, "u"), hp(v, "v"), hp(w, "w"), hp(C, "C"), hp(mdot, "mdot"), float(rho1), float(rho2),
+        float(dt_over_rho0), hp(u_out, "u_out"), hp(v_out, "v_out"), hp(w_out, "w_out"), hp(p_out, "p_out"),
+        hp(ug, "ug"), hp(vg, "vg"), hp(wg, "wg"), _stream(stream)), "vofp_project_extend_host")
+
+
 def vofp_project_extend(plan, u, v, w, C, mdot, rho1, rho2, dt_over_rho0, p, ue, ve, we, ug=None, vg=None,
                         wg=None, phi=None, stream=None, info=False):
     inf = vofp_info() if info else None

@@ -254,3 +254,41 @@ def test_project_extend_step(vp, n, bc, mode):
     assert rel(host(phi), oe[6]) < TOL
     assert abs(info["compat_defect"] - ou[4]["compat_defect"]) < 1e-10 * max(1.0, abs(ou[4]["compat_defect"]))
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "ff"])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_project_extend_host_buffers(vp, precision, pinned):
+    """vofp_project_extend_host (host buffers in and out, transfers overlapped with the compute) against the
+    oracle's two solves, twice in a row with the same plan (its device fields are reused), on pinned and on
+    pageable host memory."""
+    import torch
+    n, bc = (36, 30, 28), ("P", "P", "NN")
+    dz = synth.stretched_dz(n[2])
+    g = oracle.Grid(*n, 1.0 / n[0], 1.0 / n[1], dz, bc)
+    C, centre = synth.droplet(n, bc, 21, dz=dz)
+    mdot = 1.0 + 0.2 * synth.rng(22).standard_normal(g.shape)
+    u0 = synth.swirl_velocity(n, bc, centre, 23)
+    s = oracle.stefan_source(g, C, mdot, 100.0, 1.0)
+    ou = oracle.project(g, *u0, src=s, dt_over_rho0=0.01)
+    oe = oracle.extend_liquid_velocity(g, *ou[:3], C, mdot, 100.0, 1.0)
+    prec = vp.FP64 if precision == "fp64" else vp.FF
+    tol = TOL if prec == vp.FP64 else 1e-10
+    plan = vp.Plan(n, g.widths[0][0], g.widths[1][0], dz, bc, prec=prec, max_refine=0)
+
+    def hostt(a):
+        t = torch.tensor(np.ascontiguousarray(a), dtype=torch.float64)
+        return t.pin_memory() if pinned else t
+
+    ins = [hostt(a) for a in list(u0) + [C, mdot]]
+    outs = [hostt(np.zeros_like(a)) for a in list(u0) + [C] + list(u0)]
+    for _ in range(2):
+        for t in outs:
+            t.zero_()
+        vp.vofp_project_extend_host(plan.handle, *ins, 100.0, 1.0, 0.01, *outs)
+        torch.cuda.synchronize()
+        for a in range(3):
+            assert rel(outs[a].numpy(), ou[a]) < tol
+            assert rel(outs[4 + a].numpy(), oe[3 + a]) < tol
+        assert rel(outs[3].numpy(), ou[3]) < tol
+    plan.close()
