@@ -221,7 +221,7 @@ def bench_large(vofp, args):
     return out
 
 
-def bench_batched(vofp, args, prec=None):
+def bench_batched(vofp, args, prec=None, fp64_baseline=False):
     """64 independent instances, per-axis sizes from {32,48,64,96,128,160}, one graph replay per step."""
     import torch
     from paper_1907_00890_gb300 import synth
@@ -271,8 +271,32 @@ def bench_batched(vofp, args, prec=None):
     vofp.vofp_batch_destroy(b)
     for p in plans:
         p.close()
+    # the plain FP64 path on the same ensemble, one projection call per instance (same inputs, same stream)
+    ms64 = None
+    if fp64_baseline:
+        plans64 = [vofp.Plan(n, 1.0 / n[0], 1.0 / n[1], synth.uniform_dz(n[2]), bc) for n in sizes]
+
+        def all64():
+            for pl, u in zip(plans64, us):
+                vofp.vofp_project(pl.handle, u[0], u[1], u[2], None, 1.0, None)
+
+        prep()
+        all64()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for i in range(reps):
+            prep()
+            ev[i][0].record(st)
+            all64()
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+        ms64 = float(np.mean([a.elapsed_time(bb) for a, bb in ev]))
+        for pl in plans64:
+            pl.close()
     return {"value": cells / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_batch": ms, "instances": len(sizes),
             "cells": cells, "solves_per_s": len(sizes) / (ms / 1e3),
+            "fp64_one_call_per_instance": None if ms64 is None else {
+                "ms": ms64, "solves_per_s": len(sizes) / (ms64 / 1e3), "value": cells / (ms64 / 1e3) / 1e6},
             "dtype": "f32+f64" if prec == vofp.MIXED else "f32x2+f64",
             "max_rel_divergence_after": worst,
             "workload": "64 projection instances, sizes per axis from {32,48,64,96,128,160}, P,P,NN, %s, "
@@ -624,7 +648,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         variants["large_512"] = bench_large(vofp, args)
         torch.cuda.empty_cache()
-        variants["batched"] = bench_batched(vofp, args)
+        variants["batched"] = bench_batched(vofp, args, fp64_baseline=True)
         torch.cuda.empty_cache()
         variants["batched_ff"] = bench_batched(vofp, args, prec=vofp.FF)
         torch.cuda.empty_cache()

@@ -28,13 +28,13 @@ static void allow_smem(K kern) {
 
 template <typename T, typename C, typename TT>
 static void allow_all() {
-  allow_smem(k_xfwd<T, C, RHS_F>);
-  allow_smem(k_xfwd<T, C, RHS_DIV>);
-  allow_smem(k_xfwd<T, C, RHS_DIV_STEFAN>);
-  allow_smem(k_xfwd<T, C, RHS_RESID>);
-  allow_smem(k_ypass<T, C, false>);
-  allow_smem(k_ypass<T, C, true>);
-  allow_smem(k_xinv<T, C>);
+  allow_smem(xfwd_kernel<T, C, RHS_F>());
+  allow_smem(xfwd_kernel<T, C, RHS_DIV>());
+  allow_smem(xfwd_kernel<T, C, RHS_DIV_STEFAN>());
+  allow_smem(xfwd_kernel<T, C, RHS_RESID>());
+  allow_smem(ypass_kernel<T, C, false>());
+  allow_smem(ypass_kernel<T, C, true>());
+  allow_smem(xinv_kernel<T, C>());
   allow_smem(k_zsolve<T, T>);
   allow_smem(k_ztab<T, TT>);
   allow_smem(k_ztab_staged<T, TT>);
@@ -122,7 +122,7 @@ static void solve_red(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, b
   ya.tol2 = tol2;
   const dim3 ygrid((nx + ya.tx - 1) / ya.tx, nz);
   const size_t ysm = 2 * (size_t)(ya.tx / 2) * y_ld(fft_span(ya.fd, ya.blu)) * sizeof(C);
-  if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, (k_ypass<R, C, false><<<ygrid, 256, ysm, st>>>(ya)));
+  if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, (ypass_kernel<R, C, false>()<<<ygrid, 256, ysm, st>>>(ya)));
   ZArgs za = z_args(pl, stats);
   za.S = pl->S32;
   za.ti = pl->zti32;
@@ -159,7 +159,7 @@ static void solve_red(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, b
                   k_zlow64<R><<<(pl->nlow + 63) / 64, 64, 0, st>>>(za, pl->lowmodes, pl->nlow, nullptr,
                                                                    pl->lowscratch));
   }
-  if (ny > 1) VOFP_LAUNCH(KID_YINV, st, (k_ypass<R, C, true><<<ygrid, 256, ysm, st>>>(ya)));
+  if (ny > 1) VOFP_LAUNCH(KID_YINV, st, (ypass_kernel<R, C, true>()<<<ygrid, 256, ysm, st>>>(ya)));
 }
 
 template <typename R>
@@ -190,7 +190,7 @@ static void xinv_red(vofp_plan* pl, double* pout, int accumulate, int skip_k, do
   xi.d2_out = d2_out;
   const int xgrid = xpass_blocks(xi.ny, xi.nz, xi.pb);
   const size_t xsm = 2 * (size_t)xi.pb * fft_span(xi.fd, xi.blu) * sizeof(C);
-  VOFP_LAUNCH(KID_XINV, st, (k_xinv<R, C><<<xgrid, 256, xsm, st>>>(xi)));
+  VOFP_LAUNCH(KID_XINV, st, (xinv_kernel<R, C>()<<<xgrid, 256, xsm, st>>>(xi)));
 }
 
 template <typename R>
@@ -206,12 +206,12 @@ static void xfwd_red(vofp_plan* pl, int mode, XArgs xa, cudaStream_t st) {
   const int xgrid = xpass_blocks(pl->n[1], pl->n[2], xa.pb);
   const size_t xsm = 2 * (size_t)xa.pb * fft_span(xa.fd, xa.blu) * sizeof(C);
   switch (mode) {
-    case RHS_F: VOFP_LAUNCH(KID_XFWD, st, (k_xfwd<R, C, RHS_F><<<xgrid, 256, xsm, st>>>(xa))); break;
-    case RHS_DIV: VOFP_LAUNCH(KID_XFWD_DIV, st, (k_xfwd<R, C, RHS_DIV><<<xgrid, 256, xsm, st>>>(xa))); break;
+    case RHS_F: VOFP_LAUNCH(KID_XFWD, st, (xfwd_kernel<R, C, RHS_F>()<<<xgrid, 256, xsm, st>>>(xa))); break;
+    case RHS_DIV: VOFP_LAUNCH(KID_XFWD_DIV, st, (xfwd_kernel<R, C, RHS_DIV>()<<<xgrid, 256, xsm, st>>>(xa))); break;
     case RHS_DIV_STEFAN:
-      VOFP_LAUNCH(KID_XFWD_DIVSTEF, st, (k_xfwd<R, C, RHS_DIV_STEFAN><<<xgrid, 256, xsm, st>>>(xa)));
+      VOFP_LAUNCH(KID_XFWD_DIVSTEF, st, (xfwd_kernel<R, C, RHS_DIV_STEFAN>()<<<xgrid, 256, xsm, st>>>(xa)));
       break;
-    default: VOFP_LAUNCH(KID_RESID, st, (k_xfwd<R, C, RHS_RESID><<<xgrid, 256, xsm, st>>>(xa))); break;
+    default: VOFP_LAUNCH(KID_RESID, st, (xfwd_kernel<R, C, RHS_RESID>()<<<xgrid, 256, xsm, st>>>(xa))); break;
   }
 }
 

@@ -445,4 +445,46 @@ __global__ void __launch_bounds__(256) k_xinv(XInvArgs a) {
   xinv_block<T, C>(a, blockIdx.x, smem_raw, red);
 }
 
+// The FP32 passes with their registers capped at 48 (five 256-thread blocks per SM; left alone the compiler
+// takes 58 for the x passes and drops that to four).  The FP32 x pass that also evaluates the Stefan source
+// keeps the plain kernel: it spills under the cap.
+template <int MODE>
+__global__ void __launch_bounds__(256, 5) k_xfwd_f32(XArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  xfwd_block<float, float2, MODE>(a, blockIdx.x, smem_raw, red);
+}
+template <bool INV>
+__global__ void __launch_bounds__(256, 5) k_ypass_f32(YArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ypass_block<float, float2, INV>(a, blockIdx.x, blockIdx.y, smem_raw);
+}
+template <int UNUSED>
+__global__ void __launch_bounds__(256, 5) k_xinv_f32(XInvArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  xinv_block<float, float2>(a, blockIdx.x, smem_raw, red);
+}
+
+typedef void (*XFwdKernel)(XArgs);
+typedef void (*YPassKernel)(YArgs);
+typedef void (*XInvKernel)(XInvArgs);
+
+// The kernel that runs a pass for spectrum type T.
+template <typename T, typename C, int MODE>
+inline XFwdKernel xfwd_kernel() {
+  if constexpr (std::is_same<T, float>::value && MODE != RHS_DIV_STEFAN) return k_xfwd_f32<MODE>;
+  else return k_xfwd<T, C, MODE>;
+}
+template <typename T, typename C, bool INV>
+inline YPassKernel ypass_kernel() {
+  if constexpr (std::is_same<T, float>::value) return k_ypass_f32<INV>;
+  else return k_ypass<T, C, INV>;
+}
+template <typename T, typename C>
+inline XInvKernel xinv_kernel() {
+  if constexpr (std::is_same<T, float>::value) return k_xinv_f32<0>;
+  else return k_xinv<T, C>;
+}
+
 }  // namespace vofp

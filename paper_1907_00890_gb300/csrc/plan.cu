@@ -25,7 +25,8 @@
 
 namespace vofp {
 
-void factor_radices(int n, FftDesc* fd) {
+// The direct stages of a length-n transform (radices 8, 4, 2, 3, 5, then 7, 11, 13 and any remaining prime).
+static void factor_radices_direct(int n, FftDesc* fd) {
   fd->n = n;
   fd->nst = 0;
   int m = n, e = 0;
@@ -62,52 +63,52 @@ void factor_radices(int n, FftDesc* fd) {
       m = 1;
     }
   }
-  // a prime factor above 7 makes a stage cost O(p) per point: such lengths also get the Bluestein form
+}
+
+void factor_radices(int n, FftDesc* fd) {
+  factor_radices_direct(n, fd);
+  // a prime factor above 13 (no hand-written butterfly) makes a stage cost O(p) per point: such lengths also
+  // get the Bluestein form
   int maxp = 1;
   for (int s = 0; s < fd->nst; ++s)
     if (fd->radix[s] > maxp && fd->radix[s] != 8 && fd->radix[s] != 4) maxp = fd->radix[s];
   fd->bm = 0;
   fd->bst = 0;
-  if (maxp > 7 && 2 * n - 1 <= 4096) {  // (longer lines would not fit in shared memory twice over)
-    int M = 1, e2 = 0;
-    while (M < 2 * n - 1) {
-      M *= 2;
-      ++e2;
+  if (maxp > 13 && 2 * n - 1 <= 4096) {  // (longer lines would not fit in shared memory twice over)
+    // the shortest convolution length >= 2n - 1 of the form c * 2^k, c in {1, 3, 5, 15}: all its stages have
+    // hand-written butterflies
+    int M = 0;
+    const int cs[4] = {1, 3, 5, 15};
+    for (int c : cs) {
+      int m = c;
+      while (m < 2 * n - 1) m *= 2;
+      if (M == 0 || m < M) M = m;
     }
+    FftDesc b;
+    factor_radices_direct(M, &b);
     fd->bm = M;
-    int b8 = e2 / 3, br = e2 % 3;
-    if (br == 1 && b8 > 0) {
-      --b8;
-      fd->bradix[fd->bst++] = 4;
-      fd->bradix[fd->bst++] = 4;
-    } else if (br == 1) {
-      fd->bradix[fd->bst++] = 2;
-    } else if (br == 2) {
-      fd->bradix[fd->bst++] = 4;
-    }
-    for (int i = 0; i < b8; ++i) fd->bradix[fd->bst++] = 8;
+    fd->bst = b.nst;
+    for (int s = 0; s < b.nst; ++s) fd->bradix[s] = b.radix[s];
   }
 }
 
-// In-place forward DFT of length M (a power of two) in FP64 on the host (iterative radix 2), for the
-// Bluestein kernel spectrum.
-static void host_fft_pow2(std::vector<std::complex<double>>& x) {
-  const size_t M = x.size();
-  for (size_t i = 1, j = 0; i < M; ++i) {
-    size_t bit = M >> 1;
-    for (; j & bit; bit >>= 1) j ^= bit;
-    j ^= bit;
-    if (i < j) std::swap(x[i], x[j]);
-  }
-  for (size_t len = 2; len <= M; len <<= 1) {
-    const double ang = -2.0 * 3.14159265358979323846 / (double)len;
-    for (size_t i = 0; i < M; i += len)
-      for (size_t k = 0; k < len / 2; ++k) {
-        const std::complex<double> w(std::cos(ang * (double)k), std::sin(ang * (double)k));
-        const std::complex<double> u = x[i + k], v = x[i + k + len / 2] * w;
-        x[i + k] = u + v;
-        x[i + k + len / 2] = u - v;
-      }
+// In-place forward DFT in FP64 on the host for lengths whose prime factors are 2, 3 and 5 (recursive
+// decimation in time), for the Bluestein kernel spectrum.  W holds e^{-2 pi i t / N} for the top-level
+// length N; a sub-transform of length n = N / s uses every s-th entry.
+static void host_fft(std::vector<std::complex<double>>& x, const std::vector<std::complex<double>>& W) {
+  const size_t n = x.size();
+  if (n <= 1) return;
+  const size_t s = W.size() / n;
+  const size_t r = n % 2 == 0 ? 2 : (n % 3 == 0 ? 3 : 5);
+  const size_t m = n / r;
+  std::vector<std::vector<std::complex<double>>> sub(r, std::vector<std::complex<double>>(m));
+  for (size_t q = 0; q < r; ++q)
+    for (size_t j = 0; j < m; ++j) sub[q][j] = x[j * r + q];
+  for (auto& v : sub) host_fft(v, W);
+  for (size_t k = 0; k < n; ++k) {
+    std::complex<double> acc(0.0, 0.0);
+    for (size_t q = 0; q < r; ++q) acc += W[((q * k) % n) * s] * sub[q][k % m];
+    x[k] = acc;
   }
 }
 
@@ -124,7 +125,12 @@ static std::vector<double2> bluestein_tables(const FftDesc& fd) {
     h[j] = c;
     if (j > 0) h[M - j] = c;
   }
-  host_fft_pow2(h);
+  std::vector<std::complex<double>> W(M);
+  for (int q = 0; q < M; ++q) {
+    const double ang = -2.0 * 3.14159265358979323846 * q / M;
+    W[q] = std::complex<double>(std::cos(ang), std::sin(ang));
+  }
+  host_fft(h, W);
   for (int k = 0; k < M; ++k) t[n + k] = make_double2(h[k].real() / M, h[k].imag() / M);
   for (int q = 0; q < M; ++q) {
     const double ang = -2.0 * 3.14159265358979323846 * q / M;

@@ -114,8 +114,9 @@ struct FftDesc {
   int n;
   int nst;
   int radix[VOFP_MAX_STAGES];
-  // Bluestein (chirp-z) form, used when n has a prime factor above 7 and the plan supplies its tables: the
-  // length-n DFT as a cyclic convolution of length bm (a power of two >= 2n - 1) done with bm-point FFTs.
+  // Bluestein (chirp-z) form, used when n has a prime factor above 13 and the plan supplies its tables: the
+  // length-n DFT as a cyclic convolution of length bm (the least c * 2^k >= 2n - 1, c in {1, 3, 5, 15}) done
+  // with bm-point FFTs.
   int bm;  // 0: n's own stages only
   int bst;
   int bradix[VOFP_MAX_STAGES];
@@ -143,7 +144,7 @@ struct AxisDev {
   const double* lam; // eigenvalue of packed spectral index q, q < n
 };
 
-// Host-side factorisation of n into radices (8, 4, then 2, 3, 5, then any remaining prime).
+// Host-side factorisation of n into radices (8, 4, then 2, 3, 5, then 7, 11, 13 and any remaining prime).
 void factor_radices(int n, FftDesc* fd);
 
 // ---- shared-memory Stockham FFT ----------------------------------------------------------------------
@@ -240,33 +241,70 @@ __device__ __forceinline__ void fft_stage(const C* __restrict__ src, C* __restri
   }
 }
 
-// Stage of a radix that has no hand-written butterfly: one output per thread, O(RAD) work each.
+// Stage of an odd prime radix R >= 7 (a runtime value; no hand-written butterfly).  The twiddles are applied in
+// place first (src is scratch once a stage has run), then every butterfly is split into H + 1 work items
+// (H = (R - 1) / 2): item 0 sums the inputs, item m >= 1 forms the output pair (m, R - m) from the input pairs
+// a_r = v_r + v_{R-r}, b_r = v_r - v_{R-r} (r = 1..H) as X_m = v_0 + sum_r a_r cos(2 pi r m / R)
+// - i sum_r b_r sin(2 pi r m / R), X_{R-m} the same with +i.  That is H complex-by-real multiply-add pairs
+// per output pair, without per-output twiddles, and the loops stay rolled (few registers: the kernels that
+// hold every stage keep their register count).  cos and sin of 2 pi q / R come from the n-point twiddle
+// table, entry q n / R.
 template <typename C>
-__device__ __forceinline__ void fft_stage_generic(const C* __restrict__ src, C* __restrict__ dst, int batch, int n,
-                                                  int Ns, int RAD, const C* __restrict__ tw, int ld) {
+__device__ __forceinline__ void fft_stage_odd(C* __restrict__ src, C* __restrict__ dst, int batch, int n, int Ns,
+                                              int RAD, const C* __restrict__ tw, int ld) {
   typedef decltype(C::x) R;
   const int NR = n / RAD;
-  const int twstep = n / (Ns * RAD);
-  const int total = batch * n;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int bi = t / n;
-    const int rem = t - bi * n;
-    const int rout = rem / NR;
-    const int j = rem - rout * NR;
+  const int H = (RAD - 1) / 2;
+  if (Ns > 1) {
+    const int twstep = n / (Ns * RAD);
+#pragma unroll 1
+    for (int t = threadIdx.x; t < batch * n; t += blockDim.x) {
+      const int bi = t / n;
+      const int e = t - bi * n;  // e = j + r NR
+      const int r = e / NR;
+      const int k = (e - r * NR) % Ns;
+      if (r != 0 && k != 0) {
+        C* p = src + bi * ld + e;
+        *p = cmul(*p, tw[r * k * twstep]);
+      }
+    }
+    __syncthreads();
+  }
+  const int per = NR * (H + 1);
+#pragma unroll 1
+  for (int t = threadIdx.x; t < batch * per; t += blockDim.x) {
+    const int bi = t / per;
+    const int rem = t - bi * per;
+    const int m = rem / NR;  // item-major: a warp shares m and reads consecutive j
+    const int j = rem - m * NR;
     const int k = j % Ns;
     const C* s = src + bi * ld;
-    const int e = (k * twstep + rout * NR) % n;  // exponent step per input r
-    R ax = 0, ay = 0;
-    int idx = 0;
-    for (int r = 0; r < RAD; ++r) {
-      C x = s[j + r * NR];
-      C w = tw[idx];
-      ax += x.x * w.x - x.y * w.y;
-      ay += x.x * w.y + x.y * w.x;
-      idx += e;
-      if (idx >= n) idx -= n;
+    C* d = dst + bi * ld + (j - k) * RAD + k;
+    const C v0 = s[j];
+    if (m == 0) {
+      C x = v0;
+#pragma unroll 1
+      for (int r = 1; r < RAD; ++r) x = cadd(x, s[j + r * NR]);
+      d[0] = x;
+      continue;
     }
-    dst[bi * ld + (j - k) * RAD + k + rout * Ns] = cmk<C>(ax, ay);
+    R ax = v0.x, ay = v0.y, bx = (R)0, by = (R)0;
+    int q = m;  // r m mod R
+#pragma unroll 1
+    for (int r = 1; r <= H; ++r) {
+      const C lo = s[j + r * NR], hi = s[j + (RAD - r) * NR];
+      const bool up = q > H;  // past half a turn: cos(2 pi q / R) = cos(2 pi (R - q) / R), sin flips sign
+      const C w = tw[(up ? RAD - q : q) * NR];  // e^{-2 pi i q' / R} = cos - i sin
+      const R c = w.x, sq = up ? w.y : -w.y;
+      ax += (lo.x + hi.x) * c;
+      ay += (lo.y + hi.y) * c;
+      bx += (lo.x - hi.x) * sq;
+      by += (lo.y - hi.y) * sq;
+      q += m;
+      if (q >= RAD) q -= RAD;
+    }
+    d[m * Ns] = cmk<C>(ax + by, ay - bx);
+    d[(RAD - m) * Ns] = cmk<C>(ax - by, ay + bx);
   }
 }
 
@@ -281,7 +319,7 @@ __device__ C* fft_stages(C* a, C* b, int batch, int n, int nst, const int* radix
       case 4: fft_stage<C, 4>(a, b, batch, n, Ns, tw, ld); break;
       case 5: fft_stage<C, 5>(a, b, batch, n, Ns, tw, ld); break;
       case 8: fft_stage<C, 8>(a, b, batch, n, Ns, tw, ld); break;
-      default: fft_stage_generic<C>(a, b, batch, n, Ns, R, tw, ld); break;
+      default: fft_stage_odd<C>(a, b, batch, n, Ns, R, tw, ld); break;  // an odd prime >= 7
     }
     __syncthreads();
     C* t = a;

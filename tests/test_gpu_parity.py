@@ -83,10 +83,17 @@ def test_poisson_sizes(vp, n, bc):
     plan.close()
 
 
-# lengths with a prime factor above 7 run the Bluestein (chirp-z) form: primes, 4 * 31, 2 * 3 * 41, 251,
-# and 2039 (prime, Bluestein length 4096, the longest that takes it) on each transformed axis
-BLUESTEIN = [(11, 4, 3), (37, 13, 5), (124, 6, 4), (246, 17, 3), (251, 5, 2), (6, 97, 3), (4, 251, 3),
+# lengths with a prime factor above 13 run the Bluestein (chirp-z) form: primes, 4 * 31, 2 * 3 * 41, 251,
+# and 2039 (prime, Bluestein length 4096, the longest that takes it) on each transformed axis.  Convolution
+# lengths (the least c * 2^k >= 2n - 1, c in {1, 3, 5, 15}): 17 -> 40, 37 -> 80, 97 -> 240, 124 -> 256,
+# 246 and 251 -> 512, 2039 -> 4096
+BLUESTEIN = [(17, 4, 3), (37, 13, 5), (124, 6, 4), (246, 17, 3), (251, 5, 2), (6, 97, 3), (4, 251, 3),
              (2039, 2, 2), (3, 2039, 2)]
+
+# odd prime factors 7, 11 and 13 run their own stages (no Bluestein form): primes, prime powers, products of
+# two of them and with powers of two and 3, on each transformed axis
+ODD_PRIMES = [(7, 11, 3), (13, 5, 4), (49, 3, 2), (77, 26, 3), (143, 6, 2), (4, 121, 2), (5, 169, 2),
+              (88, 104, 3), (231, 7, 2), (3, 1001, 2)]
 
 
 @pytest.mark.parametrize("n", BLUESTEIN)
@@ -97,6 +104,20 @@ def test_poisson_bluestein_lengths(vp, n, bc, precision):
     f = synth.rng(sum(n) + 7).standard_normal(g.shape)
     ref, _ = oracle.poisson_solve(g, f)
     prec = vp.FP64 if precision == "fp64" else vp.FF
+    plan = vp.Plan(n, g.widths[0][0], g.widths[1][0], dz, bc, prec=prec, max_refine=0 if prec == vp.FF else 6)
+    p = plan.poisson_solve(dev(f))
+    assert rel(host(p), ref) < (TOL if prec == vp.FP64 else 1e-10), (n, bc)
+    plan.close()
+
+
+@pytest.mark.parametrize("n", ODD_PRIMES)
+@pytest.mark.parametrize("bc", [("P", "P", "NN"), ("NN", "DD", "P"), ("DD", "NN", "DN")])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "ff"])
+def test_poisson_odd_prime_lengths(vp, n, bc, precision):
+    g, dz = make(n, bc, stretched=bc[2] != "P")
+    f = synth.rng(sum(n) + 11).standard_normal(g.shape)
+    ref, _ = oracle.poisson_solve(g, f)
+    prec = {"fp64": vp.FP64, "mixed": vp.MIXED, "ff": vp.FF}[precision]
     plan = vp.Plan(n, g.widths[0][0], g.widths[1][0], dz, bc, prec=prec, max_refine=0 if prec == vp.FF else 6)
     p = plan.poisson_solve(dev(f))
     assert rel(host(p), ref) < (TOL if prec == vp.FP64 else 1e-10), (n, bc)
