@@ -97,6 +97,20 @@ __global__ void __launch_bounds__(128) k_ztab_batch(const ZArgs* __restrict__ ar
   ztab_block<T, TT>(a, L.zt, L.smem_d, l % gx, l / gx, smem_raw);
 }
 
+// Bounded z, every instance's tile fitting: segmented tiles of 32 systems (kZSegW warps per block).
+template <typename T, typename TT>
+__global__ void __launch_bounds__(256) k_ztab_seg_batch(const ZArgs* __restrict__ args,
+                                                        const LowArgs* __restrict__ inst,
+                                                        const int* __restrict__ off, int n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int i = find_instance(off, n, blockIdx.x);
+  const ZArgs& a = args[i];
+  const LowArgs& L = inst[i];
+  const int l = blockIdx.x - __ldg(off + i);
+  const int gx = (a.nx + kZSegTI - 1) / kZSegTI;
+  ztab_seg_block<T, TT>(a, L.zt, l % gx, l / gx, smem_raw);
+}
+
 // Bounded z: low-eigenvalue systems of all instances, one warp each.
 template <typename T>
 __global__ void __launch_bounds__(128) k_zlow_scan_batch(const ZArgs* __restrict__ args,
@@ -182,6 +196,7 @@ static void allow_batch_kernels() {
   allow_smem(k_ypass_batch<T, C, true>);
   allow_smem(k_zsolve_batch<T>);
   allow_smem(k_ztab_batch<T, ZF<T>>);
+  allow_smem(k_ztab_seg_batch<T, ZF<T>>);
   allow_smem(k_xinv_batch<T, C>);
 }
 
@@ -204,6 +219,7 @@ struct vofp_batch {
   size_t o_offx, o_offy, o_offz, o_offlow, o_offepi;
   int tot_x, tot_y, tot_z, tot_low, tot_epi;
   bool ztab;  // every instance has a bounded z axis: factor-table z kernels
+  bool zseg;  // ... and every instance's segmented tile fits in shared memory
   int prec;   // VOFP_MIXED (FP32 spectrum) or VOFP_FF (FP32-pair spectrum), the same for every instance
   size_t sm_x, sm_y, sm_z;
   cudaGraphExec_t exec;
@@ -299,13 +315,17 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
   b->ztab = true;
   for (int i = 0; i < n; ++i)
     if (!plans[i]->ztab) b->ztab = false;
+  b->zseg = b->ztab;
+  for (int i = 0; i < n; ++i)
+    if (ztab_seg_smem(plans[i]->n[2], rsz) > 200 * 1024) b->zseg = false;
   for (int i = 0; i < n; ++i) {
     const vofp_plan* p = plans[i];
     const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
     offx[i + 1] = offx[i] + xpass_blocks(ny, nz, p->xpb);
     offy[i + 1] = offy[i] + (ny > 1 ? ((nx + p->ytx32 - 1) / p->ytx32) * nz : 0);
     const int gti = generic_ti(p, rsz);
-    offz[i + 1] = offz[i] + (b->ztab ? (nx + 127) / 128 : (nx + gti - 1) / gti) * ny;
+    offz[i + 1] = offz[i] + (b->zseg ? (nx + kZSegTI - 1) / kZSegTI
+                                     : (b->ztab ? (nx + 127) / 128 : (nx + gti - 1) / gti)) * ny;
     offl[i + 1] = offl[i] + p->nlow;
     const size_t faces = total_faces(grid_dev(p));
     int eb = (int)((faces + 255) / 256);
@@ -314,7 +334,8 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
     const size_t sx = 2 * (size_t)p->xpb * fft_span(p->ax[0].fd, p->ax[0].blu64) * csz;
     const size_t sy = 2 * (size_t)(p->ytx32 / 2) * y_ld(fft_span(p->ax[1].fd, p->ax[1].blu64)) * csz;
     const ZTabShape zs = ztab_shape(128, nz, rsz);
-    const size_t sz = b->ztab ? zs.smem : (size_t)(p->bc[2] == VOFP_BC_P ? 3 : 2) * gti * nz * rsz;
+    const size_t sz = b->zseg ? ztab_seg_smem(nz, rsz)
+                              : (b->ztab ? zs.smem : (size_t)(p->bc[2] == VOFP_BC_P ? 3 : 2) * gti * nz * rsz);
     if (sx > b->sm_x) b->sm_x = sx;
     if (sy > b->sm_y) b->sm_y = sy;
     if (sz > b->sm_z) b->sm_z = sz;
@@ -477,7 +498,11 @@ static void launch_sequence_t(vofp_batch* b, cudaStream_t st) {
     if (b->tot_y > 0)
       VOFP_LAUNCH(KID_YFWD, st, (k_ypass_batch<T, C, false><<<b->tot_y, 256, b->sm_y, st>>>(YF, offy, n)));
     if (b->ztab) {
-      VOFP_LAUNCH(KID_ZSOLVE, st, k_ztab_batch<T, ZF<T>><<<b->tot_z, 128, b->sm_z, st>>>(Z, L, offz, n));
+      if (b->zseg)
+        VOFP_LAUNCH(KID_ZSOLVE, st,
+                    (k_ztab_seg_batch<T, ZF<T>><<<b->tot_z, 32 * kZSegW, b->sm_z, st>>>(Z, L, offz, n)));
+      else
+        VOFP_LAUNCH(KID_ZSOLVE, st, k_ztab_batch<T, ZF<T>><<<b->tot_z, 128, b->sm_z, st>>>(Z, L, offz, n));
       if (b->tot_low > 0)
         VOFP_LAUNCH(KID_ZLOW, st,
                     k_zlow_scan_batch<T><<<(b->tot_low + 3) / 4, 128, 0, st>>>(Z, L, offl, n, b->tot_low));

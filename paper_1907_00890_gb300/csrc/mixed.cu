@@ -38,6 +38,7 @@ static void allow_all() {
   allow_smem(k_zsolve<T, T>);
   allow_smem(k_ztab<T, TT>);
   allow_smem(k_ztab_staged<T, TT>);
+  allow_smem(k_ztab_seg<T, TT>);
 }
 
 void init_kernel_attributes_mixed() {
@@ -133,7 +134,12 @@ static void solve_red(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, b
   if (pl->ztab) {
     // bulk systems from the factor table; the low-eigenvalue ones (a prefix of each row) by one warp each.
     // Small grids: the shared-memory staged kernel (too few systems to hide the row loads one thread each)
-    if (pl->zti32 == 0) {
+    if (pl->zti32 == -1) {
+      const dim3 tgrid((nx + kZSegTI - 1) / kZSegTI, ny);
+      VOFP_LAUNCH(KID_ZSOLVE, st,
+                  (k_ztab_seg<R, typename Red<R>::TT><<<tgrid, 32 * kZSegW, ztab_seg_smem(nz, sizeof(R)), st>>>(
+                      za, ztab_args(pl))));
+    } else if (pl->zti32 == 0) {
       const dim3 tgrid((nx + kZStagedTI - 1) / kZStagedTI, ny);
       VOFP_LAUNCH(KID_ZSOLVE, st,
                   (k_ztab_staged<R, typename Red<R>::TT><<<tgrid, 128, ztab_staged_smem(nz, sizeof(R)), st>>>(

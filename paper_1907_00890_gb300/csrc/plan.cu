@@ -490,19 +490,19 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
     while (ti > 1 && (size_t)3 * ti * nz * rs > 96 * 1024) ti /= 2;
     p->zti32 = ti;
   } else {
-    // factor-table kernel: one system per thread; forward values in shared memory when 64 or 128 threads'
-    // columns fit in 96 KB, otherwise 128 threads keep them in place in the spectrum
-    // factor-table kernels: 0 = the shared-memory staged kernel (grids with few systems), otherwise the
-    // streaming kernel's threads per block (forward values in shared memory when 64 or 128 threads'
-    // columns fit in 96 KB, else kept in place in the spectrum)
-    auto table_ti = [&](size_t elem) {
+    // factor-table kernels: -1 = the segmented tile kernel (FP32 and FP32 pairs whenever a tile fits), 0 = the
+    // shared-memory staged kernel (grids with few systems), otherwise the streaming kernel's threads per
+    // block (forward values in shared memory when 64 or 128 threads' columns fit in 96 KB, else kept in
+    // place in the spectrum)
+    auto table_ti = [&](size_t elem, bool fp64) {
+      if (ztab_use_seg(nz, elem, fp64)) return -1;
       if (ztab_use_staged(nx, ny, nz, elem)) return 0;
       if ((size_t)128 * nz * elem <= 96 * 1024) return 128;
       if ((size_t)64 * nz * elem <= 96 * 1024) return 64;
       return 128;
     };
-    p->zti = table_ti(sizeof(double));
-    p->zti32 = table_ti(rs);
+    p->zti = table_ti(sizeof(double), true);
+    p->zti32 = table_ti(rs, false);
   }
   pp->p = p;
   return VOFP_OK;

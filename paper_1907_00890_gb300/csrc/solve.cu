@@ -74,6 +74,7 @@ void init_kernel_attributes_fp64() {
   allow_smem(k_zsolve<double, double>);
   allow_smem(k_ztab<double, ZF<double>>);
   allow_smem(k_ztab_staged<double, ZF<double>>);
+  allow_smem(k_ztab_seg<double, ZF<double>>);
 }
 
 int grid_blocks(size_t total, int threads) {
@@ -181,7 +182,12 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
   const size_t ysm = 2 * (size_t)(ya.tx / 2) * y_ld(fft_span(ya.fd, ya.blu)) * sizeof(double2);
   if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, k_ypass<double, double2, false><<<ygrid, 256, ysm, st>>>(ya));
   ZArgs za = z_args(pl, stats);
-  if (pl->ztab && pl->zti == 0) {
+  if (pl->ztab && pl->zti == -1) {
+    const dim3 tgrid((nx + kZSegTI - 1) / kZSegTI, ny);
+    VOFP_LAUNCH(KID_ZSOLVE, st,
+                (k_ztab_seg<double, ZF<double>><<<tgrid, 32 * kZSegW, ztab_seg_smem(nz, sizeof(double)), st>>>(
+                    za, ztab_args(pl))));
+  } else if (pl->ztab && pl->zti == 0) {
     const dim3 tgrid((nx + kZStagedTI - 1) / kZStagedTI, ny);
     VOFP_LAUNCH(KID_ZSOLVE, st,
                 (k_ztab_staged<double, ZF<double>><<<tgrid, 128, ztab_staged_smem(nz, sizeof(double)), st>>>(

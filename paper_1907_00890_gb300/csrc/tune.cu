@@ -89,9 +89,12 @@ bool fits(const vofp_plan* p, const Shape& s) {
   if (2 * (size_t)(s.ytx / 2) * vofp::y_ld(sy) * c > lim) return false;
   if (s.zti > 128) return false;  // at most 128 systems per block
   if (!p->ztab && s.zti < 1) return false;
-  if (p->ztab)  // factor-table kernels: 0 = staged (if its tile fits), else whole warps of one system each
-    return s.zti == 0 ? vofp::ztab_staged_smem(p->n[2], f32 ? sizeof(float) : sizeof(double)) <= 200 * 1024
-                      : s.zti >= 32;
+  if (p->ztab) {  // factor-table kernels: -1 = segmented tiles, 0 = staged (if the tile fits), else whole
+                  // warps of one system each
+    const size_t e = f32 ? sizeof(float) : sizeof(double);
+    if (s.zti == -1) return vofp::ztab_seg_smem(p->n[2], e) <= 200 * 1024;
+    return s.zti == 0 ? vofp::ztab_staged_smem(p->n[2], e) <= 200 * 1024 : s.zti >= 32;
+  }
   return (size_t)3 * s.zti * p->n[2] * r <= lim;
 }
 
@@ -135,10 +138,10 @@ extern "C" int vofp_plan_tune(vofp_plan* p) {
   float tbest = time_solve(p, st);
   const int xs[] = {1, 2, 4, 8, 16, 32};
   const int ys[] = {2, 4, 8, 16, 32};
-  const int zs[] = {0, 8, 16, 32, 64, 128};
+  const int zs[] = {-1, 0, 8, 16, 32, 64, 128};
   for (int knob = 0; knob < 3; ++knob) {
     const int* cand = knob == 0 ? xs : (knob == 1 ? ys : zs);
-    const int nc = knob == 0 ? 6 : (knob == 1 ? 5 : 6);
+    const int nc = knob == 0 ? 6 : (knob == 1 ? 5 : 7);
     for (int c = 0; c < nc; ++c) {
       Shape s = best;
       if (knob == 0) s.xpb = cand[c];
