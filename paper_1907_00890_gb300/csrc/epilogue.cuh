@@ -148,8 +148,8 @@ static __global__ void __launch_bounds__(256) k_geometry_ff(GridDev g, const dou
   const int j = blockIdx.y, k = blockIdx.z;
   if (i >= g.nx) return;
   const size_t t = ((size_t)k * g.ny + j) * g.nx + i;
-  const ff gx = ff_split(cval(g, C, i + 1, j, k) - cval(g, C, i - 1, j, k)) * ff_split(0.5 * g.rdx);
-  const ff gy = ff_split(cval(g, C, i, j + 1, k) - cval(g, C, i, j - 1, k)) * ff_split(0.5 * g.rdy);
+  const ff gx = ff_split(cval(g, C, i + 1, j, k) - cval(g, C, i - 1, j, k)) * ff_split(g.hrdx);
+  const ff gy = ff_split(cval(g, C, i, j + 1, k) - cval(g, C, i, j - 1, k)) * ff_split(g.hrdy);
   const ff gz = ff_split(cval(g, C, i, j, k + 1) - cval(g, C, i, j, k - 1)) * ff_split(__ldg(g.rzc + k));
   const ff m2 = gx * gx + gy * gy + gz * gz;
   double sv = 0.0, n0 = 0.0, n1 = 0.0, n2 = 0.0;

@@ -32,6 +32,8 @@ GridDev grid_dev(const vofp_plan* pl) {
   g.rdy = 1.0 / pl->dy;
   g.rdx2 = g.rdx * g.rdx;
   g.rdy2 = g.rdy * g.rdy;
+  g.hrdx = 0.5 * g.rdx;
+  g.hrdy = 0.5 * g.rdy;
   g.dz = pl->dz;
   g.hz = pl->hz;
   g.rdz = pl->rdz;

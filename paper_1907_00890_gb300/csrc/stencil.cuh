@@ -21,6 +21,7 @@ struct GridDev {
   double dx, dy;
   double rdx, rdy;    // 1/dx, 1/dy
   double rdx2, rdy2;  // 1/dx^2, 1/dy^2
+  double hrdx, hrdy;  // 1/(2 dx), 1/(2 dy): central differences
   const double* dz;   // nz widths
   const double* hz;   // nz + 1 centre distances across z faces (ghost distances at the ends)
   const double* rdz;  // 1/dz
@@ -72,8 +73,8 @@ __device__ __forceinline__ double3 grad_c_at(const GridDev& g, const double* __r
                                              int mode) {
   double3 r;
   if (mode == 0) {
-    r.x = (cval(g, C, i + 1, j, k) - cval(g, C, i - 1, j, k)) * (0.5 * g.rdx);
-    r.y = (cval(g, C, i, j + 1, k) - cval(g, C, i, j - 1, k)) * (0.5 * g.rdy);
+    r.x = (cval(g, C, i + 1, j, k) - cval(g, C, i - 1, j, k)) * g.hrdx;
+    r.y = (cval(g, C, i, j + 1, k) - cval(g, C, i, j - 1, k)) * g.hrdy;
     r.z = (cval(g, C, i, j, k + 1) - cval(g, C, i, j, k - 1)) * __ldg(g.rzc + k);
     return r;
   }
