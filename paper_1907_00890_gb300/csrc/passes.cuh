@@ -466,6 +466,26 @@ __global__ void __launch_bounds__(256, 5) k_xinv_f32(XInvArgs a) {
   xinv_block<float, float2>(a, blockIdx.x, smem_raw, red);
 }
 
+// The FP64 passes capped at 64 registers (four 256-thread blocks per SM instead of three): they are bound by
+// the FP64 pipe, which more resident warps keep busier.
+template <int MODE>
+__global__ void __launch_bounds__(256, 4) k_xfwd_f64(XArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  xfwd_block<double, double2, MODE>(a, blockIdx.x, smem_raw, red);
+}
+template <bool INV>
+__global__ void __launch_bounds__(256, 4) k_ypass_f64(YArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ypass_block<double, double2, INV>(a, blockIdx.x, blockIdx.y, smem_raw);
+}
+template <int UNUSED>
+__global__ void __launch_bounds__(256, 4) k_xinv_f64(XInvArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  xinv_block<double, double2>(a, blockIdx.x, smem_raw, red);
+}
+
 typedef void (*XFwdKernel)(XArgs);
 typedef void (*YPassKernel)(YArgs);
 typedef void (*XInvKernel)(XInvArgs);

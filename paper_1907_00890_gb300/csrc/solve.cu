@@ -66,13 +66,13 @@ bool first_use_on_device(int which) {
 
 void init_kernel_attributes_fp64() {
   if (!first_use_on_device(0)) return;
-  allow_smem(k_xfwd<double, double2, RHS_F>);
-  allow_smem(k_xfwd<double, double2, RHS_DIV>);
+  allow_smem(k_xfwd_f64<RHS_F>);
+  allow_smem(k_xfwd_f64<RHS_DIV>);
   allow_smem(k_xfwd<double, double2, RHS_STEFAN>);
   allow_smem(k_xfwd<double, double2, RHS_DIV_STEFAN>);
-  allow_smem(k_ypass<double, double2, false>);
-  allow_smem(k_ypass<double, double2, true>);
-  allow_smem(k_xinv<double, double2>);
+  allow_smem(k_ypass_f64<false>);
+  allow_smem(k_ypass_f64<true>);
+  allow_smem(k_xinv_f64<0>);
   allow_smem(k_zsolve<double, double>);
   allow_smem(k_ztab<double, ZF<double>>);
   allow_smem(k_ztab_staged<double, ZF<double>>);
@@ -156,10 +156,8 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
   const int xgrid = (int)((npairs + xa.pb - 1) / xa.pb);
   const size_t xsm = 2 * (size_t)xa.pb * fft_span(xa.fd, xa.blu) * sizeof(double2);
   switch (mode) {
-    case RHS_F: VOFP_LAUNCH(KID_XFWD, st, k_xfwd<double, double2, RHS_F><<<xgrid, 256, xsm, st>>>(xa)); break;
-    case RHS_DIV:
-      VOFP_LAUNCH(KID_XFWD_DIV, st, k_xfwd<double, double2, RHS_DIV><<<xgrid, 256, xsm, st>>>(xa));
-      break;
+    case RHS_F: VOFP_LAUNCH(KID_XFWD, st, k_xfwd_f64<RHS_F><<<xgrid, 256, xsm, st>>>(xa)); break;
+    case RHS_DIV: VOFP_LAUNCH(KID_XFWD_DIV, st, k_xfwd_f64<RHS_DIV><<<xgrid, 256, xsm, st>>>(xa)); break;
     case RHS_STEFAN:
       VOFP_LAUNCH(KID_XFWD_STEFAN, st, k_xfwd<double, double2, RHS_STEFAN><<<xgrid, 256, xsm, st>>>(xa));
       break;
@@ -182,7 +180,7 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
   ya.S = pl->S;
   const dim3 ygrid((nx + ya.tx - 1) / ya.tx, nz);
   const size_t ysm = 2 * (size_t)(ya.tx / 2) * y_ld(fft_span(ya.fd, ya.blu)) * sizeof(double2);
-  if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, k_ypass<double, double2, false><<<ygrid, 256, ysm, st>>>(ya));
+  if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, k_ypass_f64<false><<<ygrid, 256, ysm, st>>>(ya));
   ZArgs za = z_args(pl, stats);
   if (pl->ztab && pl->zti == -1) {
     const dim3 tgrid((nx + kZSegTI - 1) / kZSegTI, ny);
@@ -205,7 +203,7 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
     const dim3 zgrid((nx + za.ti - 1) / za.ti, ny);
     VOFP_LAUNCH(KID_ZSOLVE, st, (k_zsolve<double, double><<<zgrid, 128, zsm, st>>>(za)));
   }
-  if (ny > 1) VOFP_LAUNCH(KID_YINV, st, k_ypass<double, double2, true><<<ygrid, 256, ysm, st>>>(ya));
+  if (ny > 1) VOFP_LAUNCH(KID_YINV, st, k_ypass_f64<true><<<ygrid, 256, ysm, st>>>(ya));
   XInvArgs xi = {};
   xi.skip_k = -1;
   xi.nx = nx;
@@ -220,7 +218,7 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
   xi.S = pl->S;
   xi.p = pout;
   xi.accumulate = 0;
-  VOFP_LAUNCH(KID_XINV, st, k_xinv<double, double2><<<xgrid, 256, xsm, st>>>(xi));
+  VOFP_LAUNCH(KID_XINV, st, k_xinv_f64<0><<<xgrid, 256, xsm, st>>>(xi));
   return cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
 }
 
