@@ -10,7 +10,8 @@ solver for the second-order finite-difference Poisson equation, §3.2):
 
 * ``mac``        MAC-grid stencils: divergence D, gradient G, Laplacian L = D G, 1-D operator matrices.
 * ``poisson``    the exact solution of L p = f - fbar (zero volume-weighted mean gauge when L is singular),
-                 the projection u <- u - (dt/rho0) G p (Eq. lap_p and the correction that follows it).
+                 the projection u <- u - (dt/rho0) G p (Eq. lap_p and the correction that follows it), and
+                 the same step with the variable-density pressure-splitting terms of Eq. lap_p.
 * ``interface``  |grad C| and n = -grad C/|grad C| (central or Youngs differences), the Stefan potential
                  solve (Eq. ext_div), u1e = u - grad(phi) (Eq. jump_subtr), uG = u1e - (mdot/rho1) n
                  (Eq. int_vel).
@@ -19,10 +20,10 @@ Every public function is pinned by the ``-m "not gpu"`` tests against closed for
 LU solves and exact invariants; no function is "parity unpinned".
 """
 from .mac import Grid, divergence, gradient, apply_laplacian, operator_matrix_1d, face_shape
-from .poisson import poisson_solve, project
+from .poisson import poisson_solve, project, project_variable_density
 from .interface import grad_c, delta_and_normal, stefan_source, extend_liquid_velocity
 
 __all__ = [
     "Grid", "divergence", "gradient", "apply_laplacian", "operator_matrix_1d", "face_shape",
-    "poisson_solve", "project", "grad_c", "delta_and_normal", "stefan_source", "extend_liquid_velocity",
+    "poisson_solve", "project", "project_variable_density", "grad_c", "delta_and_normal", "stefan_source", "extend_liquid_velocity",
 ]

@@ -197,3 +197,50 @@ def project(grid, u, v, w, src=None, dt_over_rho0=1.0):
     gu, gv, gw = gradient(grid, p)
     return (np.asarray(u) - dt_over_rho0 * gu, np.asarray(v) - dt_over_rho0 * gv,
             np.asarray(w) - dt_over_rho0 * gw, p, info)
+
+
+def _face_mean(grid, q, axis):
+    """Face values of a cell field: the mean of the two cells across each face (wrapped on a periodic axis);
+    a bounded axis' end faces take their one adjacent cell."""
+    from .mac import _NP_AXIS
+    ax = _NP_AXIS[axis]
+    n = grid.n[axis]
+    q = np.asarray(q, dtype=np.float64)
+    if grid.bc[axis] == "P":
+        return 0.5 * (q + np.roll(q, 1, axis=ax))
+    first = np.take(q, [0], axis=ax)
+    last = np.take(q, [n - 1], axis=ax)
+    inner = 0.5 * (np.take(q, np.arange(1, n), axis=ax) + np.take(q, np.arange(0, n - 1), axis=ax))
+    return np.concatenate([first, inner, last], axis=ax)
+
+
+def project_variable_density(grid, u, v, w, C, p_n, p_nm1, dt, dt_prev, rho1, rho2, src=None):
+    """Pressure step with the variable-density pressure splitting of §3.2 (Eq. lap_p in full, and the velocity
+    update that follows it), written term by term.
+
+        p_hat   = (1 + dt/dt_prev) p^n - (dt/dt_prev) p^{n-1}
+        rho     = rho1 C + rho2 (1 - C)                                   (Eq. material_prop, H ~ C)
+        rho0    = min(rho1, rho2)
+        L p / rho0 = D[(1/rho0 - 1/rho_f) G p_hat] + (D u* - s) / dt      (Eq. lap_p)
+        u^{n+1} = u* - dt [ (1/rho0) G p + (1/rho_f - 1/rho0) G p_hat ]
+
+    rho_f: rho on the faces, the mean of the two adjacent cells (a bounded axis' end face takes its cell) --
+    a reading; the paper does not say how rho reaches the faces.  ``p_nm1`` None means p_hat = p^n.
+    Returns (u, v, w, p, info).
+    """
+    rho0 = min(rho1, rho2)
+    r = dt / dt_prev
+    p_n = np.asarray(p_n, dtype=np.float64)
+    p_hat = p_n if p_nm1 is None else (1.0 + r) * p_n - r * np.asarray(p_nm1, dtype=np.float64)
+    rho = rho1 * np.asarray(C, dtype=np.float64) + rho2 * (1.0 - np.asarray(C, dtype=np.float64))
+    gh = gradient(grid, p_hat)
+    inv_rf = [1.0 / _face_mean(grid, rho, a) for a in range(3)]
+    flux = [(1.0 / rho0 - inv_rf[a]) * gh[a] for a in range(3)]
+    rhs = divergence(grid, *flux) + divergence(grid, u, v, w) / dt
+    if src is not None:
+        rhs = rhs - np.asarray(src, dtype=np.float64) / dt
+    p, info = poisson_solve(grid, rho0 * rhs)
+    gp = gradient(grid, p)
+    vel = [np.asarray(x, dtype=np.float64) - dt * (gp[a] / rho0 + (inv_rf[a] - 1.0 / rho0) * gh[a])
+           for a, x in enumerate((u, v, w))]
+    return vel[0], vel[1], vel[2], p, info
