@@ -130,6 +130,58 @@ def bench_mixed_step(vofp, c, u0, C, md, st, flush, args, prec=None, max_refine=
     return out
 
 
+def bench_vd(vofp, c, u0, C, md, st, flush, args):
+    """The variable-density pressure step (Eq. lap_p with its pressure-splitting term) on the same 128^3
+    droplet: rho1/rho2 = 100, p^n from a constant-density projection of the same field, p^{n-1} = 0.95 p^n,
+    the Stefan source as src, dt = (dt/rho0) rho0 with rho0 = min(rho1, rho2).  One solve per step."""
+    import torch
+    plan = vofp.Plan(c["n"], c["dx"], c["dy"], c["dz"], c["bc"])
+    rho1, rho2 = c["rho1"], c["rho2"]
+    dt = c["dt_over_rho0"] * min(rho1, rho2)
+    src = plan.stefan_source(C, md, rho1, rho2)
+    uw = [x.clone() for x in u0]
+    pn = plan.project(*uw, src=src, dt_over_rho0=c["dt_over_rho0"])
+    pm = 0.95 * pn
+    u = [x.clone() for x in u0]
+    p = torch.empty_like(pn)
+
+    def step():
+        vofp.vofp_project_vd(plan.handle, u[0], u[1], u[2], src, C, pn, pm, dt, dt, rho1, rho2, p)
+
+    def prep():
+        for a, b in zip(u, u0):
+            a.copy_(b)
+        flush.zero_()
+
+    for _ in range(args.warmup):
+        prep()
+        step()
+    torch.cuda.synchronize()
+    ms, _, trace = timed_steps(vofp, st, prep, step, args.steps)
+    prep()
+    step()
+    torch.cuda.synchronize()
+    n = c["n"]
+    cells = int(np.prod(n))
+    out = {"value": cells / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_solve": ms,
+           "per_kernel_ms": {k: round(v[0] / v[1], 5) for k, v in trace.items()},
+           "workload": "variable-density pressure step %d^3, rho1/rho2 = %g, p^n, p^{n-1} given, FP64"
+                       % (n[0], rho1 / rho2)}
+    if "vd_predict" in trace:
+        tot, cnt = trace["vd_predict"]
+        by = 72 * cells  # u, v, w read and written (48 B per cell), p^n, p^{n-1}, C read once (24 B)
+        hbm, how = peaks()
+        gbs = by / (tot / cnt / 1e3) / 1e9
+        out["roofline_vd_predict"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                      "frac": gbs / hbm, "bytes_per_cell": 72, "peak_source": how}
+    out["_inputs"] = [x.cpu().numpy() for x in u0] + [C.cpu().numpy(), pn.cpu().numpy(), pm.cpu().numpy(),
+                                                       src.cpu().numpy()]
+    out["_outputs"] = [x.cpu().numpy() for x in u] + [p.cpu().numpy()]
+    out["_dt"] = dt
+    plan.close()
+    return out
+
+
 def mixed_bytes_per_cell(rs):
     """Algorithmic HBM bytes per cell of each kernel class of the refinement path (rs: bytes per spectrum
     value, 4 for FP32, 8 for FP32 pairs; fields FP64)."""
@@ -645,6 +697,7 @@ def run_ours(args):
         variants["mixed_step"] = bench_mixed_step(vofp, c, u0, C, md, st, flush, args)
         variants["ff_step"] = bench_mixed_step(vofp, c, u0, C, md, st, flush, args, prec=vofp.FF, max_refine=0)
         variants["ff_step_confirmed"] = bench_mixed_step(vofp, c, u0, C, md, st, flush, args, prec=vofp.FF)
+        variants["variable_density"] = bench_vd(vofp, c, u0, C, md, st, flush, args)
         torch.cuda.empty_cache()
         variants["large_512"] = bench_large(vofp, args)
         torch.cuda.empty_cache()
@@ -686,9 +739,21 @@ def run_ours(args):
                 got = variants[vk].pop("_outputs")
                 errs = [float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)) for a, b in zip(got, ref[:7])]
                 variants[vk]["max_rel_err_vs_oracle"] = max(errs)
+            vd = variants.get("variable_density")
+            if vd is not None:
+                import oracle
+                uu, vv, ww, Cc, pn, pm, src = vd["_inputs"]
+                g = oracle.Grid(*c["n"], c["dx"], c["dy"], c["dz"], c["bc"])
+                r = oracle.project_variable_density(g, uu, vv, ww, Cc, pn, pm, vd["_dt"], vd["_dt"], c["rho1"],
+                                                    c["rho2"], src=src)
+                got = vd["_outputs"]
+                vd["max_rel_err_vs_oracle"] = max(
+                    float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+                    for a, b in zip(got, (r[0], r[1], r[2], r[3])))
         if variants:
-            for vk in ("mixed_step", "ff_step", "ff_step_confirmed"):
-                variants.get(vk, {}).pop("_outputs", None)
+            for vk in ("mixed_step", "ff_step", "ff_step_confirmed", "variable_density"):
+                for key in ("_outputs", "_inputs", "_dt"):
+                    variants.get(vk, {}).pop(key, None)
             line["variants"] = variants
         print(json.dumps(line), flush=True)
     plan.close()

@@ -132,6 +132,25 @@ int vofp_project(vofp_plan* plan, double* u, double* v, double* w, const double*
                  double* p, void* stream, vofp_info* info);
 
 /*
+ * Pressure step with the variable-density pressure splitting of §3.2 (Eq. lap_p in full and the velocity
+ * update after it):
+ *   p_hat = (1 + dt/dt_prev) p^n - (dt/dt_prev) p^{n-1}   (p^n alone when p_nm1 is NULL),
+ *   rho = rho1 C + rho2 (1 - C)  (Eq. material_prop),  rho0 = min(rho1, rho2),
+ *   L p / rho0 = D[(1/rho0 - 1/rho_f) G p_hat] + (D u* - src) / dt,
+ *   u = u* - dt [ (1/rho0) G p + (1/rho_f - 1/rho0) G p_hat ],
+ * with rho_f on a face the mean of rho over its two cells (its one cell at a bounded end; no flux through an
+ * N face).  Computed as one face pass u** = u* - dt (1/rho_f - 1/rho0) G p_hat followed by vofp_project(u**,
+ * src, dt/rho0, p): the constant-coefficient solve the splitting exists for.
+ * u, v, w: device face arrays, u* in, u^{n+1} out.  src: device cell array or NULL.  C, p_n: device cell
+ * arrays (required); p_nm1: device cell array or NULL.  dt > 0; dt_prev > 0 when p_nm1 is given; rho1, rho2 > 0.
+ * p: device cell array or NULL (p^{n+1}; may be the p_n buffer).  Errors: INVALID_ARG, CUDA, NONFINITE (only
+ * with info).
+ */
+int vofp_project_vd(vofp_plan* plan, double* u, double* v, double* w, const double* src, const double* C,
+                    const double* p_n, const double* p_nm1, double dt, double dt_prev, double rho1, double rho2,
+                    double* p, void* stream, vofp_info* info);
+
+/*
  * Liquid-velocity extension and interface velocity (§3.6):
  *   s = mdot (1/rho2 - 1/rho1) |grad C|  (Eq. ext_div),  L phi = s - sbar,
  *   u1e = u - G phi  (Eq. jump_subtr),
@@ -143,6 +162,17 @@ int vofp_project(vofp_plan* plan, double* u, double* v, double* w, const double*
  * cell array or NULL.  Errors: INVALID_ARG, CUDA, NONFINITE (only with info).
  */
 int vofp_extend_liquid_velocity(vofp_plan* plan, const double* u, const double* v, const double* w,
+                                const double* C, const double* mdot, double rho1, double rho2, double* ue,
+                                double* ve, double* we, double* ug, double* vg, double* wg, double* phi,
+                                void* stream, vofp_info* info);
+
+/*
+ * The boiling variant (Appendix A): the interface velocity from a divergence-free extension of the vapour
+ * (phase 2) velocity.  Exchanging the phases in §3.6 leaves the Stefan potential phi and u - G phi unchanged,
+ * so u2e = u - G phi as in vofp_extend_liquid_velocity and uG = u2e - (mdot_f / rho2) n_f (Eq. rankine on the
+ * vapour side; n still points into phase 2).  Arguments, outputs and errors as vofp_extend_liquid_velocity.
+ */
+int vofp_extend_vapour_velocity(vofp_plan* plan, const double* u, const double* v, const double* w,
                                 const double* C, const double* mdot, double rho1, double rho2, double* ue,
                                 double* ve, double* we, double* ug, double* vg, double* wg, double* phi,
                                 void* stream, vofp_info* info);

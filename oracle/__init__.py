@@ -14,16 +14,17 @@ solver for the second-order finite-difference Poisson equation, §3.2):
                  the same step with the variable-density pressure-splitting terms of Eq. lap_p.
 * ``interface``  |grad C| and n = -grad C/|grad C| (central or Youngs differences), the Stefan potential
                  solve (Eq. ext_div), u1e = u - grad(phi) (Eq. jump_subtr), uG = u1e - (mdot/rho1) n
-                 (Eq. int_vel).
+                 (Eq. int_vel); the boiling variant with the vapour-velocity extension (Appendix A).
 
 Every public function is pinned by the ``-m "not gpu"`` tests against closed forms, brute-force dense
 LU solves and exact invariants; no function is "parity unpinned".
 """
 from .mac import Grid, divergence, gradient, apply_laplacian, operator_matrix_1d, face_shape
 from .poisson import poisson_solve, project, project_variable_density
-from .interface import grad_c, delta_and_normal, stefan_source, extend_liquid_velocity
+from .interface import grad_c, delta_and_normal, stefan_source, extend_liquid_velocity, extend_vapour_velocity
 
 __all__ = [
     "Grid", "divergence", "gradient", "apply_laplacian", "operator_matrix_1d", "face_shape",
-    "poisson_solve", "project", "project_variable_density", "grad_c", "delta_and_normal", "stefan_source", "extend_liquid_velocity",
+    "poisson_solve", "project", "project_variable_density", "grad_c", "delta_and_normal", "stefan_source",
+    "extend_liquid_velocity", "extend_vapour_velocity",
 ]

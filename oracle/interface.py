@@ -117,3 +117,22 @@ def extend_liquid_velocity(grid, u, v, w, C, mdot, rho1, rho2, mode=0, clip=1e-8
     mdot = np.broadcast_to(np.asarray(mdot, dtype=np.float64), grid.shape)
     ug = tuple(ue[a] - face_average(grid, mdot, a) / rho1 * face_average(grid, n[a], a) for a in range(3))
     return ue + ug + (phi, info)
+
+
+def extend_vapour_velocity(grid, u, v, w, C, mdot, rho1, rho2, mode=0, clip=1e-8):
+    """The boiling variant (Appendix A): the interface velocity from a divergence-free extension of the vapour
+    (phase 2) velocity instead of the liquid's.
+
+    Reading: exchanging the phases in §3.6 (C -> 1 - C, n -> -n, mdot -> -mdot, rho1 <-> rho2) leaves the
+    Stefan source of Eq. ext_div, hence phi and u - grad(phi) of Eq. jump_subtr, unchanged; Eq. rankine
+    written for the vapour side then gives uG = u2e - (mdot / rho2) n.  Returns (u2e, v2e, w2e, uG, vG, wG, phi,
+    info).
+    """
+    s = stefan_source(grid, C, mdot, rho1, rho2, mode)
+    phi, info = poisson_solve(grid, s)
+    g = gradient(grid, phi)
+    ue = tuple(np.asarray(q, dtype=np.float64) - gq for q, gq in zip((u, v, w), g))
+    _, n = delta_and_normal(grid, C, mode, clip)
+    mdot = np.broadcast_to(np.asarray(mdot, dtype=np.float64), grid.shape)
+    ug = tuple(ue[a] - face_average(grid, mdot, a) / rho2 * face_average(grid, n[a], a) for a in range(3))
+    return ue + ug + (phi, info)

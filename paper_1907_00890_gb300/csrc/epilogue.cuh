@@ -237,4 +237,87 @@ static __global__ void __launch_bounds__(256) k_extend_epi(ExtArgs a) {
   }
 }
 
+// Variable-density pressure splitting (§3.2, Eq. lap_p and the update after it): u* -= dt (1/rho_f - 1/rho0)
+// G p_hat on every face, p_hat = (1 + r) p^n - r p^{n-1} (p^n alone when pm is NULL), rho_f = rho2 + (rho1 -
+// rho2) C_f with C_f the mean of C over the face's two cells (its one cell at a bounded end); N faces carry no
+// flux.  The constant-coefficient projection of the result with dt/rho0 completes the step.
+struct VdArgs {
+  GridDev g;
+  const double* pn;
+  const double* pm;
+  double opr, r;        // 1 + dt/dt_prev, dt/dt_prev
+  const double* C;
+  double half_drho;     // (rho1 - rho2) / 2
+  double rho2;
+  double dt;
+  double dt_over_rho0;
+  double* u;
+  double* v;
+  double* w;
+};
+// The difference of a cell field across face f of a line (the face_grad rules, without the distance):
+// returns -1 on an N face, 0 inside or on a periodic wrap, 1 / 2 on the low / high D face, where d is the
+// adjacent value with the ghost's sign and the distance is half a cell.
+__device__ __forceinline__ int line_diff(const double* __restrict__ p, size_t base, size_t st, int n, int bc, int f,
+                                         double& d) {
+  if (bc == VOFP_BC_P) {
+    const int fm = f == 0 ? n - 1 : f - 1;
+    d = __ldg(p + base + f * st) - __ldg(p + base + fm * st);
+    return 0;
+  }
+  if (f == 0) {
+    if (bc == VOFP_BC_NN || bc == VOFP_BC_ND) return -1;
+    d = __ldg(p + base);
+    return 1;
+  }
+  if (f == n) {
+    if (bc == VOFP_BC_NN || bc == VOFP_BC_DN) return -1;
+    d = -__ldg(p + base + (size_t)(n - 1) * st);
+    return 2;
+  }
+  d = __ldg(p + base + f * st) - __ldg(p + base + (size_t)(f - 1) * st);
+  return 0;
+}
+__device__ __forceinline__ int face_diff_axis(const GridDev& g, const double* __restrict__ p, int axis, int i, int j,
+                                              int k, double& d) {
+  const size_t plane = (size_t)g.nx * g.ny;
+  if (axis == 0) return line_diff(p, (size_t)k * plane + (size_t)j * g.nx, 1, g.nx, g.bcx, i, d);
+  if (axis == 1) return line_diff(p, (size_t)k * plane + i, g.nx, g.ny, g.bcy, j, d);
+  return line_diff(p, (size_t)j * g.nx + i, plane, g.nz, g.bcz, k, d);
+}
+// 1 / x for a positive normal x: an FP32 reciprocal of its leading bits as the seed (integer-pipe split and
+// join), then two Newton steps y <- y + y (1 - x y) in FP64 (quadratic convergence: 2^-23 -> 2^-46 -> below
+// FP64 rounding), four FP64 multiply-adds against an FP64 division's longer sequence on this GPU.
+__device__ __forceinline__ double recip_newton(double x) {
+  double y = f64_of_bits(__frcp_rn(f32_lead_bits(x)));
+  y = fma(y, fma(-x, y, 1.0), y);
+  return fma(y, fma(-x, y, 1.0), y);
+}
+static __global__ void __launch_bounds__(256) k_vd_predict(VdArgs a) {
+  const GridDev& g = a.g;
+  int axis, i, j, k;
+  size_t off;
+  if (!face_coord(g, axis, i, j, k, off)) return;
+  double d;
+  const int e = face_diff_axis(g, a.pn, axis, i, j, k, d);
+  if (e < 0) return;  // N face: no flux
+  if (a.pm) {
+    double dm;
+    face_diff_axis(g, a.pm, axis, i, j, k, dm);
+    d = fma(a.opr, d, -a.r * dm);  // the difference of p_hat
+  }
+  double h;  // 1 / distance between the values differenced
+  if (axis == 0)
+    h = g.rdx;
+  else if (axis == 1)
+    h = g.rdy;
+  else
+    h = e == 0 ? __ldg(g.rhz + k) : __ldg(g.rdz + (e == 1 ? 0 : g.nz - 1));
+  if (e > 0) h = h + h;
+  const double rho_f = fma(a.half_drho, face_sum_arr(g, a.C, axis, i, j, k), a.rho2);
+  const double c = h * fma(a.dt, recip_newton(rho_f), -a.dt_over_rho0);  // dt (1/rho_f - 1/rho0) / distance
+  double* F = axis == 0 ? a.u : (axis == 1 ? a.v : a.w);
+  F[off] = fma(-c, d, F[off]);
+}
+
 }  // namespace vofp

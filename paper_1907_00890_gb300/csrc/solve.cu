@@ -299,8 +299,10 @@ static int project_common(vofp_plan* pl, int mode, XArgs& xa, double* u, double*
 }
 
 // Extension solve on the source already in G[0:cells], normals in G[cells:4 cells]; runs the epilogue.
+// rho_ext: the density of the phase whose velocity is extended (rho1, the liquid, for §3.6; rho2, the vapour,
+// for the boiling variant of Appendix A), which divides mdot in the interface velocity.
 static int extend_common(vofp_plan* pl, const double* u, const double* v, const double* w, const double* mdot,
-                         double rho1, double* ue, double* ve, double* we, double* ug, double* vg, double* wg,
+                         double rho_ext, double* ue, double* ve, double* we, double* ug, double* vg, double* wg,
                          double* phi, cudaStream_t st, vofp_info* info) {
   int s = begin_info(pl, st, info);
   if (s) return s;
@@ -326,7 +328,7 @@ static int extend_common(vofp_plan* pl, const double* u, const double* v, const 
   ea.n[0] = pl->G + cells;
   ea.n[1] = pl->G + 2 * cells;
   ea.n[2] = pl->G + 3 * cells;
-  ea.quarter_inv_rho1 = 0.25 / rho1;
+  ea.quarter_inv_rho1 = 0.25 / rho_ext;
   ea.ue = ue;
   ea.ve = ve;
   ea.we = we;
@@ -382,6 +384,33 @@ extern "C" int vofp_project(vofp_plan* pl, double* u, double* v, double* w, cons
   return project_common(pl, RHS_DIV, xa, u, v, w, dt_over_rho0, p, (cudaStream_t)stream, info);
 }
 
+extern "C" int vofp_project_vd(vofp_plan* pl, double* u, double* v, double* w, const double* src, const double* C,
+                               const double* p_n, const double* p_nm1, double dt, double dt_prev, double rho1,
+                               double rho2, double* p, void* stream, vofp_info* info) {
+  if (!pl || !u || !v || !w || !C || !p_n || !(dt > 0) || !std::isfinite(dt)) return VOFP_ERR_INVALID_ARG;
+  if (p_nm1 && (!(dt_prev > 0) || !std::isfinite(dt_prev))) return VOFP_ERR_INVALID_ARG;
+  if (!good_density(rho1) || !good_density(rho2)) return VOFP_ERR_INVALID_ARG;
+  const double rho0 = rho1 < rho2 ? rho1 : rho2;
+  cudaStream_t st = (cudaStream_t)stream;
+  VdArgs va;
+  va.g = grid_dev(pl);
+  va.pn = p_n;
+  va.pm = p_nm1;
+  va.r = p_nm1 ? dt / dt_prev : 0.0;
+  va.opr = 1.0 + va.r;
+  va.C = C;
+  va.half_drho = 0.5 * (rho1 - rho2);
+  va.rho2 = rho2;
+  va.dt = dt;
+  va.dt_over_rho0 = dt / rho0;
+  va.u = u;
+  va.v = v;
+  va.w = w;
+  VOFP_LAUNCH(KID_VD, st, k_vd_predict<<<face_grid(va.g, 256), 256, 0, st>>>(va));
+  if (cudaGetLastError() != cudaSuccess) return VOFP_ERR_CUDA;
+  return vofp_project(pl, u, v, w, src, dt / rho0, p, stream, info);
+}
+
 extern "C" int vofp_project_stefan(vofp_plan* pl, double* u, double* v, double* w, const double* C,
                                    const double* mdot, double rho1, double rho2, double dt_over_rho0, double* p,
                                    void* stream, vofp_info* info) {
@@ -412,6 +441,20 @@ extern "C" int vofp_extend_liquid_velocity(vofp_plan* pl, const double* u, const
   const int gs = launch_geometry(pl, C, mdot, 1.0 / rho2 - 1.0 / rho1, ug != nullptr, nullptr, st);
   if (gs) return gs;
   return extend_common(pl, u, v, w, mdot, rho1, ue, ve, we, ug, vg, wg, phi, st, info);
+}
+
+extern "C" int vofp_extend_vapour_velocity(vofp_plan* pl, const double* u, const double* v, const double* w,
+                                           const double* C, const double* mdot, double rho1, double rho2,
+                                           double* ue, double* ve, double* we, double* ug, double* vg, double* wg,
+                                           double* phi, void* stream, vofp_info* info) {
+  if (!pl || !u || !v || !w || !C || !mdot || !ue || !ve || !we) return VOFP_ERR_INVALID_ARG;
+  if (!good_density(rho1) || !good_density(rho2)) return VOFP_ERR_INVALID_ARG;
+  const int nug = (ug != nullptr) + (vg != nullptr) + (wg != nullptr);
+  if (nug != 0 && nug != 3) return VOFP_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int gs = launch_geometry(pl, C, mdot, 1.0 / rho2 - 1.0 / rho1, ug != nullptr, nullptr, st);
+  if (gs) return gs;
+  return extend_common(pl, u, v, w, mdot, rho2, ue, ve, we, ug, vg, wg, phi, st, info);
 }
 
 extern "C" int vofp_project_extend(vofp_plan* pl, double* u, double* v, double* w, const double* C,

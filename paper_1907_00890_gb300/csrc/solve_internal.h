@@ -29,6 +29,7 @@ enum KernelId {
   KID_ZLOW,     // refinement plans: the low-eigenvalue z systems in FP64
   KID_GAUGE,    // gauge restoration of p
   KID_RESNORM,  // reporting residual norm
+  KID_VD,       // variable-density splitting: u* -= dt (1/rho_f - 1/rho0) G p_hat
   KID_COUNT
 };
 

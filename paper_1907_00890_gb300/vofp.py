@@ -49,10 +49,15 @@ _lib.vofp_project.restype = _I
 _lib.vofp_extend_liquid_velocity.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P,
                                              ctypes.POINTER(vofp_info)]
 _lib.vofp_extend_liquid_velocity.restype = _I
+_lib.vofp_extend_vapour_velocity.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P,
+                                             ctypes.POINTER(vofp_info)]
+_lib.vofp_extend_vapour_velocity.restype = _I
 _lib.vofp_stefan_source.argtypes = [_P, _P, _P, _D, _D, _P, _P]
 _lib.vofp_stefan_source.restype = _I
 _lib.vofp_project_stefan.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _D, _P, _P, ctypes.POINTER(vofp_info)]
 _lib.vofp_project_stefan.restype = _I
+_lib.vofp_project_vd.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P, ctypes.POINTER(vofp_info)]
+_lib.vofp_project_vd.restype = _I
 _lib.vofp_trace_enable.argtypes = [_I]
 _lib.vofp_trace_enable.restype = _I
 _lib.vofp_trace_collect.argtypes = [ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_ulonglong), _I]
@@ -355,6 +360,16 @@ def vofp_project(plan, u, v, w, src, dt_over_rho0, p, stream=None, info=False):
     return (s, _info_dict(inf)) if info else s
 
 
+def vofp_project_vd(plan, u, v, w, src, C, p_n, p_nm1, dt, dt_prev, rho1, rho2, p, stream=None, info=False):
+    inf = vofp_info() if info else None
+    s = _check(_lib.vofp_project_vd(plan, _ptr(u, name="u"), _ptr(v, name="v"), _ptr(w, name="w"),
+                                    _ptr(src, name="src"), _ptr(C, name="C"), _ptr(p_n, name="p_n"),
+                                    _ptr(p_nm1, name="p_nm1"), float(dt), float(dt_prev), float(rho1), float(rho2),
+                                    _ptr(p, name="p"), _stream(stream), ctypes.byref(inf) if info else None),
+               "vofp_project_vd")
+    return (s, _info_dict(inf)) if info else s
+
+
 def vofp_stefan_source(plan, C, mdot, rho1, rho2, s, stream=None):
     return _check(_lib.vofp_stefan_source(plan, _ptr(C, name="C"), _ptr(mdot, name="mdot"), float(rho1),
                                           float(rho2), _ptr(s, name="s"), _stream(stream)), "vofp_stefan_source")
@@ -377,6 +392,17 @@ def vofp_extend_liquid_velocity(plan, u, v, w, C, mdot, rho1, rho2, ue, ve, we, 
         _ptr(mdot, name="mdot"), float(rho1), float(rho2), _ptr(ue, name="ue"), _ptr(ve, name="ve"),
         _ptr(we, name="we"), _ptr(ug, name="ug"), _ptr(vg, name="vg"), _ptr(wg, name="wg"), _ptr(phi, name="phi"),
         _stream(stream), ctypes.byref(inf) if info else None), "vofp_extend_liquid_velocity")
+    return (s, _info_dict(inf)) if info else s
+
+
+def vofp_extend_vapour_velocity(plan, u, v, w, C, mdot, rho1, rho2, ue, ve, we, ug=None, vg=None, wg=None,
+                                phi=None, stream=None, info=False):
+    inf = vofp_info() if info else None
+    s = _check(_lib.vofp_extend_vapour_velocity(
+        plan, _ptr(u, name="u"), _ptr(v, name="v"), _ptr(w, name="w"), _ptr(C, name="C"),
+        _ptr(mdot, name="mdot"), float(rho1), float(rho2), _ptr(ue, name="ue"), _ptr(ve, name="ve"),
+        _ptr(we, name="we"), _ptr(ug, name="ug"), _ptr(vg, name="vg"), _ptr(wg, name="wg"), _ptr(phi, name="phi"),
+        _stream(stream), ctypes.byref(inf) if info else None), "vofp_extend_vapour_velocity")
     return (s, _info_dict(inf)) if info else s
 
 
@@ -420,6 +446,15 @@ class Plan:
         r = vofp_project(self.handle, u, v, w, src, dt_over_rho0, p, stream, info)
         return (p, r[1]) if info else p
 
+    def project_vd(self, u, v, w, C, p_n, p_nm1, dt, dt_prev, rho1, rho2, src=None, p=None, stream=None,
+                   info=False):
+        """Variable-density pressure step (u, v, w in place); returns p^{n+1}."""
+        import torch
+        if p is None:
+            p = torch.empty(self.cell_shape, dtype=torch.float64, device=u.device)
+        r = vofp_project_vd(self.handle, u, v, w, src, C, p_n, p_nm1, dt, dt_prev, rho1, rho2, p, stream, info)
+        return (p, r[1]) if info else p
+
     def stefan_source(self, C, mdot, rho1, rho2, stream=None):
         import torch
         s = torch.empty_like(C)
@@ -434,7 +469,9 @@ class Plan:
         r = vofp_project_stefan(self.handle, u, v, w, C, mdot, rho1, rho2, dt_over_rho0, p, stream, info)
         return (p, r[1]) if info else p
 
-    def extend(self, u, v, w, C, mdot, rho1, rho2, want_ug=True, want_phi=True, stream=None, info=False):
+    def extend(self, u, v, w, C, mdot, rho1, rho2, want_ug=True, want_phi=True, stream=None, info=False,
+               vapour=False):
+        """Liquid-velocity extension (§3.6); vapour=True: the boiling variant (Appendix A)."""
         import torch
         ue, ve, we = torch.empty_like(u), torch.empty_like(v), torch.empty_like(w)
         ug = vg = wg = phi = None
@@ -442,8 +479,8 @@ class Plan:
             ug, vg, wg = torch.empty_like(u), torch.empty_like(v), torch.empty_like(w)
         if want_phi:
             phi = torch.empty(self.cell_shape, dtype=torch.float64, device=u.device)
-        r = vofp_extend_liquid_velocity(self.handle, u, v, w, C, mdot, rho1, rho2, ue, ve, we, ug, vg, wg, phi,
-                                        stream, info)
+        fn = vofp_extend_vapour_velocity if vapour else vofp_extend_liquid_velocity
+        r = fn(self.handle, u, v, w, C, mdot, rho1, rho2, ue, ve, we, ug, vg, wg, phi, stream, info)
         out = (ue, ve, we, ug, vg, wg, phi)
         return (out, r[1]) if info else out
 

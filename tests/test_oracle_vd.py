@@ -9,6 +9,12 @@ the velocity update after it) against facts the equations fix, on the CPU:
   step returns p = P and u = u_df exactly (the splitting is exact at a steady pressure).  p^n and p^{n-1} are
   chosen so that the second-order extrapolation with dt / dt_prev gives P (a wrong extrapolation, sign, face
   density or mixture rule breaks it).  The face density here is written independently of the oracle's.
+
+And of the boiling variant (Appendix A, the interface velocity from the vapour-velocity extension):
+
+* exchanging the phases (C -> 1 - C, mdot -> -mdot, rho1 <-> rho2) turns it into the liquid extension of
+  §3.6, pinned in test_oracle_pins.py;
+* a pure Stefan flow (a static bubble) extends to zero and gives uG = -(mdot_f / rho2) n_f.
 """
 import numpy as np
 import pytest
@@ -109,3 +115,41 @@ def test_steady_pressure_is_a_fixed_point(n, bc, rho1, rho2):
     assert rel(p, P) < 1e-10
     for x, y in zip((uo, vo, wo), udf):
         assert np.abs(x - y).max() < 1e-10 * max(np.abs(y).max(), 1.0)
+
+
+# ---- the boiling variant (Appendix A): vapour-velocity extension ----------------------------------------
+
+@pytest.mark.parametrize("n,bc", CASES[:3])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_vapour_extension_is_the_phase_exchanged_liquid_extension(n, bc, mode):
+    """Exchanging the phases (C -> 1 - C, mdot -> -mdot, rho1 <-> rho2) turns the vapour extension into the
+    liquid one of §3.6, whose pins live in test_oracle_pins.py."""
+    g = grid_for(n, bc, 4)
+    C, _ = synth.droplet(n, bc, 401)
+    mdot = 1.0 + 0.3 * synth.rng(402).standard_normal(g.shape)
+    u, v, w = synth.random_velocity(n, bc, 403)
+    a = oracle.extend_vapour_velocity(g, u, v, w, C, mdot, 1000.0, 1.5, mode=mode)
+    b = oracle.extend_liquid_velocity(g, u, v, w, 1.0 - C, -mdot, 1.5, 1000.0, mode=mode)
+    for x, y in zip(a[:7], b[:7]):
+        assert np.abs(x - y).max() <= 1e-12 * max(np.abs(y).max(), 1.0)
+
+
+@pytest.mark.parametrize("n,bc", CASES[:3])
+def test_vapour_extension_of_a_pure_stefan_flow(n, bc):
+    """u = grad(phi) (the Stefan flow alone, a static bubble): u2e = 0 and uG = -(mdot_f / rho2) n_f."""
+    g = grid_for(n, bc, 5)
+    C, _ = synth.droplet(n, bc, 501)
+    mdot = np.full(g.shape, 0.7)
+    rho1, rho2 = 1000.0, 1.5
+    s = oracle.stefan_source(g, C, mdot, rho1, rho2)
+    phi, _ = oracle.poisson_solve(g, s)
+    u = oracle.gradient(g, phi)
+    out = oracle.extend_vapour_velocity(g, *u, C, mdot, rho1, rho2)
+    scale = max(np.abs(x).max() for x in u)
+    for a in range(3):
+        assert np.abs(out[a]).max() < 1e-12 * scale
+    _, nrm = oracle.delta_and_normal(g, C)
+    from oracle.interface import face_average
+    for a in range(3):
+        want = -0.7 / rho2 * face_average(g, nrm[a], a)
+        assert np.abs(out[3 + a] - want).max() < 1e-12 * max(scale, 1.0)
