@@ -8,7 +8,10 @@
  *     constant-density part) and the velocity correction that follows it;
  *   - the Stefan-flow potential lap(phi) = mdot (1/rho2 - 1/rho1) |grad C| (§3.6, Eq. ext_div), the
  *     divergence-free liquid extension u1e = u - grad(phi) (Eq. jump_subtr) and the interface velocity
- *     uG = u1e - (mdot/rho1) n (Eq. int_vel).
+ *     uG = u1e - (mdot/rho1) n (Eq. int_vel);
+ *   - the full variable-density pressure step of Eq. lap_p (the pressure-splitting term with the
+ *     extrapolated pressure, vofp_project_vd) and the boiling variant of the interface velocity (Appendix A,
+ *     vofp_extend_vapour_velocity).
  *
  * Both are solved exactly (direct solver, §3.2) on a uniform-in-x,y MAC grid: real-to-real transforms in x
  * and y (periodic: DFT; Neumann: DCT-II; Dirichlet: DST-II), one tridiagonal system in z per (x, y)
