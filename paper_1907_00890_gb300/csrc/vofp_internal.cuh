@@ -341,26 +341,63 @@ __device__ __forceinline__ C cconj(C a) {
 // (n entries), then Bh = FFT_bm(h) / bm with h_m = conj(w_|m|) placed cyclically (bm entries), then the
 // bm-point twiddles (bm entries) -- or NULL.  With them, X_k = w_k * y_k, y = the cyclic convolution of
 // (x_j w_j) with h, computed as conj(FFT(conj(FFT(x w) * Bh))).  Lines need a stride ld >= bm then.
-// FP64 transforms read their twiddles from a shared-memory copy of the n-point table (lengths up to
-// kTwSmem): the scattered per-butterfly twiddle loads then go to shared memory instead of queueing on the
-// texture/L1 path, the top stall of these FP64-pipe-bound passes (measured 9-10% faster per pass at 128^3).
+// FP64 transforms read their twiddles from a shared-memory copy of the table of the stages that run (the
+// n-point table, or the bm-point one of a Bluestein length; up to kTwSmem points): the scattered
+// per-butterfly twiddle loads then go to shared memory instead of queueing on the texture/L1 path, the top
+// stall of these FP64-pipe-bound passes (measured 6-10% faster per pass at 128^3).
 // The reduced-precision passes keep the table in global memory (no gain there, and the copy's registers cost
 // the FP32-pair x pass a block per SM).
 constexpr int kTwSmem = 1024;
+// The Bluestein convolution of fft_smem with the bm-point twiddles twM.
+template <typename C>
+__device__ __forceinline__ C* blu_conv(C* a, C* b, int batch, const FftDesc& fd, const C* __restrict__ blu,
+                                       const C* __restrict__ twM, int ld) {
+  const int n = fd.n, M = fd.bm;
+  const C* __restrict__ w = blu;
+  const C* __restrict__ Bh = blu + n;
+  for (int t = threadIdx.x; t < batch * M; t += blockDim.x) {
+    const int bi = t / M, j = t - bi * M;
+    C* p = a + bi * ld + j;
+    *p = j < n ? cmul(*p, w[j]) : cmk<C>((decltype(C::x))0, (decltype(C::x))0);
+  }
+  __syncthreads();
+  C* r = fft_stages(a, b, batch, M, fd.bst, fd.bradix, twM, ld);
+  C* o = r == a ? b : a;
+  for (int t = threadIdx.x; t < batch * M; t += blockDim.x) {
+    const int bi = t / M, j = t - bi * M;
+    C* p = r + bi * ld + j;
+    *p = cconj(cmul(*p, Bh[j]));
+  }
+  __syncthreads();
+  C* r2 = fft_stages(r, o, batch, M, fd.bst, fd.bradix, twM, ld);
+  for (int t = threadIdx.x; t < batch * n; t += blockDim.x) {
+    const int bi = t / n, k = t - bi * n;
+    C* p = r2 + bi * ld + k;
+    *p = cmul(cconj(*p), w[k]);
+  }
+  __syncthreads();
+  return r2;
+}
+
 template <typename C>
 __device__ C* fft_smem(C* a, C* b, int batch, const FftDesc& fd, const C* __restrict__ tw, int ld,
                        const C* __restrict__ blu) {
-  if (!blu || fd.bm == 0) {
-    if constexpr (std::is_same<C, double2>::value) {
-      if (fd.n <= kTwSmem) {
-        __shared__ C tws[kTwSmem];
-        for (int t = threadIdx.x; t < fd.n; t += blockDim.x) tws[t] = tw[t];
-        __syncthreads();
-        return fft_stages(a, b, batch, fd.n, fd.nst, fd.radix, (const C*)tws, ld);
-      }
+  const bool bl = blu && fd.bm != 0;
+  if constexpr (std::is_same<C, double2>::value) {
+    const int m = bl ? fd.bm : fd.n;
+    if (m <= kTwSmem) {
+      // the shared copy is passed on as a shared-memory pointer in both branches (a pointer that may be
+      // either would compile to generic loads, which queue on the same path as global ones)
+      __shared__ C tws[kTwSmem];
+      const C* src = bl ? blu + fd.n + fd.bm : tw;
+      for (int t = threadIdx.x; t < m; t += blockDim.x) tws[t] = src[t];
+      __syncthreads();
+      if (bl) return blu_conv(a, b, batch, fd, blu, (const C*)tws, ld);
+      return fft_stages(a, b, batch, fd.n, fd.nst, fd.radix, (const C*)tws, ld);
     }
-    return fft_stages(a, b, batch, fd.n, fd.nst, fd.radix, tw, ld);
   }
+  // (the reduced-precision types keep this code shape: their register allocation is sensitive to it)
+  if (!bl) return fft_stages(a, b, batch, fd.n, fd.nst, fd.radix, tw, ld);
   const int n = fd.n, M = fd.bm;
   const C* __restrict__ w = blu;
   const C* __restrict__ Bh = blu + n;
