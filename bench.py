@@ -50,8 +50,9 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "ff"],
                     help="arithmetic of the main step (the 128^3 droplet step is specified in FP64)")
-    ap.add_argument("--only", choices=["large", "batched", "batched_ff", "served"], default=None,
-                    help="run one variant alone and print its JSON (for profiling captures)")
+    ap.add_argument("--only", choices=["large", "batched", "batched_ff", "served", "vd"], default=None,
+                    help="run one variant alone and print its JSON (for profiling captures); vd: the "
+                         "variable-density pressure step on the droplet")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     return ap.parse_args()
@@ -854,6 +855,11 @@ def roofline_from_trace(trace, n, workload=None):
     return r
 
 
+def synth_droplet(n):
+    from paper_1907_00890_gb300 import synth
+    return synth.config_droplet(n)
+
+
 def run_only(args):
     from paper_1907_00890_gb300 import build
     build.build()
@@ -864,6 +870,16 @@ def run_only(args):
         r = bench_batched(vofp, args)
     elif args.only == "batched_ff":
         r = bench_batched(vofp, args, prec=vofp.FF)
+    elif args.only == "vd":
+        import torch
+        c = synth_droplet(args.n)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)  # noqa: E731
+        u0 = [T(a) for a in (c["u"], c["v"], c["w"])]
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        r = bench_vd(vofp, c, u0, T(c["C"]), T(c["mdot"]), torch.cuda.current_stream(), flush, args)
+        for key in ("_inputs", "_outputs", "_dt"):
+            r.pop(key, None)
     else:
         r = bench_served(vofp, args)
     print(json.dumps({"only": args.only, "result": r}))
