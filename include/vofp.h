@@ -14,7 +14,8 @@
  *     vofp_extend_vapour_velocity).
  *
  * Both are solved exactly (direct solver, §3.2) on a uniform-in-x,y MAC grid: real-to-real transforms in x
- * and y (periodic: DFT; Neumann: DCT-II; Dirichlet: DST-II), one tridiagonal system in z per (x, y)
+ * and y (periodic: DFT; Neumann: DCT-II; Dirichlet: DST-II; mixed: DCT-IV / DST-IV), one tridiagonal system
+ * in z per (x, y)
  * wavenumber pair, inverse transforms, gradient correction.  All kernels are hand-written CUDA for sm_103a.
  *
  * GRID AND LAYOUT (all arrays C-ordered [z][y][x], x fastest, FP64):
@@ -26,7 +27,8 @@
  *   Boundary conditions are homogeneous, per axis (§3.2: several combinations of homogeneous pressure
  *   boundary conditions; §3.6: phi takes the pressure's).  N = zero normal gradient at the boundary face
  *   (the face velocity there is an input the projection leaves unchanged); D = zero value at the boundary
- *   face (ghost value -p).  ND/DN are accepted on z only.
+ *   face (ghost value -p).  ND / DN (N at the low end, D at the high end, and the reverse) are accepted on
+ *   every axis: on x and y they make the transform a DCT-IV / DST-IV.
  *   When no axis has a D end the operator is singular: the volume-weighted mean of the right-hand side is
  *   removed (reported as compat_defect) and the returned potential has zero volume-weighted mean.
  *
@@ -95,10 +97,11 @@ void vofp_opts_default(vofp_opts* opt);
 
 /*
  * Create a plan for an nx x ny x nz grid (each >= 1) with uniform spacings dx, dy > 0 and z cell widths
- * dz[0..nz-1] > 0 (HOST pointer, copied), boundary conditions bc[3] (x, y, z; ND/DN only on z), options
- * `opt` (NULL = defaults).  Builds the eigenvalue, twiddle and z-coefficient tables on the current CUDA
+ * dz[0..nz-1] > 0 (HOST pointer, copied), boundary conditions bc[3] (x, y, z; each P, NN, DD, ND or DN),
+ * options `opt` (NULL = defaults).  Builds the eigenvalue, twiddle and z-coefficient tables on the current CUDA
  * device and allocates the workspace.  §3 (grid), §3.2 (solver, boundary conditions).
- * Errors: INVALID_ARG (sizes, spacings, bc), UNSUPPORTED (ND/DN on x or y), OOM, CUDA.
+ * Errors: INVALID_ARG (sizes, spacings, bc), UNSUPPORTED (an axis above 4096 cells, or above 2^31 - 1
+ * cells in all), OOM, CUDA.
  */
 int vofp_plan_create(int nx, int ny, int nz, double dx, double dy, const double* dz, const int bc[3],
                      const vofp_opts* opt, vofp_plan** out);

@@ -60,18 +60,21 @@ __device__ __forceinline__ double lap_at(const GridDev& g, const double* __restr
   double xs, ys, zlo, zhi;
   {
     double lo, hi;
+    // ghosts: wrapped (P), copied at an N end, negated at a D end (low end D for DD, DN; high end for DD, ND)
     if (i > 0) lo = __ldg(p + c - 1);
-    else lo = g.bcx == VOFP_BC_P ? __ldg(p + c + g.nx - 1) : neg_if(pc, g.bcx == VOFP_BC_DD);
+    else lo = g.bcx == VOFP_BC_P ? __ldg(p + c + g.nx - 1) : neg_if(pc, g.bcx == VOFP_BC_DD || g.bcx == VOFP_BC_DN);
     if (i < g.nx - 1) hi = __ldg(p + c + 1);
-    else hi = g.bcx == VOFP_BC_P ? __ldg(p + c - (g.nx - 1)) : neg_if(pc, g.bcx == VOFP_BC_DD);
+    else hi = g.bcx == VOFP_BC_P ? __ldg(p + c - (g.nx - 1)) : neg_if(pc, g.bcx == VOFP_BC_DD || g.bcx == VOFP_BC_ND);
     xs = hi + lo;
   }
   {
     double lo, hi;
     if (j > 0) lo = __ldg(p + c - g.nx);
-    else lo = g.bcy == VOFP_BC_P ? __ldg(p + c + (size_t)(g.ny - 1) * g.nx) : neg_if(pc, g.bcy == VOFP_BC_DD);
+    else lo = g.bcy == VOFP_BC_P ? __ldg(p + c + (size_t)(g.ny - 1) * g.nx)
+                                 : neg_if(pc, g.bcy == VOFP_BC_DD || g.bcy == VOFP_BC_DN);
     if (j < g.ny - 1) hi = __ldg(p + c + g.nx);
-    else hi = g.bcy == VOFP_BC_P ? __ldg(p + c - (size_t)(g.ny - 1) * g.nx) : neg_if(pc, g.bcy == VOFP_BC_DD);
+    else hi = g.bcy == VOFP_BC_P ? __ldg(p + c - (size_t)(g.ny - 1) * g.nx)
+                                 : neg_if(pc, g.bcy == VOFP_BC_DD || g.bcy == VOFP_BC_ND);
     ys = hi + lo;
   }
   {
@@ -175,6 +178,13 @@ __device__ __forceinline__ void xfwd_block(const XArgs& a, int bx, unsigned char
           fa = fr;
       }
     }
+    if (quarter_bc(bc)) {
+      int pos;
+      C v;
+      quarter_load<C>(i, n, bc, fa, fb, reinterpret_cast<const C*>(a.quart), pos, v);
+      b0[pb * ld + pos] = v;
+      continue;
+    }
     int idx = i;
     bool fl = false;
     if (bc != VOFP_BC_P) {
@@ -265,6 +275,13 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
       const size_t o = base + (size_t)j * a.nx + i;
       const R va = i < a.nx ? (R)S[o] : (R)0;
       const R vb = i + 1 < a.nx ? (R)S[o + 1] : (R)0;
+      if (quarter_bc(bc)) {
+        int pos;
+        C v;
+        quarter_load<C>(j, n, bc, va, vb, quart, pos, v);
+        b0[c * ld + pos] = v;
+        continue;
+      }
       int idx = j;
       bool fl = false;
       if (bc != VOFP_BC_P) {
@@ -300,6 +317,13 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
       const int c = t / n, m = t - c * n;
       const R* ra = st + (2 * c) * n;
       const R* rb = st + (2 * c + 1) * n;
+      if (quarter_bc(bc)) {  // the inverse is the same transform: spectral index m placed as a sample
+        int pos;
+        C v;
+        quarter_load<C>(m, n, bc, ra[m], rb[m], quart, pos, v);
+        b0[c * ld + pos] = v;
+        continue;
+      }
       b0[c * ld + m] = inv_pre<C>([&](int q) { return ra[q]; }, [&](int q) { return rb[q]; }, n, bc, m, quart);
     }
     __syncthreads();
@@ -308,6 +332,14 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
     for (int t = threadIdx.x; t < B * n; t += blockDim.x) {
       const int c = t % B, j = t / B;
       const int i = i0 + 2 * c;
+      const size_t o = base + (size_t)j * a.nx + i;
+      if (quarter_bc(bc)) {  // the transform again (twice it, as every pass): a forward-inverse pair gives 2n x
+        R oa, ob;
+        fwd_post<C>(Y + c * ld, n, bc, j, quart, oa, ob);
+        if (i < a.nx) S[o] = (T)oa;
+        if (i + 1 < a.nx) S[o + 1] = (T)ob;
+        continue;
+      }
       int idx = j;
       bool fl = false;
       if (bc != VOFP_BC_P) {
@@ -315,7 +347,6 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
         fl = bc == VOFP_BC_DD && (j & 1);
       }
       const C y = Y[c * ld + idx];
-      const size_t o = base + (size_t)j * a.nx + i;
       if (i < a.nx) S[o] = (T)neg_if(y.x, fl);
       if (i + 1 < a.nx) S[o + 1] = (T)neg_if(y.y, !fl);
     }
@@ -372,6 +403,13 @@ __device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned c
     const int pb = t / n, m = t - pb * n;
     const R* ra = st + (2 * pb) * n;
     const R* rb = st + (2 * pb + 1) * n;
+    if (quarter_bc(bc)) {  // the inverse is the same transform: spectral index m placed as a sample
+      int pos;
+      C v;
+      quarter_load<C>(m, n, bc, ra[m], rb[m], quart, pos, v);
+      b0[pb * ld + pos] = v;
+      continue;
+    }
     b0[pb * ld + m] = inv_pre<C>([&](int q) { return ra[q]; }, [&](int q) { return rb[q]; }, n, bc, m, quart);
   }
   __syncthreads();
@@ -387,14 +425,20 @@ __device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned c
   for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
     const int pb = t / n, i = t - pb * n;
     const long l0 = 2 * (pair0 + pb), l1 = l0 + 1;
-    int idx = i;
-    bool fl = false;
-    if (bc != VOFP_BC_P) {
-      idx = dct_perm(i, n);
-      fl = bc == VOFP_BC_DD && (i & 1);
+    R ya, yb;
+    if (quarter_bc(bc)) {  // the transform again (twice it, as every pass): a forward-inverse pair gives 2n x
+      fwd_post<C>(Y + pb * ld, n, bc, i, quart, ya, yb);
+    } else {
+      int idx = i;
+      bool fl = false;
+      if (bc != VOFP_BC_P) {
+        idx = dct_perm(i, n);
+        fl = bc == VOFP_BC_DD && (i & 1);
+      }
+      const C y = Y[pb * ld + idx];
+      ya = neg_if(y.x, fl);
+      yb = neg_if(y.y, !fl);
     }
-    const C y = Y[pb * ld + idx];
-    const R ya = neg_if(y.x, fl), yb = neg_if(y.y, !fl);
     const double va = wide_of(ya), vb = wide_of(yb);  // integer-pipe widening (one FP64 add for a pair)
     if (a.accumulate) {
       if (l0 < nlines) a.p[l0 * n + i] += va;

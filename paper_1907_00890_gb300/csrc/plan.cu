@@ -168,8 +168,10 @@ static double eig_1d(int bc, int n, double h, int q) {
     arg = kPi * ((q + 1) / 2) / n;
   else if (bc == VOFP_BC_NN)
     arg = kPi * q / (2.0 * n);
-  else
+  else if (bc == VOFP_BC_DD)
     arg = kPi * (q + 1) / (2.0 * n);
+  else  // ND, DN: cos / sin (pi (2q+1)(2j+1) / (4n))
+    arg = kPi * (2 * q + 1) / (4.0 * n);
   const double s = std::sin(arg);
   return -4.0 / (h * h) * s * s;
 }
@@ -187,7 +189,6 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   if (nx > 4096 || ny > 4096 || nz > 4096) return VOFP_ERR_UNSUPPORTED;
   for (int a = 0; a < 3; ++a)
     if (bc[a] < VOFP_BC_P || bc[a] > VOFP_BC_DN) return VOFP_ERR_INVALID_ARG;
-  if (bc[0] > VOFP_BC_DD || bc[1] > VOFP_BC_DD) return VOFP_ERR_UNSUPPORTED;
   for (int k = 0; k < nz; ++k)
     if (!(dz[k] > 0) || !std::isfinite(dz[k])) return VOFP_ERR_INVALID_ARG;
   vofp_opts o;
@@ -237,22 +238,28 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   };
   for (int a = 0; a < 2; ++a) {
     const int n = nn[a];
+    const int nq = quarter_bc(bc[a]) ? 2 * n : n;
     lam[a].resize(n);
     tw[a].resize(n);
-    quart[a].resize(n);
+    quart[a].resize(nq);
     tw32[a].resize(n);
-    quart32[a].resize(n);
+    quart32[a].resize(nq);
     twff[a].resize(n);
-    quartff[a].resize(n);
+    quartff[a].resize(nq);
     for (int q = 0; q < n; ++q) {
       lam[a][q] = eig_1d(bc[a], n, hh[a], q);
       const double t = -2.0 * kPi * q / n;
       tw[a][q] = make_double2(std::cos(t), std::sin(t));
-      const double u = -kPi * q / (2.0 * n);
-      quart[a][q] = make_double2(std::cos(u), std::sin(u));
       tw32[a][q] = make_float2((float)tw[a][q].x, (float)tw[a][q].y);
-      quart32[a][q] = make_float2((float)quart[a][q].x, (float)quart[a][q].y);
       twff[a][q] = to_cff(tw[a][q]);
+    }
+    // quarter-wave twiddles: DCT-II / DST-II e^{-i pi q / (2n)}; ND / DN (DCT-IV / DST-IV) the pre-twiddles
+    // e^{-i pi q / n} (q < n), then the post-twiddles e^{-i pi (2q+1) / (4n)}
+    for (int q = 0; q < nq; ++q) {
+      const double u = !quarter_bc(bc[a]) ? -kPi * q / (2.0 * n)
+                                          : (q < n ? -kPi * q / n : -kPi * (2 * (q - n) + 1) / (4.0 * n));
+      quart[a][q] = make_double2(std::cos(u), std::sin(u));
+      quart32[a][q] = make_float2((float)quart[a][q].x, (float)quart[a][q].y);
       quartff[a][q] = to_cff(quart[a][q]);
     }
     factor_radices(n, &p->ax[a].fd);
@@ -328,15 +335,15 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
     L.tw[a] = off;
     off = align256(off + sizeof(double2) * nn[a]);
     L.q[a] = off;
-    off = align256(off + sizeof(double2) * nn[a]);
+    off = align256(off + sizeof(double2) * quart[a].size());
     L.tw32[a] = off;
     off = align256(off + sizeof(float2) * nn[a]);
     L.q32[a] = off;
-    off = align256(off + sizeof(float2) * nn[a]);
+    off = align256(off + sizeof(float2) * quart32[a].size());
     L.twff[a] = off;
     off = align256(off + sizeof(cff) * nn[a]);
     L.qff[a] = off;
-    off = align256(off + sizeof(cff) * nn[a]);
+    off = align256(off + sizeof(cff) * quartff[a].size());
     L.blu64[a] = L.blu32[a] = L.bluff[a] = 0;
     if (!blu[a].empty()) {
       L.blu64[a] = off;
@@ -419,11 +426,11 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   for (int a = 0; a < 2; ++a) {
     memcpy(&host[L.lam[a]], lam[a].data(), sizeof(double) * nn[a]);
     memcpy(&host[L.tw[a]], tw[a].data(), sizeof(double2) * nn[a]);
-    memcpy(&host[L.q[a]], quart[a].data(), sizeof(double2) * nn[a]);
+    memcpy(&host[L.q[a]], quart[a].data(), sizeof(double2) * quart[a].size());
     memcpy(&host[L.tw32[a]], tw32[a].data(), sizeof(float2) * nn[a]);
-    memcpy(&host[L.q32[a]], quart32[a].data(), sizeof(float2) * nn[a]);
+    memcpy(&host[L.q32[a]], quart32[a].data(), sizeof(float2) * quart32[a].size());
     memcpy(&host[L.twff[a]], twff[a].data(), sizeof(cff) * nn[a]);
-    memcpy(&host[L.qff[a]], quartff[a].data(), sizeof(cff) * nn[a]);
+    memcpy(&host[L.qff[a]], quartff[a].data(), sizeof(cff) * quartff[a].size());
     if (!blu[a].empty()) {
       const size_t m = blu[a].size();
       memcpy(&host[L.blu64[a]], blu[a].data(), sizeof(double2) * m);

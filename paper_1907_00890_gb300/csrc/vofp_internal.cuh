@@ -432,8 +432,26 @@ __device__ C* fft_smem(C* a, C* b, int batch, const FftDesc& fd, const C* __rest
 // index fall in different banks.
 __host__ __device__ __forceinline__ int y_ld(int n) { return n | 1; }
 
-// Position of sample j in the reordered sequence used by DCT-II / DST-II.
+// Position of sample j in the reordered sequence used by DCT-II / DST-II (and DCT-IV / DST-IV).
 __device__ __forceinline__ int dct_perm(int j, int n) { return (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1); }
+
+// ND / DN on a transformed axis: the quarter-wave transforms DCT-IV / DST-IV, X[m] = sum_j x[j] cos (resp.
+// sin) (pi (2m+1)(2j+1) / (4n)).  With the DCT-II reordering and the odd samples negated (v), X[m] =
+// Re(e^{-i pi (2m+1)/(4n)} W[m]), W the length-n DFT of v_k e^{-i pi k/n}; for real v, W[n-1-m] =
+// conj(W[m]), so two packed lines split about n-1.  DST-IV is the DCT-IV of the reversed line with signs
+// (-1)^m.  Both are their own inverses up to n/2.  The axis' quart table then holds the pre-twiddles
+// e^{-i pi k/n} (k < n) followed by the post-twiddles e^{-i pi (2m+1)/(4n)}.
+__host__ __device__ __forceinline__ bool quarter_bc(int bc) { return bc == VOFP_BC_ND || bc == VOFP_BC_DN; }
+
+// Place sample i of two packed lines (a, b) for a quarter-wave transform: position, value (pre-twiddled).
+template <typename C>
+__device__ __forceinline__ void quarter_load(int i, int n, int bc, decltype(C::x) a, decltype(C::x) b,
+                                             const C* __restrict__ quart, int& pos, C& v) {
+  const int s = bc == VOFP_BC_ND ? i : n - 1 - i;
+  pos = dct_perm(s, n);
+  const bool neg = s & 1;
+  v = cmul(cmk<C>(neg_if(a, neg), neg_if(b, neg)), quart[pos]);
+}
 
 // Split the FFT Z of (a + i b) at index m into the spectra of a and b: A = (Z[m] + conj Z[n-m]) / 2,
 // B = (Z[m] - conj Z[n-m]) / (2 i).
@@ -451,7 +469,18 @@ __device__ __forceinline__ void split_two(const C* Z, int n, int m, C& A, C& B) 
 template <typename C>
 __device__ __forceinline__ void fwd_post(const C* Z, int n, int bc, int q, const C* __restrict__ quart,
                                          decltype(C::x)& oa, decltype(C::x)& ob) {
-  if (bc == VOFP_BC_P) {
+  if (quarter_bc(bc)) {
+    // 2 W_a = Z[q] + conj Z[n-1-q], 2 W_b = (Z[q] - conj Z[n-1-q]) / i; outputs Re(w 2W) with the post-twiddle
+    const C P = Z[q];
+    const C Q = Z[n - 1 - q];
+    const C w = quart[n + q];
+    oa = w.x * (P.x + Q.x) - w.y * (P.y - Q.y);
+    ob = w.x * (P.y + Q.y) - w.y * (Q.x - P.x);
+    if (bc == VOFP_BC_DN && (q & 1)) {
+      oa = -oa;
+      ob = -ob;
+    }
+  } else if (bc == VOFP_BC_P) {
     const int m = (q + 1) >> 1;
     const C P = Z[m];
     const C Q = Z[m == 0 ? 0 : n - m];

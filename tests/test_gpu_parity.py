@@ -238,7 +238,7 @@ def test_invalid_arguments_rejected_before_launch(vp):
     with pytest.raises(vp.VofpError):
         vp.Plan((4, 4, 4), 1.0, 1.0, np.array([1.0, -1.0, 1.0, 1.0]), ("P", "P", "NN"))
     with pytest.raises(vp.VofpError) as e:
-        vp.Plan((4, 4, 4), 1.0, 1.0, np.ones(4), ("ND", "P", "NN"))
+        vp.Plan((5000, 4, 4), 1.0, 1.0, np.ones(4), ("P", "P", "NN"))  # axes up to 4096 cells
     assert e.value.status == -2
     plan = vp.Plan((4, 4, 4), 1.0, 1.0, np.ones(4), ("P", "P", "NN"))
     assert vp._lib.vofp_poisson_solve(plan.handle, None, None, None, None) == -1
@@ -312,4 +312,56 @@ def test_project_extend_host_buffers(vp, precision, pinned):
             assert rel(outs[a].numpy(), ou[a]) < tol
             assert rel(outs[4 + a].numpy(), oe[3 + a]) < tol
         assert rel(outs[3].numpy(), ou[3]) < tol
+    plan.close()
+
+
+# ---- ND / DN on the transformed axes (quarter-wave transforms, DCT-IV / DST-IV) ---------------------------
+
+QXY = list(itertools.product(("ND", "DN", "NN"), ("DN", "ND", "DD"), ZB))
+
+
+@pytest.mark.parametrize("bcx,bcy,bcz", QXY)
+def test_poisson_quarter_wave_xy(vp, bcx, bcy, bcz):
+    n = (20, 12, 9)
+    bc = (bcx, bcy, bcz)
+    g, dz = make(n, bc, stretched=bcz != "P")
+    f = synth.rng(13).standard_normal(g.shape)
+    ref, _ = oracle.poisson_solve(g, f)
+    plan = vp.Plan(n, g.widths[0][0], g.widths[1][0], dz, bc)
+    assert rel(host(plan.poisson_solve(dev(f))), ref) < TOL
+    plan.close()
+
+
+@pytest.mark.parametrize("n", [(1, 6, 8), (7, 1, 5), (37, 17, 6), (31, 40, 5), (128, 96, 16), (250, 3, 4)])
+@pytest.mark.parametrize("bc", [("ND", "DN", "NN"), ("DN", "P", "DD"), ("P", "ND", "P")])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "ff"])
+def test_poisson_quarter_wave_sizes(vp, n, bc, precision):
+    g, dz = make(n, bc, stretched=bc[2] != "P")
+    f = synth.rng(sum(n) + 17).standard_normal(g.shape)
+    ref, _ = oracle.poisson_solve(g, f)
+    prec = {"fp64": vp.FP64, "mixed": vp.MIXED, "ff": vp.FF}[precision]
+    plan = vp.Plan(n, g.widths[0][0], g.widths[1][0], dz, bc, prec=prec, max_refine=0 if prec == vp.FF else 6)
+    p = plan.poisson_solve(dev(f))
+    assert rel(host(p), ref) < (TOL if prec == vp.FP64 else 1e-10), (n, bc)
+    plan.close()
+
+
+@pytest.mark.parametrize("bc", [("ND", "DN", "NN"), ("DN", "ND", "P")])
+def test_project_and_extend_quarter_wave_xy(vp, bc):
+    n = (26, 22, 14)
+    g, dz = make(n, bc, stretched=bc[2] != "P")
+    u0 = synth.random_velocity(n, bc, 81)
+    ou = oracle.project(g, *u0, dt_over_rho0=0.5)
+    plan = vp.Plan(n, g.widths[0][0], g.widths[1][0], dz, bc)
+    u = [dev(a) for a in u0]
+    p = plan.project(*u, dt_over_rho0=0.5)
+    assert rel(host(p), ou[3]) < TOL
+    for a in range(3):
+        assert rel(host(u[a]), ou[a]) < TOL
+    C, _ = synth.droplet(n, bc, 82, dz=dz)
+    mdot = np.ones(g.shape)
+    ref = oracle.extend_liquid_velocity(g, *ou[:3], C, mdot, 100.0, 1.0)
+    out = plan.extend(*u, dev(C), dev(mdot), 100.0, 1.0)
+    for a in range(7):
+        assert rel(host(out[a]), ref[a]) < TOL, a
     plan.close()
