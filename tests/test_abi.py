@@ -52,3 +52,21 @@ def test_error_strings_and_default_opts(lib):
 def test_sm103a_only_build_flags():
     from paper_1907_00890_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_entry_points_refuse_a_null_plan_on_the_host(lib):
+    """Argument checks run on the host before any CUDA call: a NULL plan is INVALID_ARG (-1) everywhere."""
+    P, D = ctypes.c_void_p, ctypes.c_double
+    lib.vofp_project_vd.argtypes = [P] * 8 + [D] * 4 + [P] * 3
+    lib.vofp_project_vd.restype = ctypes.c_int
+    assert lib.vofp_project_vd(None, None, None, None, None, None, None, None, 1e-3, 1e-3, 1.0, 1.0, None, None,
+                               None) == -1
+    for name in ("vofp_extend_liquid_velocity", "vofp_extend_vapour_velocity"):
+        f = getattr(lib, name)
+        f.argtypes = [P] * 6 + [D] * 2 + [P] * 9
+        f.restype = ctypes.c_int
+        assert f(None, None, None, None, None, None, 100.0, 1.0, None, None, None, None, None, None, None, None,
+                 None) == -1
+    lib.vofp_project.argtypes = [P] * 5 + [D] + [P] * 3
+    lib.vofp_project.restype = ctypes.c_int
+    assert lib.vofp_project(None, None, None, None, None, 1.0, None, None, None) == -1
