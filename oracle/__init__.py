@@ -15,6 +15,8 @@ solver for the second-order finite-difference Poisson equation, §3.2):
 * ``interface``  |grad C| and n = -grad C/|grad C| (central or Youngs differences), the Stefan potential
                  solve (Eq. ext_div), u1e = u - grad(phi) (Eq. jump_subtr), uG = u1e - (mdot/rho1) n
                  (Eq. int_vel); the boiling variant with the vapour-velocity extension (Appendix A).
+* ``vof``        the split VoF update with the interface velocity and its implicit volume deflation
+                 (§3.1, Eqs. fluxes, final_corr_2; upwind fluxes in place of the MTHINC ones).
 
 Every public function is pinned by the ``-m "not gpu"`` tests against closed forms, brute-force dense
 LU solves and exact invariants; no function is "parity unpinned".
@@ -22,9 +24,10 @@ LU solves and exact invariants; no function is "parity unpinned".
 from .mac import Grid, divergence, gradient, apply_laplacian, operator_matrix_1d, face_shape
 from .poisson import poisson_solve, project, project_variable_density
 from .interface import grad_c, delta_and_normal, stefan_source, extend_liquid_velocity, extend_vapour_velocity
+from .vof import vof_update
 
 __all__ = [
     "Grid", "divergence", "gradient", "apply_laplacian", "operator_matrix_1d", "face_shape",
     "poisson_solve", "project", "project_variable_density", "grad_c", "delta_and_normal", "stefan_source",
-    "extend_liquid_velocity", "extend_vapour_velocity",
+    "extend_liquid_velocity", "extend_vapour_velocity", "vof_update",
 ]
