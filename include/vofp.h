@@ -184,6 +184,19 @@ int vofp_extend_vapour_velocity(vofp_plan* plan, const double* u, const double* 
                                 void* stream, vofp_info* info);
 
 /*
+ * Volume-of-fluid update with the interface velocity uG (§3.1): the directional split of Eq. fluxes (x, y, z,
+ * each step implicit in its own result), then the correction with the implicit volume deflation of Eq.
+ * final_corr_2, C^{n+1} (1 - dt div uG) = C*** - dt (C* du/dx + C** dv/dy + C*** dw/dz).  The numerical
+ * fluxes are first-order upwind ones (the paper takes MTHINC fluxes from its reference; beyond a bounded end
+ * the boundary cell is used).  C: device cell array (input); uG, vG, wG: device face arrays; dt > 0 (the
+ * implicit factors 1 - dt du/dx etc. must stay positive: a Courant condition); C_out: device cell array
+ * (may be C); work: device workspace of 2 * nx * ny * nz doubles, disjoint from C and C_out.
+ * Errors: INVALID_ARG, CUDA.
+ */
+int vofp_vof_update(vofp_plan* plan, const double* C, const double* uG, const double* vG, const double* wG,
+                    double dt, double* C_out, double* work, void* stream);
+
+/*
  * Stefan source s = mdot (1/rho2 - 1/rho1) |grad C| at cell centres (§3.2 last term of Eq. lap_p with the
  * regularised delta |grad C|; §3.6 Eq. ext_div right-hand side), |grad C| per opts.grad_mode.
  * C, mdot: device cell arrays; s: device cell array (output).  Errors: INVALID_ARG, CUDA.

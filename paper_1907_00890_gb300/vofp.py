@@ -58,6 +58,8 @@ _lib.vofp_project_stefan.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _D, _P, _P,
 _lib.vofp_project_stefan.restype = _I
 _lib.vofp_project_vd.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P, ctypes.POINTER(vofp_info)]
 _lib.vofp_project_vd.restype = _I
+_lib.vofp_vof_update.argtypes = [_P, _P, _P, _P, _P, _D, _P, _P, _P]
+_lib.vofp_vof_update.restype = _I
 _lib.vofp_trace_enable.argtypes = [_I]
 _lib.vofp_trace_enable.restype = _I
 _lib.vofp_trace_collect.argtypes = [ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_ulonglong), _I]
@@ -370,6 +372,12 @@ def vofp_project_vd(plan, u, v, w, src, C, p_n, p_nm1, dt, dt_prev, rho1, rho2, 
     return (s, _info_dict(inf)) if info else s
 
 
+def vofp_vof_update(plan, C, uG, vG, wG, dt, C_out, work, stream=None):
+    return _check(_lib.vofp_vof_update(plan, _ptr(C, name="C"), _ptr(uG, name="uG"), _ptr(vG, name="vG"),
+                                       _ptr(wG, name="wG"), float(dt), _ptr(C_out, name="C_out"),
+                                       _ptr(work, name="work"), _stream(stream)), "vofp_vof_update")
+
+
 def vofp_stefan_source(plan, C, mdot, rho1, rho2, s, stream=None):
     return _check(_lib.vofp_stefan_source(plan, _ptr(C, name="C"), _ptr(mdot, name="mdot"), float(rho1),
                                           float(rho2), _ptr(s, name="s"), _stream(stream)), "vofp_stefan_source")
@@ -454,6 +462,15 @@ class Plan:
             p = torch.empty(self.cell_shape, dtype=torch.float64, device=u.device)
         r = vofp_project_vd(self.handle, u, v, w, src, C, p_n, p_nm1, dt, dt_prev, rho1, rho2, p, stream, info)
         return (p, r[1]) if info else p
+
+    def vof_update(self, C, uG, vG, wG, dt, out=None, stream=None):
+        """One VoF step with the interface velocity (§3.1); returns C^{n+1} (in `out` if given)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(C)
+        work = torch.empty((2,) + tuple(self.cell_shape), dtype=torch.float64, device=C.device)
+        vofp_vof_update(self.handle, C, uG, vG, wG, dt, out, work, stream)
+        return out
 
     def stefan_source(self, C, mdot, rho1, rho2, stream=None):
         import torch
