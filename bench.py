@@ -50,9 +50,9 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "ff"],
                     help="arithmetic of the main step (the 128^3 droplet step is specified in FP64)")
-    ap.add_argument("--only", choices=["large", "batched", "batched_ff", "served", "vd"], default=None,
+    ap.add_argument("--only", choices=["large", "batched", "batched_ff", "served", "vd", "vof"], default=None,
                     help="run one variant alone and print its JSON (for profiling captures); vd: the "
-                         "variable-density pressure step on the droplet")
+                         "variable-density pressure step on the droplet; vof: the VoF update on the droplet")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     return ap.parse_args()
@@ -181,6 +181,44 @@ def bench_vd(vofp, c, u0, C, md, st, flush, args):
     out["_dt"] = dt
     plan.close()
     return out
+
+
+def bench_vof(vofp, c, u0, C, md, st, flush, args):
+    """The VoF update with the interface velocity (§3.1, Eqs. fluxes and final_corr_2) on the 128^3 droplet:
+    uG from the liquid-velocity extension of the droplet's velocity field, dt at a Courant number of 0.5.
+    One update per step; the compulsory traffic is C and uG, vG, wG read and C^{n+1} written, 40 B per cell."""
+    import torch
+    plan = vofp.Plan(c["n"], c["dx"], c["dy"], c["dz"], c["bc"])
+    ext = plan.extend(*u0, C, md, c["rho1"], c["rho2"], want_phi=False)
+    ug = ext[3:6]
+    h = min(c["dx"], c["dy"], float(np.min(c["dz"])))
+    dt = 0.5 * h / max(float(x.abs().max()) for x in ug)
+    out = torch.empty_like(C)
+    work = torch.empty((2,) + tuple(plan.cell_shape), dtype=torch.float64, device=C.device)
+
+    def step():
+        vofp.vofp_vof_update(plan.handle, C, ug[0], ug[1], ug[2], dt, out, work, None)
+
+    def prep():
+        flush.zero_()
+
+    for _ in range(args.warmup):
+        prep()
+        step()
+    torch.cuda.synchronize()
+    ms, _, trace = timed_steps(vofp, st, prep, step, args.steps)
+    cells = int(np.prod(c["n"]))
+    r = {"value": cells / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_update": ms, "dt": dt,
+         "per_kernel_ms": {k: round(v[0] / v[1], 5) for k, v in trace.items()},
+         "workload": "VoF update with the interface velocity, %d^3 droplet, Courant 0.5, FP64" % c["n"][0]}
+    if "vof_update" in trace:
+        tot, cnt = trace["vof_update"]
+        hbm, how = peaks()
+        gbs = 40 * cells / (tot / (cnt / 3) / 1e3) / 1e9  # three launches per update
+        r["roofline_vof_update"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                    "frac": gbs / hbm, "bytes_per_cell": 40, "peak_source": how}
+    plan.close()
+    return r
 
 
 def mixed_bytes_per_cell(rs):
@@ -870,14 +908,15 @@ def run_only(args):
         r = bench_batched(vofp, args)
     elif args.only == "batched_ff":
         r = bench_batched(vofp, args, prec=vofp.FF)
-    elif args.only == "vd":
+    elif args.only in ("vd", "vof"):
         import torch
         c = synth_droplet(args.n)
         dev = torch.device("cuda", torch.cuda.current_device())
         T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)  # noqa: E731
         u0 = [T(a) for a in (c["u"], c["v"], c["w"])]
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-        r = bench_vd(vofp, c, u0, T(c["C"]), T(c["mdot"]), torch.cuda.current_stream(), flush, args)
+        fn = bench_vd if args.only == "vd" else bench_vof
+        r = fn(vofp, c, u0, T(c["C"]), T(c["mdot"]), torch.cuda.current_stream(), flush, args)
         for key in ("_inputs", "_outputs", "_dt"):
             r.pop(key, None)
     else:

@@ -70,3 +70,6 @@ def test_entry_points_refuse_a_null_plan_on_the_host(lib):
     lib.vofp_project.argtypes = [P] * 5 + [D] + [P] * 3
     lib.vofp_project.restype = ctypes.c_int
     assert lib.vofp_project(None, None, None, None, None, 1.0, None, None, None) == -1
+    lib.vofp_vof_update.argtypes = [P] * 5 + [D] + [P] * 3
+    lib.vofp_vof_update.restype = ctypes.c_int
+    assert lib.vofp_vof_update(None, None, None, None, None, 0.01, None, None, None) == -1
