@@ -285,14 +285,6 @@ __device__ __forceinline__ int face_diff_axis(const GridDev& g, const double* __
   if (axis == 1) return line_diff(p, (size_t)k * plane + i, g.nx, g.ny, g.bcy, j, d);
   return line_diff(p, (size_t)j * g.nx + i, plane, g.nz, g.bcz, k, d);
 }
-// 1 / x for a positive normal x: an FP32 reciprocal of its leading bits as the seed (integer-pipe split and
-// join), then two Newton steps y <- y + y (1 - x y) in FP64 (quadratic convergence: 2^-23 -> 2^-46 -> below
-// FP64 rounding), four FP64 multiply-adds against an FP64 division's longer sequence on this GPU.
-__device__ __forceinline__ double recip_newton(double x) {
-  double y = f64_of_bits(__frcp_rn(f32_lead_bits(x)));
-  y = fma(y, fma(-x, y, 1.0), y);
-  return fma(y, fma(-x, y, 1.0), y);
-}
 static __global__ void __launch_bounds__(256) k_vd_predict(VdArgs a) {
   const GridDev& g = a.g;
   int axis, i, j, k;

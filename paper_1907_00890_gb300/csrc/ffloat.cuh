@@ -140,6 +140,15 @@ __device__ __forceinline__ double f64_of_bits(float f) {
   return __longlong_as_double((long long)r);
 }
 
+// 1 / x for a normal x within the FP32 range: an FP32 reciprocal of its leading bits as the seed (integer-pipe
+// split and join), then two Newton steps y <- y + y (1 - x y) in FP64 (quadratic convergence: 2^-23 -> 2^-46 ->
+// below FP64 rounding), four FP64 multiply-adds against an FP64 division's longer sequence on this GPU.
+__device__ __forceinline__ double recip_newton(double x) {
+  double y = f64_of_bits(__frcp_rn(f32_lead_bits(x)));
+  y = fma(y, fma(-x, y, 1.0), y);
+  return fma(y, fma(-x, y, 1.0), y);
+}
+
 // Reduced-precision value <-> double with the conversions above (one FP64 addition for a pair).
 __device__ __forceinline__ float red_of(double d, float*) { return f32_lead_bits(d); }
 __device__ __forceinline__ ff red_of(double d, ff*) { return ff_split(d); }

@@ -10,7 +10,8 @@
 // with du/dx = (uG_{i+1/2} - uG_{i-1/2}) / dx and so on.  The paper takes f, g, h from an MTHINC reconstruction
 // it does not restate; these are first-order upwind fluxes (the cell the face velocity comes from; beyond a
 // bounded end the boundary cell itself).  One FP64 pass per direction, one thread per cell; C* and C** live in
-// a caller-provided workspace.
+// a caller-provided workspace.  The passes are bound by FP64 arithmetic, not by their ~32 bytes per cell, so the
+// implicit steps divide through an FP32-seeded Newton reciprocal and pick upwind cells by an integer sign test.
 #include <cmath>
 
 #include "solve_internal.h"
@@ -18,10 +19,11 @@
 
 namespace vofp {
 
-// Upwind flux dt * vel * C_upwind through face f (the low face of cell f) of a line of n cells at `base` with
-// stride `st`; the face velocity is `vel`.
-__device__ __forceinline__ double upwind_flux(const double* __restrict__ q, size_t base, size_t st, int n, int bc,
-                                              int f, double vel, double dt) {
+// Upwind value C_upwind across face f (the low face of cell f) of a line of n cells at `base` with stride
+// `st`, for the face velocity `vel`: the cell the flow comes from (sign bit of vel, an integer test; a zero
+// velocity of either sign gives a zero flux whichever cell is taken), beyond a bounded end the boundary cell.
+__device__ __forceinline__ double upwind_value(const double* __restrict__ q, size_t base, size_t st, int n, int bc,
+                                               int f, double vel) {
   int lo = f - 1, hi = f;  // the cells across the face
   if (bc == VOFP_BC_P) {
     if (lo < 0) lo += n;
@@ -30,11 +32,13 @@ __device__ __forceinline__ double upwind_flux(const double* __restrict__ q, size
     if (lo < 0) lo = 0;
     if (hi >= n) hi = n - 1;
   }
-  return dt * vel * __ldg(q + base + (size_t)(vel >= 0.0 ? lo : hi) * st);
+  return __ldg(q + base + (size_t)(__double2hiint(vel) >= 0 ? lo : hi) * st);
 }
 
 // One implicit directional step along `axis` for cell (i, j, k): returns the new value of q there and sets
-// `du` to the face-velocity difference over the cell width.
+// `du` to the face-velocity difference over the cell width.  With dt factored out of the fluxes,
+//   q_new = (q - dt/w (v_hi q_up(hi) - v_lo q_up(lo))) / (1 - dt/w (v_hi - v_lo)),
+// the quotient taken as a product with the Newton reciprocal of the denominator.
 __device__ __forceinline__ double vof_step(const GridDev& g, const double* __restrict__ q,
                                            const double* __restrict__ vel, int axis, int i, int j, int k, double dt,
                                            double& du) {
@@ -54,10 +58,12 @@ __device__ __forceinline__ double vof_step(const GridDev& g, const double* __res
   }
   const int fp = (bc == VOFP_BC_P && f + 1 == n) ? 0 : f + 1;  // the high face of the cell
   const double vlo = __ldg(vel + fbase + (size_t)f * fst), vhi = __ldg(vel + fbase + (size_t)fp * fst);
-  const double flo = upwind_flux(q, base, st, n, bc, f, vlo, dt);
-  const double fhi = upwind_flux(q, base, st, n, bc, f + 1, vhi, dt);
-  du = (vhi - vlo) * rw;
-  return (__ldg(q + base + (size_t)f * st) - (fhi - flo) * rw) / (1.0 - dt * du);
+  const double qlo = upwind_value(q, base, st, n, bc, f, vlo);
+  const double qhi = upwind_value(q, base, st, n, bc, f + 1, vhi);
+  const double dtrw = dt * rw, dv = vhi - vlo;
+  du = dv * rw;
+  const double num = fma(-dtrw, fma(vhi, qhi, -vlo * qlo), __ldg(q + base + (size_t)f * st));
+  return num * recip_newton(fma(-dtrw, dv, 1.0));
 }
 
 // x or y step: out = the implicit step of q along `axis`.
@@ -93,7 +99,7 @@ static __global__ void __launch_bounds__(128) k_vof_final(GridDev g, const doubl
     dv = (__ldg(vG + vb + (size_t)jp * g.nx) - __ldg(vG + vb + (size_t)j * g.nx)) * g.rdy;
   }
   const double F = fma(__ldg(c1 + c), du, fma(__ldg(c2 + c), dv, c3 * dw));
-  out[c] = (c3 - dt * F) / (1.0 - dt * (du + dv + dw));
+  out[c] = fma(-dt, F, c3) * recip_newton(fma(-dt, du + dv + dw, 1.0));
 }
 
 }  // namespace vofp
