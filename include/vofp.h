@@ -11,12 +11,14 @@
  *     uG = u1e - (mdot/rho1) n (Eq. int_vel);
  *   - the full variable-density pressure step of Eq. lap_p (the pressure-splitting term with the
  *     extrapolated pressure, vofp_project_vd) and the boiling variant of the interface velocity (Appendix A,
- *     vofp_extend_vapour_velocity).
+ *     vofp_extend_vapour_velocity);
+ *   - the volume-fraction update that the interface velocity drives (§3.1, Eqs. fluxes and final_corr_2,
+ *     vofp_vof_update).
  *
- * Both are solved exactly (direct solver, §3.2) on a uniform-in-x,y MAC grid: real-to-real transforms in x
- * and y (periodic: DFT; Neumann: DCT-II; Dirichlet: DST-II; mixed: DCT-IV / DST-IV), one tridiagonal system
- * in z per (x, y)
- * wavenumber pair, inverse transforms, gradient correction.  All kernels are hand-written CUDA for sm_103a.
+ * Both Poisson equations are solved exactly (direct solver, §3.2) on a uniform-in-x,y MAC grid: real-to-real
+ * transforms in x and y (periodic: DFT; Neumann: DCT-II; Dirichlet: DST-II; mixed: DCT-IV / DST-IV), one
+ * tridiagonal system in z per (x, y) wavenumber pair, inverse transforms, gradient correction.  All kernels
+ * are hand-written CUDA for sm_103a.
  *
  * GRID AND LAYOUT (all arrays C-ordered [z][y][x], x fastest, FP64):
  *   cell arrays (p, f, src, C, mdot, phi): nz * ny * nx values.
