@@ -133,16 +133,17 @@ def bench_mixed_step(vofp, c, u0, C, md, st, flush, args, prec=None, max_refine=
 
 def bench_vd(vofp, c, u0, C, md, st, flush, args):
     """The variable-density pressure step (Eq. lap_p with its pressure-splitting term) on the same 128^3
-    droplet: rho1/rho2 = 100, p^n from a constant-density projection of the same field, p^{n-1} = 0.95 p^n,
-    the Stefan source as src, dt = (dt/rho0) rho0 with rho0 = min(rho1, rho2).  One solve per step."""
+    droplet: rho1/rho2 = 100, p^n and p^{n-1} = 0.95 p^n from the seeded pressure-history generator, the
+    Stefan source as src, dt = (dt/rho0) rho0 with rho0 = min(rho1, rho2).  One solve per step."""
     import torch
+    from paper_1907_00890_gb300 import synth
     plan = vofp.Plan(c["n"], c["dx"], c["dy"], c["dz"], c["bc"])
     rho1, rho2 = c["rho1"], c["rho2"]
     dt = c["dt_over_rho0"] * min(rho1, rho2)
     src = plan.stefan_source(C, md, rho1, rho2)
-    uw = [x.clone() for x in u0]
-    pn = plan.project(*uw, src=src, dt_over_rho0=c["dt_over_rho0"])
-    pm = 0.95 * pn
+    pn_h, pm_h = synth.pressure_history(c["C"], synth.BASE_SEED + 7)
+    pn = torch.tensor(pn_h, dtype=torch.float64, device=C.device)
+    pm = torch.tensor(pm_h, dtype=torch.float64, device=C.device)
     u = [x.clone() for x in u0]
     p = torch.empty_like(pn)
 
@@ -175,8 +176,7 @@ def bench_vd(vofp, c, u0, C, md, st, flush, args):
         gbs = by / (tot / cnt / 1e3) / 1e9
         out["roofline_vd_predict"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                                       "frac": gbs / hbm, "bytes_per_cell": 72, "peak_source": how}
-    out["_inputs"] = [x.cpu().numpy() for x in u0] + [C.cpu().numpy(), pn.cpu().numpy(), pm.cpu().numpy(),
-                                                       src.cpu().numpy()]
+    out["_inputs"] = [pn_h, pm_h]  # host arrays from the generator; the oracle computes its own source
     out["_outputs"] = [x.cpu().numpy() for x in u] + [p.cpu().numpy()]
     out["_dt"] = dt
     plan.close()
@@ -781,10 +781,11 @@ def run_ours(args):
             vd = variants.get("variable_density")
             if vd is not None:
                 import oracle
-                uu, vv, ww, Cc, pn, pm, src = vd["_inputs"]
+                pn, pm = vd["_inputs"]
                 g = oracle.Grid(*c["n"], c["dx"], c["dy"], c["dz"], c["bc"])
-                r = oracle.project_variable_density(g, uu, vv, ww, Cc, pn, pm, vd["_dt"], vd["_dt"], c["rho1"],
-                                                    c["rho2"], src=src)
+                src = oracle.stefan_source(g, c["C"], c["mdot"], c["rho1"], c["rho2"])
+                r = oracle.project_variable_density(g, c["u"], c["v"], c["w"], c["C"], pn, pm, vd["_dt"], vd["_dt"],
+                                                    c["rho1"], c["rho2"], src=src)
                 got = vd["_outputs"]
                 vd["max_rel_err_vs_oracle"] = max(
                     float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))

@@ -12,6 +12,8 @@ Workloads (droplet fields standing in for the paper's droplet cases, ยง4.1 and ย
                         mdot = 1; rho1 = 100, rho2 = 1 (density ratio 100, Table tbl:table_groups).
 * ``swirl_velocity``    solid-body rotation about the z axis through the droplet centre (Omega = 2) plus
                         N(0, 0.1) noise on interior faces.
+* ``pressure_history``  p^n and p^{n-1} for the variable-density step: a pressure jump of 0.1 across the
+                        droplet interface (0.1 C) plus N(0, 0.01) noise, and p^{n-1} = 0.95 p^n.
 * ``stretched_dz``      tanh-clustered z widths with maximum neighbour ratio 1.05 (bisection on the
                         clustering parameter).
 * ``batch_sizes`` / ``serve_sizes``  instance grid sizes for the batched and served workloads.
@@ -142,6 +144,12 @@ def config_droplet(N=128, seed_offset=0):
     mdot = np.ones(C.shape)
     return dict(n=n, bc=bc, dx=1.0 / N, dy=1.0 / N, dz=uniform_dz(N), u=u, v=v, w=w, C=C, mdot=mdot,
                 rho1=100.0, rho2=1.0, dt_over_rho0=1.0)
+
+
+def pressure_history(C, seed, jump=0.1, noise=0.01):
+    """(p^n, p^{n-1}) at cell centres: jump * C plus N(0, noise), and 0.95 times that."""
+    pn = jump * np.asarray(C, dtype=np.float64) + noise * rng(seed).standard_normal(np.shape(C))
+    return pn, 0.95 * pn
 
 
 def batch_sizes(count=64, seed=BASE_SEED + 4, choices=(32, 48, 64, 96, 128, 160)):
