@@ -2,8 +2,11 @@
 
 TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import, call or execute this package; only
 ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline arm of ``bench.py`` use it.  It shares no code,
-table or constant with the CUDA library: the separable solve below diagonalises the stencil matrices
-numerically (``numpy.linalg.eigh``) instead of using closed-form transforms, and solves z by a banded LU.
+table or constant with the CUDA library: the separable solve takes the textbook orthonormal Fourier, cosine
+and sine vectors of each x and y stencil matrix as dense basis matrices, with every eigenvalue computed as the
+Rayleigh quotient of the stencil matrix itself (no closed-form eigenvalue table), transforms by plain matrix
+products, and solves each z system by Thomas elimination (Sherman-Morrison around it for a periodic z axis, a
+bordered dense solve for the singular mean mode).
 
 What it computes (the plain definition of the method's result, because the paper's solver is a direct
 solver for the second-order finite-difference Poisson equation, §3.2):

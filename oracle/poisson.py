@@ -8,8 +8,10 @@ with the GPU library:
 
 1. If L is singular (no Dirichlet end on any axis) the volume-weighted mean of f is removed (the least-squares
    reading of an incompatible right-hand side) and reported as the compatibility defect.
-2. The x and y 1-D operator matrices (symmetric, uniform spacing) are diagonalised numerically with
-   ``numpy.linalg.eigh``; f is transformed with the eigenvector matrices (plain matrix products).
+2. The x and y 1-D operator matrices (symmetric, uniform spacing) are diagonalised by the textbook
+   orthonormal Fourier / cosine / sine vectors at the cell centres (one dense basis matrix per axis), each
+   eigenvalue taken as the Rayleigh quotient q^T A q of the stencil matrix A itself; f is transformed with
+   the basis matrices (plain matrix products).
 3. For every (x, y) eigenpair the z system (A_z + (lx + ly) I) p_hat = f_hat is solved: Thomas elimination
    for a bounded z axis, Sherman-Morrison around it for a periodic one, a bordered dense solve with the
    constraint sum(dz * p_hat) = 0 for the singular mode.

@@ -6,7 +6,9 @@
 * projection invariants: zero-mean gauge, machine-epsilon divergence, idempotence, discrete Pythagoras,
   linearity, translation equivariance, x <-> y symmetry;
 * the extension of §3.6: exact decomposition u = u_df + grad(psi), the static-droplet case of §4.1
-  (u1e = 0, uG = -(mdot/rho1) n), divergence-free u1e (Eq. jump_subtr), planar-interface normals.
+  (u1e = 0, uG = -(mdot/rho1) n), divergence-free u1e (Eq. jump_subtr), planar-interface normals;
+* Youngs' corner-average gradient (§3.2) against closed forms on quadratic and periodic-wave fields and a
+  corner-by-corner restatement; face values of Eq. int_vel against linear fields at the face position.
 """
 import itertools
 import json
@@ -349,3 +351,210 @@ def test_quarter_wave_xy_closed_form_and_dense_lu(bcx, bcy, bcz):
         gg = Grid(*nn, 1.0 / nn[0], 0.7 / nn[1], dz, (bcx, bcy, bcz))
         ff = rr.standard_normal(gg.shape)
         assert rel(oracle.poisson_solve(gg, ff)[0], brute_solve(gg, ff)) < 1e-11, nn
+
+
+# ---- Youngs gradient and face values (§3.2 Youngs' method; §3.6 Eq. int_vel) ---------------------------------
+
+def _quadratic(r):
+    """Random quadratic a + b t + c t^2 with its value and its exact first and second derivatives."""
+    a, b, c = r.uniform(-1.0, 1.0, 3)
+    return (lambda t: a + b * t + c * t * t), (lambda t: b + 2 * c * t), 2 * c
+
+
+def test_youngs_gradient_closed_form_on_quadratic_product():
+    """For C = f(x) g(y) h(z) with quadratic factors sampled at cell centres of a uniform grid, Youngs'
+    corner average gives exactly d/dx C = f'(x) (g + dy^2 g''/4)(h + dz^2 h''/4) in every cell whose
+    3x3x3 neighbourhood is inside the grid: the two x face differences around the cell average to the
+    centred difference, exact for a quadratic, and each transverse corner average is the (1, 2, 1) / 4
+    filter, which adds d^2/4 times the second derivative.  A (1, 1) / 2 transverse average, a dropped
+    transverse average or a one-sided face difference each miss it."""
+    r = np.random.default_rng(20190701)
+    n = (9, 8, 7)
+    h = (0.11, 0.07, 0.13)
+    g = Grid(*n, h[0], h[1], np.full(n[2], h[2]), ("NN", "DD", "NN"))
+    xs = [(np.arange(n[a]) + 0.5) * h[a] for a in range(3)]
+    fs = [_quadratic(r) for _ in range(3)]
+    val = [fs[a][0](xs[a]) for a in range(3)]
+    der = [fs[a][1](xs[a]) for a in range(3)]
+    smooth = [val[a] + h[a] ** 2 / 4.0 * fs[a][2] for a in range(3)]
+    C = val[2][:, None, None] * val[1][None, :, None] * val[0][None, None, :]
+    gx, gy, gz = oracle.grad_c(g, C, mode=1)
+    ex = smooth[2][:, None, None] * smooth[1][None, :, None] * der[0][None, None, :]
+    ey = smooth[2][:, None, None] * der[1][None, :, None] * smooth[0][None, None, :]
+    ez = der[2][:, None, None] * smooth[1][None, :, None] * smooth[0][None, None, :]
+    inner = (slice(1, -1),) * 3
+    for got, want in ((gx, ex), (gy, ey), (gz, ez)):
+        assert np.abs(got[inner] - want[inner]).max() < 1e-13 * np.abs(want).max()
+    # the central-difference default has no transverse smoothing: f'(x) g(y) h(z)
+    cx = oracle.grad_c(g, C, mode=0)[0]
+    want0 = val[2][:, None, None] * val[1][None, :, None] * der[0][None, None, :]
+    assert np.abs(cx[inner] - want0[inner]).max() < 1e-13 * np.abs(want0).max()
+
+
+def test_youngs_gradient_closed_form_periodic_wave():
+    """On an all-periodic grid C = cos(a x) cos(b y) cos(c z) has, in every cell (wrap-around included),
+    the Youngs x derivative -sin(a x) sin(a dx)/dx * cos(b y) cos^2(b dy/2) * cos(c z) cos^2(c dz/2):
+    centred face differences and a (1, 2, 1) / 4 filter (= cos^2 of half the phase step) per transverse
+    axis."""
+    n = (8, 6, 10)
+    L = (1.0, 0.9, 1.3)
+    h = tuple(L[a] / n[a] for a in range(3))
+    g = Grid(*n, h[0], h[1], np.full(n[2], h[2]), ("P", "P", "P"))
+    k = (2 * math.pi * 3 / L[0], 2 * math.pi * 1 / L[1], 2 * math.pi * 2 / L[2])
+    xs = [(np.arange(n[a]) + 0.5) * h[a] for a in range(3)]
+    cs = [np.cos(k[a] * xs[a]) for a in range(3)]
+    ds = [-np.sin(k[a] * xs[a]) * math.sin(k[a] * h[a]) / h[a] for a in range(3)]
+    ss = [cs[a] * math.cos(k[a] * h[a] / 2) ** 2 for a in range(3)]
+    C = cs[2][:, None, None] * cs[1][None, :, None] * cs[0][None, None, :]
+    got = oracle.grad_c(g, C, mode=1)
+    want = (ss[2][:, None, None] * ss[1][None, :, None] * ds[0][None, None, :],
+            ss[2][:, None, None] * ds[1][None, :, None] * ss[0][None, None, :],
+            ds[2][:, None, None] * ss[1][None, :, None] * ss[0][None, None, :])
+    for a in range(3):
+        assert np.abs(got[a] - want[a]).max() < 1e-12 * max(np.abs(want[a]).max(), 1.0)
+
+
+def _youngs_by_corners(grid, C):
+    """Youngs' method written corner by corner: at each of the 8 corners of a cell, the derivative along an
+    axis is the mean of the 4 differences across that axis inside the 2x2x2 block of cells sharing the
+    corner (each over its centre distance); the cell value is the mean over its 8 corners.  Ghost cells copy
+    C at bounded ends and wrap at periodic ones."""
+    nx, ny, nz = grid.n
+    w = grid.widths
+
+    def cell(a, i):
+        n = grid.n[a]
+        if 0 <= i < n:
+            return i
+        if grid.bc[a] == "P":
+            return i % n
+        return 0 if i < 0 else n - 1
+
+    def centre_dist(a, i):
+        # distance between the centres of cells i and i + 1 (either may be a ghost)
+        n = grid.n[a]
+        wa = w[a]
+        if grid.bc[a] == "P":
+            return 0.5 * (wa[i % n] + wa[(i + 1) % n])
+        if i < 0:
+            return wa[0]
+        if i >= n - 1:
+            return wa[n - 1]
+        return 0.5 * (wa[i] + wa[i + 1])
+
+    out = [np.zeros(grid.shape) for _ in range(3)]
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                acc = [0.0, 0.0, 0.0]
+                for sx in (0, 1):
+                    for sy in (0, 1):
+                        for sz in (0, 1):
+                            lo = (i - 1 + sx, j - 1 + sy, k - 1 + sz)   # low cell of the 2x2x2 block
+                            for a in range(3):
+                                d = 0.0
+                                for t1 in (0, 1):
+                                    for t2 in (0, 1):
+                                        idx_lo = list(lo)
+                                        others = [b for b in range(3) if b != a]
+                                        idx_lo[others[0]] += t1
+                                        idx_lo[others[1]] += t2
+                                        idx_hi = list(idx_lo)
+                                        idx_hi[a] += 1
+                                        clo = C[cell(2, idx_lo[2]), cell(1, idx_lo[1]), cell(0, idx_lo[0])]
+                                        chi = C[cell(2, idx_hi[2]), cell(1, idx_hi[1]), cell(0, idx_hi[0])]
+                                        d += (chi - clo) / centre_dist(a, idx_lo[a])
+                                acc[a] += d / 4.0
+                for a in range(3):
+                    out[a][k, j, i] = acc[a] / 8.0
+    return out
+
+
+@pytest.mark.parametrize("bc", [("P", "NN", "DD"), ("NN", "P", "P"), ("DD", "DD", "ND")])
+def test_youngs_gradient_matches_corner_by_corner_definition(bc):
+    """The oracle's separable Youngs filter equals the corner-by-corner definition on every cell, boundary
+    cells and a stretched z axis included."""
+    r = np.random.default_rng(3)
+    n = (5, 4, 6)
+    dz = r.uniform(0.6, 1.4, n[2]) / n[2]
+    g = Grid(*n, 0.2, 0.25, dz, bc)
+    C = r.uniform(0.0, 1.0, g.shape)
+    got = oracle.grad_c(g, C, mode=1)
+    want = _youngs_by_corners(g, C)
+    for a in range(3):
+        assert np.abs(got[a] - want[a]).max() < 1e-12 * np.abs(want[a]).max()
+
+
+@pytest.mark.parametrize("bc", [("NN", "P", "DD"), ("P", "DD", "NN")])
+def test_face_average_of_linear_field_is_value_at_face(bc):
+    """Face values of a cell field (the mdot_f and n_f of Eq. int_vel): for q linear in space on a uniform
+    grid, every interior face (index i = low face of cell i, at x = i dx) carries q at the face position;
+    the periodic face 0 averages the last and first cells; a bounded axis' end faces copy their one
+    cell.  A half-cell offset (the mean of cells i and i + 1, or the cell value itself) fails."""
+    from oracle.interface import face_average
+    n = (6, 5, 7)
+    h = (0.1, 0.2, 0.15)
+    g = Grid(*n, h[0], h[1], np.full(n[2], h[2]), bc)
+    coef = (0.7, -1.3, 2.1)
+    xs = [(np.arange(n[a]) + 0.5) * h[a] for a in range(3)]
+    q = 0.4 + coef[0] * xs[0][None, None, :] + coef[1] * xs[1][None, :, None] + coef[2] * xs[2][:, None, None]
+    np_ax = (2, 1, 0)
+    for a in range(3):
+        f = face_average(g, q, a)
+        faces = np.arange(f.shape[np_ax[a]]) * h[a]
+        shape = [1, 1, 1]
+        shape[np_ax[a]] = -1
+        # value at the face: replace the coordinate of axis a by the face position
+        others = 0.4 + sum(coef[b] * xs[b].reshape([-1 if np_ax[b] == d else 1 for d in range(3)])
+                           for b in range(3) if b != a)
+        at_face = others + coef[a] * faces.reshape(shape)
+        nf = f.shape[np_ax[a]]
+        interior = [slice(None)] * 3
+        interior[np_ax[a]] = slice(1, n[a])
+        interior = tuple(interior)
+        assert np.abs(f[interior] - np.broadcast_to(at_face, f.shape)[interior]).max() < 1e-13
+        first = np.take(f, [0], axis=np_ax[a])
+        if g.bc[a] == "P":
+            assert nf == n[a]
+            want = 0.5 * (np.take(q, [0], axis=np_ax[a]) + np.take(q, [n[a] - 1], axis=np_ax[a]))
+            assert np.abs(first - want).max() < 1e-14
+        else:
+            assert nf == n[a] + 1
+            assert np.array_equal(first, np.take(q, [0], axis=np_ax[a]))
+            assert np.array_equal(np.take(f, [n[a]], axis=np_ax[a]), np.take(q, [n[a] - 1], axis=np_ax[a]))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_interface_velocity_with_linear_mdot_on_planar_ramp(mode):
+    """Eq. int_vel on a linear volume-fraction ramp C = c0 + g.x (both gradient stencils exact, so
+    n = -g/|g| in every cell whose neighbours are inside the grid) with mdot linear in x: on every face
+    between two such cells uG - u1e = -(mdot(face)/rho1) n, mdot taken at the face position itself (x faces
+    at i dx, y and z faces at the cell's own x).  A face value offset by half a cell, a wrong normal sign or
+    rho2 in place of rho1 fails."""
+    n = (10, 9, 8)
+    h = (0.1, 0.1, 0.1)
+    g = Grid(*n, h[0], h[1], np.full(n[2], h[2]), ("NN", "NN", "NN"))
+    xs = [(np.arange(n[a]) + 0.5) * h[a] for a in range(3)]
+    grad = np.array([0.05, -0.08, 0.03])
+    C = 0.5 + grad[0] * (xs[0][None, None, :] - 0.5) + grad[1] * (xs[1][None, :, None] - 0.45) \
+        + grad[2] * (xs[2][:, None, None] - 0.4)
+    assert C.min() > 0.3 and C.max() < 0.7
+    mdot = 1.0 + 0.6 * xs[0][None, None, :] + 0.0 * C
+    rho1, rho2 = 50.0, 2.0
+    zero = [np.zeros(oracle.face_shape(g, a)) for a in range(3)]
+    out = oracle.extend_liquid_velocity(g, *zero, C, mdot, rho1, rho2, mode)
+    nvec = -grad / np.linalg.norm(grad)
+    # x faces i = 2..n-2 lie between interior cells i-1, i (both in 1..n-2); mdot there = 1 + 0.6 i dx
+    fx = np.arange(n[0] + 1) * h[0]
+    dx_ = out[3] - out[0]
+    want_x = -(1.0 + 0.6 * fx)[None, None, :] / rho1 * nvec[0]
+    sl = (slice(1, -1), slice(1, -1), slice(2, n[0] - 1))
+    assert np.abs(dx_[sl] - np.broadcast_to(want_x, dx_.shape)[sl]).max() < 1e-14
+    # y and z faces: mdot at the cell's own x
+    want_yz = -(1.0 + 0.6 * xs[0])[None, None, :] / rho1
+    dy_ = out[4] - out[1]
+    sl = (slice(1, -1), slice(2, n[1] - 1), slice(1, -1))
+    assert np.abs(dy_[sl] - np.broadcast_to(want_yz * nvec[1], dy_.shape)[sl]).max() < 1e-14
+    dz_ = out[5] - out[2]
+    sl = (slice(2, n[2] - 1), slice(1, -1), slice(1, -1))
+    assert np.abs(dz_[sl] - np.broadcast_to(want_yz * nvec[2], dz_.shape)[sl]).max() < 1e-14
