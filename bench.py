@@ -53,8 +53,14 @@ def parse():
     ap.add_argument("--only", choices=["large", "batched", "batched_ff", "served", "vd", "vof"], default=None,
                     help="run one variant alone and print its JSON (for profiling captures); vd: the "
                          "variable-density pressure step on the droplet; vof: the VoF update on the droplet")
+    ap.add_argument("--large-n", type=int, default=512,
+                    help="cells per axis of the stretched-z projection variant (512 = the specified workload; "
+                         "smaller sizes only for profiling captures)")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-sets", type=int, default=8, help="field sets per ensemble run in the served stream")
+    ap.add_argument("--no-serve-sweep", dest="serve_sweep", action="store_false",
+                    help="skip the served rate sweep")
     return ap.parse_args()
 
 
@@ -248,14 +254,31 @@ def roofline_mixed(trace, n, rs=4, workload=None):
             "note": "averages include launches that returned at once after convergence"}
 
 
+def _torch_laplacian_ppnn(torch, p, dx, dy, dz):
+    """The MAC 7-point operator L p for periodic x, y and Neumann z ends (ghost = p), in plain PyTorch FP64:
+    the manufactured right-hand sides of the error statements below (no library kernel involved)."""
+    lx = (torch.roll(p, -1, 2) - 2.0 * p + torch.roll(p, 1, 2)) / (dx * dx)
+    ly = (torch.roll(p, -1, 1) - 2.0 * p + torch.roll(p, 1, 1)) / (dy * dy)
+    dzt = torch.tensor(dz, dtype=torch.float64, device=p.device)
+    h = 0.5 * (dzt[1:] + dzt[:-1])                      # centre distances across interior z faces
+    flux = (p[1:] - p[:-1]) / h[:, None, None]           # interior z faces; the two N end faces carry 0
+    lz = torch.zeros_like(p)
+    lz[:-1] += flux
+    lz[1:] -= flux
+    lz /= dzt[:, None, None]
+    return lx + ly + lz
+
+
 def bench_large(vofp, args):
     """512^3 pressure projection, stretched z (tanh clustering, ratio 1.05), P,P,NN, random face velocities:
-    refinement path (FP32 transforms + FP64 low modes / reductions / defect correction), FP32-pair direct
-    solve, and the plain FP64 path.  Error stated against the FP64 GPU path (parity-tested against the oracle
-    at sizes the oracle finishes) and as the FP64 residual of the returned p."""
+    refinement path (FP32 transforms + FP64 low modes / reductions / defect correction), FP32 pairs with one
+    confirming correction, and the plain FP64 path.  Each result's error is stated against exact solutions of
+    the same discrete system: p* smooth (low modes, where a direct solve's eps * cond error sits) and p*
+    white noise, f = L p* by a plain PyTorch FP64 stencil; beside them the library's own a-posteriori
+    estimate for the projection (info.err_estimate) and its FP64 residual."""
     import torch
     from paper_1907_00890_gb300 import synth
-    n = (512, 512, 512)
+    n = (args.large_n,) * 3
     bc = ("P", "P", "NN")
     dz = synth.stretched_dz(n[2])
     dx = dy = 1.0 / n[0]
@@ -267,11 +290,28 @@ def bench_large(vofp, args):
     u0[2][-1].zero_()
     u = [x.clone() for x in u0]
     p = torch.empty(n[::-1], dtype=torch.float64, device="cuda")
-    ref = None
-    out = {"workload": "pressure projection 512^3, stretched z (tanh, ratio 1.05), P,P,NN, N(0,1) face velocities; "
-                       "one solve per call, inputs > L2"}
+    # manufactured exact solutions (zero volume-weighted mean, the solver's gauge)
+    dzt = torch.tensor(dz, dtype=torch.float64, device="cuda")
+    zc = torch.cumsum(dzt, 0) - 0.5 * dzt
+    xc = (torch.arange(n[0], dtype=torch.float64, device="cuda") + 0.5) * dx
+    yc = (torch.arange(n[1], dtype=torch.float64, device="cuda") + 0.5) * dy
+    smooth = (torch.cos(2 * math.pi * xc)[None, None, :] * torch.sin(2 * math.pi * yc)[None, :, None]
+              * torch.cos(math.pi * zc)[:, None, None] + 0.5 * torch.cos(math.pi * zc)[:, None, None]
+              + 0.25 * torch.sin(4 * math.pi * xc)[None, None, :] * torch.cos(2 * math.pi * zc)[:, None, None])
+    white = torch.randn(n[::-1], generator=gen, dtype=torch.float64, device="cuda")
+    vol = dzt[:, None, None].expand(n[::-1])
+    exact = {}
+    for name, ps in (("smooth", smooth), ("white", white)):
+        ps -= (ps * vol).sum() / vol.sum()
+        exact[name] = (ps, _torch_laplacian_ppnn(torch, ps, dx, dy, dz))
+    del smooth, white, vol
+    out = {"workload": "pressure projection %d^3, stretched z (tanh, ratio 1.05), P,P,NN, N(0,1) face velocities; "
+                       "one solve per call, inputs > L2" % n[0],
+           "error_statement": "rel. L2 error of p against exact solutions p* of the same discrete system (smooth "
+                              "low-mode p* and white-noise p*, f = L p* by a plain PyTorch FP64 stencil); "
+                              "err_estimate: the library's a-posteriori estimate for the projection"}
     reps = max(3, min(args.steps, 8))
-    for name, prec, mr in (("fp64", vofp.FP64, 1), ("mixed", vofp.MIXED, 3), ("ff", vofp.FF, 0)):
+    for name, prec, mr in (("fp64", vofp.FP64, 1), ("mixed", vofp.MIXED, 3), ("ff", vofp.FF, 1)):
         plan = vofp.Plan(n, dx, dy, dz, bc, prec=prec, max_refine=mr)
         st = torch.cuda.current_stream()
 
@@ -295,19 +335,21 @@ def bench_large(vofp, args):
         cells = int(np.prod(n))
         r = {"value": cells / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_solve": ms, "solves_per_s": 1e3 / ms,
              "rel_residual": info["rel_residual"], "refine_iters": info["refine_iters"],
+             "err_estimate": info["err_estimate"], "max_refine": mr,
              "per_step_ms": {k: round(v[0] / reps, 4) for k, v in trace.items()}}
+        for ename, (ps, fs_) in exact.items():
+            plan.poisson_solve(fs_, p)
+            r["rel_err_vs_exact_" + ename] = float(torch.linalg.vector_norm(p - ps) / torch.linalg.vector_norm(ps))
         if prec == vofp.FP64:
-            ref = p.clone()
             r["dtype"] = "f64"
             r["roofline"] = roofline_from_trace(trace, n, "projection512_fp64")
         else:
             r["dtype"] = "f32+f64" if prec == vofp.MIXED else "f32x2+f64"
-            r["rel_err_vs_fp64"] = float(torch.linalg.vector_norm(p - ref) / torch.linalg.vector_norm(ref))
             r["roofline"] = roofline_mixed(trace, n, 8 if prec == vofp.FF else 4, "projection512_" + name)
         out[name] = r
         plan.close()
         torch.cuda.empty_cache()
-    del u, u0, p, ref
+    del u, u0, p, exact
     torch.cuda.empty_cache()
     return out
 
@@ -410,78 +452,125 @@ def _div_ratio(torch, plan, u, u0):
     return div(u) / max(div(u0), 1e-300)
 
 
+def _serve_stream(vofp, torch, prec, max_refine, rate, warm, dur, runs, bufs, seed):
+    """One server fed a Poisson arrival stream: every request belongs to one of the ensemble's runs and uses
+    one of that run's field sets; a request whose run has no free set waits on the client side (its latency
+    still counts from its arrival, passed to the server as arrival_s)."""
+    from paper_1907_00890_gb300 import synth
+    rng = synth.rng(seed)
+    nreq = int((warm + dur) * rate * 1.2) + 16
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+    arrivals = arrivals[arrivals < warm + dur]
+    pick = rng.integers(0, len(runs), size=len(arrivals))
+    bc = ("P", "P", "NN")
+    o = vofp.vofp_opts_default()
+    o.prec = prec
+    o.max_refine = max_refine
+    s = vofp.vofp_server_create(0, 64, o)
+    free = [list(range(len(bufs[k]))) for k in range(len(runs))]
+    busy = {}
+    waiting = []
+    t_srv0 = vofp.vofp_server_clock(s)
+    t0 = time.perf_counter()
+    reset_done = False
+    i = 0
+    late = 0
+    offered = 0
+    while i < len(arrivals) or busy or waiting:
+        now = time.perf_counter() - t0
+        if not reset_done and now >= warm:
+            vofp.vofp_server_stats(s, reset=True)
+            reset_done = True
+        for t in list(busy):
+            st_, _ = vofp.vofp_server_poll(s, t)
+            if st_ == 0:
+                k, b = busy.pop(t)
+                free[k].append(b)
+        while i < len(arrivals) and arrivals[i] <= now:
+            waiting.append(i)
+            offered += arrivals[i] >= warm
+            i += 1
+        still = []
+        for j in waiting:
+            k = int(pick[j])
+            if not free[k]:
+                still.append(j)
+                continue
+            b = free[k].pop()
+            n = runs[k]
+            t = vofp.vofp_server_submit(s, n, 1.0 / n[0], 1.0 / n[1], synth.uniform_dz(n[2]), bc, *bufs[k][b],
+                                        arrival_s=t_srv0 + arrivals[j])
+            busy[t] = (k, b)
+            if now - arrivals[j] > 0.01:
+                late += 1
+        waiting = still
+        if now > warm + dur + 60.0:
+            break
+        time.sleep(0.0001)
+    st = vofp.vofp_server_stats(s)
+    vofp.vofp_server_destroy(s)
+    return {"offered_per_s": offered / dur, "solves_per_s": st["completed"] / st["seconds"],
+            "p50_ms": st["p50_s"] * 1e3, "p99_ms": st["p99_s"] * 1e3,
+            "p99_wait_before_submit_ms": st["p99_wait_submit_s"] * 1e3,
+            "p99_wait_in_queue_ms": st["p99_wait_queue_s"] * 1e3,
+            "value": st["cells"] / st["seconds"] / 1e6, "unit": UNIT, "completed": int(st["completed"]),
+            "rejected": int(st["rejected"]), "late_submissions": late,
+            "plan_hits": int(st["plan_hits"]), "plan_misses": int(st["plan_misses"]),
+            "resident_plans": int(st["resident_plans"])}
+
+
+SERVE_SLO_P99_MS = 100.0
+
+
 def bench_served(vofp, args):
     """Poisson arrivals of projection requests from an ensemble of 64 droplet runs, each run with its own grid
     (per-axis sizes log-uniform in 48..256, drawn once per run), every request from a run drawn at random;
     served with continuous batching and resident plans: FP32 + refinement, FP32 pairs, and the plain FP64
-    path."""
+    path.  Latency runs from each request's scheduled arrival to its completion.  A short sweep then finds
+    the highest offered rate each server sustains (completes >= 98% of the offered rate with p99 <= 100 ms)."""
     import torch
     from paper_1907_00890_gb300 import synth
     rate = args.serve_rate
     warm = 1.0
     dur = args.serve_seconds
-    rng = synth.rng(synth.BASE_SEED + 5)
-    nreq = int((warm + dur) * rate * 1.2) + 16
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
-    arrivals = arrivals[arrivals < warm + dur]
     runs = synth.serve_sizes(64)
-    pick = rng.integers(0, len(runs), size=len(arrivals))
-    sizes = [runs[k] for k in pick]
     bc = ("P", "P", "NN")
-    # pool of field buffers at the largest shape; each request views a contiguous prefix of one slot
-    pool = 128
-    maxc = 257 * 256 * 256
+    # field sets per run at the run's own shape (8 per run, 23 GB in all): a run's requests in flight use
+    # distinct sets
     gen = torch.Generator(device="cuda")
     gen.manual_seed(synth.BASE_SEED + 6)
-    bufs = [[torch.randn(maxc, generator=gen, dtype=torch.float64, device="cuda") for _ in range(3)]
-            for _ in range(pool)]
+    bufs = [[[torch.randn(fs, generator=gen, dtype=torch.float64, device="cuda") for fs in synth.face_shapes(n, bc)]
+             for _ in range(args.serve_sets)] for n in runs]
+    servers = (("mixed", vofp.MIXED, 3), ("ff", vofp.FF, 0), ("fp64", vofp.FP64, 1))
     out = {}
-    for name, prec, mr in (("mixed", vofp.MIXED, 3), ("ff", vofp.FF, 0), ("fp64", vofp.FP64, 1)):
-        o = vofp.vofp_opts_default()
-        o.prec = prec
-        o.max_refine = mr
-        s = vofp.vofp_server_create(0, 64, o)
-        free = list(range(pool))
-        busy = {}
-        t0 = time.perf_counter()
-        reset_done = False
-        i = 0
-        late = 0
-        while i < len(arrivals) or busy:
-            now = time.perf_counter() - t0
-            if not reset_done and now >= warm:
-                vofp.vofp_server_stats(s, reset=True)
-                reset_done = True
-            # retire completed requests
-            for t in list(busy):
-                st_, _ = vofp.vofp_server_poll(s, t)
-                if st_ == 0:
-                    free.append(busy.pop(t))
-            while i < len(arrivals) and arrivals[i] <= now and free:
-                n = sizes[i]
-                k = free.pop()
-                fs = synth.face_shapes(n, bc)
-                views = [bufs[k][a][:int(np.prod(fs[a]))].view(fs[a]) for a in range(3)]
-                t = vofp.vofp_server_submit(s, n, 1.0 / n[0], 1.0 / n[1], synth.uniform_dz(n[2]), bc, *views)
-                busy[t] = k
-                if now - arrivals[i] > 0.01:
-                    late += 1
-                i += 1
-            if now > warm + dur + 60.0:
-                break
-            time.sleep(0.0001)
-        st = vofp.vofp_server_stats(s)
-        vofp.vofp_server_destroy(s)
-        out[name] = {"p50_ms": st["p50_s"] * 1e3, "p99_ms": st["p99_s"] * 1e3,
-                     "solves_per_s": st["completed"] / st["seconds"],
-                     "plan_hits": int(st["plan_hits"]), "plan_misses": int(st["plan_misses"]),
-                     "resident_plans": int(st["resident_plans"]),
-                     "value": st["cells"] / st["seconds"] / 1e6, "unit": UNIT, "completed": int(st["completed"]),
-                     "rejected": int(st["rejected"]), "late_submissions": late,
-                     "dtype": {vofp.MIXED: "f32+f64", vofp.FF: "f32x2+f64"}.get(prec, "f64")}
+    for name, prec, mr in servers:
+        r = _serve_stream(vofp, torch, prec, mr, rate, warm, dur, runs, bufs, synth.BASE_SEED + 5)
+        r["dtype"] = {vofp.MIXED: "f32+f64", vofp.FF: "f32x2+f64"}.get(prec, "f64")
+        r["keeps_up"] = bool(r["solves_per_s"] >= 0.98 * r["offered_per_s"])
+        out[name] = r
+    if args.serve_sweep:
+        sweep = {}
+        for name, prec, mr in servers:
+            rows = []
+            best = 0.0
+            for rt in (1000.0, 1500.0, 2000.0, 2500.0, 3000.0, 4000.0):
+                r = _serve_stream(vofp, torch, prec, mr, rt, 0.5, 2.0, runs, bufs, synth.BASE_SEED + 50 + int(rt))
+                ok = r["solves_per_s"] >= 0.98 * r["offered_per_s"] and r["p99_ms"] <= SERVE_SLO_P99_MS
+                rows.append({"rate": rt, "solves_per_s": round(r["solves_per_s"], 1), "p50_ms": round(r["p50_ms"], 2),
+                             "p99_ms": round(r["p99_ms"], 2), "sustained": bool(ok)})
+                if not ok:
+                    break
+                best = rt
+            sweep[name] = {"max_sustained_req_per_s": best, "rows": rows}
+        out["sweep"] = sweep
+        out["sweep_rule"] = ("offered rate sustained: >= 98%% of it completed and p99 (arrival -> completion) <= "
+                             "%.0f ms, 2 s per rate after 0.5 s warm-up" % SERVE_SLO_P99_MS)
     out["workload"] = ("Poisson arrivals at %.0f req/s for %.0f s after %.0f s warm-up from an ensemble of 64 runs "
-                       "(per-axis sizes log-uniform in [48, 256], drawn once per run), P,P,NN, N(0,1) fields, "
-                       "64 in flight, resident plans" % (rate, dur, warm))
+                       "(per-axis sizes log-uniform in [48, 256], drawn once per run, %d field sets per run), "
+                       "P,P,NN, N(0,1) fields, 64 in flight, resident plans; latency from the scheduled arrival "
+                       "to completion" % (rate, dur, warm, args.serve_sets))
+    del bufs
+    torch.cuda.empty_cache()
     return out
 
 

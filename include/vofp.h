@@ -86,10 +86,20 @@ typedef struct {
 } vofp_opts;
 
 typedef struct {
-  double compat_defect; /* volume-weighted mean removed from the right-hand side (0 if L regular) */
-  double rel_residual;  /* mixed: final ||f - L p||_2 / ||f||_2; FP64: not computed (0)             */
-  int refine_iters;     /* mixed: defect-correction iterations performed                            */
-  int status;           /* same as the return value                                                 */
+  double compat_defect; /* volume-weighted mean removed from the right-hand side (0 if L regular)     */
+  double mean_removed;  /* volume-weighted mean subtracted from the potential to restore the zero-mean
+                           gauge (FP32 spectra; 0 where the pinned mean mode keeps the gauge exactly)   */
+  double rel_residual;  /* refinement plans: ||f - fbar - L p||_2 / ||f||_2 of the returned p (FP64
+                           stencil); FP64 plans: not computed (0)                                       */
+  double err_estimate;  /* estimated relative 2-norm error of p against the exact solution of the
+                           discrete system.  Refinement plans (VOFP_MIXED, VOFP_FF): a posteriori -- the
+                           FP64 residual of the returned p is solved once more in the plan's precision and
+                           the size of that correction (not applied) relative to p is reported.  FP64
+                           plans: the a-priori scale cond(L) * 2^-53 of a direct FP64 solve, cond(L)
+                           estimated from the eigenvalue extremes at plan time (an upper scale: typical
+                           errors are well below it)                                                   */
+  int refine_iters;     /* refinement plans: defect-correction iterations performed                     */
+  int status;           /* same as the return value                                                     */
 } vofp_info;
 
 typedef struct vofp_plan vofp_plan;
@@ -280,13 +290,19 @@ void vofp_batch_destroy(vofp_batch* b);
  * arriving while others run are admitted as those complete), builds each plan in its arena block and runs
  * the projection asynchronously; no device memory is allocated or freed while serving.  A request whose
  * plan alone exceeds the arena completes with VOFP_ERR_BUSY.
- * vofp_server_poll: 0 = done (the ticket is consumed; *latency_s = completion - submission), 1 = pending,
+ * Latency runs from the request's ARRIVAL to its completion: arrival_s is the time the request arrived on the
+ * server clock (seconds since vofp_server_create, read with vofp_server_clock), so a request that waited on
+ * the caller's side before it could be submitted is charged for that wait; arrival_s <= 0 (or later than the
+ * submission) means the submission time.
+ * vofp_server_poll: 0 = done (the ticket is consumed; *latency_s = completion - arrival), 1 = pending,
  * < 0 = the request's error (also consumes the ticket).  vofp_server_wait: the same, blocking up to
- * timeout_s (VOFP_ERR_TIMEOUT, ticket kept).  vofp_server_stats: out[0..16] (the first n are written) =
- * completed, admitted, rejected, queued (submitted, not yet admitted), arena bytes in use, arena bytes, p50
- * and p99 latency (s), cells solved, seconds since creation or the last reset, worker seconds spent building
- * plans, worker seconds spent enqueuing work, worker loop iterations, requests served by a resident plan,
- * requests that needed a new plan, plans evicted, resident plans (reset != 0 clears the counters).  Plans
+ * timeout_s (VOFP_ERR_TIMEOUT, ticket kept).  vofp_server_stats: out[0..VOFP_SERVER_STATS-1] (the first n are
+ * written) = completed, admitted, rejected, queued (submitted, not yet admitted), arena bytes in use, arena
+ * bytes, p50 and p99 latency (s, arrival -> completion), cells solved, seconds since creation or the last
+ * reset, worker seconds spent building plans, worker seconds spent enqueuing work, worker loop iterations,
+ * requests served by a resident plan, requests that needed a new plan, plans evicted, resident plans, p99 wait
+ * from arrival to submission (s), p99 wait from submission to the launch of its work (s) (reset != 0 clears
+ * the counters).  Plans
  * stay resident in the arena after their request and serve later requests of the same grid, spacings and
  * boundary conditions; idle ones are evicted, least recently used first, when a new plan needs the space.
  * vofp_server_destroy waits for in-flight work.
@@ -302,7 +318,9 @@ typedef struct {
   const double* src;
   double dt_over_rho0;
   double* p;
+  double arrival_s; /* arrival time on the server clock (vofp_server_clock); <= 0: the submission time */
 } vofp_request;
+#define VOFP_SERVER_STATS 19
 typedef struct vofp_server vofp_server;
 int vofp_server_create(size_t mem_budget_bytes, int max_inflight, const vofp_opts* opt, vofp_server** out);
 int vofp_server_submit(vofp_server* s, const vofp_request* r, unsigned long long* ticket);
@@ -310,6 +328,8 @@ int vofp_server_poll(vofp_server* s, unsigned long long ticket, vofp_info* info,
 int vofp_server_wait(vofp_server* s, unsigned long long ticket, double timeout_s, vofp_info* info,
                      double* latency_s);
 int vofp_server_stats(vofp_server* s, double* out, int n, int reset);
+/* Seconds since the server's creation on its steady clock (the clock of vofp_request.arrival_s). */
+int vofp_server_clock(vofp_server* s, double* seconds);
 void vofp_server_destroy(vofp_server* s);
 
 /*
@@ -320,7 +340,8 @@ void vofp_server_destroy(vofp_server* s);
  * its workspace and tables live in one fixed file-scope device array of the library, sized for at most
  * VOFP_NOALLOC_MAX_CELLS cells with no axis longer than VOFP_NOALLOC_MAX_N (about 16.3 MiB, held by every
  * GPU that loads the library until the process exits).
- *   Arguments: grid as vofp_plan_create (dz is a HOST array of nz widths, copied on the stream), f and p
+ *   Arguments: grid as vofp_plan_create (dz is a HOST array of nz widths, read during the call and passed to the kernels by value: it
+ *   may be freed as soon as the call returns), f and p
  *   device cell arrays (may alias), stream as elsewhere.  Result identical (to rounding) to
  *   vofp_poisson_solve with a default FP64 plan.
  *   The first call on each device looks up the array's device address with that device current; make that

@@ -62,26 +62,6 @@ __global__ void k_shift(double* p, size_t n, const double* sum, double scale) {
     p[t] -= m;
 }
 
-// ||f - fbar - L p||^2 into *out (reporting pass after the last correction).
-__global__ void k_resid_norm(GridDev g, const double* __restrict__ F, const double* __restrict__ p,
-                             const double* defect_sum, double inv_volume, double* out, const double* skip_conv,
-                             int skip_k, double tol2) {
-  __shared__ double red[32];
-  if (launch_skipped(skip_conv, skip_k, tol2)) return;
-  const size_t total = (size_t)g.nx * g.ny * g.nz;
-  const double fbar = defect_sum ? *defect_sum * inv_volume : 0.0;
-  double acc = 0;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t % g.nx);
-    const size_t r = t / g.nx;
-    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-    const double v = __ldg(F + t) - fbar - lap_at(g, p, i, j, k);
-    acc += v * v;
-  }
-  const double s = block_sum(acc, red);
-  if (threadIdx.x == 0 && s != 0) atomicAdd(out, s);
-}
-
 // Reduced-precision element types: R (real) / C (complex) of the spectrum and its tables.
 template <typename R>
 struct Red;
@@ -168,6 +148,7 @@ static void solve_red(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, b
   if (ny > 1) VOFP_LAUNCH(KID_YINV, st, (ypass_kernel<R, C, true>()<<<ygrid, 256, ysm, st>>>(ya)));
 }
 
+// pout == NULL: norm only (d2_out), nothing stored and no gauge sum (the error-estimate solve).
 template <typename R>
 static void xinv_red(vofp_plan* pl, double* pout, int accumulate, int skip_k, double tol2, double* d2_out,
                      cudaStream_t st) {
@@ -192,7 +173,7 @@ static void xinv_red(vofp_plan* pl, double* pout, int accumulate, int skip_k, do
   xi.dzff = pl->dzff;
   // gauge: the FP32 spectrum's rounding leaves p with a mean of ~1e-7 |p| that is removed in FP64 at the end;
   // FP32-pair transforms keep the zero-mean gauge of the pinned mean mode to ~1e-14 and need no shift
-  xi.mean_out = (pl->singular && pl->opts.prec == VOFP_MIXED) ? pl->conv + VOFP_CONV_MEAN : nullptr;
+  xi.mean_out = (pout && pl->singular && pl->opts.prec == VOFP_MIXED) ? pl->conv + VOFP_CONV_MEAN : nullptr;
   xi.d2_out = d2_out;
   const int xgrid = xpass_blocks(xi.ny, xi.nz, xi.pb);
   const size_t xsm = 2 * (size_t)xi.pb * fft_span(xi.fd, xi.blu) * sizeof(C);
@@ -227,7 +208,7 @@ static void refine_sequence(vofp_plan* pl, int mode, XArgs xa, double* pout, int
   double* conv = pl->conv;
   xfwd_red<R>(pl, mode, xa, st);
   solve_red<R>(pl, st, -1, tol2, stats);
-  xinv_red<R>(pl, pout, 0, -1, tol2, M > 0 ? conv + VOFP_CONV_DEL : nullptr, st);
+  xinv_red<R>(pl, pout, 0, -1, tol2, (M > 0 || stats) ? conv + VOFP_CONV_DEL : nullptr, st);
   // correction j: residual pass R_j (skipped when F_{j-1}), solve S_j and inverse pass X_j (skipped when F_j)
   for (int j = 1; j <= M; ++j) {
     XArgs ra = {};
@@ -243,6 +224,27 @@ static void refine_sequence(vofp_plan* pl, int mode, XArgs xa, double* pout, int
     solve_red<R>(pl, st, j, tol2, stats);
     xinv_red<R>(pl, pout, 1, j, tol2, conv + VOFP_CONV_DEL + j, st);
   }
+}
+
+// Error estimate of the returned p (with info only): its FP64 residual r = f - fbar - L p (squared norm into
+// VOFP_CONV_FINAL) solved once more in the plan's precision, the correction S(r) not applied; ||S(r)|| is
+// the error left in p to the relative accuracy of one reduced-precision solve (~1e-6 FP32, ~1e-13 FP32
+// pairs), plus the rounding of r itself.
+template <typename R>
+static void estimate_sequence(vofp_plan* pl, double* pout, double tol2, cudaStream_t st) {
+  double* conv = pl->conv;
+  XArgs ra = {};
+  ra.f = pl->F;
+  ra.p = pout;
+  ra.defect_sum = pl->singular ? conv + 1 : nullptr;
+  ra.inv_volume = 1.0 / pl->volume;
+  ra.sq_out = conv + VOFP_CONV_FINAL;
+  ra.skip_conv = nullptr;
+  ra.skip_k = -1;
+  ra.tol2 = tol2;
+  xfwd_red<R>(pl, RHS_RESID, ra, st);
+  solve_red<R>(pl, st, -1, tol2, true);
+  xinv_red<R>(pl, nullptr, 0, -1, tol2, conv + VOFP_CONV_EST, st);
 }
 
 int mixed_solve(vofp_plan* pl, int mode, const XArgs* xin, const double* f, double* pout, cudaStream_t st,
@@ -278,10 +280,10 @@ int mixed_solve(vofp_plan* pl, int mode, const XArgs* xin, const double* f, doub
   else
     refine_sequence<float>(pl, mode, xa, pout, M, tol2, stats, st);
   if (info) {
-    VOFP_LAUNCH(KID_RESNORM, st,
-                k_resid_norm<<<grid_blocks(cells, 256), 256, 0, st>>>(
-                    grid_dev(pl), pl->F, pout, pl->singular ? conv + 1 : nullptr, 1.0 / pl->volume,
-                    conv + VOFP_CONV_FINAL, conv, -1, tol2));
+    if (pl->opts.prec == VOFP_FF)
+      estimate_sequence<ff>(pl, pout, tol2, st);
+    else
+      estimate_sequence<float>(pl, pout, tol2, st);
   }
   if (pl->singular && pl->opts.prec == VOFP_MIXED && pout != pl->P) {
     const double scale = 1.0 / ((double)pl->n[0] * pl->n[1] * (pl->volume / (pl->n[0] * pl->dx * pl->n[1] * pl->dy)));
@@ -312,6 +314,13 @@ int mixed_solve(vofp_plan* pl, int mode, const XArgs* xin, const double* f, doub
   }
   const double defect = pl->singular ? h[1] / pl->volume : 0.0;
   info->compat_defect = defect;
+  // the gauge shift subtracted from p by k_shift (FP32 spectra); FP32-pair and FP64 keep the pinned mean
+  // mode and subtract nothing
+  info->mean_removed = (pl->singular && pl->opts.prec == VOFP_MIXED)
+                           ? h[VOFP_CONV_MEAN] / ((double)pl->n[0] * pl->n[1] *
+                                                  (pl->volume / (pl->n[0] * pl->dx * pl->n[1] * pl->dy)))
+                           : 0.0;
+  info->err_estimate = h[VOFP_CONV_DEL] > 0 ? std::sqrt(h[VOFP_CONV_EST] / h[VOFP_CONV_DEL]) : 0.0;
   info->rel_residual = rr;
   info->refine_iters = iters;
   if (hi.nonfinite || !std::isfinite(f2) || !std::isfinite(rr)) status = VOFP_ERR_NONFINITE;

@@ -48,16 +48,23 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace vofp {
 
-// Eigenvalue of packed spectral index q (same conventions as the plan's tables), twiddles and z rows.
+// The z widths travel by value in the launch's parameters (8 KiB at most), so the call reads the caller's
+// host array once, when it returns nothing refers to it any more, and no host-to-device copy is needed.
+struct NoallocDz {
+  double w[kMaxN];
+};
+
+// Eigenvalue of packed spectral index q (same conventions as the plan's tables), twiddles and z rows; the
+// widths are stored into the table region for the solve's later kernels.
 __global__ void k_noalloc_tables(int nx, int ny, int nz, double dx, double dy, int bcx, int bcy, int bcz,
-                                 unsigned char* tab) {
+                                 unsigned char* tab, const __grid_constant__ NoallocDz dzp) {
   double* lam[2] = {(double*)(tab + kOffLamX), (double*)(tab + kOffLamY)};
   double2* tw[2] = {(double2*)(tab + kOffTwX), (double2*)(tab + kOffTwY)};
   double2* qt[2] = {(double2*)(tab + kOffQX), (double2*)(tab + kOffQY)};
   const int nn[2] = {nx, ny};
   const double hh[2] = {dx, dy};
   const int bb[2] = {bcx, bcy};
-  const double* dz = (const double*)(tab + kOffDz);
+  const double* dz = dzp.w;
   double* za = (double*)(tab + kOffZa);
   double* zb = (double*)(tab + kOffZb);
   double* zc = (double*)(tab + kOffZc);
@@ -115,6 +122,7 @@ __global__ void k_noalloc_tables(int nx, int ny, int nz, double dx, double dy, i
     za[t] = aa;
     zb[t] = b;
     zc[t] = cc;
+    ((double*)(tab + kOffDz))[t] = dz[t];
     rdz[t] = 1.0 / dz[t];
     rzc[t] = 1.0 / (hlo + hhi);
   }
@@ -165,11 +173,12 @@ extern "C" int vofp_poisson_solve_noalloc(int nx, int ny, int nz, double dx, dou
   if (s) return s;
   cudaStream_t st = (cudaStream_t)stream;
   unsigned char* tab = base + kSpecBytes;
-  if (cudaMemcpyAsync(tab + kOffDz, dz, sizeof(double) * nz, cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return VOFP_ERR_CUDA;
+  NoallocDz dzp;
+  for (int k = 0; k < nz; ++k) dzp.w[k] = dz[k];
   const int tmax = (nx > ny ? nx : ny) > nz + 1 ? (nx > ny ? nx : ny) : nz + 1;
   VOFP_LAUNCH(KID_NOALLOC_TABLES, st,
-              k_noalloc_tables<<<(tmax + 127) / 128, 128, 0, st>>>(nx, ny, nz, dx, dy, bc[0], bc[1], bc[2], tab));
+              k_noalloc_tables<<<(tmax + 127) / 128, 128, 0, st>>>(nx, ny, nz, dx, dy, bc[0], bc[1], bc[2], tab,
+                                                                   dzp));
 
   // a plan that lives on this stack frame and points into the scratch array
   vofp_plan pl = {};

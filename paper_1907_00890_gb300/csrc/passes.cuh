@@ -440,7 +440,9 @@ __device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned c
       yb = neg_if(y.y, !fl);
     }
     const double va = wide_of(ya), vb = wide_of(yb);  // integer-pipe widening (one FP64 add for a pair)
-    if (a.accumulate) {
+    if (!a.p) {
+      // norm only (the error estimate of a refinement plan): the transform's output is not stored
+    } else if (a.accumulate) {
       if (l0 < nlines) a.p[l0 * n + i] += va;
       if (l1 < nlines) a.p[l1 * n + i] += vb;
     } else {

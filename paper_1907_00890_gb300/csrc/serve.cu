@@ -10,8 +10,9 @@
 // so the work of requests admitted while others are on the GPU overlaps on the device.  An event recorded
 // after each request's kernels is polled by the worker (every 50 us while work is in flight), which then
 // stamps the completion and frees the slot and the plan: there is no cudaMalloc, cudaFree, host callback
-// or device synchronisation on the serving path.  Latency is measured from submission to that completion
-// stamp.  Each request runs exactly the kernels it would run alone (its plan depends only on its own grid),
+// or device synchronisation on the serving path.  Latency is measured from the request's arrival (a time on
+// the server's clock the caller gives, else the submission) to that completion stamp, so any wait before
+// the caller could submit counts; the waits before submission and in the server's queue are kept apart.  Each request runs exactly the kernels it would run alone (its plan depends only on its own grid),
 // so its result does not depend on what else is in flight.
 #include <algorithm>
 #include <chrono>
@@ -49,7 +50,9 @@ struct Req {
   std::vector<double> dz;
   std::string key;    // grid, spacing, boundary conditions: requests with equal keys share plans
   CachedPlan* plan;   // while admitted
+  Clock::time_point t_arrive;  // arrival (given by the caller on the server clock, else the submission)
   Clock::time_point t_submit;
+  Clock::time_point t_launch;  // enqueued on its slot's stream
   Clock::time_point t_done;
   int status;
   bool done;
@@ -83,8 +86,11 @@ struct vofp_server {
   bool stop;
   std::thread worker;
   int device;
+  Clock::time_point origin;  // zero of the server clock (vofp_server_clock)
   // statistics
-  std::vector<double> lat;
+  std::vector<double> lat;       // arrival -> completion
+  std::vector<double> wait_sub;  // arrival -> submission
+  std::vector<double> wait_q;    // submission -> enqueued
   unsigned long long completed, rejected, admitted;
   long long queued;  // submitted, not yet admitted or rejected
   double t_prepare, t_launch;  // worker seconds spent building plans and enqueuing work
@@ -149,7 +155,9 @@ void complete(vofp_server* s, int k, Clock::time_point t) {
   q->plan = nullptr;
   s->completed++;
   s->cells_done += (double)q->r.n[0] * q->r.n[1] * q->r.n[2];
-  s->lat.push_back(std::chrono::duration<double>(q->t_done - q->t_submit).count());
+  s->lat.push_back(std::chrono::duration<double>(q->t_done - q->t_arrive).count());
+  s->wait_sub.push_back(std::chrono::duration<double>(q->t_submit - q->t_arrive).count());
+  s->wait_q.push_back(std::chrono::duration<double>(q->t_launch - q->t_submit).count());
 }
 
 // An idle resident plan for `key` (lock held), or NULL.
@@ -252,6 +260,7 @@ void launch_request(vofp_server* s, Req* q) {
   Slot& sl = s->slots[q->slot];
   CachedPlan* cp = q->plan;
   int st = VOFP_OK;
+  q->t_launch = Clock::now();
   if (!cp->bound) {
     st = plan_bind(&cp->prep, s->arena + cp->block_off, sl.st, sl.stage);
     cp->bound = true;  // the stage buffer is free again once this stream passes the upload
@@ -393,6 +402,7 @@ extern "C" int vofp_server_create(size_t mem_budget_bytes, int max_inflight, con
   s->loops = 0;
   s->cells_done = 0;
   s->t0 = Clock::now();
+  s->origin = s->t0;
   init_kernel_attributes_fp64();
   init_kernel_attributes_mixed();
   s->worker = std::thread(worker_loop, s);
@@ -418,6 +428,13 @@ extern "C" int vofp_server_submit(vofp_server* s, const vofp_request* r, unsigne
   }
   q->plan = nullptr;
   q->t_submit = Clock::now();
+  q->t_arrive = q->t_submit;
+  if (r->arrival_s > 0) {
+    const Clock::time_point a =
+        s->origin + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(r->arrival_s));
+    if (a < q->t_submit) q->t_arrive = a;  // an arrival in the future is taken as the submission
+  }
+  q->t_launch = q->t_submit;
   q->status = VOFP_OK;
   q->done = false;
   q->prepared = false;
@@ -436,7 +453,7 @@ extern "C" int vofp_server_submit(vofp_server* s, const vofp_request* r, unsigne
 
 static int finish_ticket(vofp_server* s, Req* q, vofp_info* info, double* latency_s) {
   const int st = q->status;
-  if (latency_s) *latency_s = std::chrono::duration<double>(q->t_done - q->t_submit).count();
+  if (latency_s) *latency_s = std::chrono::duration<double>(q->t_done - q->t_arrive).count();
   if (info) {
     memset(info, 0, sizeof(*info));
     info->status = st;
@@ -471,25 +488,28 @@ extern "C" int vofp_server_wait(vofp_server* s, unsigned long long ticket, doubl
 // [6] p50 latency s, [7] p99 latency s, [8] cells solved (sum), [9] seconds since creation or reset,
 // [10] worker seconds building plans, [11] worker seconds enqueuing work, [12] worker loop iterations,
 // [13] requests served by a resident plan, [14] requests that needed a new plan, [15] plans evicted,
-// [16] resident plans.
+// [16] resident plans, [17] p99 arrival -> submission (s), [18] p99 submission -> enqueued (s).
+static double percentile(std::vector<double> l, double q) {
+  if (l.empty()) return 0.0;
+  std::sort(l.begin(), l.end());
+  size_t i = (size_t)(q * (l.size() - 1) + 0.5);
+  return l[std::min(i, l.size() - 1)];
+}
+
 extern "C" int vofp_server_stats(vofp_server* s, double* out, int n, int reset) {
   if (!s || !out || n < 1) return VOFP_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(s->mu);
-  std::vector<double> l = s->lat;
-  std::sort(l.begin(), l.end());
-  auto pct = [&](double q) {
-    if (l.empty()) return 0.0;
-    size_t i = (size_t)(q * (l.size() - 1) + 0.5);
-    return l[std::min(i, l.size() - 1)];
-  };
-  double v[17] = {(double)s->completed, (double)s->admitted, (double)s->rejected, (double)s->queued,
-                  (double)s->in_use,    (double)s->arena_bytes, pct(0.50), pct(0.99), s->cells_done,
-                  std::chrono::duration<double>(Clock::now() - s->t0).count(), s->t_prepare, s->t_launch,
-                  (double)s->loops, (double)s->plan_hits, (double)s->plan_misses, (double)s->plan_evictions,
-                  (double)s->plans.size()};
-  for (int i = 0; i < n && i < 17; ++i) out[i] = v[i];
+  double v[VOFP_SERVER_STATS] = {
+      (double)s->completed, (double)s->admitted, (double)s->rejected, (double)s->queued, (double)s->in_use,
+      (double)s->arena_bytes, percentile(s->lat, 0.50), percentile(s->lat, 0.99), s->cells_done,
+      std::chrono::duration<double>(Clock::now() - s->t0).count(), s->t_prepare, s->t_launch, (double)s->loops,
+      (double)s->plan_hits, (double)s->plan_misses, (double)s->plan_evictions, (double)s->plans.size(),
+      percentile(s->wait_sub, 0.99), percentile(s->wait_q, 0.99)};
+  for (int i = 0; i < n && i < VOFP_SERVER_STATS; ++i) out[i] = v[i];
   if (reset) {
     s->lat.clear();
+    s->wait_sub.clear();
+    s->wait_q.clear();
     s->completed = s->admitted = s->rejected = 0;
     s->cells_done = 0;
     s->t_prepare = s->t_launch = 0;
@@ -497,6 +517,12 @@ extern "C" int vofp_server_stats(vofp_server* s, double* out, int n, int reset) 
     s->plan_hits = s->plan_misses = s->plan_evictions = 0;
     s->t0 = Clock::now();
   }
+  return VOFP_OK;
+}
+
+extern "C" int vofp_server_clock(vofp_server* s, double* seconds) {
+  if (!s || !seconds) return VOFP_ERR_INVALID_ARG;
+  *seconds = std::chrono::duration<double>(Clock::now() - s->origin).count();
   return VOFP_OK;
 }
 

@@ -243,6 +243,8 @@ int finish_info(vofp_plan* pl, cudaStream_t st, vofp_info* info, int status) {
   if (status >= 0 && pl->opts.prec == VOFP_FP64) {
     info->rel_residual = 0;
     info->refine_iters = 0;
+    info->mean_removed = 0;  // the mean mode is pinned at zero in the z pass: nothing is subtracted
+    info->err_estimate = pl->cond_est * 0x1p-53;  // a-priori scale of a direct FP64 solve's error
   }
   info->status = status;
   return status;
@@ -481,9 +483,12 @@ extern "C" int vofp_project_extend(vofp_plan* pl, double* u, double* v, double* 
   int s2 = extend_common(pl, u, v, w, mdot, rho1, ue, ve, we, ug, vg, wg, phi, st, info);
   if (s2 < 0) return s2;
   if (info) {
-    // report the projection's defect and the worse of the two statuses
+    // report the projection's defect and gauge shift, the worse of the two statuses, residuals and error
+    // estimates
     info->compat_defect = i1.compat_defect;
+    info->mean_removed = i1.mean_removed;
     if (i1.rel_residual > info->rel_residual) info->rel_residual = i1.rel_residual;
+    if (i1.err_estimate > info->err_estimate) info->err_estimate = i1.err_estimate;
     info->refine_iters += i1.refine_iters;
     info->status = s1 > s2 ? s1 : s2;
   }

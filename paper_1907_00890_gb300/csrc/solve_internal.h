@@ -28,7 +28,6 @@ enum KernelId {
   KID_NOALLOC_TABLES,
   KID_ZLOW,     // refinement plans: the low-eigenvalue z systems in FP64
   KID_GAUGE,    // gauge restoration of p
-  KID_RESNORM,  // reporting residual norm
   KID_VD,       // variable-density splitting: u* -= dt (1/rho_f - 1/rho0) G p_hat
   KID_VOF,      // volume-of-fluid update with the interface velocity
   KID_COUNT

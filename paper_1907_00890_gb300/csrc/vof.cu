@@ -13,6 +13,7 @@
 // a caller-provided workspace.  The passes are bound by FP64 arithmetic, not by their ~32 bytes per cell, so the
 // implicit steps divide through an FP32-seeded Newton reciprocal and pick upwind cells by an integer sign test.
 #include <cmath>
+#include <cstdint>
 
 #include "solve_internal.h"
 #include "stencil.cuh"
@@ -112,7 +113,14 @@ extern "C" int vofp_vof_update(vofp_plan* pl, const double* C, const double* uG,
     return VOFP_ERR_INVALID_ARG;
   const GridDev g = grid_dev(pl);
   const size_t cells = (size_t)g.nx * g.ny * g.nz;
-  if (work == C || work == C_out || work + cells == C || work + cells == C_out) return VOFP_ERR_INVALID_ARG;
+  // the workspace [work, work + 2 cells) must not overlap C or C_out (the passes read and write through
+  // restrict pointers)
+  auto overlaps = [](const double* a, size_t na, const double* b, size_t nb) {
+    const uintptr_t a0 = (uintptr_t)a, a1 = a0 + na * sizeof(double);
+    const uintptr_t b0 = (uintptr_t)b, b1 = b0 + nb * sizeof(double);
+    return a0 < b1 && b0 < a1;
+  };
+  if (overlaps(work, 2 * cells, C, cells) || overlaps(work, 2 * cells, C_out, cells)) return VOFP_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   double* c1 = work;          // C*
   double* c2 = work + cells;  // C**

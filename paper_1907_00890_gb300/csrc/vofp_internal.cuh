@@ -76,7 +76,9 @@ __device__ __forceinline__ ff neg_if(ff x, bool f) { return ff(neg_if(x.hi, f), 
 //        conv[VOFP_CONV_RES + j] = ||r_j||^2, r_j = f - fbar - L p_j the residual after j corrections,
 //        conv[VOFP_CONV_DEL + j] = ||delta_j||^2 (delta_0 = the initial FP32 solve, delta_j the j-th
 //        correction), conv[VOFP_CONV_MEAN] = sum of delta dz over all of them (the gauge of p),
-//        conv[VOFP_CONV_FINAL] = ||r||^2 of the returned p (reporting pass).
+//        conv[VOFP_CONV_FINAL] = ||r||^2 of the returned p (reporting pass),
+//        conv[VOFP_CONV_EST] = ||S(r)||^2, the reduced-precision solve of that residual (not applied): the
+//        error left in p, reported as the error estimate.
 // Correction m (m >= 1) is a residual pass R_m (r_{m-1} = f - fbar - L p_{m-1}, its squared norm into
 // conv[VOFP_CONV_RES + m - 1]), a reduced-precision solve S_m and the inverse pass X_m (p_m = p_{m-1} +
 // delta_m, ||delta_m||^2 into conv[VOFP_CONV_DEL + m]).  F_k ("done after correction k - 1"): the residual
@@ -88,6 +90,7 @@ __device__ __forceinline__ ff neg_if(ff x, bool f) { return ff(neg_if(x.hi, f), 
 // pass that shows convergence.
 #define VOFP_CONV_RES 3
 #define VOFP_CONV_DEL 16
+#define VOFP_CONV_EST 29
 #define VOFP_CONV_MEAN 30
 #define VOFP_CONV_FINAL 31
 #define VOFP_MAX_REFINE 12
@@ -599,6 +602,8 @@ struct vofp_plan {
   int Ux, Uy;    // distinct eigenvalue counts in x, y
   // mixed path
   double lowthr;       // |lx + ly| at or below which a z system is solved in FP64
+  double cond_est;     // estimated condition number of L over its non-null modes (error scale of a direct
+                       // solve)
   int nlow;            // number of such systems
   int2* lowmodes;      // their (x, y) spectral indices
   double* lowscratch;  // FP64 columns for them (3 nz each)

@@ -26,7 +26,8 @@ class vofp_opts(ctypes.Structure):
 
 
 class vofp_info(ctypes.Structure):
-    _fields_ = [("compat_defect", ctypes.c_double), ("rel_residual", ctypes.c_double),
+    _fields_ = [("compat_defect", ctypes.c_double), ("mean_removed", ctypes.c_double),
+                ("rel_residual", ctypes.c_double), ("err_estimate", ctypes.c_double),
                 ("refine_iters", ctypes.c_int), ("status", ctypes.c_int)]
 
 
@@ -117,7 +118,8 @@ def vofp_project_extend(plan, u, v, w, C, mdot, rho1, rho2, dt_over_rho0, p, ue,
 
 class vofp_request(ctypes.Structure):
     _fields_ = [("n", _I * 3), ("dx", _D), ("dy", _D), ("dz", ctypes.POINTER(_D)), ("bc", _I * 3),
-                ("u", _P), ("v", _P), ("w", _P), ("src", _P), ("dt_over_rho0", _D), ("p", _P)]
+                ("u", _P), ("v", _P), ("w", _P), ("src", _P), ("dt_over_rho0", _D), ("p", _P),
+                ("arrival_s", _D)]
 
 
 _ULL = ctypes.c_ulonglong
@@ -133,8 +135,11 @@ _lib.vofp_server_stats.argtypes = [_P, ctypes.POINTER(_D), _I, _I]
 _lib.vofp_server_stats.restype = _I
 _lib.vofp_server_destroy.argtypes = [_P]
 _lib.vofp_server_destroy.restype = None
+_lib.vofp_server_clock.argtypes = [_P, ctypes.POINTER(_D)]
+_lib.vofp_server_clock.restype = _I
 EXPORTED += ["vofp_server_create", "vofp_server_submit", "vofp_server_poll", "vofp_server_wait",
-             "vofp_server_stats", "vofp_server_destroy"]
+             "vofp_server_stats", "vofp_server_destroy", "vofp_server_clock"]
+SERVER_STATS = 19
 
 
 def vofp_server_create(mem_budget_bytes=0, max_inflight=16, opts=None):
@@ -145,8 +150,9 @@ def vofp_server_create(mem_budget_bytes=0, max_inflight=16, opts=None):
     return h.value
 
 
-def vofp_server_submit(server, n, dx, dy, dz, bc, u, v, w, src=None, dt_over_rho0=1.0, p=None):
-    """Submit a projection request; returns its ticket.  The fields must stay valid until it completes."""
+def vofp_server_submit(server, n, dx, dy, dz, bc, u, v, w, src=None, dt_over_rho0=1.0, p=None, arrival_s=0.0):
+    """Submit a projection request; returns its ticket.  The fields must stay valid until it completes.
+    ``arrival_s``: when the request arrived, on the server clock (``vofp_server_clock``); 0 = now."""
     dzh = np.ascontiguousarray(np.broadcast_to(np.asarray(dz, dtype=np.float64), (int(n[2]),)))
     r = vofp_request()
     r.n[:] = [int(x) for x in n]
@@ -157,6 +163,7 @@ def vofp_server_submit(server, n, dx, dy, dz, bc, u, v, w, src=None, dt_over_rho
     r.src = _ptr(src, name="src")
     r.dt_over_rho0 = float(dt_over_rho0)
     r.p = _ptr(p, name="p")
+    r.arrival_s = float(arrival_s)
     t = _ULL()
     _check(_lib.vofp_server_submit(server, ctypes.byref(r), ctypes.byref(t)), "vofp_server_submit")
     return t.value
@@ -178,12 +185,19 @@ def vofp_server_wait(server, ticket, timeout_s=60.0):
 
 
 def vofp_server_stats(server, reset=False):
-    out = (_D * 17)()
-    _check(_lib.vofp_server_stats(server, out, 17, 1 if reset else 0), "vofp_server_stats")
+    out = (_D * SERVER_STATS)()
+    _check(_lib.vofp_server_stats(server, out, SERVER_STATS, 1 if reset else 0), "vofp_server_stats")
     keys = ["completed", "admitted", "rejected", "pending", "arena_in_use", "arena_bytes", "p50_s", "p99_s",
             "cells", "seconds", "worker_prepare_s", "worker_launch_s", "worker_loops", "plan_hits",
-            "plan_misses", "plan_evictions", "resident_plans"]
+            "plan_misses", "plan_evictions", "resident_plans", "p99_wait_submit_s", "p99_wait_queue_s"]
     return dict(zip(keys, list(out)))
+
+
+def vofp_server_clock(server):
+    """Seconds since the server's creation on its own steady clock (the clock of ``arrival_s``)."""
+    t = _D()
+    _check(_lib.vofp_server_clock(server, ctypes.byref(t)), "vofp_server_clock")
+    return t.value
 
 
 def vofp_server_destroy(server):
@@ -343,7 +357,8 @@ def vofp_plan_workspace_bytes(plan):
 
 
 def _info_dict(i):
-    return {"compat_defect": i.compat_defect, "rel_residual": i.rel_residual, "refine_iters": i.refine_iters,
+    return {"compat_defect": i.compat_defect, "mean_removed": i.mean_removed, "rel_residual": i.rel_residual,
+            "err_estimate": i.err_estimate, "refine_iters": i.refine_iters,
             "status": i.status}
 
 

@@ -51,3 +51,21 @@ def test_reference_arm_two_ranks():
     lines = [ln for ln in out.stdout.splitlines() if ln.strip().startswith("{")]
     assert len(lines) == 1
     check_line(json.loads(lines[0]), 2, n=128)
+
+
+def test_bench_manufactured_stencil_is_the_mac_operator():
+    """The plain-PyTorch stencil the bench uses to manufacture f = L p* for its error statements equals the
+    oracle's MAC operator (periodic x, y; Neumann z; stretched z)."""
+    torch = pytest.importorskip("torch")
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_1907_00890_gb300 import synth
+    n = (12, 10, 9)
+    dz = synth.stretched_dz(n[2])
+    g = oracle.Grid(*n, 1.0 / n[0], 0.8 / n[1], dz, ("P", "P", "NN"))
+    p = synth.rng(5).standard_normal(g.shape)
+    got = bench._torch_laplacian_ppnn(torch, torch.tensor(p), 1.0 / n[0], 0.8 / n[1], dz).numpy()
+    want = oracle.apply_laplacian(g, p)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()

@@ -190,3 +190,41 @@ def test_ff_project_extend_128(vp):
             assert rel(host(ug[a]), oe[3 + a]) < TOL
         assert rel(host(phi), oe[6]) < TOL
         plan.close()
+
+
+@pytest.mark.parametrize("prec,max_refine", [("mixed", 0), ("mixed", 1), ("mixed", 3), ("ff", 0), ("ff", 1),
+                                             ("fp64", 1)])
+@pytest.mark.parametrize("bc", [("P", "P", "NN"), ("NN", "DD", "P")])
+def test_error_estimate_and_mean_removed(vp, prec, max_refine, bc):
+    """info.err_estimate against the error actually left in p (vs the oracle): the refinement plans' a
+    posteriori estimate (one more solve of the final FP64 residual) tracks it within a factor of 10 wherever
+    the error is above the oracle's own rounding; the FP64 plans' a-priori cond * 2^-53 bounds it.
+    info.mean_removed: the gauge shift of FP32 spectra (zero-mean p after it), 0 for FP32 pairs and FP64."""
+    n = (48, 40, 36)
+    dz = synth.stretched_dz(n[2]) if bc[2] != "P" else synth.uniform_dz(n[2])
+    g = oracle.Grid(*n, 1.0 / n[0], 1.0 / n[1], dz, bc)
+    f = synth.rng(77).standard_normal(g.shape)
+    ref, _ = oracle.poisson_solve(g, f)
+    pr = {"mixed": vp.MIXED, "ff": vp.FF, "fp64": vp.FP64}[prec]
+    plan = vp.Plan(n, g.widths[0][0], g.widths[1][0], dz, bc, prec=pr, max_refine=max_refine)
+    p, info = plan.poisson_solve(dev(f), info=True)
+    err = rel(host(p), ref)
+    est = info["err_estimate"]
+    assert np.isfinite(est) and est > 0
+    if prec == "fp64":
+        assert err <= est and est < 1e-9
+    else:
+        floor = 3e-14  # the oracle's and the FP64 residual's own rounding
+        assert err <= 10 * est + floor, (err, est)
+        if err > floor:
+            assert est <= 10 * err, (err, est)
+        if max_refine >= 1 and prec == "mixed" or prec == "ff":
+            assert est <= TOL
+    V = g.cell_volumes()
+    if g.singular():
+        assert abs((host(p) * V).sum()) <= 1e-12 * np.abs(host(p) * V).sum()
+    if prec == "mixed" and g.singular():
+        assert info["mean_removed"] != 0.0 and abs(info["mean_removed"]) < 1e-4 * np.abs(ref).max()
+    else:
+        assert info["mean_removed"] == 0.0
+    plan.close()

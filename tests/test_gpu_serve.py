@@ -150,3 +150,26 @@ def test_resident_plans_reused_and_evicted(vp, precision):
             assert rel(p.cpu().numpy(), ou[3]) < TOL
             for a in range(3):
                 assert rel(u[a].cpu().numpy(), ou[a]) < TOL
+
+
+def test_latency_runs_from_arrival(vp):
+    """Latency is charged from the arrival the caller states on the server clock: a request that arrived
+    50 ms before it was submitted reports at least 50 ms, and the server's p99 wait before submission shows
+    it; an arrival later than the submission counts as the submission."""
+    n = (24, 20, 16)
+    bc = ("P", "P", "NN")
+    o = vp.vofp_opts_default()
+    o.prec = vp.FF
+    o.max_refine = 0
+    s = vp.vofp_server_create(1 << 30, 2, o)
+    u = [dev(a) for a in synth.random_velocity(n, bc, 5)]
+    now = vp.vofp_server_clock(s)
+    t = vp.vofp_server_submit(s, n, 1.0 / n[0], 1.0 / n[1], synth.uniform_dz(n[2]), bc, *u, arrival_s=now - 0.05)
+    lat = vp.vofp_server_wait(s, t, 60.0)
+    assert lat >= 0.05
+    st = vp.vofp_server_stats(s)
+    assert st["p99_wait_submit_s"] >= 0.05 and st["p50_s"] >= 0.05
+    t = vp.vofp_server_submit(s, n, 1.0 / n[0], 1.0 / n[1], synth.uniform_dz(n[2]), bc, *u,
+                              arrival_s=vp.vofp_server_clock(s) + 10.0)
+    assert 0 < vp.vofp_server_wait(s, t, 60.0) < 5.0
+    vp.vofp_server_destroy(s)

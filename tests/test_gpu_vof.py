@@ -46,3 +46,27 @@ def test_vof_update_vs_oracle(vp, n, bc):
     plan.vof_update(Cd, *[dev(a) for a in uG], dt, out=Cd)  # in place
     assert np.abs(Cd.cpu().numpy() - ref).max() <= 1e-12 * max(np.abs(ref).max(), 1.0)
     plan.close()
+
+
+def test_vof_workspace_overlap_refused(vp):
+    """A workspace that overlaps C or C_out, even partly, is refused on the host before any launch."""
+    import torch
+    n = (8, 6, 5)
+    bc = ("P", "P", "NN")
+    plan = vp.Plan(n, 1.0 / 8, 1.0 / 6, synth.uniform_dz(5), bc)
+    cells = 8 * 6 * 5
+    big = torch.zeros(4 * cells, dtype=torch.float64, device="cuda")
+    uG = [dev(a) for a in synth.random_velocity(n, bc, 3, sigma=0.1)]
+    C = big[:cells].view(5, 6, 8)
+    out = torch.empty(cells, dtype=torch.float64, device="cuda").view(5, 6, 8)
+    before = vp.vofp_launch_count()
+    for off in (cells // 2, cells - 1, 1):  # work starts inside C or ends inside it
+        work = big[off:off + 2 * cells]
+        with pytest.raises(RuntimeError):
+            vp.vofp_vof_update(plan.handle, C, *uG, 1e-3, out, work)
+    work = torch.empty(2 * cells, dtype=torch.float64, device="cuda")
+    with pytest.raises(RuntimeError):  # C_out inside the workspace
+        vp.vofp_vof_update(plan.handle, C, *uG, 1e-3, work[cells // 3:cells // 3 + cells], work)
+    assert vp.vofp_launch_count() == before
+    vp.vofp_vof_update(plan.handle, C, *uG, 1e-3, out, work)  # disjoint: accepted
+    plan.close()
