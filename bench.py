@@ -339,7 +339,13 @@ def bench_large(vofp, args):
              "per_step_ms": {k: round(v[0] / reps, 4) for k, v in trace.items()}}
         for ename, (ps, fs_) in exact.items():
             plan.poisson_solve(fs_, p)
-            r["rel_err_vs_exact_" + ename] = float(torch.linalg.vector_norm(p - ps) / torch.linalg.vector_norm(ps))
+            nps = torch.linalg.vector_norm(ps)
+            d = p - ps
+            r["rel_err_vs_exact_" + ename] = float(torch.linalg.vector_norm(d) / nps)
+            # the part of that error that is a constant offset (the gauge), relative like the error
+            off = (d * dzt[:, None, None]).sum() / (dzt.sum() * n[0] * n[1])
+            r["gauge_offset_" + ename] = float(off.abs() * math.sqrt(d.numel()) / nps)
+            del d
         if prec == vofp.FP64:
             r["dtype"] = "f64"
             r["roofline"] = roofline_from_trace(trace, n, "projection512_fp64")

@@ -95,9 +95,9 @@ typedef struct {
                            discrete system.  Refinement plans (VOFP_MIXED, VOFP_FF): a posteriori -- the
                            FP64 residual of the returned p is solved once more in the plan's precision and
                            the size of that correction (not applied) relative to p is reported.  FP64
-                           plans: the a-priori scale cond(L) * 2^-53 of a direct FP64 solve, cond(L)
-                           estimated from the eigenvalue extremes at plan time (an upper scale: typical
-                           errors are well below it)                                                   */
+                           plans: -1, not estimated (an FP64 plan keeps no copy of the right-hand side;
+                           an a-priori bound cond(L) * 2^-53 is vacuous on stretched grids, where cond(L)
+                           reaches 1e13)                                                               */
   int refine_iters;     /* refinement plans: defect-correction iterations performed                     */
   int status;           /* same as the return value                                                     */
 } vofp_info;

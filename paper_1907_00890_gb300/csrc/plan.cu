@@ -303,41 +303,6 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
     kz[2 * nz + k] = czm;
     kz[3 * nz + k] = -2.0 * (1.0 / (dx * dx) + 1.0 / (dy * dy)) - czp - czm;
   }
-  // condition number of L over its non-null modes, estimated: the largest eigenvalue magnitude bounded by the
-  // x and y tables' largest plus the z operator's largest Gershgorin row sum; the smallest from the x and y
-  // tables and the lowest z modes of a uniform axis of the same length (every eigenvalue is <= 0).  A
-  // direct solve's relative error is of order cond_est times the unit roundoff of its arithmetic.
-  {
-    double lmax = 0, xy0 = 0, xy1 = 0;  // xy0: smallest |lx| + |ly|; xy1: smallest nonzero one
-    double mn[2], mn1[2];
-    for (int a = 0; a < 2; ++a) {
-      double big = 0;
-      mn[a] = INFINITY;
-      mn1[a] = INFINITY;
-      for (int q = 0; q < nn[a]; ++q) {
-        const double v = std::fabs(lam[a][q]);
-        big = std::max(big, v);
-        mn[a] = std::min(mn[a], v);
-        if (v > 0) mn1[a] = std::min(mn1[a], v);
-      }
-      lmax += big;
-    }
-    double zg = 0;
-    for (int k = 0; k < nz; ++k) zg = std::max(zg, std::fabs(zb[k]) + std::fabs(za[k]) + std::fabs(zc[k]));
-    lmax += zg;
-    xy0 = mn[0] + mn[1];
-    xy1 = xy0 > 0 ? xy0 : std::min(mn[0] + mn1[1], mn1[0] + mn[1]);
-    const double pz = kPi / lz;
-    double z0 = 0, z1 = 0;  // smallest and smallest nonzero z eigenvalue magnitudes
-    switch (bc[2]) {
-      case VOFP_BC_P: z1 = nz > 1 ? 4.0 * pz * pz : INFINITY; break;
-      case VOFP_BC_NN: z1 = nz > 1 ? pz * pz : INFINITY; break;
-      case VOFP_BC_DD: z0 = z1 = pz * pz; break;
-      default: z0 = z1 = 0.25 * pz * pz; break;
-    }
-    const double lmin = (xy0 + z0 > 0) ? xy0 + z0 : std::min(xy1, z1);
-    p->cond_est = (lmin > 0 && std::isfinite(lmin)) ? lmax / lmin : 1.0;
-  }
   // refinement plans: the low-eigenvalue (x, y) pairs, |lx + ly| <= 64 * (smallest positive |eigenvalue|).
   // Every eigenvalue is <= 0 and |lx_i| is non-decreasing in the packed index i for each boundary
   // condition, so the low pairs of row j are a prefix i < lowcut[j] of it.

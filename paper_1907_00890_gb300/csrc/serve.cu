@@ -104,6 +104,10 @@ struct vofp_server {
 
 namespace {
 
+// Requests beyond the free slots that the worker prepares and tries to admit per iteration (the oldest
+// first; a request that cannot be placed does not block the ones behind it inside this window).
+constexpr int kLookahead = 16;
+
 bool arena_alloc(vofp_server* s, size_t bytes, size_t* off) {
   bytes = (bytes + 255) & ~(size_t)255;
   for (auto it = s->free_list.begin(); it != s->free_list.end(); ++it) {
@@ -305,10 +309,19 @@ void worker_loop(vofp_server* s) {
       local.push_back(s->pending.front());
       s->pending.pop_front();
     }
-    // host tables for new requests whose shape has no idle resident plan
+    int free_slots = 0;
+    for (const Slot& sl : s->slots) free_slots += !sl.busy;
+    // host tables for the requests next in line whose shape has no idle resident plan -- only as many as
+    // could be admitted now, plus a short look-ahead: under overload thousands wait, and building (or even
+    // matching) tables for all of them every iteration would starve the admissions
     std::vector<std::pair<Req*, int>> built;
-    for (Req* q : local)
-      if (!q->prepared && !q->done && !find_idle(s, q->key)) built.emplace_back(q, 0);
+    {
+      int window = free_slots + kLookahead;
+      for (Req* q : local) {
+        if (window-- <= 0) break;
+        if (!q->prepared && !q->done && !find_idle(s, q->key)) built.emplace_back(q, 0);
+      }
+    }
     if (!built.empty()) {
       lk.unlock();
       const Clock::time_point a = Clock::now();
@@ -323,6 +336,7 @@ void worker_loop(vofp_server* s) {
         }
     }
     bool progress = retired;
+    int window = free_slots + kLookahead;
     for (auto it = local.begin(); it != local.end();) {
       Req* q = *it;
       if (q->done) {  // rejected above
@@ -330,11 +344,14 @@ void worker_loop(vofp_server* s) {
         progress = true;
         continue;
       }
+      // nothing more can start without a free slot; past the look-ahead window no tables are ready
+      if (free_slots == 0 || window-- <= 0) break;
       if (!reserve(s, q)) {
         ++it;
         continue;
       }
       s->slots[q->slot].req = q;
+      --free_slots;
       it = local.erase(it);
       lk.unlock();
       const Clock::time_point a = Clock::now();

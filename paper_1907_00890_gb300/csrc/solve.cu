@@ -244,7 +244,7 @@ int finish_info(vofp_plan* pl, cudaStream_t st, vofp_info* info, int status) {
     info->rel_residual = 0;
     info->refine_iters = 0;
     info->mean_removed = 0;  // the mean mode is pinned at zero in the z pass: nothing is subtracted
-    info->err_estimate = pl->cond_est * 0x1p-53;  // a-priori scale of a direct FP64 solve's error
+    info->err_estimate = -1.0;  // not estimated (an FP64 plan keeps no copy of the right-hand side)
   }
   info->status = status;
   return status;

@@ -602,8 +602,6 @@ struct vofp_plan {
   int Ux, Uy;    // distinct eigenvalue counts in x, y
   // mixed path
   double lowthr;       // |lx + ly| at or below which a z system is solved in FP64
-  double cond_est;     // estimated condition number of L over its non-null modes (error scale of a direct
-                       // solve)
   int nlow;            // number of such systems
   int2* lowmodes;      // their (x, y) spectral indices
   double* lowscratch;  // FP64 columns for them (3 nz each)

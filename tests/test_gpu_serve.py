@@ -7,6 +7,8 @@
 * a request whose plan alone exceeds the arena completes with VOFP_ERR_BUSY;
 * the latency statistics are filled.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -163,6 +165,7 @@ def test_latency_runs_from_arrival(vp):
     o.max_refine = 0
     s = vp.vofp_server_create(1 << 30, 2, o)
     u = [dev(a) for a in synth.random_velocity(n, bc, 5)]
+    time.sleep(0.2)  # the server clock starts at its creation: an arrival 50 ms back must be > 0 on it
     now = vp.vofp_server_clock(s)
     t = vp.vofp_server_submit(s, n, 1.0 / n[0], 1.0 / n[1], synth.uniform_dz(n[2]), bc, *u, arrival_s=now - 0.05)
     lat = vp.vofp_server_wait(s, t, 60.0)
