@@ -370,6 +370,14 @@ int vofp_trace_collect(double* ms, unsigned long long* count, int n);
 int vofp_trace_kernel_classes(void);
 const char* vofp_trace_name(int id);
 
+/*
+ * Allocation-failure injection (diagnostics and tests of the out-of-memory paths; the paper has no
+ * counterpart).  after >= 0: the next `after` device or pinned-host allocations of the library succeed and
+ * the one after them fails once (the call that needed it returns VOFP_ERR_OOM and frees what it had taken);
+ * after < 0 switches the injection off.  Process-wide.  Returns VOFP_OK.
+ */
+int vofp_debug_fail_alloc(long long after);
+
 /* Static message for a status code. */
 const char* vofp_error_string(int status);
 

@@ -292,12 +292,12 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
   b->o_offepi = o;
   o = a256(o + sizeof(int) * (n + 1));
   b->args_bytes = o;
-  if (cudaMalloc(&b->dmem, o) != cudaSuccess) {
+  if (device_alloc(&b->dmem, o) != cudaSuccess) {
     cudaGetLastError();
     delete b;
     return VOFP_ERR_OOM;
   }
-  if (cudaMallocHost((void**)&b->hstage, o) != cudaSuccess) {
+  if (pinned_alloc((void**)&b->hstage, o) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(b->dmem);
     delete b;

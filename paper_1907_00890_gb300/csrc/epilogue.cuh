@@ -83,19 +83,21 @@ __host__ __device__ __forceinline__ size_t total_faces(const GridDev& g) {
          (size_t)g.nx * g.ny * nface(g.nz, g.bcz);
 }
 
-// Face launch shape: blockIdx.z = axis, blockIdx.y = plane k of that face array, blockIdx.x * blockDim.x +
-// threadIdx.x = index within the plane (32-bit arithmetic; no 64-bit division per face).
+// Face launch shape: blockIdx.z = plane k, blockIdx.y = axis, blockIdx.x * blockDim.x + threadIdx.x = index
+// within the plane of that axis' face array (32-bit arithmetic; no 64-bit division per face).  Blocks run
+// x fastest, then y: the three face arrays of plane k are done back to back, so the cell fields they share
+// (the potential, mdot, C) are read from DRAM once and then hit L2, instead of once per axis.
 inline dim3 face_grid(const GridDev& g, int threads) {
   const long a = (long)nface(g.nx, g.bcx) * g.ny, b = (long)g.nx * nface(g.ny, g.bcy), c = (long)g.nx * g.ny;
   const long m = a > b ? (a > c ? a : c) : (b > c ? b : c);
-  return dim3((unsigned)((m + threads - 1) / threads), (unsigned)(g.nz + 1), 3);
+  return dim3((unsigned)((m + threads - 1) / threads), 3, (unsigned)(g.nz + 1));
 }
 __device__ __forceinline__ bool face_coord(const GridDev& g, int& axis, int& i, int& j, int& k, size_t& off) {
-  axis = blockIdx.z;
+  axis = blockIdx.y;
   const int fx = axis == 0 ? nface(g.nx, g.bcx) : g.nx;
   const int fy = axis == 1 ? nface(g.ny, g.bcy) : g.ny;
   const int fz = axis == 2 ? nface(g.nz, g.bcz) : g.nz;
-  k = blockIdx.y;
+  k = blockIdx.z;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= fz || idx >= fx * fy) return false;
   j = idx / fx;

@@ -9,12 +9,18 @@
 // graph).  The singular operator's mean is removed from the residual in FP64 (the compatibility defect is
 // the FP64 volume-weighted mean of f, not the reduced-precision spectrum's), and the gauge of p (zero
 // volume-weighted mean) is restored in FP64 at the end from the exact sums of the corrections.
+#include <cudaTypedefs.h>
+
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
 #include "passes.cuh"
 #include "solve_internal.h"
+#include "ypass_tma.cuh"
 #include "zsolve.cuh"
 
 namespace vofp {
@@ -41,10 +47,112 @@ static void allow_all() {
   allow_smem(k_ztab_seg<T, TT>);
 }
 
+// Shared memory a TMA y-pass CTA may take (of the 227 KiB an sm_103a CTA can opt into).
+static const int kYTmaSmem = 225 * 1024;
+
+// The TMA y-pass kernel for a length 2^lgn and 2^lgB lines per tile: compiled for ny = 128, 256, 512 with the
+// tile width ytma_setup picks for them, else the version that reads both from its arguments.
+typedef void (*YTmaKernel)(const YTmaArgs, const CUtensorMap);
+template <typename R>
+static YTmaKernel ytma_kernel(bool inv, int lgn, int lgB) {
+  constexpr bool F = std::is_same<R, float>::value;
+  constexpr int B9 = F ? 4 : 3;
+  if (lgn == 9 && lgB == B9) return inv ? k_ypass_tma<R, true, 9, B9> : k_ypass_tma<R, false, 9, B9>;
+  if (lgn == 8 && lgB == 4) return inv ? k_ypass_tma<R, true, 8, 4> : k_ypass_tma<R, false, 8, 4>;
+  if (lgn == 7 && lgB == 4) return inv ? k_ypass_tma<R, true, 7, 4> : k_ypass_tma<R, false, 7, 4>;
+  return inv ? k_ypass_tma<R, true> : k_ypass_tma<R, false>;
+}
+
 void init_kernel_attributes_mixed() {
   if (!first_use_on_device(1)) return;
   allow_all<float, float2, ZF<float>>();
   allow_all<ff, cff, ZF<ff>>();
+  for (int inv = 0; inv < 2; ++inv)
+    for (int lgn = 0; lgn <= 9; ++lgn)
+      for (int lgB = 2; lgB <= 4; ++lgB) {
+        cudaFuncSetAttribute(ytma_kernel<float>(inv, lgn, lgB), cudaFuncAttributeMaxDynamicSharedMemorySize, kYTmaSmem);
+        cudaFuncSetAttribute(ytma_kernel<ff>(inv, lgn, lgB), cudaFuncAttributeMaxDynamicSharedMemorySize, kYTmaSmem);
+      }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// First use of the TMA y pass on a reduced-precision plan: applicable when ny is a power of two of at least 8
+// (the tile is loaded in boxes of at most 256 rows), a row of the spectrum is a multiple of 16 bytes (the
+// tensor map's stride rule) and at least one tile wide; then the widest tile (2^lgB complex lines, lgB = 4, 3
+// or 2) whose three buffers fit, the persistent grid (resident CTAs x SMs, at most one CTA per tile) and the
+// tensor map over the plan's spectrum.
+template <typename R>
+static void ytma_setup(vofp_plan* pl) {
+  pl->ytma_state = -1;
+  const char* env = getenv("VOFP_Y_TMA");
+  if (env && env[0] == '0') return;
+  const int nx = pl->n[0], ny = pl->n[1], nz = pl->n[2];
+  if (ny < 8 || ny > 4096 || (ny & (ny - 1)) || ((size_t)nx * sizeof(R)) % 16) return;
+  int lgB = -1;
+  for (int lb = 4; lb >= 2 && lgB < 0; --lb)
+    if ((2 << lb) <= nx && ytma_smem_bytes(ny, lb, 2 * sizeof(R)) <= (size_t)kYTmaSmem) lgB = lb;
+  if (lgB < 0) return;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return;
+  CUtensorMap tm;
+  const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny * nz};
+  const cuuint64_t strides[1] = {(cuuint64_t)nx * sizeof(R)};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 << lgB), (cuuint32_t)(ny < 256 ? ny : 256)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType dt = sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  if (enc(&tm, dt, 2, pl->S32, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return;
+  const size_t sm = ytma_smem_bytes(ny, lgB, 2 * sizeof(R));
+  int per_sm = 0, nsm = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ytma_kernel<R>(false, 31 - __builtin_clz((unsigned)ny), lgB),
+                                                    kYTmaThreads, sm) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return;
+  }
+  const int tiles = ((nx + (2 << lgB) - 1) / (2 << lgB)) * nz;
+  pl->ytma_lgB = lgB;
+  pl->ytma_grid = tiles < per_sm * nsm ? tiles : per_sm * nsm;
+  static_assert(sizeof(CUtensorMap) <= sizeof(pl->ytma_map), "tensor map storage");
+  memcpy(pl->ytma_map, &tm, sizeof(tm));
+  pl->ytma_state = 1;
+}
+
+// The y pass through TMA-staged tiles when the plan allows it; false: the caller runs the gather kernel.
+template <typename R>
+static bool ypass_tma(vofp_plan* pl, const YArgs& ya, bool inv, cudaStream_t st) {
+  if (pl->ytma_state == 0) ytma_setup<R>(pl);
+  if (pl->ytma_state != 1) return false;
+  CUtensorMap tm;
+  memcpy(&tm, pl->ytma_map, sizeof(tm));
+  YTmaArgs ta;
+  ta.y = ya;
+  ta.lgB = pl->ytma_lgB;
+  ta.tiles_x = (pl->n[0] + (2 << ta.lgB) - 1) / (2 << ta.lgB);
+  ta.info = pl->info;
+  const size_t sm = ytma_smem_bytes(pl->n[1], ta.lgB, 2 * sizeof(R));
+  const YTmaKernel kern = ytma_kernel<R>(inv, 31 - __builtin_clz((unsigned)pl->n[1]), ta.lgB);
+  VOFP_LAUNCH(inv ? KID_YINV : KID_YFWD, st, (kern<<<pl->ytma_grid, kYTmaThreads, sm, st>>>(ta, tm)));
+  return true;
 }
 
 int build_low_factors(vofp_plan* pl, cudaStream_t st, bool sync) {
@@ -103,7 +211,8 @@ static void solve_red(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, b
   ya.tol2 = tol2;
   const dim3 ygrid((nx + ya.tx - 1) / ya.tx, nz);
   const size_t ysm = 2 * (size_t)(ya.tx / 2) * y_ld(fft_span(ya.fd, ya.blu)) * sizeof(C);
-  if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, (ypass_kernel<R, C, false>()<<<ygrid, 256, ysm, st>>>(ya)));
+  if (ny > 1 && !ypass_tma<R>(pl, ya, false, st))
+    VOFP_LAUNCH(KID_YFWD, st, (ypass_kernel<R, C, false>()<<<ygrid, 256, ysm, st>>>(ya)));
   ZArgs za = z_args(pl, stats);
   za.S = pl->S32;
   za.ti = pl->zti32;
@@ -145,7 +254,8 @@ static void solve_red(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, b
                   k_zlow64<R><<<(pl->nlow + 63) / 64, 64, 0, st>>>(za, pl->lowmodes, pl->nlow, nullptr,
                                                                    pl->lowscratch));
   }
-  if (ny > 1) VOFP_LAUNCH(KID_YINV, st, (ypass_kernel<R, C, true>()<<<ygrid, 256, ysm, st>>>(ya)));
+  if (ny > 1 && !ypass_tma<R>(pl, ya, true, st))
+    VOFP_LAUNCH(KID_YINV, st, (ypass_kernel<R, C, true>()<<<ygrid, 256, ysm, st>>>(ya)));
 }
 
 // pout == NULL: norm only (d2_out), nothing stored and no gauge sum (the error-estimate solve).
@@ -324,6 +434,7 @@ int mixed_solve(vofp_plan* pl, int mode, const XArgs* xin, const double* f, doub
   info->rel_residual = rr;
   info->refine_iters = iters;
   if (hi.nonfinite || !std::isfinite(f2) || !std::isfinite(rr)) status = VOFP_ERR_NONFINITE;
+  if (hi.timeout) status = VOFP_ERR_TIMEOUT;  // a bounded wait for a tile load gave up
   if (status == VOFP_OK && !conv_ok) status = VOFP_WARN_NOT_CONVERGED;
   if (status == VOFP_OK && pl->singular && std::fabs(defect) > 1e-12 * h[2] / pl->volume)
     status = VOFP_WARN_INCOMPATIBLE_RHS;

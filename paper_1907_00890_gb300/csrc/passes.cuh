@@ -126,6 +126,19 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// Item t of a block's (line pair, sample) loop: pair t / n, sample t % n -- by shift and mask for a
+// power-of-two n (lgn >= 0), else by division.
+__device__ __forceinline__ void split_item(int t, int n, int lgn, int& pb, int& i) {
+  if (lgn >= 0) {
+    pb = t >> lgn;
+    i = t & (n - 1);
+  } else {
+    pb = t / n;
+    i = t - pb * n;
+  }
+}
+__device__ __forceinline__ int pow2_log(int n) { return (n & (n - 1)) == 0 ? 31 - __clz(n) : -1; }
+
 // x pass, forward: RHS + transform of line pairs (2p, 2p+1) of the flattened (k, j) line index.
 // Block body: `bx` is the block's index within this grid's launch (batched launches pass a local index).
 template <typename T, typename C, int MODE>
@@ -140,6 +153,15 @@ __device__ __forceinline__ void xfwd_block(const XArgs& a, int bx, unsigned char
   const long nlines = (long)a.g.ny * a.g.nz;
   const long pair0 = (long)bx * PB;
   const int bc = a.g.bcx;
+  const int lgn = pow2_log(n);
+  // (k, j) of the block's 2 PB lines, computed once instead of a 64-bit division per sample
+  __shared__ int lk[2 * kMaxPB], lj[2 * kMaxPB];
+  if (threadIdx.x < 2 * PB) {
+    const long l = 2 * pair0 + threadIdx.x;
+    lk[threadIdx.x] = (int)(l / a.g.ny);
+    lj[threadIdx.x] = (int)(l - (long)lk[threadIdx.x] * a.g.ny);
+  }
+  __syncthreads();
   const bool stats = a.info || a.sq_out || a.fv_out || a.abs_out;
   // FP64 plans keep every sum in FP64; reduced-precision plans keep only sum f V (the compatibility defect)
   // in FP64 and accumulate the norms, which feed thresholds only, in FP32
@@ -148,14 +170,15 @@ __device__ __forceinline__ void xfwd_block(const XArgs& a, int bx, unsigned char
   double acc_abs = 0, acc_sq = 0, acc_fv = 0;
   float accf_abs = 0.0f, accf_sq = 0.0f;
   for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
-    const int pb = t / n, i = t - pb * n;
+    int pb, i;
+    split_item(t, n, lgn, pb, i);
     const long l0 = 2 * (pair0 + pb), l1 = l0 + 1;
     R fa = (R)0, fb = (R)0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const long l = h ? l1 : l0;
       if (l < nlines) {
-        const int k = (int)(l / a.g.ny), j = (int)(l - (long)k * a.g.ny);
+        const int k = lk[2 * pb + h], j = lj[2 * pb + h];
         const double f = rhs_at<MODE>(a, i, j, k, fbar);
         const R fr = red_of(f, (R*)nullptr);  // integer-pipe conversion in reduced-precision plans
         if (a.fsave) a.fsave[l * n + i] = f;
@@ -218,7 +241,8 @@ __device__ __forceinline__ void xfwd_block(const XArgs& a, int bx, unsigned char
   const C* quart = reinterpret_cast<const C*>(a.quart);
   T* S = reinterpret_cast<T*>(a.S);
   for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
-    const int pb = t / n, q = t - pb * n;
+    int pb, q;
+    split_item(t, n, lgn, pb, q);
     const long l0 = 2 * (pair0 + pb), l1 = l0 + 1;
     R oa, ob;
     fwd_post<C>(Z + pb * ld, n, bc, q, quart, oa, ob);
@@ -394,13 +418,21 @@ __device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned c
   const int bc = a.bc;
   const C* quart = reinterpret_cast<const C*>(a.quart);
   R* st = reinterpret_cast<R*>(b1);
-  for (int t = threadIdx.x; t < 2 * PB * n; t += blockDim.x) {
-    const long l = 2 * pair0 + t / n;
-    st[t] = l < nlines ? (R)S[l * n + (t % n)] : (R)0;
+  const int lgn = pow2_log(n);
+  // z plane of each of the block's 2 PB lines (the gauge sum's dz), computed once instead of a 64-bit
+  // division per sample
+  __shared__ int lplane[2 * kMaxPB];
+  if (threadIdx.x < 2 * PB) lplane[threadIdx.x] = (int)((2 * pair0 + threadIdx.x) / a.ny);
+  {
+    // the block's lines are consecutive: one contiguous run of the spectrum
+    const long lim = (nlines - 2 * pair0) * n;
+    const T* src = S + 2 * pair0 * n;
+    for (int t = threadIdx.x; t < 2 * PB * n; t += blockDim.x) st[t] = t < lim ? (R)src[t] : (R)0;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
-    const int pb = t / n, m = t - pb * n;
+    int pb, m;
+    split_item(t, n, lgn, pb, m);
     const R* ra = st + (2 * pb) * n;
     const R* rb = st + (2 * pb + 1) * n;
     if (quarter_bc(bc)) {  // the inverse is the same transform: spectral index m placed as a sample
@@ -423,7 +455,8 @@ __device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned c
   ff accm(0.0f, 0.0f);
   float acc2f = 0.0f;
   for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
-    const int pb = t / n, i = t - pb * n;
+    int pb, i;
+    split_item(t, n, lgn, pb, i);
     const long l0 = 2 * (pair0 + pb), l1 = l0 + 1;
     R ya, yb;
     if (quarter_bc(bc)) {  // the transform again (twice it, as every pass): a forward-inverse pair gives 2n x
@@ -451,8 +484,8 @@ __device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned c
     }
     if (f64) {
       if (a.mean_out) {
-        if (l0 < nlines) acc = fma(va, __ldg(a.dz + l0 / a.ny), acc);
-        if (l1 < nlines) acc = fma(vb, __ldg(a.dz + l1 / a.ny), acc);
+        if (l0 < nlines) acc = fma(va, __ldg(a.dz + lplane[2 * pb]), acc);
+        if (l1 < nlines) acc = fma(vb, __ldg(a.dz + lplane[2 * pb + 1]), acc);
       }
       if (a.d2_out) {
         if (l0 < nlines) acc2 = fma(va, va, acc2);
@@ -460,8 +493,8 @@ __device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned c
       }
     } else {
       if (a.mean_out) {
-        if (l0 < nlines) accm += ff_of(ya) * a.dzff[l0 / a.ny];
-        if (l1 < nlines) accm += ff_of(yb) * a.dzff[l1 / a.ny];
+        if (l0 < nlines) accm += ff_of(ya) * a.dzff[lplane[2 * pb]];
+        if (l1 < nlines) accm += ff_of(yb) * a.dzff[lplane[2 * pb + 1]];
       }
       if (a.d2_out) {
         const float fa = lead(ya), fb = lead(yb);
@@ -495,18 +528,18 @@ __global__ void __launch_bounds__(256) k_xinv(XInvArgs a) {
 // takes 58 for the x passes and drops that to four).  The FP32 x pass that also evaluates the Stefan source
 // keeps the plain kernel: it spills under the cap.
 template <int MODE>
-__global__ void __launch_bounds__(256, 5) k_xfwd_f32(XArgs a) {
+__global__ void __launch_bounds__(256, 4) k_xfwd_f32(XArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   xfwd_block<float, float2, MODE>(a, blockIdx.x, smem_raw, red);
 }
 template <bool INV>
-__global__ void __launch_bounds__(256, 5) k_ypass_f32(YArgs a) {
+__global__ void __launch_bounds__(256, 4) k_ypass_f32(YArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ypass_block<float, float2, INV>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 template <int UNUSED>
-__global__ void __launch_bounds__(256, 5) k_xinv_f32(XInvArgs a) {
+__global__ void __launch_bounds__(256, 4) k_xinv_f32(XInvArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   xinv_block<float, float2>(a, blockIdx.x, smem_raw, red);

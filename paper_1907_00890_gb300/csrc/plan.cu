@@ -524,7 +524,7 @@ int plan_bind(PlanPrep* pp, void* block, cudaStream_t st, unsigned char* stage) 
   const PlanLayout& L = pp->L;
   const bool own = block == nullptr;
   if (own) {
-    if (cudaMalloc(&block, L.total) != cudaSuccess) {
+    if (device_alloc(&block, L.total) != cudaSuccess) {
       cudaGetLastError();
       return VOFP_ERR_OOM;
     }
@@ -606,7 +606,7 @@ int ensure_geometry(vofp_plan* p) {
   if (p->G) return VOFP_OK;
   const size_t cells = (size_t)p->n[0] * p->n[1] * p->n[2];
   void* m = nullptr;
-  if (cudaMalloc(&m, 4 * sizeof(double) * cells) != cudaSuccess) {
+  if (device_alloc(&m, 4 * sizeof(double) * cells) != cudaSuccess) {
     cudaGetLastError();
     return VOFP_ERR_OOM;
   }

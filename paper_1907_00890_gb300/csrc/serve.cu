@@ -390,7 +390,7 @@ extern "C" int vofp_server_create(size_t mem_budget_bytes, int max_inflight, con
     mem_budget_bytes = fr / 2;
   }
   s->arena_bytes = mem_budget_bytes & ~(size_t)255;
-  if (cudaMalloc((void**)&s->arena, s->arena_bytes) != cudaSuccess) {
+  if (device_alloc((void**)&s->arena, s->arena_bytes) != cudaSuccess) {
     cudaGetLastError();
     delete s;
     return VOFP_ERR_OOM;
@@ -398,17 +398,29 @@ extern "C" int vofp_server_create(size_t mem_budget_bytes, int max_inflight, con
   s->free_list[0] = s->arena_bytes;
   s->in_use = 0;
   s->slots.resize(max_inflight);
+  bool staged = true;
   for (auto& sl : s->slots) {
     cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
     cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
     sl.req = nullptr;
     sl.stage_bytes = 4 << 20;
-    if (cudaMallocHost((void**)&sl.stage, sl.stage_bytes) != cudaSuccess) {
+    if (!staged || pinned_alloc((void**)&sl.stage, sl.stage_bytes) != cudaSuccess) {
       cudaGetLastError();
       sl.stage = nullptr;
       sl.stage_bytes = 0;
+      staged = false;
     }
     sl.busy = false;
+  }
+  if (!staged) {  // every slot needs its pinned staging buffer for the plan uploads: give everything back
+    for (auto& sl : s->slots) {
+      cudaStreamDestroy(sl.st);
+      cudaEventDestroy(sl.done);
+      if (sl.stage) cudaFreeHost(sl.stage);
+    }
+    cudaFree(s->arena);
+    delete s;
+    return VOFP_ERR_OOM;
   }
   s->next_id = 1;
   s->stop = false;

@@ -519,7 +519,7 @@ static int ensure_host_step(vofp_plan* pl, HostStep** out) {
   h->nw = (size_t)nx * ny * nface(nz, pl->bc[2]);
   h->cells = (size_t)nx * ny * nz;
   const size_t faces = h->nu + h->nv + h->nw;
-  if (cudaMalloc((void**)&h->buf, sizeof(double) * (3 * faces + 4 * h->cells)) != cudaSuccess) {
+  if (device_alloc((void**)&h->buf, sizeof(double) * (3 * faces + 4 * h->cells)) != cudaSuccess) {
     cudaGetLastError();
     delete h;
     return VOFP_ERR_OOM;

@@ -41,6 +41,11 @@ struct TraceTok {
 void trace_begin(int kid, cudaStream_t st, TraceTok* tok);
 void trace_end(TraceTok* tok, cudaStream_t st);
 
+// Every device (and pinned host) block the library allocates goes through these: cudaMalloc /
+// cudaMallocHost, or an injected failure (vofp_debug_fail_alloc).
+cudaError_t device_alloc(void** p, size_t bytes);
+cudaError_t pinned_alloc(void** p, size_t bytes);
+
 // Count `n` kernel launches (read by vofp_launch_count).
 void note_launches(int n);
 // Graph capture on this thread: launches are counted apart and not traced; capture_end returns their number.

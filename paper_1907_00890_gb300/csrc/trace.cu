@@ -55,9 +55,41 @@ void trace_end(TraceTok* tok, cudaStream_t st) {
   g_recs.push_back({tok->kid, tok->a, tok->b});
 }
 
+// Allocation-failure injection (tests of the out-of-memory paths without exhausting a GPU): while
+// g_fail_after = k >= 0, the next k allocations succeed and the one after fails, once.
+static std::atomic<long long> g_fail_after{-1};
+
+static bool inject_failure() {
+  long long v = g_fail_after.load();
+  while (v >= 0)
+    if (g_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;
+  return false;
+}
+
+cudaError_t device_alloc(void** p, size_t bytes) {
+  if (inject_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t pinned_alloc(void** p, size_t bytes) {
+  if (inject_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(p, bytes);
+}
+
 }  // namespace vofp
 
 using namespace vofp;
+
+extern "C" int vofp_debug_fail_alloc(long long after) {
+  g_fail_after.store(after < 0 ? -1 : after);
+  return VOFP_OK;
+}
 
 extern "C" int vofp_trace_enable(int on) {
   const int prev = g_on.exchange(on ? 1 : 0);

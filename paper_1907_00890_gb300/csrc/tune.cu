@@ -85,6 +85,7 @@ bool fits(const vofp_plan* p, const Shape& s) {
   const size_t r = f32 ? sizeof(float) : sizeof(double);
   const size_t lim = 160 * 1024;
   const int sx = vofp::fft_span(p->ax[0].fd, p->ax[0].blu64), sy = vofp::fft_span(p->ax[1].fd, p->ax[1].blu64);
+  if (s.xpb < 1 || s.xpb > vofp::kMaxPB) return false;  // the x passes keep per-line tables of 2 kMaxPB
   if (2 * (size_t)s.xpb * sx * c > lim) return false;
   if (2 * (size_t)(s.ytx / 2) * vofp::y_ld(sy) * c > lim) return false;
   if (s.zti > 128) return false;  // at most 128 systems per block

@@ -112,6 +112,9 @@ __device__ __forceinline__ bool launch_skipped(const double* conv, int j, double
   return refine_done(conv, j, tol2);
 }
 
+// Most line pairs per block of an x pass (the plan's default takes at most 16, the tuner at most 32).
+constexpr int kMaxPB = 32;
+
 // ---- FFT descriptor ----------------------------------------------------------------------------------
 
 struct FftDesc {
@@ -312,8 +315,58 @@ __device__ __forceinline__ void fft_stage_odd(C* __restrict__ src, C* __restrict
   }
 }
 
+// The same stage for a power-of-two n: every index is a shift or a mask of the thread's item number (no
+// integer division by a runtime length, which costs the reduced-precision passes more issue slots than their
+// butterflies).
+template <typename C, int RAD>
+__device__ __forceinline__ void fft_stage_p2(const C* __restrict__ src, C* __restrict__ dst, int batch, int lgn,
+                                             int lgNs, const C* __restrict__ tw, int ld) {
+  constexpr int lgR = RAD == 8 ? 3 : (RAD == 4 ? 2 : 1);
+  const int lgNR = lgn - lgR;
+  const int mNR = (1 << lgNR) - 1;
+  const int mNs = (1 << lgNs) - 1;
+  const int lgtw = lgn - lgNs - lgR;  // twiddle step n / (Ns RAD)
+  const int total = batch << lgNR;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int bi = t >> lgNR;
+    const int j = t & mNR;
+    const C* s = src + bi * ld;
+    C* d = dst + bi * ld;
+    const int k = j & mNs;
+    C v[RAD];
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[r] = s[j + (r << lgNR)];
+    if (k != 0) {
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], tw[(r * k) << lgtw]);
+    }
+    dft_small<C, RAD>(v);
+    const int base = ((j - k) << lgR) + k;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) d[base + (r << lgNs)] = v[r];
+  }
+}
+
 template <typename C>
 __device__ C* fft_stages(C* a, C* b, int batch, int n, int nst, const int* radix, const C* __restrict__ tw, int ld) {
+  if constexpr (!std::is_same<C, double2>::value) {
+    if ((n & (n - 1)) == 0) {  // radices 8, 4, 2 only: the shift-and-mask stages
+      const int lgn = 31 - __clz(n);
+      int lgNs = 0;
+      for (int s = 0; s < nst; ++s) {
+        const int R = radix[s];
+        if (R == 8) fft_stage_p2<C, 8>(a, b, batch, lgn, lgNs, tw, ld);
+        else if (R == 4) fft_stage_p2<C, 4>(a, b, batch, lgn, lgNs, tw, ld);
+        else fft_stage_p2<C, 2>(a, b, batch, lgn, lgNs, tw, ld);
+        __syncthreads();
+        C* t = a;
+        a = b;
+        b = t;
+        lgNs += R == 8 ? 3 : (R == 4 ? 2 : 1);
+      }
+      return a;
+    }
+  }
   int Ns = 1;
   for (int s = 0; s < nst; ++s) {
     const int R = radix[s];
@@ -469,13 +522,14 @@ __device__ __forceinline__ void split_two(const C* Z, int n, int m, C& A, C& B) 
 
 // Forward post-processing: spectral output q of both lines from the FFT result Z, returned TWICE the
 // transform (2A, 2B of split_two without the halving; the z pass folds the factor into its scale).
+// `es`: element stride of the line in Z (1: contiguous; the TMA y pass keeps its lines element-major).
 template <typename C>
 __device__ __forceinline__ void fwd_post(const C* Z, int n, int bc, int q, const C* __restrict__ quart,
-                                         decltype(C::x)& oa, decltype(C::x)& ob) {
+                                         decltype(C::x)& oa, decltype(C::x)& ob, int es = 1) {
   if (quarter_bc(bc)) {
     // 2 W_a = Z[q] + conj Z[n-1-q], 2 W_b = (Z[q] - conj Z[n-1-q]) / i; outputs Re(w 2W) with the post-twiddle
-    const C P = Z[q];
-    const C Q = Z[n - 1 - q];
+    const C P = Z[q * es];
+    const C Q = Z[(n - 1 - q) * es];
     const C w = quart[n + q];
     oa = w.x * (P.x + Q.x) - w.y * (P.y - Q.y);
     ob = w.x * (P.y + Q.y) - w.y * (Q.x - P.x);
@@ -485,8 +539,8 @@ __device__ __forceinline__ void fwd_post(const C* Z, int n, int bc, int q, const
     }
   } else if (bc == VOFP_BC_P) {
     const int m = (q + 1) >> 1;
-    const C P = Z[m];
-    const C Q = Z[m == 0 ? 0 : n - m];
+    const C P = Z[m * es];
+    const C Q = Z[(m == 0 ? 0 : n - m) * es];
     if ((q == 0) || (q & 1)) {  // real parts
       oa = P.x + Q.x;
       ob = P.y + Q.y;
@@ -496,8 +550,8 @@ __device__ __forceinline__ void fwd_post(const C* Z, int n, int bc, int q, const
     }
   } else {
     const int m = (bc == VOFP_BC_DD) ? (n - 1 - q) : q;
-    const C P = Z[m];
-    const C Q = Z[m == 0 ? 0 : n - m];
+    const C P = Z[m * es];
+    const C Q = Z[(m == 0 ? 0 : n - m) * es];
     const C w = quart[m];
     // Re(w * 2A) and Re(w * 2B)
     oa = w.x * (P.x + Q.x) - w.y * (P.y - Q.y);
@@ -566,7 +620,7 @@ struct vofp_devinfo {
   double res2;     // mixed: ||f - L p||^2
   double f2;       // mixed: ||f||^2
   unsigned int nonfinite;
-  unsigned int pad;
+  unsigned int timeout;  // a bounded device wait (TMA tile load) gave up
 };
 
 struct vofp_plan {
@@ -608,6 +662,11 @@ struct vofp_plan {
   double2* lowtab;     // bounded z: their Thomas factors (k-major), NULL for periodic z
   void* low_block;     // allocation holding lowmodes and lowscratch
   int ytx32, zti32;    // launch shapes of the FP32 y and z passes
+  // TMA-staged y pass of the reduced-precision spectra (set up on first use): state 0 = not yet examined,
+  // 1 = in use, -1 = not applicable (or switched off by VOFP_Y_TMA=0); its tile width, persistent grid and the
+  // encoded tensor map (a CUtensorMap, kept as bytes)
+  int ytma_state, ytma_lgB, ytma_grid;
+  unsigned char ytma_map[128];
   // workspace
   double* S;   // spectrum, nx*ny*nz (FP64 path)
   double* P;   // potential scratch when the caller passes none

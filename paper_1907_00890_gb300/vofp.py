@@ -71,13 +71,20 @@ _lib.vofp_trace_name.argtypes = [_I]
 _lib.vofp_trace_name.restype = ctypes.c_char_p
 _lib.vofp_launch_count.argtypes = []
 _lib.vofp_launch_count.restype = ctypes.c_ulonglong
+_lib.vofp_debug_fail_alloc.argtypes = [ctypes.c_longlong]
+_lib.vofp_debug_fail_alloc.restype = _I
 _lib.vofp_error_string.argtypes = [_I]
 _lib.vofp_error_string.restype = ctypes.c_char_p
 
 EXPORTED = ["vofp_opts_default", "vofp_plan_create", "vofp_plan_destroy", "vofp_plan_workspace_bytes",
             "vofp_poisson_solve", "vofp_project", "vofp_extend_liquid_velocity", "vofp_error_string",
             "vofp_stefan_source", "vofp_project_stefan", "vofp_launch_count", "vofp_trace_enable",
-            "vofp_trace_collect", "vofp_trace_kernel_classes", "vofp_trace_name"]
+            "vofp_trace_collect", "vofp_trace_kernel_classes", "vofp_trace_name", "vofp_debug_fail_alloc"]
+
+
+def vofp_debug_fail_alloc(after):
+    """Make the (after + 1)-th next device / pinned allocation of the library fail once (after < 0: off)."""
+    return _lib.vofp_debug_fail_alloc(int(after))
 
 
 _lib.vofp_project_extend.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P,
