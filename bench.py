@@ -522,7 +522,8 @@ def _serve_stream(vofp, torch, prec, max_refine, rate, warm, dur, runs, bufs, se
             "value": st["cells"] / st["seconds"] / 1e6, "unit": UNIT, "completed": int(st["completed"]),
             "rejected": int(st["rejected"]), "late_submissions": late,
             "plan_hits": int(st["plan_hits"]), "plan_misses": int(st["plan_misses"]),
-            "resident_plans": int(st["resident_plans"])}
+            "plan_evictions": int(st["plan_evictions"]), "resident_plans": int(st["resident_plans"]),
+            "worker_prepare_s": round(st["worker_prepare_s"], 3), "worker_launch_s": round(st["worker_launch_s"], 3)}
 
 
 SERVE_SLO_P99_MS = 100.0

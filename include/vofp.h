@@ -259,8 +259,9 @@ int vofp_project_extend_host(vofp_plan* plan, const double* u, const double* v, 
  * solver runs one instance, so this is the data-parallel form of vofp_project).  plans[0..n-1]: distinct
  * VOFP_MIXED plans on one device (each plan's workspace serves exactly one instance).  Every pass of the
  * mixed-precision projection runs as one launch over all instances and the whole sequence is captured once
- * into a CUDA graph and replayed per call.  Each instance's result is bitwise identical to running it alone
- * in a batch of one.
+ * into a CUDA graph and replayed per call.  Each instance runs the same kernels on the same data as in a batch
+ * of one, so its result agrees with running it alone to rounding (1e-12 in the tests) -- not bit for bit: the
+ * FP64 block partials of its norms and means are added with atomics, in an order that varies between runs.
  * Errors: INVALID_ARG (NULL, n < 1, repeated plan, mixed devices), UNSUPPORTED (an FP64 plan), OOM.
  */
 typedef struct vofp_batch vofp_batch;

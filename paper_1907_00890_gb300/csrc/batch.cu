@@ -7,7 +7,9 @@
 // with their device-side convergence tests, the gauge restoration and the velocity correction -- is captured
 // once into a CUDA graph and replayed per call; a call only refreshes the per-instance argument records
 // when the field pointers change.  Instances are independent and no kernel choice of one depends on the
-// others, so an instance's result is bitwise the same alone and in any batch.
+// others, so an instance runs the same arithmetic alone and in any batch; its results agree to rounding, not
+// bit for bit, because the FP64 block partials of its norms and means are added with atomics in an order
+// that varies from run to run.
 #include <cmath>
 #include <cstring>
 #include <vector>

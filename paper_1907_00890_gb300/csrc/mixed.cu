@@ -285,6 +285,7 @@ static void xinv_red(vofp_plan* pl, double* pout, int accumulate, int skip_k, do
   // FP32-pair transforms keep the zero-mean gauge of the pinned mean mode to ~1e-14 and need no shift
   xi.mean_out = (pout && pl->singular && pl->opts.prec == VOFP_MIXED) ? pl->conv + VOFP_CONV_MEAN : nullptr;
   xi.d2_out = d2_out;
+  if (std::is_same<R, float>::value && xtc_xinv(pl, xi, st)) return;  // tensor-core transform
   const int xgrid = xpass_blocks(xi.ny, xi.nz, xi.pb);
   const size_t xsm = 2 * (size_t)xi.pb * fft_span(xi.fd, xi.blu) * sizeof(C);
   VOFP_LAUNCH(KID_XINV, st, (xinv_kernel<R, C>()<<<xgrid, 256, xsm, st>>>(xi)));
@@ -300,6 +301,7 @@ static void xfwd_red(vofp_plan* pl, int mode, XArgs xa, cudaStream_t st) {
   xa.blu = Red<R>::blu(pl->ax[0]);
   xa.pb = pl->xpb;
   xa.S = pl->S32;
+  if (std::is_same<R, float>::value && xtc_xfwd(pl, mode, xa, st)) return;  // tensor-core transform
   const int xgrid = xpass_blocks(pl->n[1], pl->n[2], xa.pb);
   const size_t xsm = 2 * (size_t)xa.pb * fft_span(xa.fd, xa.blu) * sizeof(C);
   switch (mode) {

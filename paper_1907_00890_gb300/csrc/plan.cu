@@ -417,6 +417,13 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
     L.T = off;
     off = align256(off + tsz * (size_t)Ux * Uy * nz);
   }
+  // FP32 refinement plans: the x transform matrices of the tensor-core x passes
+  L.xtc = 0;
+  const size_t xb = xtc_table_bytes(nx, (long)ny * nz, o.prec);
+  if (xb) {
+    L.xtc = off;
+    off = align256(off + xb);
+  }
   L.total = off;
   p->Ux = Ux;
   p->Uy = Uy;
@@ -589,6 +596,13 @@ int plan_bind(PlanPrep* pp, void* block, cudaStream_t st, unsigned char* stage) 
   if (p->lowtab) {
     const int s = build_low_factors(p, st, own);
     if (s) return s;
+  }
+  p->xtc_fwd = p->xtc_inv = nullptr;
+  p->xtc_grid = 0;
+  if (L.xtc) {
+    const int s = xtc_build(p, b + L.xtc, st);
+    if (s) return s;
+    if (own && cudaStreamSynchronize(st) != cudaSuccess) return VOFP_ERR_CUDA;
   }
   return VOFP_OK;
 }

@@ -140,6 +140,51 @@ int build_z_factors(vofp_plan* pl, cudaStream_t st, bool sync) {
   return VOFP_OK;
 }
 
+// The plan's FP64 x transform -- forward (as applied to a right-hand side) or inverse -- of `nlines` lines of
+// length nx from `in` into `out` (FP64, line-major).  The tensor-core x passes of the refinement plans take
+// their transform matrices from it (identity lines in), so they share every convention of the FFT passes.
+int fp64_x_lines(vofp_plan* pl, bool inverse, const double* in, double* out, int nlines, cudaStream_t st) {
+  const AxisDev& ax = pl->ax[0];
+  const int span = fft_span(ax.fd, ax.blu64);
+  int pb = pl->xpb;
+  while (pb > 1 && 2 * (size_t)pb * span * sizeof(double2) > 96 * 1024) --pb;
+  const int xgrid = xpass_blocks(nlines, 1, pb);
+  const size_t xsm = 2 * (size_t)pb * span * sizeof(double2);
+  if (!inverse) {
+    XArgs xa = {};
+    xa.g = grid_dev(pl);
+    xa.g.ny = nlines;
+    xa.g.nz = 1;
+    xa.fd = ax.fd;
+    xa.tw = ax.tw64;
+    xa.quart = ax.quart64;
+    xa.blu = ax.blu64;
+    xa.pb = pb;
+    xa.S = out;
+    xa.f = in;
+    xa.scale = 1.0;
+    xa.skip_k = -1;
+    VOFP_LAUNCH(KID_XFWD, st, k_xfwd_f64<RHS_F><<<xgrid, 256, xsm, st>>>(xa));
+  } else {
+    XInvArgs xi = {};
+    xi.skip_k = -1;
+    xi.nx = pl->n[0];
+    xi.ny = nlines;
+    xi.nz = 1;
+    xi.bc = pl->bc[0];
+    xi.fd = ax.fd;
+    xi.tw = ax.tw64;
+    xi.quart = ax.quart64;
+    xi.blu = ax.blu64;
+    xi.pb = pb;
+    xi.S = in;
+    xi.p = out;
+    xi.accumulate = 0;
+    VOFP_LAUNCH(KID_XINV, st, k_xinv_f64<0><<<xgrid, 256, xsm, st>>>(xi));
+  }
+  return cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
+}
+
 // x forward + y forward + z solve + y inverse + x inverse into `pout`.
 int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st, bool stats) {
   if (!pl->S) return VOFP_ERR_INVALID_ARG;  // a refinement plan has no FP64 spectrum

@@ -68,7 +68,7 @@ struct PlanLayout {
   size_t lam[2], tw[2], q[2], tw32[2], q32[2], twff[2], qff[2], blu64[2], blu32[2], bluff[2];
   size_t za, zb, zc, dz, hz, rdz, rhz, rzc, conv, info, low, za32, zaff, lowcut, kz, volf, dzff;
   size_t table_bytes;  // host-built part, uploaded as one copy
-  size_t P, S, T, S32, F, lowscr, lowtab;
+  size_t P, S, T, S32, F, lowscr, lowtab, xtc;
   size_t total;
 };
 struct PlanPrep {
@@ -88,6 +88,7 @@ int ensure_geometry(vofp_plan* p);
 void free_host_step(vofp_plan* p);
 
 struct XArgs;
+struct XInvArgs;
 struct GridDev;
 struct ZArgs;
 GridDev grid_dev(const vofp_plan* pl);
@@ -101,6 +102,14 @@ void init_kernel_attributes_mixed();
 // once per device and process, not on every plan).
 bool first_use_on_device(int which);
 int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st, bool stats);
+// The plan's FP64 x transform (forward, or inverse) of nlines lines `in` -> `out` (see solve.cu).
+int fp64_x_lines(vofp_plan* pl, bool inverse, const double* in, double* out, int nlines, cudaStream_t st);
+// Tensor-core x passes of FP32 refinement plans (xtc.cu): table sizes at plan preparation, the tables' build
+// at plan placement, and the passes themselves (false: not applicable, the caller runs the FFT pass).
+size_t xtc_table_bytes(int nx, long nlines, int prec);
+int xtc_build(vofp_plan* pl, void* tables, cudaStream_t st);
+bool xtc_xfwd(vofp_plan* pl, int mode, const XArgs& xa, cudaStream_t st);
+bool xtc_xinv(vofp_plan* pl, const XInvArgs& xi, cudaStream_t st);
 // Mixed-precision solve: FP32 transforms with FP64 defect correction.  `xa` carries the right-hand-side
 // inputs for RHS_DIV / RHS_DIV_STEFAN (NULL for RHS_F, which reads `f`).  Fills `info` (if non-NULL) and
 // synchronises the stream in that case.

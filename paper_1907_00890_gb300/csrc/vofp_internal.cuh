@@ -667,6 +667,11 @@ struct vofp_plan {
   // encoded tensor map (a CUtensorMap, kept as bytes)
   int ytma_state, ytma_lgB, ytma_grid;
   unsigned char ytma_map[128];
+  // tensor-core x passes of FP32 refinement plans: the forward and inverse x transform matrices (TF32 hi / lo,
+  // MMA operand layout) in the plan's memory, NULL when not used; persistent grid (0 = not yet sized)
+  float* xtc_fwd;
+  float* xtc_inv;
+  int xtc_grid;
   // workspace
   double* S;   // spectrum, nx*ny*nz (FP64 path)
   double* P;   // potential scratch when the caller passes none
