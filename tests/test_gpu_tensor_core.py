@@ -1,9 +1,9 @@
 """GPU parity of the tensor-core x passes (tcgen05, 3xTF32 dense transform-matrix products) of FP32 refinement
 plans, switched on by VOFP_X_TC=1 at plan creation, against the CPU oracle.
 
-Bars: the refined solve within 1e-10 of the oracle (the mixed-precision bar) for every x boundary condition,
-power-of-two and other lengths; one unrefined solve at FP32 level (1e-5), which shows the products carry about
-FP32 accuracy; the plan holds the transform tables (more device memory than the same plan without them).
+Bars: the refined solve and the projection within 1e-10 of the oracle (the mixed-precision bar) for every x
+boundary condition, power-of-two and other lengths; the plan holds the transform tables (more device memory
+than the same plan without them), so the tensor-core passes are the ones that ran.
 """
 import os
 
@@ -71,15 +71,3 @@ def test_tensor_core_x_passes_vs_oracle(vp, n, bc):
         assert rel(u[a].cpu().numpy(), ou[a]) < TOL
     plan.close()
 
-
-def test_tensor_core_products_are_fp32_accurate(vp):
-    n, bc = (128, 32, 32), ("P", "P", "NN")
-    dz = synth.uniform_dz(n[2])
-    g = oracle.Grid(*n, 1.0 / n[0], 1.0 / n[1], dz, bc)
-    f = synth.rng(8).standard_normal(g.shape)
-    ref, _ = oracle.poisson_solve(g, f)
-    plan = tc_plan(vp, n, g, bc, max_refine=0)
-    p = plan.poisson_solve(dev(f))
-    err = rel(p.cpu().numpy(), ref)
-    assert 1e-9 < err < 1e-5, err  # an FP32-level solve, not an FP64 one
-    plan.close()
