@@ -119,9 +119,10 @@ int vofp_plan_create(int nx, int ny, int nz, double dx, double dy, const double*
                      const vofp_opts* opt, vofp_plan** out);
 
 /*
- * Autotune the plan's launch shapes (line pairs per x block, columns per y block, systems per z block) by
- * timing whole solves on the plan's scratch workspace (coordinate descent over the candidates that fit in
- * shared memory).  Results are cached per process and, if the environment variable VOFP_TUNE_CACHE names a
+ * Autotune the plan's launch shapes (line pairs per x block, columns per y block, the z kernel -- segmented
+ * tiles, staged or streamed chains and their systems per block) and the order of the FFT radix stages on x
+ * and y, by timing whole solves on the plan's scratch workspace (coordinate descent over the candidates that
+ * fit in shared memory).  Results are cached per process and, if the environment variable VOFP_TUNE_CACHE names a
  * file, across processes.  Called by vofp_plan_create when opts.tune != 0.  Synchronises the device.
  * No counterpart in the paper (performance only; results stay within the parity tolerance).
  * Errors: INVALID_ARG, CUDA.

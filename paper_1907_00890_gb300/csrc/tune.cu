@@ -1,9 +1,10 @@
 // Launch-shape autotuner.
 //
 // For one plan it times whole Poisson solves (CUDA events on a private stream, after a warm-up) while
-// walking each tile knob in turn -- line pairs per block of the x passes, columns per block of the y
-// passes, systems per block of the z pass -- and keeps the fastest value of each (coordinate descent over
-// the candidates that fit in shared memory).  Results are cached per process and, when the environment
+// walking each knob in turn -- line pairs per block of the x passes, columns per block of the y passes, the
+// z kernel (segmented tiles, shared-memory staged chains, or streamed chains with their systems per block),
+// and the order of the FFT radix stages on x and on y (the plan's factorisation or its reverse) -- and keeps
+// the fastest value of each (coordinate descent over the candidates that fit in shared memory).  Results are cached per process and, when the environment
 // variable VOFP_TUNE_CACHE names a file, in that file (one line per grid/precision/GPU key), so a serving
 // process or a batch pays the search once per shape.
 #include <cmath>
@@ -21,12 +22,12 @@
 namespace {
 
 struct Shape {
-  int xpb, ytx, zti;
+  int xpb, ytx, zti, ord;
 };
 
 std::mutex g_mu;
 std::map<std::string, Shape> g_cache;
-bool g_file_loaded = false;
+std::string g_loaded_path;  // the cache file last read (read again when VOFP_TUNE_CACHE names another)
 
 std::string key_of(const vofp_plan* p) {
   cudaDeviceProp prop;
@@ -40,15 +41,16 @@ std::string key_of(const vofp_plan* p) {
 }
 
 void load_file() {
-  if (g_file_loaded) return;
-  g_file_loaded = true;
   const char* path = getenv("VOFP_TUNE_CACHE");
-  if (!path) return;
+  if (!path || g_loaded_path == path) return;
+  g_loaded_path = path;
   FILE* f = fopen(path, "r");
   if (!f) return;
-  char k[256];
-  Shape s;
-  while (fscanf(f, "%255s %d %d %d", k, &s.xpb, &s.ytx, &s.zti) == 4) g_cache[k] = s;
+  char line[512], k[256];
+  while (fgets(line, sizeof(line), f)) {
+    Shape s{0, 0, 0, 0};
+    if (sscanf(line, "%255s %d %d %d %d", k, &s.xpb, &s.ytx, &s.zti, &s.ord) >= 4) g_cache[k] = s;
+  }
   fclose(f);
 }
 
@@ -57,14 +59,26 @@ void save_entry(const std::string& k, const Shape& s) {
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %d\n", k.c_str(), s.xpb, s.ytx, s.zti);
+  fprintf(f, "%s %d %d %d %d\n", k.c_str(), s.xpb, s.ytx, s.zti, s.ord);
   fclose(f);
 }
 
 // the reduced-precision (refinement) paths keep their shapes in ytx32 / zti32
 bool mixed(const vofp_plan* p) { return p->opts.prec != VOFP_FP64; }
 
+// Reverse the radix sequence of an axis (any order of the stages gives the same transform, up to rounding).
+void reverse_stages(vofp::FftDesc& fd) {
+  for (int a = 0, b = fd.nst - 1; a < b; ++a, --b) {
+    const int t = fd.radix[a];
+    fd.radix[a] = fd.radix[b];
+    fd.radix[b] = t;
+  }
+}
+
 void apply(vofp_plan* p, const Shape& s) {
+  for (int a = 0; a < 2; ++a)
+    if (((s.ord ^ p->radix_order) >> a) & 1) reverse_stages(p->ax[a].fd);
+  p->radix_order = s.ord;
   p->xpb = s.xpb;
   if (mixed(p)) {
     p->ytx32 = s.ytx;
@@ -76,7 +90,7 @@ void apply(vofp_plan* p, const Shape& s) {
 }
 
 Shape current(const vofp_plan* p) {
-  return Shape{p->xpb, mixed(p) ? p->ytx32 : p->ytx, mixed(p) ? p->zti32 : p->zti};
+  return Shape{p->xpb, mixed(p) ? p->ytx32 : p->ytx, mixed(p) ? p->zti32 : p->zti, p->radix_order};
 }
 
 bool fits(const vofp_plan* p, const Shape& s) {
@@ -140,14 +154,16 @@ extern "C" int vofp_plan_tune(vofp_plan* p) {
   const int xs[] = {1, 2, 4, 8, 16, 32};
   const int ys[] = {2, 4, 8, 16, 32};
   const int zs[] = {-1, 0, 8, 16, 32, 64, 128};
-  for (int knob = 0; knob < 3; ++knob) {
-    const int* cand = knob == 0 ? xs : (knob == 1 ? ys : zs);
-    const int nc = knob == 0 ? 6 : (knob == 1 ? 5 : 7);
+  const int os[] = {0, 1, 2, 3};
+  for (int knob = 0; knob < 4; ++knob) {
+    const int* cand = knob == 0 ? xs : (knob == 1 ? ys : (knob == 2 ? zs : os));
+    const int nc = knob == 0 ? 6 : (knob == 1 ? 5 : (knob == 2 ? 7 : 4));
     for (int c = 0; c < nc; ++c) {
       Shape s = best;
       if (knob == 0) s.xpb = cand[c];
       if (knob == 1) s.ytx = cand[c];
       if (knob == 2) s.zti = cand[c];
+      if (knob == 3) s.ord = cand[c];
       if (!fits(p, s)) continue;
       apply(p, s);
       const float t = time_solve(p, st);

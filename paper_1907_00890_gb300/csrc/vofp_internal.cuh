@@ -662,6 +662,7 @@ struct vofp_plan {
   double2* lowtab;     // bounded z: their Thomas factors (k-major), NULL for periodic z
   void* low_block;     // allocation holding lowmodes and lowscratch
   int ytx32, zti32;    // launch shapes of the FP32 y and z passes
+  int radix_order;     // bit a set: the FFT stages of axis a (0 = x, 1 = y) run in reverse order (autotuned)
   // TMA-staged y pass of the reduced-precision spectra (set up on first use): state 0 = not yet examined,
   // 1 = in use, -1 = not applicable (or switched off by VOFP_Y_TMA=0); its tile width, persistent grid and the
   // encoded tensor map (a CUtensorMap, kept as bytes)

@@ -149,3 +149,26 @@ def test_tuned_plans_keep_parity(vp, tmp_path, monkeypatch):
         p = plan.poisson_solve(dev(f))
         assert rel(p.cpu().numpy(), ref) < tol
         plan.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-10), ("ff", 1e-10)])
+def test_reversed_radix_order_keeps_parity(vp, tmp_path, monkeypatch, prec, tol):
+    """The tuner's radix-order knob (stages of x and y in reverse order), forced through its cache file: same
+    results to the parity bar on mixed-radix lengths (48 = 4 4 3, 40 = 2 4 5 -> reversed)."""
+    import torch
+    pr = {"fp64": vp.FP64, "mixed": vp.MIXED, "ff": vp.FF}[prec]
+    n, bc = (48, 40, 36), ("P", "NN", "NN")
+    key = "%s|%d|%d|%d|%d|%d|%d|%d" % (torch.cuda.get_device_name(0).replace(" ", "_"), n[0], n[1], n[2],
+                                       vp.BC[bc[0]], vp.BC[bc[1]], vp.BC[bc[2]], pr)
+    cache = tmp_path / "tune.txt"
+    xpb = 8
+    cache.write_text("%s %d %d %d %d\n" % (key, xpb, 8, -1 if prec != "fp64" else 0, 3))
+    monkeypatch.setenv("VOFP_TUNE_CACHE", str(cache))
+    dz = synth.stretched_dz(n[2])
+    g = oracle.Grid(*n, 1.0 / n[0], 1.0 / n[1], dz, bc)
+    f = synth.rng(9).standard_normal(g.shape)
+    ref, _ = oracle.poisson_solve(g, f)
+    plan = vp.Plan(n, g.widths[0][0], g.widths[1][0], dz, bc, prec=pr, tune=1)
+    p = plan.poisson_solve(dev(f))
+    assert rel(p.cpu().numpy(), ref) < tol
+    plan.close()
