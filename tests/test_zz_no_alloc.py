@@ -3,8 +3,9 @@
 ``vofp_poisson_solve_noalloc`` is for callers that cannot call cudaMalloc at solve time (for instance a host
 code whose device memory is handed out entirely by its own pool allocator, or a time-stepping loop that must
 not pay cudaMalloc's implicit synchronisation): it keeps its workspace in a fixed device array of the
-library.  Two calls in a row, on different grids, must each reproduce ``vofp_poisson_solve`` within the FP64
-parity tolerance, so nothing left in the shared array by the first call leaks into the second.  This file is
+library.  Calls in a row, on different grids up to the array's limits, must each reproduce
+``vofp_poisson_solve`` within the FP64 parity tolerance, so nothing left in the shared array by one call
+leaks into the next.  This file is
 collected last so that a run stopping at the first failure has already run every other test.
 """
 import ctypes
@@ -46,7 +47,12 @@ def _noalloc(vp, n, dx, dy, dz, bc, f, p):
 
 def test_noalloc_matches_plan_solve_twice_in_a_row(vp):
     import torch
-    cases = [((32, 32, 32), ("P", "P", "NN"), False, 1), ((20, 12, 9), ("DD", "NN", "DN"), True, 2)]
+    # two grids in a row, then the declared limits: odd prime lengths (rolled odd-prime stages, no Bluestein
+    # tables in the static array), 1024-cell x and y axes, and the full 2 Mi cells
+    cases = [((32, 32, 32), ("P", "P", "NN"), False, 1), ((20, 12, 9), ("DD", "NN", "DN"), True, 2),
+             ((31, 13, 10), ("P", "DD", "NN"), True, 3), ((17, 19, 6), ("NN", "P", "P"), False, 4),
+             ((1024, 16, 8), ("P", "P", "NN"), True, 5), ((16, 1024, 8), ("NN", "P", "DD"), False, 6),
+             ((128, 128, 128), ("P", "P", "NN"), True, 7)]
     for n, bc, stretched, seed in cases:
         dz = synth.stretched_dz(n[2]) if stretched else synth.uniform_dz(n[2])
         dx, dy = 1.0 / n[0], 0.8 / n[1]
