@@ -220,7 +220,7 @@ def bench_vof(vofp, c, u0, C, md, st, flush, args):
     if "vof_update" in trace:
         tot, cnt = trace["vof_update"]
         hbm, how = peaks()
-        gbs = 40 * cells / (tot / (cnt / 3) / 1e3) / 1e9  # three launches per update
+        gbs = 40 * cells / (tot / cnt / 1e3) / 1e9  # one launch per update (the fused pass)
         r["roofline_vof_update"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                                     "frac": gbs / hbm, "bytes_per_cell": 40, "peak_source": how}
     plan.close()

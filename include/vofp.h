@@ -203,7 +203,8 @@ int vofp_extend_vapour_velocity(vofp_plan* plan, const double* u, const double* 
  * fluxes are first-order upwind ones (the paper takes MTHINC fluxes from its reference; beyond a bounded end
  * the boundary cell is used).  C: device cell array (input); uG, vG, wG: device face arrays; dt > 0 (the
  * implicit factors 1 - dt du/dx etc. must stay positive: a Courant condition); C_out: device cell array
- * (may be C); work: device workspace of 2 * nx * ny * nz doubles, disjoint from C and C_out.
+ * (may be C); work: device workspace of 2 * nx * ny * nz doubles, disjoint from C and C_out (used only when
+ * C_out is C: the result is formed there and copied back).  One FP64 pass marching through the z planes.
  * Errors: INVALID_ARG, CUDA.
  */
 int vofp_vof_update(vofp_plan* plan, const double* C, const double* uG, const double* vG, const double* wG,

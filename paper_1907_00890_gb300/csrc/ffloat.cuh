@@ -149,6 +149,12 @@ __device__ __forceinline__ double recip_newton(double x) {
   return fma(y, fma(-x, y, 1.0), y);
 }
 
+// The same with one Newton step: relative error about 2^-46 (1.4e-14), two FP64 multiply-adds.
+__device__ __forceinline__ double recip_newton1(double x) {
+  const double y = f64_of_bits(__frcp_rn(f32_lead_bits(x)));
+  return fma(y, fma(-x, y, 1.0), y);
+}
+
 // Reduced-precision value <-> double with the conversions above (one FP64 addition for a pair).
 __device__ __forceinline__ float red_of(double d, float*) { return f32_lead_bits(d); }
 __device__ __forceinline__ ff red_of(double d, ff*) { return ff_split(d); }

@@ -12,6 +12,7 @@
 #include <cudaTypedefs.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -20,6 +21,7 @@
 
 #include "passes.cuh"
 #include "solve_internal.h"
+#include "xinv_tma.cuh"
 #include "ypass_tma.cuh"
 #include "zsolve.cuh"
 
@@ -50,6 +52,22 @@ static void allow_all() {
 // Shared memory a TMA y-pass CTA may take (of the 227 KiB an sm_103a CTA can opt into).
 static const int kYTmaSmem = 225 * 1024;
 
+// The TMA inverse x-pass kernel for nx = 2^lgn (7, 8 or 9), with the tile (2^lgB complex lines) that fills
+// about 130 KB of shared memory; NULL for other lengths.
+typedef void (*XTmaKernel)(const XTmaArgs, const CUtensorMap, const CUtensorMap);
+template <typename R>
+static int xtma_lgB(int lgn) {
+  return std::is_same<R, float>::value ? (lgn >= 9 ? 3 : 4) : (lgn >= 9 ? 2 : (lgn == 8 ? 3 : 4));
+}
+template <typename R>
+static XTmaKernel xtma_kernel(int lgn) {
+  constexpr bool F = std::is_same<R, float>::value;
+  if (lgn == 9) return F ? k_xinv_tma<R, 9, 3> : k_xinv_tma<R, 9, 2>;
+  if (lgn == 8) return F ? k_xinv_tma<R, 8, 4> : k_xinv_tma<R, 8, 3>;
+  if (lgn == 7) return k_xinv_tma<R, 7, 4>;
+  return nullptr;
+}
+
 // The TMA y-pass kernel for a length 2^lgn and 2^lgB lines per tile: compiled for ny = 128, 256, 512 with the
 // tile width ytma_setup picks for them, else the version that reads both from its arguments.
 typedef void (*YTmaKernel)(const YTmaArgs, const CUtensorMap);
@@ -72,7 +90,13 @@ void init_kernel_attributes_mixed() {
       for (int lgB = 2; lgB <= 4; ++lgB) {
         cudaFuncSetAttribute(ytma_kernel<float>(inv, lgn, lgB), cudaFuncAttributeMaxDynamicSharedMemorySize, kYTmaSmem);
         cudaFuncSetAttribute(ytma_kernel<ff>(inv, lgn, lgB), cudaFuncAttributeMaxDynamicSharedMemorySize, kYTmaSmem);
+        cudaFuncSetAttribute(ytma_kernel<double>(inv, lgn, lgB), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kYTmaSmem);
       }
+  for (int lgn = 7; lgn <= 9; ++lgn) {
+    cudaFuncSetAttribute(xtma_kernel<float>(lgn), cudaFuncAttributeMaxDynamicSharedMemorySize, kYTmaSmem);
+    cudaFuncSetAttribute(xtma_kernel<ff>(lgn), cudaFuncAttributeMaxDynamicSharedMemorySize, kYTmaSmem);
+  }
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link against the driver library).
@@ -98,12 +122,16 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // or 2) whose three buffers fit, the persistent grid (resident CTAs x SMs, at most one CTA per tile) and the
 // tensor map over the plan's spectrum.
 template <typename R>
-static void ytma_setup(vofp_plan* pl) {
+static void ytma_setup(vofp_plan* pl, void* spectrum) {
   pl->ytma_state = -1;
   const char* env = getenv("VOFP_Y_TMA");
   if (env && env[0] == '0') return;
   const int nx = pl->n[0], ny = pl->n[1], nz = pl->n[2];
   if (ny < 8 || ny > 4096 || (ny & (ny - 1)) || ((size_t)nx * sizeof(R)) % 16) return;
+  // FP64 spectra only from ny = 256: their passes are bound by the FP64 pipe, and at ny = 128 (under two tiles
+  // per persistent CTA) the gather kernel was measured faster (128^3 droplet step 0.825 against 0.850 ms); at
+  // 512^3 the tiles win by 9% per pass
+  if (std::is_same<R, double>::value && ny < 256) return;
   int lgB = -1;
   for (int lb = 4; lb >= 2 && lgB < 0; --lb)
     if ((2 << lb) <= nx && ytma_smem_bytes(ny, lb, 2 * sizeof(R)) <= (size_t)kYTmaSmem) lgB = lb;
@@ -116,7 +144,7 @@ static void ytma_setup(vofp_plan* pl) {
   const cuuint32_t box[2] = {(cuuint32_t)(2 << lgB), (cuuint32_t)(ny < 256 ? ny : 256)};
   const cuuint32_t estr[2] = {1, 1};
   const CUtensorMapDataType dt = sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-  if (enc(&tm, dt, 2, pl->S32, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+  if (enc(&tm, dt, 2, spectrum, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return;
   const size_t sm = ytma_smem_bytes(ny, lgB, 2 * sizeof(R));
@@ -137,10 +165,87 @@ static void ytma_setup(vofp_plan* pl) {
   pl->ytma_state = 1;
 }
 
+// First use of the TMA inverse x pass: nx of 128, 256 or 512 (VOFP_X_TMA=0 switches it off); the tensor map
+// views the spectrum as {min(nx, 256), nx / min(nx, 256), ny nz} so that one box is a tile of whole lines.
+template <typename R>
+static void xtma_setup(vofp_plan* pl) {
+  pl->xtma_state = -1;
+  const char* env = getenv("VOFP_X_TMA");
+  if (env && env[0] == '0') return;
+  const int nx = pl->n[0];
+  if (nx != 128 && nx != 256 && nx != 512) return;
+  const int lgn = 31 - __builtin_clz((unsigned)nx), lgB = xtma_lgB<R>(lgn);
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return;
+  const int h = nx < 256 ? nx : 256;
+  const long nlines = (long)pl->n[1] * pl->n[2];
+  CUtensorMap tm;
+  const cuuint64_t dims[3] = {(cuuint64_t)h, (cuuint64_t)(nx / h), (cuuint64_t)nlines};
+  const cuuint64_t strides[2] = {(cuuint64_t)h * sizeof(R), (cuuint64_t)nx * sizeof(R)};
+  const cuuint32_t box[3] = {(cuuint32_t)h, (cuuint32_t)(nx / h), (cuuint32_t)(2 << lgB)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUtensorMapDataType dt = sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  if (enc(&tm, dt, 3, pl->S32, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return;
+  int per_sm = 0, nsm = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xtma_kernel<R>(lgn), kXTmaThreads,
+                                                    xtma_smem_bytes(nx, lgB, sizeof(R), true)) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return;
+  }
+  const long tiles = (nlines + (2 << lgB) - 1) / (2 << lgB);
+  pl->xtma_grid = (int)(tiles < (long)per_sm * nsm ? tiles : (long)per_sm * nsm);
+  static_assert(sizeof(CUtensorMap) <= sizeof(pl->xtma_map), "tensor map storage");
+  memcpy(pl->xtma_map, &tm, sizeof(tm));
+  pl->xtma_state = 1;
+}
+
+// Tensor map of the potential p for an accumulating inverse x pass: the spectrum's 3-D view with FP64 elements.
+// (Encoded per call: the potential is the caller's array or the plan's scratch; a host-side encode takes about a
+// microsecond.)
+static bool xtma_potential_map(int nx, long nlines, double* p, int lgB, CUtensorMap* tm) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || ((uintptr_t)p & 15)) return false;
+  const int h = nx < 256 ? nx : 256;
+  const cuuint64_t dims[3] = {(cuuint64_t)h, (cuuint64_t)(nx / h), (cuuint64_t)nlines};
+  const cuuint64_t strides[2] = {(cuuint64_t)h * sizeof(double), (cuuint64_t)nx * sizeof(double)};
+  const cuuint32_t box[3] = {(cuuint32_t)h, (cuuint32_t)(nx / h), (cuuint32_t)(2 << lgB)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, p, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+template <typename R>
+static bool xinv_tma(vofp_plan* pl, const XInvArgs& xi, cudaStream_t st) {
+  if (pl->xtma_state == 0) xtma_setup<R>(pl);
+  if (pl->xtma_state != 1) return false;
+  CUtensorMap tm, tp;
+  memcpy(&tm, pl->xtma_map, sizeof(tm));
+  const int lgn = 31 - __builtin_clz((unsigned)pl->n[0]);
+  XTmaArgs ta;
+  ta.xi = xi;
+  ta.lgB = xtma_lgB<R>(lgn);
+  ta.info = pl->info;
+  const bool acc = xi.p && xi.accumulate;
+  if (acc) {
+    if (!xtma_potential_map(pl->n[0], (long)pl->n[1] * pl->n[2], xi.p, ta.lgB, &tp)) return false;
+  } else {
+    tp = tm;  // not read
+  }
+  const size_t sm = xtma_smem_bytes(pl->n[0], ta.lgB, sizeof(R), acc);
+  VOFP_LAUNCH(KID_XINV, st, (xtma_kernel<R>(lgn)<<<pl->xtma_grid, kXTmaThreads, sm, st>>>(ta, tm, tp)));
+  return true;
+}
+
 // The y pass through TMA-staged tiles when the plan allows it; false: the caller runs the gather kernel.
 template <typename R>
 static bool ypass_tma(vofp_plan* pl, const YArgs& ya, bool inv, cudaStream_t st) {
-  if (pl->ytma_state == 0) ytma_setup<R>(pl);
+  if (pl->ytma_state == 0) ytma_setup<R>(pl, ya.S);
   if (pl->ytma_state != 1) return false;
   CUtensorMap tm;
   memcpy(&tm, pl->ytma_map, sizeof(tm));
@@ -286,6 +391,7 @@ static void xinv_red(vofp_plan* pl, double* pout, int accumulate, int skip_k, do
   xi.mean_out = (pout && pl->singular && pl->opts.prec == VOFP_MIXED) ? pl->conv + VOFP_CONV_MEAN : nullptr;
   xi.d2_out = d2_out;
   if (std::is_same<R, float>::value && xtc_xinv(pl, xi, st)) return;  // tensor-core transform
+  if (xinv_tma<R>(pl, xi, st)) return;                                   // TMA-staged tiles
   const int xgrid = xpass_blocks(xi.ny, xi.nz, xi.pb);
   const size_t xsm = 2 * (size_t)xi.pb * fft_span(xi.fd, xi.blu) * sizeof(C);
   VOFP_LAUNCH(KID_XINV, st, (xinv_kernel<R, C>()<<<xgrid, 256, xsm, st>>>(xi)));
@@ -442,6 +548,11 @@ int mixed_solve(vofp_plan* pl, int mode, const XArgs* xin, const double* f, doub
     status = VOFP_WARN_INCOMPATIBLE_RHS;
   info->status = status;
   return status;
+}
+
+// The FP64 plans' y pass on TMA tiles (same kernel, FP64 spectrum); false: the caller runs the gather kernel.
+bool ypass_tma_f64(vofp_plan* pl, const YArgs& ya, bool inv, cudaStream_t st) {
+  return ypass_tma<double>(pl, ya, inv, st);
 }
 
 }  // namespace vofp

@@ -225,7 +225,8 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
   ya.S = pl->S;
   const dim3 ygrid((nx + ya.tx - 1) / ya.tx, nz);
   const size_t ysm = 2 * (size_t)(ya.tx / 2) * y_ld(fft_span(ya.fd, ya.blu)) * sizeof(double2);
-  if (ny > 1) VOFP_LAUNCH(KID_YFWD, st, k_ypass_f64<false><<<ygrid, 256, ysm, st>>>(ya));
+  if (ny > 1 && !ypass_tma_f64(pl, ya, false, st))
+    VOFP_LAUNCH(KID_YFWD, st, k_ypass_f64<false><<<ygrid, 256, ysm, st>>>(ya));
   ZArgs za = z_args(pl, stats);
   if (pl->ztab && pl->zti == -1) {
     const dim3 tgrid((nx + kZSegTI - 1) / kZSegTI, ny);
@@ -248,7 +249,8 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
     const dim3 zgrid((nx + za.ti - 1) / za.ti, ny);
     VOFP_LAUNCH(KID_ZSOLVE, st, (k_zsolve<double, double><<<zgrid, 128, zsm, st>>>(za)));
   }
-  if (ny > 1) VOFP_LAUNCH(KID_YINV, st, k_ypass_f64<true><<<ygrid, 256, ysm, st>>>(ya));
+  if (ny > 1 && !ypass_tma_f64(pl, ya, true, st))
+    VOFP_LAUNCH(KID_YINV, st, k_ypass_f64<true><<<ygrid, 256, ysm, st>>>(ya));
   XInvArgs xi = {};
   xi.skip_k = -1;
   xi.nx = nx;
@@ -281,6 +283,7 @@ int finish_info(vofp_plan* pl, cudaStream_t st, vofp_info* info, int status) {
     return VOFP_ERR_CUDA;
   info->compat_defect = pl->singular ? h.compat_defect : 0.0;
   if (status == VOFP_OK && h.nonfinite) status = VOFP_ERR_NONFINITE;
+  if (status >= 0 && h.timeout) status = VOFP_ERR_TIMEOUT;  // a bounded wait for a tile load gave up
   if (status == VOFP_OK && pl->singular) {
     const double mean_abs = h.abs_sum / pl->volume;
     if (fabs(h.compat_defect) > 1e-12 * mean_abs) status = VOFP_WARN_INCOMPATIBLE_RHS;

@@ -102,6 +102,9 @@ void init_kernel_attributes_mixed();
 // once per device and process, not on every plan).
 bool first_use_on_device(int which);
 int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st, bool stats);
+// The FP64 plans' y pass on TMA-staged tiles when applicable (power-of-two ny; mixed.cu); false: not run.
+struct YArgs;
+bool ypass_tma_f64(vofp_plan* pl, const YArgs& ya, bool inv, cudaStream_t st);
 // The plan's FP64 x transform (forward, or inverse) of nlines lines `in` -> `out` (see solve.cu).
 int fp64_x_lines(vofp_plan* pl, bool inverse, const double* in, double* out, int nlines, cudaStream_t st);
 // Tensor-core x passes of FP32 refinement plans (xtc.cu): table sizes at plan preparation, the tables' build

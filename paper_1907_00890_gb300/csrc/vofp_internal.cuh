@@ -668,6 +668,9 @@ struct vofp_plan {
   // encoded tensor map (a CUtensorMap, kept as bytes)
   int ytma_state, ytma_lgB, ytma_grid;
   unsigned char ytma_map[128];
+  // the same for the TMA-staged inverse x pass (power-of-two nx of 128, 256 or 512)
+  int xtma_state, xtma_grid;
+  unsigned char xtma_map[128];
   // tensor-core x passes of FP32 refinement plans: the forward and inverse x transform matrices (TF32 hi / lo,
   // MMA operand layout) in the plan's memory, NULL when not used; persistent grid (0 = not yet sized)
   float* xtc_fwd;

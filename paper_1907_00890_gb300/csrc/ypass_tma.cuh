@@ -1,4 +1,4 @@
-// y transform of the reduced-precision spectra on column tiles staged by the Tensor Memory Accelerator.
+// y transform on column tiles staged by the Tensor Memory Accelerator (FP64, FP32 and FP32-pair spectra).
 //
 // The y pass (A3 forward, A5 inverse) transforms every column of each z plane.  A column tile -- tx = 2B
 // adjacent columns, all ny rows of one plane -- is one box of the spectrum viewed as a (ny nz) x nx matrix, and
@@ -163,6 +163,10 @@ struct CplxOf<float> {
 template <>
 struct CplxOf<ff> {
   typedef cff C;
+};
+template <>
+struct CplxOf<double> {
+  typedef double2 C;
 };
 
 struct YTmaArgs {
