@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--large-n", type=int, default=512,
                     help="cells per axis of the stretched-z projection variant (512 = the specified workload; "
                          "smaller sizes only for profiling captures)")
+    ap.add_argument("--tune", action="store_true",
+                    help="autotune the stretched-z projection variant's plans (launch shapes, z kernel, radix order)")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-sets", type=int, default=8, help="field sets per ensemble run in the served stream")
@@ -312,7 +314,7 @@ def bench_large(vofp, args):
                               "err_estimate: the library's a-posteriori estimate for the projection"}
     reps = max(3, min(args.steps, 8))
     for name, prec, mr in (("fp64", vofp.FP64, 1), ("mixed", vofp.MIXED, 3), ("ff", vofp.FF, 1)):
-        plan = vofp.Plan(n, dx, dy, dz, bc, prec=prec, max_refine=mr)
+        plan = vofp.Plan(n, dx, dy, dz, bc, prec=prec, max_refine=mr, tune=1 if args.tune else 0)
         st = torch.cuda.current_stream()
 
         def call(info=False):

@@ -483,6 +483,9 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
   // shared-memory line lengths (the Bluestein length where an axis uses it)
   const int sx = p->ax[0].fd.bm ? p->ax[0].fd.bm : nx, sy = p->ax[1].fd.bm ? p->ax[1].fd.bm : ny;
   p->xpb = sx >= 1024 ? 1 : (1024 / sx > 16 ? 16 : 1024 / sx);
+  // reduced-precision x passes of long lines: twice the line pairs per block (the autotuner's choice at 256^3
+  // and 512^3 for both FP32 and FP32 pairs: the 512^3 FP32 + refinement projection 23.4 -> 22.2 ms)
+  if (mixed && sx >= 256 && sx <= 1024) p->xpb = 2048 / sx;
   if (p->xpb < 1) p->xpb = 1;
   // y pass: columns per block so that each row segment read is 128 bytes (full cache lines), shrunk while the
   // tile (two buffers of tx/2 complex lines) exceeds its shared-memory budget: 96 KB for the FP64 pass (two
