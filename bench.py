@@ -63,6 +63,12 @@ def parse():
     ap.add_argument("--serve-sets", type=int, default=8, help="field sets per ensemble run in the served stream")
     ap.add_argument("--no-serve-sweep", dest="serve_sweep", action="store_false",
                     help="skip the served rate sweep")
+    ap.add_argument("--record-traffic", metavar="CSV", default=None,
+                    help="no GPU: read an ncu launch list (--csv --print-units base, metrics gpu__time_duration.sum, "
+                         "dram__bytes_read.sum, dram__bytes_write.sum) and record the DRAM bytes per launch of each "
+                         "kernel class in profiles/traffic.json under --traffic-workload, keyed to these sources")
+    ap.add_argument("--traffic-workload", default="droplet128_fp64")
+    ap.add_argument("--traffic-out", default=os.path.join(ROOT, "profiles", "traffic.json"))
     return ap.parse_args()
 
 
@@ -1023,8 +1029,122 @@ def run_only(args):
     print(json.dumps({"only": args.only, "result": r}))
 
 
+# kernel function name (as ncu prints it) -> the library's trace class
+_KCLASS = [(r"k_zlow", "z_low_modes"), (r"k_z", "z_tridiag"), (r"k_xinv", "x_inverse"),
+           (r"k_xtc\b", "x_tensor_core"), (r"k_grad", "grad_update"), (r"k_extend_epi", "extend_epilogue"),
+           (r"k_geometry", "stefan_source"), (r"k_vd_predict", "vd_predict"), (r"k_vof_fused", "vof_update"),
+           (r"k_shift", "gauge_shift")]
+_XMODE = {0: "x_forward", 1: "x_forward_div", 2: "x_forward_stefan", 3: "residual_update", 4: "x_forward_div"}
+CLASSES = set(c for _, c in _KCLASS) | set(_XMODE.values()) | {"y_forward", "y_inverse"}
+
+
+def _template_args(name):
+    i = name.find("<")
+    if i < 0:
+        return []
+    depth, cur, out = 0, "", []
+    for ch in name[i + 1:]:
+        if ch == "<":
+            depth += 1
+        elif ch == ">":
+            if depth == 0:
+                break
+            depth -= 1
+        if ch == "," and depth == 0:
+            out.append(cur.strip())
+            cur = ""
+        else:
+            cur += ch
+    out.append(cur.strip())
+    return out
+
+
+def kernel_class(name):
+    """The trace class of a kernel of this library from its (demangled) name; None for others."""
+    import re
+    ta = [re.sub(r"^\(\w+\)", "", t) for t in _template_args(name)]
+    if re.search(r"k_xfwd", name) and ta:
+        return _XMODE.get(int(ta[-1])) if ta[-1].isdigit() else None
+    if re.search(r"k_ypass", name) and ta:
+        inv = ta[1] if "k_ypass_tma" in name else ta[-1]
+        return "y_inverse" if inv in ("true", "1") else "y_forward"
+    for pat, cls in _KCLASS:
+        if re.search(pat, name):
+            return cls
+    return None
+
+
+def read_launch_list(path):
+    """Per launch (in order): kernel name, class, duration in us, DRAM bytes read + written, from an ncu CSV."""
+    import csv
+    scale = {"byte": 1.0, "b": 1.0, "kbyte": 1e3, "kb": 1e3, "mbyte": 1e6, "mb": 1e6, "gbyte": 1e9, "gb": 1e9,
+             "nsecond": 1e-3, "ns": 1e-3, "usecond": 1.0, "us": 1.0, "msecond": 1e3, "ms": 1e3, "second": 1e6,
+             "s": 1e6}
+    launches = {}
+    with open(path, newline="") as fh:
+        rows = [r for r in csv.reader(fh)]
+    hdr = next(i for i, r in enumerate(rows) if "Metric Name" in r)
+    cols = rows[hdr]
+    ci = {c: cols.index(c) for c in ("ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value")}
+    for r in rows[hdr + 1:]:
+        if len(r) < len(cols):
+            continue
+        lid = int(r[ci["ID"]])
+        d = launches.setdefault(lid, {"name": r[ci["Kernel Name"]], "us": 0.0, "bytes": 0.0})
+        v = float(r[ci["Metric Value"]].replace(",", "")) * scale.get(r[ci["Metric Unit"]].lower(), 1.0)
+        m = r[ci["Metric Name"]]
+        if m == "gpu__time_duration.sum":
+            d["us"] = v
+        elif m in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            d["bytes"] += v
+    out = []
+    for lid in sorted(launches):
+        d = launches[lid]
+        out.append(dict(d, cls=kernel_class(d["name"])))
+    return out
+
+
+def record_traffic(args):
+    """Write the per-class DRAM bytes per launch of one ncu launch list into profiles/traffic.json (other
+    workloads kept only when they were recorded on the same sources) and print the markdown summary table."""
+    ls = read_launch_list(args.record_traffic)
+    agg = {}
+    for d in ls:
+        a = agg.setdefault(d["cls"] or d["name"][:40], {"n": 0, "us": 0.0, "bytes": 0.0})
+        a["n"] += 1
+        a["us"] += d["us"]
+        a["bytes"] += d["bytes"]
+    path = args.traffic_out
+    try:
+        with open(path) as fh:
+            t = json.load(fh)
+    except Exception:
+        t = {}
+    sha = source_sha()
+    if t.get("source_sha") != sha:
+        t = {"workloads": {}}
+    t["source_sha"] = sha
+    t["note"] = ("DRAM bytes (read + write) per launch and kernel class from ncu launch lists of these sources "
+                 "(written by bench.py --record-traffic); summaries in profiles/launches_*.md")
+    t.setdefault("workloads", {})[args.traffic_workload] = {
+        k: round(a["bytes"] / a["n"]) for k, a in sorted(agg.items()) if a["bytes"] > 0 and k in CLASSES}
+    with open(path, "w") as fh:
+        json.dump(t, fh, indent=1)
+        fh.write("\n")
+    tot = sum(a["us"] for a in agg.values())
+    print("| kernel class | launches | total us | share | DRAM MB / launch |")
+    print("|---|---|---|---|---|")
+    for k, a in sorted(agg.items(), key=lambda kv: -kv[1]["us"]):
+        print("| %s | %d | %.1f | %.3f | %.1f |" % (k, a["n"], a["us"], a["us"] / tot if tot else 0.0,
+                                                 a["bytes"] / a["n"] / 1e6))
+    print("| total | %d | %.1f | 1.000 | |" % (sum(a["n"] for a in agg.values()), tot))
+
+
 def main():
     args = parse()
+    if args.record_traffic:
+        record_traffic(args)
+        return
     if args.only:
         run_only(args)
         return

@@ -381,6 +381,23 @@ const char* vofp_trace_name(int id);
  */
 int vofp_debug_fail_alloc(long long after);
 
+/*
+ * Bounds-checked build (libvofp_checked.so, compiled with -DVOFP_CHECKED; a stand-in for a device memory
+ * checker, no counterpart in the paper).  Its kernels test the index of each guarded global-memory access
+ * against the array's extent; an index out of range skips the access and is counted, nothing traps.
+ * vofp_debug_check_word synchronises the current device and reads the counts of all the library's
+ * translation units: out[0] = number of failed tests, out[1] = site of the first (1 cell loads of the
+ * stencils, 2 face loads, 3 x forward stores, 4 y pass, 5 x inverse, 6 z column, 7 z factor table, 8 face
+ * stores, 9 face-gradient lines, 10 per-cell stores, 11 VoF loads, 12 TMA y pass, 13 TMA x inverse,
+ * 14 tensor-core x passes, 15 batch block mapping, 99 self-test), out[2] its index, out[3] the extent;
+ * reset != 0 clears the counts.  Returns 1 from the checked library, 0 from the plain one (out zeroed, no
+ * device call), VOFP_ERR_CUDA if a read fails, VOFP_ERR_INVALID_ARG for out NULL.
+ * vofp_debug_check_selftest launches, on `stream`, one test that fails by construction (index 5 against
+ * extent 4, without an access): the checked library records it under site 99; the plain one does nothing.
+ */
+int vofp_debug_check_word(long long* out, int reset);
+int vofp_debug_check_selftest(void* stream);
+
 /* Static message for a status code. */
 const char* vofp_error_string(int status);
 

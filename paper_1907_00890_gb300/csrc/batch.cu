@@ -10,6 +10,7 @@
 // others, so an instance runs the same arithmetic alone and in any batch; its results agree to rounding, not
 // bit for bit, because the FP64 block partials of its norms and means are added with atomics in an order
 // that varies from run to run.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -28,6 +29,8 @@ __device__ __forceinline__ int find_instance(const int* __restrict__ off, int n,
     if (__ldg(off + mid) <= b) lo = mid;
     else hi = mid;
   }
+  // (bounds-checked builds: the block lies in its instance's range; recorded, the accesses are checked on)
+  (void)VOFP_IN(b - __ldg(off + lo), __ldg(off + lo + 1) - __ldg(off + lo), CHK_BATCH);
   return lo;
 }
 
@@ -100,7 +103,7 @@ __global__ void __launch_bounds__(128) k_ztab_batch(const ZArgs* __restrict__ ar
 }
 
 // Bounded z, every instance's tile fitting: segmented tiles of 32 systems (kZSegW warps per block).
-template <typename T, typename TT>
+template <typename T, typename TT, bool LEAN>
 __global__ void __launch_bounds__(256) k_ztab_seg_batch(const ZArgs* __restrict__ args,
                                                         const LowArgs* __restrict__ inst,
                                                         const int* __restrict__ off, int n) {
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(256) k_ztab_seg_batch(const ZArgs* __restrict_
   const LowArgs& L = inst[i];
   const int l = blockIdx.x - __ldg(off + i);
   const int gx = (a.nx + kZSegTI - 1) / kZSegTI;
-  ztab_seg_block<T, TT>(a, L.zt, l % gx, l / gx, smem_raw);
+  ztab_seg_block<T, TT, LEAN>(a, L.zt, l % gx, l / gx, smem_raw);
 }
 
 // Bounded z: low-eigenvalue systems of all instances, one warp each.
@@ -145,6 +148,8 @@ struct EpiArgs {
   double* v;
   double* w;
   double s;           // dt / rho0
+  double sx, sy;      // s / dx, s / dy
+  int bpp;            // gradient launch: blocks per plane and axis (face_blocks_per_plane, 256 threads)
   const double* mean; // gauge sum (NULL: no shift)
   double mean_scale;
   double* conv;       // convergence slots, cleared by k_clear_batch
@@ -166,22 +171,20 @@ __global__ void k_shift_batch(const EpiArgs* __restrict__ e, const int* __restri
   for (size_t t = (size_t)l * blockDim.x + threadIdx.x; t < cells; t += (size_t)nb * blockDim.x) a.p[t] -= m;
 }
 
-__global__ void k_grad_batch(const EpiArgs* __restrict__ e, const int* __restrict__ off, int n) {
-  const int i = find_instance(off, n, blockIdx.x);
-  const EpiArgs& a = e[i];
-  const int nb = __ldg(off + i + 1) - __ldg(off + i);
-  const int l = blockIdx.x - __ldg(off + i);
-  const GridDev g = a.g;
-  const size_t total = total_faces(g);
-  for (size_t t = (size_t)l * blockDim.x + threadIdx.x; t < total; t += (size_t)nb * blockDim.x) {
-    int fi, fj, fk;
-    size_t o;
-    const int axis = decode_face(g, t, fi, fj, fk, o);
-    double gr;
-    if (!grad_on_face(g, a.p, axis, fi, fj, fk, gr)) continue;
-    double* F = axis == 0 ? a.u : (axis == 1 ? a.v : a.w);
-    F[o] -= a.s * gr;
-  }
+// Velocity correction of every instance: the single-grid face launch shape (plane k, axis, position in the
+// plane) laid out per instance, 3 bpp blocks per plane (one 32-bit division per thread, none of 64 bits).
+__global__ void __launch_bounds__(256) k_grad_batch(const EpiArgs* __restrict__ e, const int* __restrict__ off,
+                                                    int n) {
+  const int inst = find_instance(off, n, blockIdx.x);
+  const EpiArgs& a = e[inst];
+  const int l = blockIdx.x - __ldg(off + inst);
+  const int per_k = 3 * a.bpp;
+  const int k = l / per_k, r = l - k * per_k;
+  const int axis = r / a.bpp, xb = r - axis * a.bpp;
+  int i, j;
+  size_t o;
+  if (!face_at(a.g, axis, k, xb * blockDim.x + threadIdx.x, i, j, o)) return;
+  grad_face(a.g, a.p, a.u, a.v, a.w, a.s, a.sx, a.sy, axis, i, j, k, o);
 }
 
 static const int kMaxDynSmem = 200 * 1024;
@@ -198,7 +201,8 @@ static void allow_batch_kernels() {
   allow_smem(k_ypass_batch<T, C, true>);
   allow_smem(k_zsolve_batch<T>);
   allow_smem(k_ztab_batch<T, ZF<T>>);
-  allow_smem(k_ztab_seg_batch<T, ZF<T>>);
+  allow_smem(k_ztab_seg_batch<T, ZF<T>, false>);
+  allow_smem(k_ztab_seg_batch<T, ZF<T>, true>);
   allow_smem(k_xinv_batch<T, C>);
 }
 
@@ -218,10 +222,11 @@ struct vofp_batch {
   unsigned char* hstage;  // pinned host copy of the argument records
   size_t args_bytes;
   size_t o_x, o_yf, o_yi, o_z, o_xi, o_low, o_epi;  // per-solve stride arrays start offsets
-  size_t o_offx, o_offy, o_offz, o_offlow, o_offepi;
-  int tot_x, tot_y, tot_z, tot_low, tot_epi;
+  size_t o_offx, o_offy, o_offz, o_offlow, o_offepi, o_offgrad;
+  int tot_x, tot_y, tot_z, tot_low, tot_epi, tot_grad;
   bool ztab;  // every instance has a bounded z axis: factor-table z kernels
   bool zseg;  // ... and every instance's segmented tile fits in shared memory
+  bool zlean;  // the segmented kernel's lean tile layout (some instance's full tile would hold an SM alone)
   int prec;   // VOFP_MIXED (FP32 spectrum) or VOFP_FF (FP32-pair spectrum), the same for every instance
   size_t sm_x, sm_y, sm_z;
   cudaGraphExec_t exec;
@@ -293,6 +298,8 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
   o = a256(o + sizeof(int) * (n + 1));
   b->o_offepi = o;
   o = a256(o + sizeof(int) * (n + 1));
+  b->o_offgrad = o;
+  o = a256(o + sizeof(int) * (n + 1));
   b->args_bytes = o;
   if (device_alloc(&b->dmem, o) != cudaSuccess) {
     cudaGetLastError();
@@ -312,14 +319,18 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
   int* offz = (int*)(b->hstage + b->o_offz);
   int* offl = (int*)(b->hstage + b->o_offlow);
   int* offe = (int*)(b->hstage + b->o_offepi);
-  offx[0] = offy[0] = offz[0] = offl[0] = offe[0] = 0;
+  int* offg = (int*)(b->hstage + b->o_offgrad);
+  offx[0] = offy[0] = offz[0] = offl[0] = offe[0] = offg[0] = 0;
   b->sm_x = b->sm_y = b->sm_z = 0;
   b->ztab = true;
   for (int i = 0; i < n; ++i)
     if (!plans[i]->ztab) b->ztab = false;
   b->zseg = b->ztab;
+  b->zlean = false;
   for (int i = 0; i < n; ++i)
-    if (ztab_seg_smem(plans[i]->n[2], rsz) > 200 * 1024) b->zseg = false;
+    if (ztab_seg_code(plans[i]->n[2], rsz) != -1) b->zlean = true;
+  for (int i = 0; i < n; ++i)
+    if (ztab_seg_smem(plans[i]->n[2], rsz, b->zlean) > 200 * 1024) b->zseg = false;
   for (int i = 0; i < n; ++i) {
     const vofp_plan* p = plans[i];
     const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
@@ -329,14 +340,15 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
     offz[i + 1] = offz[i] + (b->zseg ? (nx + kZSegTI - 1) / kZSegTI
                                      : (b->ztab ? (nx + 127) / 128 : (nx + gti - 1) / gti)) * ny;
     offl[i + 1] = offl[i] + p->nlow;
-    const size_t faces = total_faces(grid_dev(p));
-    int eb = (int)((faces + 255) / 256);
-    if (eb > 512) eb = 512;
-    offe[i + 1] = offe[i] + eb;
+    // gauge shift: up to 512 blocks striding over the cells; gradient: the face launch shape of the instance
+    // (3 axes, nz + 1 planes)
+    const size_t cells = (size_t)nx * ny * nz;
+    offe[i + 1] = offe[i] + (int)std::min<size_t>(512, (cells + 255) / 256);
+    offg[i + 1] = offg[i] + face_blocks_per_plane(grid_dev(p), 256) * 3 * (nz + 1);
     const size_t sx = 2 * (size_t)p->xpb * fft_span(p->ax[0].fd, p->ax[0].blu64) * csz;
     const size_t sy = 2 * (size_t)(p->ytx32 / 2) * y_ld(fft_span(p->ax[1].fd, p->ax[1].blu64)) * csz;
     const ZTabShape zs = ztab_shape(128, nz, rsz);
-    const size_t sz = b->zseg ? ztab_seg_smem(nz, rsz)
+    const size_t sz = b->zseg ? ztab_seg_smem(nz, rsz, b->zlean)
                               : (b->ztab ? zs.smem : (size_t)(p->bc[2] == VOFP_BC_P ? 3 : 2) * gti * nz * rsz);
     if (sx > b->sm_x) b->sm_x = sx;
     if (sy > b->sm_y) b->sm_y = sy;
@@ -347,6 +359,7 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
   b->tot_z = offz[n];
   b->tot_low = offl[n];
   b->tot_epi = offe[n];
+  b->tot_grad = offg[n];
   if (first_use_on_device(2)) {
     allow_batch_kernels<float, float2>();
     allow_batch_kernels<ff, cff>();
@@ -468,6 +481,9 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
     e.v = v[i];
     e.w = w[i];
     e.s = dt[i];
+    e.sx = dt[i] * e.g.rdx;
+    e.sy = dt[i] * e.g.rdy;
+    e.bpp = face_blocks_per_plane(e.g, 256);
     e.mean = (pl->singular && !ffp && p && p[i]) ? conv + VOFP_CONV_MEAN : nullptr;
     e.mean_scale = 1.0 / ((double)pl->n[0] * pl->n[1] * (pl->volume / (pl->n[0] * pl->dx * pl->n[1] * pl->dy)));
     e.conv = conv;
@@ -484,6 +500,7 @@ static void launch_sequence_t(vofp_batch* b, cudaStream_t st) {
   const int* offz = (const int*)(d + b->o_offz);
   const int* offl = (const int*)(d + b->o_offlow);
   const int* offe = (const int*)(d + b->o_offepi);
+  const int* offg = (const int*)(d + b->o_offgrad);
   const EpiArgs* E = (const EpiArgs*)(d + b->o_epi);
   const LowArgs* L = (const LowArgs*)(d + b->o_low);
   VOFP_LAUNCH(KID_BATCHED, st, k_clear_batch<<<n, 32, 0, st>>>(E, n));
@@ -500,9 +517,12 @@ static void launch_sequence_t(vofp_batch* b, cudaStream_t st) {
     if (b->tot_y > 0)
       VOFP_LAUNCH(KID_YFWD, st, (k_ypass_batch<T, C, false><<<b->tot_y, 256, b->sm_y, st>>>(YF, offy, n)));
     if (b->ztab) {
-      if (b->zseg)
+      if (b->zseg && b->zlean)
         VOFP_LAUNCH(KID_ZSOLVE, st,
-                    (k_ztab_seg_batch<T, ZF<T>><<<b->tot_z, 32 * kZSegW, b->sm_z, st>>>(Z, L, offz, n)));
+                    (k_ztab_seg_batch<T, ZF<T>, true><<<b->tot_z, 32 * kZSegW, b->sm_z, st>>>(Z, L, offz, n)));
+      else if (b->zseg)
+        VOFP_LAUNCH(KID_ZSOLVE, st,
+                    (k_ztab_seg_batch<T, ZF<T>, false><<<b->tot_z, 32 * kZSegW, b->sm_z, st>>>(Z, L, offz, n)));
       else
         VOFP_LAUNCH(KID_ZSOLVE, st, k_ztab_batch<T, ZF<T>><<<b->tot_z, 128, b->sm_z, st>>>(Z, L, offz, n));
       if (b->tot_low > 0)
@@ -518,7 +538,7 @@ static void launch_sequence_t(vofp_batch* b, cudaStream_t st) {
     VOFP_LAUNCH(KID_XINV, st, (k_xinv_batch<T, C><<<b->tot_x, 256, b->sm_x, st>>>(XI, offx, n)));
   }
   VOFP_LAUNCH(KID_GAUGE, st, k_shift_batch<<<b->tot_epi, 256, 0, st>>>(E, offe, n));
-  VOFP_LAUNCH(KID_GRAD, st, k_grad_batch<<<b->tot_epi, 256, 0, st>>>(E, offe, n));
+  VOFP_LAUNCH(KID_GRAD, st, k_grad_batch<<<b->tot_grad, 256, 0, st>>>(E, offg, n));
 }
 
 static void launch_sequence(vofp_batch* b, cudaStream_t st) {

@@ -10,112 +10,108 @@
 
 namespace vofp {
 
-// Face-normal gradient of a cell field at face `f` (low face of cell f) along a line of n cells with
-// stride `st` starting at `base`; `rh` is 1 / centre distance across that face, `rw_lo`, `rw_hi` the
-// reciprocal end widths.  Returns false for an N boundary face (left unchanged).
-__device__ __forceinline__ bool face_grad(const double* __restrict__ p, size_t base, size_t st, int n, int bc, int f,
-                                          double rh, double rw_lo, double rw_hi, double& g) {
+// The cell line along `axis` through (i, j, k) lies inside the cell array (bounds-checked builds; offsets along
+// the line then run over 0 .. n - 1).
+__device__ __forceinline__ bool line_in(const GridDev& g, int axis, int i, int j, int k) {
+  const size_t plane = (size_t)g.nx * g.ny;
+  const size_t last = axis == 0 ? (size_t)k * plane + (size_t)j * g.nx + (g.nx - 1)
+                                : (axis == 1 ? (size_t)k * plane + i + (size_t)(g.ny - 1) * g.nx
+                                             : (size_t)j * g.nx + i + (size_t)(g.nz - 1) * plane);
+  return VOFP_IN(last, ncells(g), CHK_FACE_LINE);
+}
+
+// The difference d of a cell field across face f (low face of cell f) of a line of n cells with stride `st`
+// from `base`: returns -1 on an N face (no difference), 0 inside or across a periodic wrap (d = q_f - q_{f-1}),
+// 1 / 2 on the low / high D face (d = the adjacent value with the ghost's sign, the distance half a cell).  The
+// face-normal gradient is d * face_rdist(...).
+__device__ __forceinline__ int line_diff(const double* __restrict__ p, size_t base, size_t st, int n, int bc, int f,
+                                         double& d) {
   if (bc == VOFP_BC_P) {
     const int fm = f == 0 ? n - 1 : f - 1;
-    g = (__ldg(p + base + f * st) - __ldg(p + base + fm * st)) * rh;
-    return true;
-  }
-  const bool lowN = bc == VOFP_BC_NN || bc == VOFP_BC_ND;
-  const bool highN = bc == VOFP_BC_NN || bc == VOFP_BC_DN;
-  if (f == 0) {
-    if (lowN) return false;
-    g = 2.0 * __ldg(p + base) * rw_lo;
-    return true;
-  }
-  if (f == n) {
-    if (highN) return false;
-    g = -2.0 * __ldg(p + base + (size_t)(n - 1) * st) * rw_hi;
-    return true;
-  }
-  g = (__ldg(p + base + f * st) - __ldg(p + base + (size_t)(f - 1) * st)) * rh;
-  return true;
-}
-
-// Decode a flat face index over the three face arrays; returns the axis and sets (i, j, k) and the offset.
-__device__ __forceinline__ int decode_face(const GridDev& g, size_t t, int& i, int& j, int& k, size_t& off) {
-  const int nxf = nface(g.nx, g.bcx), nyf = nface(g.ny, g.bcy);
-  const size_t nu = (size_t)nxf * g.ny * g.nz, nv = (size_t)g.nx * nyf * g.nz;
-  if (t < nu) {
-    off = t;
-    i = (int)(t % nxf);
-    const size_t r = t / nxf;
-    j = (int)(r % g.ny);
-    k = (int)(r / g.ny);
+    d = __ldg(p + base + f * st) - __ldg(p + base + fm * st);
     return 0;
   }
-  t -= nu;
-  if (t < nv) {
-    off = t;
-    i = (int)(t % g.nx);
-    const size_t r = t / g.nx;
-    j = (int)(r % nyf);
-    k = (int)(r / nyf);
+  if (f == 0) {
+    if (bc == VOFP_BC_NN || bc == VOFP_BC_ND) return -1;
+    d = __ldg(p + base);
     return 1;
   }
-  t -= nv;
-  off = t;
-  i = (int)(t % g.nx);
-  const size_t r = t / g.nx;
-  j = (int)(r % g.ny);
-  k = (int)(r / g.ny);
-  return 2;
-}
-
-__device__ __forceinline__ bool grad_on_face(const GridDev& g, const double* __restrict__ p, int axis, int i, int j,
-                                             int k, double& gr) {
-  const size_t plane = (size_t)g.nx * g.ny;
-  if (axis == 0) {
-    return face_grad(p, (size_t)k * plane + (size_t)j * g.nx, 1, g.nx, g.bcx, i, g.rdx, g.rdx, g.rdx, gr);
-  } else if (axis == 1) {
-    return face_grad(p, (size_t)k * plane + i, g.nx, g.ny, g.bcy, j, g.rdy, g.rdy, g.rdy, gr);
+  if (f == n) {
+    if (bc == VOFP_BC_NN || bc == VOFP_BC_DN) return -1;
+    d = -__ldg(p + base + (size_t)(n - 1) * st);
+    return 2;
   }
-  return face_grad(p, (size_t)j * g.nx + i, plane, g.nz, g.bcz, k, __ldg(g.rhz + k), __ldg(g.rdz),
-                   __ldg(g.rdz + g.nz - 1), gr);
+  d = __ldg(p + base + f * st) - __ldg(p + base + (size_t)(f - 1) * st);
+  return 0;
+}
+__device__ __forceinline__ int face_diff_axis(const GridDev& g, const double* __restrict__ p, int axis, int i, int j,
+                                              int k, double& d) {
+  if (!line_in(g, axis, i, j, k)) return -1;
+  const size_t plane = (size_t)g.nx * g.ny;
+  if (axis == 0) return line_diff(p, (size_t)k * plane + (size_t)j * g.nx, 1, g.nx, g.bcx, i, d);
+  if (axis == 1) return line_diff(p, (size_t)k * plane + i, g.nx, g.ny, g.bcy, j, d);
+  return line_diff(p, (size_t)j * g.nx + i, plane, g.nz, g.bcz, k, d);
 }
 
-__host__ __device__ __forceinline__ size_t total_faces(const GridDev& g) {
-  return (size_t)nface(g.nx, g.bcx) * g.ny * g.nz + (size_t)g.nx * nface(g.ny, g.bcy) * g.nz +
-         (size_t)g.nx * g.ny * nface(g.nz, g.bcz);
+// 1 / distance between the two values that face_diff_axis differences (return code e >= 0): the centre distance
+// inside and across a periodic wrap, half the end cell's width at a D face.
+__device__ __forceinline__ double face_rdist(const GridDev& g, int axis, int k, int e) {
+  const double h = axis == 0 ? g.rdx
+                             : (axis == 1 ? g.rdy : (e == 0 ? __ldg(g.rhz + k) : __ldg(g.rdz + (e == 1 ? 0 : g.nz - 1))));
+  return e > 0 ? h + h : h;
 }
 
+
+// Blocks per plane and axis of the face launch shape (face_grid).
+__host__ __device__ __forceinline__ int face_blocks_per_plane(const GridDev& g, int threads) {
+  const long a = (long)nface(g.nx, g.bcx) * g.ny, b = (long)g.nx * nface(g.ny, g.bcy), c = (long)g.nx * g.ny;
+  const long m = a > b ? (a > c ? a : c) : (b > c ? b : c);
+  return (int)((m + threads - 1) / threads);
+}
 // Face launch shape: blockIdx.z = plane k, blockIdx.y = axis, blockIdx.x * blockDim.x + threadIdx.x = index
 // within the plane of that axis' face array (32-bit arithmetic; no 64-bit division per face).  Blocks run
 // x fastest, then y: the three face arrays of plane k are done back to back, so the cell fields they share
 // (the potential, mdot, C) are read from DRAM once and then hit L2, instead of once per axis.
 inline dim3 face_grid(const GridDev& g, int threads) {
-  const long a = (long)nface(g.nx, g.bcx) * g.ny, b = (long)g.nx * nface(g.ny, g.bcy), c = (long)g.nx * g.ny;
-  const long m = a > b ? (a > c ? a : c) : (b > c ? b : c);
-  return dim3((unsigned)((m + threads - 1) / threads), 3, (unsigned)(g.nz + 1));
+  return dim3((unsigned)face_blocks_per_plane(g, threads), 3, (unsigned)(g.nz + 1));
 }
-__device__ __forceinline__ bool face_coord(const GridDev& g, int& axis, int& i, int& j, int& k, size_t& off) {
-  axis = blockIdx.y;
+// Face `idx` of plane k of the `axis` face array: sets (i, j) and the offset; false past the plane or the
+// array.  (32-bit arithmetic, one division.)
+__device__ __forceinline__ bool face_at(const GridDev& g, int axis, int k, int idx, int& i, int& j, size_t& off) {
   const int fx = axis == 0 ? nface(g.nx, g.bcx) : g.nx;
   const int fy = axis == 1 ? nface(g.ny, g.bcy) : g.ny;
   const int fz = axis == 2 ? nface(g.nz, g.bcz) : g.nz;
-  k = blockIdx.z;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= fz || idx >= fx * fy) return false;
   j = idx / fx;
   i = idx - j * fx;
   off = ((size_t)k * fy + j) * fx + i;
-  return true;
+  return VOFP_IN(off, (size_t)fx * fy * fz, CHK_FACE_STORE);
+}
+__device__ __forceinline__ bool face_coord(const GridDev& g, int& axis, int& i, int& j, int& k, size_t& off) {
+  axis = blockIdx.y;
+  k = blockIdx.z;
+  return face_at(g, axis, k, blockIdx.x * blockDim.x + threadIdx.x, i, j, off);
 }
 
-// u -= s * G p on all three face arrays.
+// u -= s * G p on all three face arrays; sx = s / dx, sy = s / dy (the x and y scales folded into one product,
+// so that an x or y face costs one subtraction and one multiply-add in FP64).
+__device__ __forceinline__ void grad_face(const GridDev& g, const double* __restrict__ p, double* u, double* v,
+                                          double* w, double s, double sx, double sy, int axis, int i, int j, int k,
+                                          size_t off) {
+  double d;
+  const int e = face_diff_axis(g, p, axis, i, j, k, d);
+  if (e < 0) return;  // N face
+  double c = axis == 0 ? sx : (axis == 1 ? sy : s * (e == 0 ? __ldg(g.rhz + k) : __ldg(g.rdz + (e == 1 ? 0 : g.nz - 1))));
+  if (e > 0) c = c + c;
+  double* F = axis == 0 ? u : (axis == 1 ? v : w);
+  F[off] = fma(-c, d, F[off]);
+}
 static __global__ void __launch_bounds__(256) k_grad_update(GridDev g, const double* __restrict__ p, double* u,
-                                                           double* v, double* w, double s) {
+                                                           double* v, double* w, double s, double sx, double sy) {
   int axis, i, j, k;
   size_t off;
   if (!face_coord(g, axis, i, j, k, off)) return;
-  double gr;
-  if (!grad_on_face(g, p, axis, i, j, k, gr)) return;
-  double* F = axis == 0 ? u : (axis == 1 ? v : w);
-  F[off] = fma(-s, gr, F[off]);
+  grad_face(g, p, u, v, w, s, sx, sy, axis, i, j, k, off);
 }
 
 // Interface geometry per cell: s = coef * mdot * |grad C| and n = -grad C / |grad C| (clipped).  The
@@ -129,6 +125,7 @@ static __global__ void __launch_bounds__(256) k_geometry(GridDev g, const double
   const int j = blockIdx.y, k = blockIdx.z;
   if (i >= g.nx) return;
   const size_t t = ((size_t)k * g.ny + j) * g.nx + i;
+  if (!VOFP_IN(t, ncells(g), CHK_CELL_STORE)) return;
   double3 n;
   const double m = geometry_at(g, C, i, j, k, MODE, n);
   s[t] = __ldg(mdot + t) * coef * m;
@@ -150,6 +147,7 @@ static __global__ void __launch_bounds__(256) k_geometry_ff(GridDev g, const dou
   const int j = blockIdx.y, k = blockIdx.z;
   if (i >= g.nx) return;
   const size_t t = ((size_t)k * g.ny + j) * g.nx + i;
+  if (!VOFP_IN(t, ncells(g), CHK_CELL_STORE)) return;
   const ff gx = ff_split(cval(g, C, i + 1, j, k) - cval(g, C, i - 1, j, k)) * ff_split(g.hrdx);
   const ff gy = ff_split(cval(g, C, i, j + 1, k) - cval(g, C, i, j - 1, k)) * ff_split(g.hrdy);
   const ff gz = ff_split(cval(g, C, i, j, k + 1) - cval(g, C, i, j, k - 1)) * ff_split(__ldg(g.rzc + k));
@@ -201,6 +199,7 @@ __device__ __forceinline__ double face_sum_arr(const GridDev& g, const double* _
     if (lo < 0) lo = 0;
     if (hi >= n) hi = n - 1;
   }
+  if (!line_in(g, axis, i, j, k)) return 0.0;
   return __ldg(q + base + lo * st) + __ldg(q + base + hi * st);
 }
 
@@ -227,9 +226,9 @@ static __global__ void __launch_bounds__(256) k_extend_epi(ExtArgs a) {
   size_t off;
   if (!face_coord(g, axis, i, j, k, off)) return;
   const double* U = axis == 0 ? a.u : (axis == 1 ? a.v : a.w);
-  double gr = 0;
-  grad_on_face(g, a.phi, axis, i, j, k, gr);
-  const double ue = __ldg(U + off) - gr;
+  double d;
+  const int e = face_diff_axis(g, a.phi, axis, i, j, k, d);
+  const double ue = e < 0 ? __ldg(U + off) : fma(-face_rdist(g, axis, k, e), d, __ldg(U + off));
   (axis == 0 ? a.ue : (axis == 1 ? a.ve : a.we))[off] = ue;
   if (a.ug) {
     // (mean mdot)(mean n) / rho1 = (sum mdot)(sum n) / (4 rho1)
@@ -257,36 +256,6 @@ struct VdArgs {
   double* v;
   double* w;
 };
-// The difference of a cell field across face f of a line (the face_grad rules, without the distance):
-// returns -1 on an N face, 0 inside or on a periodic wrap, 1 / 2 on the low / high D face, where d is the
-// adjacent value with the ghost's sign and the distance is half a cell.
-__device__ __forceinline__ int line_diff(const double* __restrict__ p, size_t base, size_t st, int n, int bc, int f,
-                                         double& d) {
-  if (bc == VOFP_BC_P) {
-    const int fm = f == 0 ? n - 1 : f - 1;
-    d = __ldg(p + base + f * st) - __ldg(p + base + fm * st);
-    return 0;
-  }
-  if (f == 0) {
-    if (bc == VOFP_BC_NN || bc == VOFP_BC_ND) return -1;
-    d = __ldg(p + base);
-    return 1;
-  }
-  if (f == n) {
-    if (bc == VOFP_BC_NN || bc == VOFP_BC_DN) return -1;
-    d = -__ldg(p + base + (size_t)(n - 1) * st);
-    return 2;
-  }
-  d = __ldg(p + base + f * st) - __ldg(p + base + (size_t)(f - 1) * st);
-  return 0;
-}
-__device__ __forceinline__ int face_diff_axis(const GridDev& g, const double* __restrict__ p, int axis, int i, int j,
-                                              int k, double& d) {
-  const size_t plane = (size_t)g.nx * g.ny;
-  if (axis == 0) return line_diff(p, (size_t)k * plane + (size_t)j * g.nx, 1, g.nx, g.bcx, i, d);
-  if (axis == 1) return line_diff(p, (size_t)k * plane + i, g.nx, g.ny, g.bcy, j, d);
-  return line_diff(p, (size_t)j * g.nx + i, plane, g.nz, g.bcz, k, d);
-}
 static __global__ void __launch_bounds__(256) k_vd_predict(VdArgs a) {
   const GridDev& g = a.g;
   int axis, i, j, k;
@@ -300,14 +269,7 @@ static __global__ void __launch_bounds__(256) k_vd_predict(VdArgs a) {
     face_diff_axis(g, a.pm, axis, i, j, k, dm);
     d = fma(a.opr, d, -a.r * dm);  // the difference of p_hat
   }
-  double h;  // 1 / distance between the values differenced
-  if (axis == 0)
-    h = g.rdx;
-  else if (axis == 1)
-    h = g.rdy;
-  else
-    h = e == 0 ? __ldg(g.rhz + k) : __ldg(g.rdz + (e == 1 ? 0 : g.nz - 1));
-  if (e > 0) h = h + h;
+  const double h = face_rdist(g, axis, k, e);  // 1 / distance between the values differenced
   const double rho_f = fma(a.half_drho, face_sum_arr(g, a.C, axis, i, j, k), a.rho2);
   const double c = h * fma(a.dt, recip_newton(rho_f), -a.dt_over_rho0);  // dt (1/rho_f - 1/rho0) / distance
   double* F = axis == 0 ? a.u : (axis == 1 ? a.v : a.w);

@@ -46,7 +46,8 @@ static void allow_all() {
   allow_smem(k_zsolve<T, T>);
   allow_smem(k_ztab<T, TT>);
   allow_smem(k_ztab_staged<T, TT>);
-  allow_smem(k_ztab_seg<T, TT>);
+  allow_smem(k_ztab_seg<T, TT, false>);
+  allow_smem(k_ztab_seg<T, TT, true>);
 }
 
 // Shared memory a TMA y-pass CTA may take (of the 227 KiB an sm_103a CTA can opt into).
@@ -328,11 +329,15 @@ static void solve_red(vofp_plan* pl, cudaStream_t st, int skip_k, double tol2, b
   if (pl->ztab) {
     // bulk systems from the factor table; the low-eigenvalue ones (a prefix of each row) by one warp each.
     // Small grids: the shared-memory staged kernel (too few systems to hide the row loads one thread each)
-    if (pl->zti32 == -1) {
+    if (pl->zti32 == -1 || pl->zti32 == -2) {
       const dim3 tgrid((nx + kZSegTI - 1) / kZSegTI, ny);
-      VOFP_LAUNCH(KID_ZSOLVE, st,
-                  (k_ztab_seg<R, typename Red<R>::TT><<<tgrid, 32 * kZSegW, ztab_seg_smem(nz, sizeof(R)), st>>>(
-                      za, ztab_args(pl))));
+      const size_t sm = ztab_seg_smem(nz, sizeof(R), pl->zti32 == -2);
+      if (pl->zti32 == -2)
+        VOFP_LAUNCH(KID_ZSOLVE, st,
+                    (k_ztab_seg<R, typename Red<R>::TT, true><<<tgrid, 32 * kZSegW, sm, st>>>(za, ztab_args(pl))));
+      else
+        VOFP_LAUNCH(KID_ZSOLVE, st,
+                    (k_ztab_seg<R, typename Red<R>::TT, false><<<tgrid, 32 * kZSegW, sm, st>>>(za, ztab_args(pl))));
     } else if (pl->zti32 == 0) {
       const dim3 tgrid((nx + kZStagedTI - 1) / kZStagedTI, ny);
       VOFP_LAUNCH(KID_ZSOLVE, st,

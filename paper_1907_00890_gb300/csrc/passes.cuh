@@ -50,12 +50,14 @@ struct XArgs {
   void* S;            // spectrum output
 };
 
-// 7-point L p at a cell with the ghost rules of the MAC operator, as a weighted sum of the neighbours with
-// per-plane coefficients (rdx2, rdy2, czp, czm, and czc for the centre): two additions and five
-// multiply(-add)s in FP64.
-__device__ __forceinline__ double lap_at(const GridDev& g, const double* __restrict__ p, int i, int j, int k) {
+// base - L p at a cell, L the 7-point operator with the ghost rules of the MAC grid, as a weighted sum of the
+// neighbours with per-plane coefficients (rdx2, rdy2, czp, czm, and czc for the centre) subtracted from `base`
+// in one multiply-add chain: two additions and five multiply-adds in FP64.
+__device__ __forceinline__ double resid_at(const GridDev& g, const double* __restrict__ p, int i, int j, int k,
+                                           double base) {
   const size_t plane = (size_t)g.nx * g.ny;
   const size_t c = k * plane + (size_t)j * g.nx + i;
+  if (!VOFP_IN(c, ncells(g), CHK_CELL_LOAD)) return base;
   const double pc = __ldg(p + c);
   double xs, ys, zlo, zhi;
   {
@@ -85,30 +87,30 @@ __device__ __forceinline__ double lap_at(const GridDev& g, const double* __restr
     if (k < g.nz - 1) zhi = __ldg(p + c + plane);
     else zhi = g.bcz == VOFP_BC_P ? __ldg(p + c - (size_t)(g.nz - 1) * plane) : neg_if(pc, !highN);
   }
-  return fma(xs, g.rdx2,
-             fma(ys, g.rdy2, fma(__ldg(g.czc + k), pc, fma(__ldg(g.czp + k), zhi, __ldg(g.czm + k) * zlo))));
+  return fma(-g.rdx2, xs,
+             fma(-g.rdy2, ys, fma(-__ldg(g.czc + k), pc, fma(-__ldg(g.czp + k), zhi, fma(-__ldg(g.czm + k), zlo, base)))));
 }
 
 template <int MODE>
 __device__ __forceinline__ double rhs_at(const XArgs& a, int i, int j, int k, double fbar) {
   const size_t c = ((size_t)k * a.g.ny + j) * a.g.nx + i;
+  if (!VOFP_IN(c, ncells(a.g), CHK_CELL_LOAD)) return 0.0;
   double f;
   if (MODE == RHS_F) {
     f = __ldg(a.f + c);
     if (a.scale != 1.0) f *= a.scale;
   } else if (MODE == RHS_DIV) {
-    f = divergence_at(a.g, a.u, a.v, a.w, i, j, k);
-    if (a.src) f -= __ldg(a.src + c);
-    f *= a.scale;
+    f = divergence_at(a.g, a.u, a.v, a.w, i, j, k, a.src ? -__ldg(a.src + c) : 0.0) * a.scale;
   } else if (MODE == RHS_STEFAN) {
     const double3 gc = grad_c_at(a.g, a.C, i, j, k, a.grad_mode);
     f = __ldg(a.mdot + c) * a.coef * sqrt(gc.x * gc.x + gc.y * gc.y + gc.z * gc.z);
   } else if (MODE == RHS_DIV_STEFAN) {
     const double3 gc = grad_c_at(a.g, a.C, i, j, k, a.grad_mode);
     const double s = __ldg(a.mdot + c) * a.coef * sqrt(gc.x * gc.x + gc.y * gc.y + gc.z * gc.z);
-    f = (divergence_at(a.g, a.u, a.v, a.w, i, j, k) - s) * a.scale;
+    f = divergence_at(a.g, a.u, a.v, a.w, i, j, k, -s) * a.scale;
   } else {
-    f = (__ldg(a.f + c) - fbar) - lap_at(a.g, a.p, i, j, k);
+    // (fbar = 0 unless the operator is singular: no subtraction then)
+    f = resid_at(a.g, a.p, i, j, k, a.defect_sum ? __ldg(a.f + c) - fbar : __ldg(a.f + c));
   }
   return f;
 }
@@ -181,7 +183,7 @@ __device__ __forceinline__ void xfwd_block(const XArgs& a, int bx, unsigned char
         const int k = lk[2 * pb + h], j = lj[2 * pb + h];
         const double f = rhs_at<MODE>(a, i, j, k, fbar);
         const R fr = red_of(f, (R*)nullptr);  // integer-pipe conversion in reduced-precision plans
-        if (a.fsave) a.fsave[l * n + i] = f;
+        if (a.fsave && VOFP_IN(l * n + i, nlines * n, CHK_XFWD_STORE)) a.fsave[l * n + i] = f;
         if (stats) {
           if (f64) {
             const double vol = __ldg(a.g.vol + k);
@@ -246,8 +248,8 @@ __device__ __forceinline__ void xfwd_block(const XArgs& a, int bx, unsigned char
     const long l0 = 2 * (pair0 + pb), l1 = l0 + 1;
     R oa, ob;
     fwd_post<C>(Z + pb * ld, n, bc, q, quart, oa, ob);
-    if (l0 < nlines) S[l0 * n + q] = (T)oa;
-    if (l1 < nlines) S[l1 * n + q] = (T)ob;
+    if (l0 < nlines && VOFP_IN(l0 * n + q, nlines * n, CHK_XFWD_STORE)) S[l0 * n + q] = (T)oa;
+    if (l1 < nlines && VOFP_IN(l1 * n + q, nlines * n, CHK_XFWD_STORE)) S[l1 * n + q] = (T)ob;
   }
 }
 
@@ -289,6 +291,7 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
   C* b1 = b0 + B * ld;
   const int i0 = bx * a.tx;
   const size_t base = (size_t)by * a.ny * a.nx;
+  const size_t cells = (size_t)a.nx * a.ny * a.nz;  // (bounds-checked builds)
   T* S = reinterpret_cast<T*>(a.S);
   const int bc = a.bc;
   const C* quart = reinterpret_cast<const C*>(a.quart);
@@ -297,8 +300,8 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
       const int c = t % B, j = t / B;
       const int i = i0 + 2 * c;
       const size_t o = base + (size_t)j * a.nx + i;
-      const R va = i < a.nx ? (R)S[o] : (R)0;
-      const R vb = i + 1 < a.nx ? (R)S[o + 1] : (R)0;
+      const R va = i < a.nx && VOFP_IN(o, cells, CHK_Y_PASS) ? (R)S[o] : (R)0;
+      const R vb = i + 1 < a.nx && VOFP_IN(o + 1, cells, CHK_Y_PASS) ? (R)S[o + 1] : (R)0;
       if (quarter_bc(bc)) {
         int pos;
         C v;
@@ -323,8 +326,8 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
       R oa, ob;
       fwd_post<C>(Z + c * ld, n, bc, q, quart, oa, ob);
       const size_t o = base + (size_t)q * a.nx + i;
-      if (i < a.nx) S[o] = (T)oa;
-      if (i + 1 < a.nx) S[o + 1] = (T)ob;
+      if (i < a.nx && VOFP_IN(o, cells, CHK_Y_PASS)) S[o] = (T)oa;
+      if (i + 1 < a.nx && VOFP_IN(o + 1, cells, CHK_Y_PASS)) S[o + 1] = (T)ob;
     }
   } else {
     // stage the tile column-major in b1: column col holds the packed line of length n
@@ -333,8 +336,8 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
       const int c = t % B, q = t / B;
       const int i = i0 + 2 * c;
       const size_t o = base + (size_t)q * a.nx + i;
-      st[(2 * c) * n + q] = i < a.nx ? (R)S[o] : (R)0;
-      st[(2 * c + 1) * n + q] = i + 1 < a.nx ? (R)S[o + 1] : (R)0;
+      st[(2 * c) * n + q] = i < a.nx && VOFP_IN(o, cells, CHK_Y_PASS) ? (R)S[o] : (R)0;
+      st[(2 * c + 1) * n + q] = i + 1 < a.nx && VOFP_IN(o + 1, cells, CHK_Y_PASS) ? (R)S[o + 1] : (R)0;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < B * n; t += blockDim.x) {
@@ -360,8 +363,8 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
       if (quarter_bc(bc)) {  // the transform again (twice it, as every pass): a forward-inverse pair gives 2n x
         R oa, ob;
         fwd_post<C>(Y + c * ld, n, bc, j, quart, oa, ob);
-        if (i < a.nx) S[o] = (T)oa;
-        if (i + 1 < a.nx) S[o + 1] = (T)ob;
+        if (i < a.nx && VOFP_IN(o, cells, CHK_Y_PASS)) S[o] = (T)oa;
+        if (i + 1 < a.nx && VOFP_IN(o + 1, cells, CHK_Y_PASS)) S[o + 1] = (T)ob;
         continue;
       }
       int idx = j;
@@ -371,8 +374,8 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
         fl = bc == VOFP_BC_DD && (j & 1);
       }
       const C y = Y[c * ld + idx];
-      if (i < a.nx) S[o] = (T)neg_if(y.x, fl);
-      if (i + 1 < a.nx) S[o + 1] = (T)neg_if(y.y, !fl);
+      if (i < a.nx && VOFP_IN(o, cells, CHK_Y_PASS)) S[o] = (T)neg_if(y.x, fl);
+      if (i + 1 < a.nx && VOFP_IN(o + 1, cells, CHK_Y_PASS)) S[o + 1] = (T)neg_if(y.y, !fl);
     }
   }
 }
@@ -427,7 +430,8 @@ __device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned c
     // the block's lines are consecutive: one contiguous run of the spectrum
     const long lim = (nlines - 2 * pair0) * n;
     const T* src = S + 2 * pair0 * n;
-    for (int t = threadIdx.x; t < 2 * PB * n; t += blockDim.x) st[t] = t < lim ? (R)src[t] : (R)0;
+    for (int t = threadIdx.x; t < 2 * PB * n; t += blockDim.x)
+      st[t] = t < lim && VOFP_IN(2 * pair0 * n + t, nlines * n, CHK_XINV) ? (R)src[t] : (R)0;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < PB * n; t += blockDim.x) {
@@ -476,11 +480,11 @@ __device__ __forceinline__ void xinv_block(const XInvArgs& a, int bx, unsigned c
     if (!a.p) {
       // norm only (the error estimate of a refinement plan): the transform's output is not stored
     } else if (a.accumulate) {
-      if (l0 < nlines) a.p[l0 * n + i] += va;
-      if (l1 < nlines) a.p[l1 * n + i] += vb;
+      if (l0 < nlines && VOFP_IN(l0 * n + i, nlines * n, CHK_XINV)) a.p[l0 * n + i] += va;
+      if (l1 < nlines && VOFP_IN(l1 * n + i, nlines * n, CHK_XINV)) a.p[l1 * n + i] += vb;
     } else {
-      if (l0 < nlines) a.p[l0 * n + i] = va;
-      if (l1 < nlines) a.p[l1 * n + i] = vb;
+      if (l0 < nlines && VOFP_IN(l0 * n + i, nlines * n, CHK_XINV)) a.p[l0 * n + i] = va;
+      if (l1 < nlines && VOFP_IN(l1 * n + i, nlines * n, CHK_XINV)) a.p[l1 * n + i] = vb;
     }
     if (f64) {
       if (a.mean_out) {

@@ -507,12 +507,12 @@ int plan_prepare(int nx, int ny, int nz, double dx, double dy, const double* dz,
     while (ti > 1 && (size_t)3 * ti * nz * rs > 96 * 1024) ti /= 2;
     p->zti32 = ti;
   } else {
-    // factor-table kernels: -1 = the segmented tile kernel (FP32 and FP32 pairs whenever a tile fits), 0 = the
-    // shared-memory staged kernel (grids with few systems), otherwise the streaming kernel's threads per
-    // block (forward values in shared memory when 64 or 128 threads' columns fit in 96 KB, else kept in
-    // place in the spectrum)
+    // factor-table kernels: -1 / -2 = the segmented tile kernel with the full / lean tile layout (FP32 and
+    // FP32 pairs whenever two tiles fit per SM), 0 = the shared-memory staged kernel (grids with few
+    // systems), otherwise the streaming kernel's threads per block (forward values in shared memory when 64
+    // or 128 threads' columns fit in 96 KB, else kept in place in the spectrum)
     auto table_ti = [&](size_t elem, bool fp64) {
-      if (ztab_use_seg(nz, elem, fp64)) return -1;
+      if (!fp64 && ztab_seg_code(nz, elem) != 0) return ztab_seg_code(nz, elem);
       if (ztab_use_staged(nx, ny, nz, elem)) return 0;
       if ((size_t)128 * nz * elem <= 96 * 1024) return 128;
       if ((size_t)64 * nz * elem <= 96 * 1024) return 64;

@@ -76,7 +76,8 @@ void init_kernel_attributes_fp64() {
   allow_smem(k_zsolve<double, double>);
   allow_smem(k_ztab<double, ZF<double>>);
   allow_smem(k_ztab_staged<double, ZF<double>>);
-  allow_smem(k_ztab_seg<double, ZF<double>>);
+  allow_smem(k_ztab_seg<double, ZF<double>, false>);
+  allow_smem(k_ztab_seg<double, ZF<double>, true>);
 }
 
 int grid_blocks(size_t total, int threads) {
@@ -228,11 +229,15 @@ int fp64_solve(vofp_plan* pl, int mode, XArgs xa, double* pout, cudaStream_t st,
   if (ny > 1 && !ypass_tma_f64(pl, ya, false, st))
     VOFP_LAUNCH(KID_YFWD, st, k_ypass_f64<false><<<ygrid, 256, ysm, st>>>(ya));
   ZArgs za = z_args(pl, stats);
-  if (pl->ztab && pl->zti == -1) {
+  if (pl->ztab && (pl->zti == -1 || pl->zti == -2)) {  // (only by the autotuner's choice on FP64 plans)
     const dim3 tgrid((nx + kZSegTI - 1) / kZSegTI, ny);
-    VOFP_LAUNCH(KID_ZSOLVE, st,
-                (k_ztab_seg<double, ZF<double>><<<tgrid, 32 * kZSegW, ztab_seg_smem(nz, sizeof(double)), st>>>(
-                    za, ztab_args(pl))));
+    const size_t sm = ztab_seg_smem(nz, sizeof(double), pl->zti == -2);
+    if (pl->zti == -2)
+      VOFP_LAUNCH(KID_ZSOLVE, st,
+                  (k_ztab_seg<double, ZF<double>, true><<<tgrid, 32 * kZSegW, sm, st>>>(za, ztab_args(pl))));
+    else
+      VOFP_LAUNCH(KID_ZSOLVE, st,
+                  (k_ztab_seg<double, ZF<double>, false><<<tgrid, 32 * kZSegW, sm, st>>>(za, ztab_args(pl))));
   } else if (pl->ztab && pl->zti == 0) {
     const dim3 tgrid((nx + kZStagedTI - 1) / kZStagedTI, ny);
     VOFP_LAUNCH(KID_ZSOLVE, st,
@@ -335,7 +340,8 @@ static int project_common(vofp_plan* pl, int mode, XArgs& xa, double* u, double*
   }
   const GridDev g = grid_dev(pl);
   VOFP_LAUNCH(KID_GRAD, st,
-              k_grad_update<<<face_grid(g, 256), 256, 0, st>>>(g, pout, u, v, w, dt_over_rho0));
+              k_grad_update<<<face_grid(g, 256), 256, 0, st>>>(g, pout, u, v, w, dt_over_rho0,
+                                                                      dt_over_rho0 * g.rdx, dt_over_rho0 * g.rdy));
   const int ls = cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
   if (pl->opts.prec != VOFP_FP64) {
     if (ls) return ls;

@@ -36,6 +36,12 @@ struct GridDev {
 };
 
 __host__ __device__ __forceinline__ int nface(int n, int bc) { return n + (bc != VOFP_BC_P); }
+__host__ __device__ __forceinline__ size_t ncells(const GridDev& g) { return (size_t)g.nx * g.ny * g.nz; }
+// the u, v, w face arrays: nface cells along their own axis
+__host__ __device__ __forceinline__ size_t nfaces(const GridDev& g, int axis) {
+  return (size_t)(axis == 0 ? nface(g.nx, g.bcx) : g.nx) * (axis == 1 ? nface(g.ny, g.bcy) : g.ny) *
+         (axis == 2 ? nface(g.nz, g.bcz) : g.nz);
+}
 
 // Neighbour index for a cell field: wrapped on a periodic axis, clamped (ghost copy) on a bounded one.
 __device__ __forceinline__ int cw(int i, int n, int bc) {
@@ -44,28 +50,32 @@ __device__ __forceinline__ int cw(int i, int n, int bc) {
   return i;
 }
 
+// Divergence of the face field (u, v, w) at cell (i, j, k) plus `addend`, the addend taken into the last
+// multiply-add (three subtractions and three multiply-adds in FP64).
 __device__ __forceinline__ double divergence_at(const GridDev& g, const double* __restrict__ u,
                                                 const double* __restrict__ v, const double* __restrict__ w, int i,
-                                                int j, int k) {
+                                                int j, int k, double addend = 0.0) {
   const int nxf = nface(g.nx, g.bcx), nyf = nface(g.ny, g.bcy);
   const size_t ub = ((size_t)k * g.ny + j) * nxf;
   const int ip = (g.bcx == VOFP_BC_P && i + 1 == g.nx) ? 0 : i + 1;
-  const double du = __ldg(u + ub + ip) - __ldg(u + ub + i);
+  const size_t nu = nfaces(g, 0), nv = nfaces(g, 1), nw = nfaces(g, 2);
+  const double du = ldg_in(u, ub + ip, nu, CHK_FACE_LOAD) - ldg_in(u, ub + i, nu, CHK_FACE_LOAD);
   const size_t vb = (size_t)k * nyf * g.nx + i;
   const int jp = (g.bcy == VOFP_BC_P && j + 1 == g.ny) ? 0 : j + 1;
-  const double dv = __ldg(v + vb + (size_t)jp * g.nx) - __ldg(v + vb + (size_t)j * g.nx);
+  const double dv = ldg_in(v, vb + (size_t)jp * g.nx, nv, CHK_FACE_LOAD) -
+                    ldg_in(v, vb + (size_t)j * g.nx, nv, CHK_FACE_LOAD);
   const size_t plane = (size_t)g.ny * g.nx;
   const int kp = (g.bcz == VOFP_BC_P && k + 1 == g.nz) ? 0 : k + 1;
   const size_t wb = (size_t)j * g.nx + i;
-  const double dw = __ldg(w + wb + kp * plane) - __ldg(w + wb + k * plane);
-  return fma(du, g.rdx, fma(dv, g.rdy, dw * __ldg(g.rdz + k)));
+  const double dw = ldg_in(w, wb + kp * plane, nw, CHK_FACE_LOAD) - ldg_in(w, wb + k * plane, nw, CHK_FACE_LOAD);
+  return fma(du, g.rdx, fma(dv, g.rdy, fma(dw, __ldg(g.rdz + k), addend)));
 }
 
 __device__ __forceinline__ double cval(const GridDev& g, const double* __restrict__ C, int i, int j, int k) {
   i = cw(i, g.nx, g.bcx);
   j = cw(j, g.ny, g.bcy);
   k = cw(k, g.nz, g.bcz);
-  return __ldg(C + ((size_t)k * g.ny + j) * g.nx + i);
+  return ldg_in(C, ((size_t)k * g.ny + j) * g.nx + i, ncells(g), CHK_CELL_LOAD);
 }
 
 // Cell-centred gradient of C: mode 0 central, mode 1 Youngs.
@@ -108,7 +118,7 @@ __device__ __forceinline__ double geometry_at(const GridDev& g, const double* __
   n = make_double3(0.0, 0.0, 0.0);
   if (m2 == 0.0) return 0.0;
   const double r = rsqrt(m2);
-  const double c = __ldg(C + ((size_t)k * g.ny + j) * g.nx + i);
+  const double c = ldg_in(C, ((size_t)k * g.ny + j) * g.nx + i, ncells(g), CHK_CELL_LOAD);
   if (fmin(c, 1.0 - c) >= 1e-8) {
     n.x = -gc.x * r;
     n.y = -gc.y * r;

@@ -82,6 +82,21 @@ cudaError_t pinned_alloc(void** p, size_t bytes) {
   return cudaMallocHost(p, bytes);
 }
 
+// Readers of the bounds-checked build's device words, one per translation unit (registered during the
+// library's static initialisation; the plain build registers none).
+typedef int (*ChkReader)(long long*, int);
+static std::vector<ChkReader>& chk_readers() {
+  static std::vector<ChkReader> r;
+  return r;
+}
+int chk_register(int (*read)(long long* out, int reset)) {
+  chk_readers().push_back(read);
+  return (int)chk_readers().size();
+}
+
+// One index test that fails by construction and touches no memory.
+static __global__ void k_check_selftest(int idx, int ext) { (void)VOFP_IN(idx, ext, CHK_SELFTEST); }
+
 }  // namespace vofp
 
 using namespace vofp;
@@ -89,6 +104,29 @@ using namespace vofp;
 extern "C" int vofp_debug_fail_alloc(long long after) {
   g_fail_after.store(after < 0 ? -1 : after);
   return VOFP_OK;
+}
+
+extern "C" int vofp_debug_check_word(long long* out, int reset) {
+  if (!out) return VOFP_ERR_INVALID_ARG;
+  for (int q = 0; q < 4; ++q) out[q] = 0;
+  if (chk_readers().empty()) return 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) return VOFP_ERR_CUDA;
+  for (ChkReader rd : chk_readers()) {
+    long long w[4];
+    if (rd(w, reset) != 0) return VOFP_ERR_CUDA;
+    if (w[0] > 0 && out[0] == 0) {
+      out[1] = w[1];
+      out[2] = w[2];
+      out[3] = w[3];
+    }
+    out[0] += w[0];
+  }
+  return 1;
+}
+
+extern "C" int vofp_debug_check_selftest(void* stream) {
+  k_check_selftest<<<1, 1, 0, (cudaStream_t)stream>>>(5, 4);
+  return cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
 }
 
 extern "C" int vofp_trace_enable(int on) {

@@ -107,7 +107,7 @@ bool fits(const vofp_plan* p, const Shape& s) {
   if (p->ztab) {  // factor-table kernels: -1 = segmented tiles, 0 = staged (if the tile fits), else whole
                   // warps of one system each
     const size_t e = f32 ? sizeof(float) : sizeof(double);
-    if (s.zti == -1) return vofp::ztab_seg_smem(p->n[2], e) <= 200 * 1024;
+    if (s.zti == -1 || s.zti == -2) return vofp::ztab_seg_smem(p->n[2], e, s.zti == -2) <= 200 * 1024;
     return s.zti == 0 ? vofp::ztab_staged_smem(p->n[2], e) <= 200 * 1024 : s.zti >= 32;
   }
   return (size_t)3 * s.zti * p->n[2] * r <= lim;
@@ -153,11 +153,11 @@ extern "C" int vofp_plan_tune(vofp_plan* p) {
   float tbest = time_solve(p, st);
   const int xs[] = {1, 2, 4, 8, 16, 32};
   const int ys[] = {2, 4, 8, 16, 32};
-  const int zs[] = {-1, 0, 8, 16, 32, 64, 128};
+  const int zs[] = {-1, -2, 0, 8, 16, 32, 64, 128};
   const int os[] = {0, 1, 2, 3};
   for (int knob = 0; knob < 4; ++knob) {
     const int* cand = knob == 0 ? xs : (knob == 1 ? ys : (knob == 2 ? zs : os));
-    const int nc = knob == 0 ? 6 : (knob == 1 ? 5 : (knob == 2 ? 7 : 4));
+    const int nc = knob == 0 ? 6 : (knob == 1 ? 5 : (knob == 2 ? 8 : 4));
     for (int c = 0; c < nc; ++c) {
       Shape s = best;
       if (knob == 0) s.xpb = cand[c];

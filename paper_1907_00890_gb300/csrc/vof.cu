@@ -58,6 +58,12 @@ __device__ __forceinline__ double vof_step(const GridDev& g, const double* __res
     fbase = (size_t)j * g.nx + i, fst = plane, rw = __ldg(g.rdz + k);
   }
   const int fp = (bc == VOFP_BC_P && f + 1 == n) ? 0 : f + 1;  // the high face of the cell
+  if (!VOFP_IN(base + (size_t)(n - 1) * st, ncells(g), CHK_VOF_LOAD) ||
+      !VOFP_IN(fbase + (size_t)(nface(n, bc) - 1) * fst, nfaces(g, axis), CHK_VOF_LOAD) ||
+      !VOFP_IN(f, n, CHK_VOF_LOAD)) {
+    du = 0.0;
+    return 0.0;
+  }
   const double vlo = __ldg(vel + fbase + (size_t)f * fst), vhi = __ldg(vel + fbase + (size_t)fp * fst);
   const double qlo = upwind_value(q, base, st, n, bc, f, vlo);
   const double qhi = upwind_value(q, base, st, n, bc, f + 1, vhi);
@@ -127,7 +133,8 @@ static __global__ void __launch_bounds__(kVofTX * kVofTY) k_vof_fused(GridDev g,
     if (!act) return;
     const int jp = (g.bcy == VOFP_BC_P && j + 1 == ny) ? 0 : j + 1;
     const size_t vb = (size_t)k * nyf * nx + i;
-    const double vlo = __ldg(vG + vb + (size_t)j * nx), vhi = __ldg(vG + vb + (size_t)jp * nx);
+    const double vlo = ldg_in(vG, vb + (size_t)j * nx, nfaces(g, 1), CHK_VOF_LOAD);
+    const double vhi = ldg_in(vG, vb + (size_t)jp * nx, nfaces(g, 1), CHK_VOF_LOAD);
     double dv;
     dst[ty * kVofTX + tx] = vof_step_local(src[ty * kVofTX + tx], src[(ty + 1) * kVofTX + tx],
                                            src[(ty + 2) * kVofTX + tx], vlo, vhi, g.rdy, dt, dv);
@@ -138,18 +145,22 @@ static __global__ void __launch_bounds__(kVofTX * kVofTY) k_vof_fused(GridDev g,
     const int o = ty * kVofTX + tx;
     const size_t fb = (size_t)j * nx + i;
     const int kp = (g.bcz == VOFP_BC_P && k + 1 == nz) ? 0 : k + 1;
-    const double wlo = __ldg(wG + fb + (size_t)k * plane), whi = __ldg(wG + fb + (size_t)kp * plane);
+    const double wlo = ldg_in(wG, fb + (size_t)k * plane, nfaces(g, 2), CHK_VOF_LOAD);
+    const double whi = ldg_in(wG, fb + (size_t)kp * plane, nfaces(g, 2), CHK_VOF_LOAD);
     double dw;
     const double c3 = vof_step_local(qm[o], q[o], qp[o], wlo, whi, __ldg(g.rdz + k), dt, dw);
     const int nxf = nface(nx, g.bcx);
     const int ip = (g.bcx == VOFP_BC_P && i + 1 == nx) ? 0 : i + 1;
     const size_t ub = ((size_t)k * ny + j) * nxf;
-    const double du = (__ldg(uG + ub + ip) - __ldg(uG + ub + i)) * g.rdx;
+    const double du =
+        (ldg_in(uG, ub + ip, nfaces(g, 0), CHK_VOF_LOAD) - ldg_in(uG, ub + i, nfaces(g, 0), CHK_VOF_LOAD)) * g.rdx;
     const int jp = (g.bcy == VOFP_BC_P && j + 1 == ny) ? 0 : j + 1;
     const size_t vb = (size_t)k * nyf * nx + i;
-    const double dv = (__ldg(vG + vb + (size_t)jp * nx) - __ldg(vG + vb + (size_t)j * nx)) * g.rdy;
+    const double dv = (ldg_in(vG, vb + (size_t)jp * nx, nfaces(g, 1), CHK_VOF_LOAD) -
+                       ldg_in(vG, vb + (size_t)j * nx, nfaces(g, 1), CHK_VOF_LOAD)) * g.rdy;
     const double F = fma(c1[(ty + 1) * kVofTX + tx], du, fma(q[o], dv, c3 * dw));
-    out[(size_t)k * plane + fb] = fma(-dt, F, c3) * recip_newton1(fma(-dt, du + dv + dw, 1.0));
+    if (VOFP_IN((size_t)k * plane + fb, plane * nz, CHK_CELL_STORE))
+      out[(size_t)k * plane + fb] = fma(-dt, F, c3) * recip_newton1(fma(-dt, du + dv + dw, 1.0));
   };
   for (int m = k0 - 1; m <= k1; ++m) {
     const int s = m - (k0 - 1);  // march step: ring slots s & 1 (C*) and s % 3 (C**)

@@ -16,6 +16,7 @@
 #include <type_traits>
 #include <stdint.h>
 
+#include "checked.cuh"
 #include "ffloat.cuh"
 #include "vofp.h"
 

@@ -192,11 +192,12 @@ __global__ void __launch_bounds__(kXTmaThreads) k_xinv_tma(const XTmaArgs a, con
       const double va = wide_of(ya), vb = wide_of(yb);
       if (x.p) {
         if (x.accumulate) {
-          if (la < nlines) x.p[la * n + i] = pt[(2 * pb) * n + i] + va;
-          if (lb < nlines) x.p[lb * n + i] = pt[(2 * pb + 1) * n + i] + vb;
+          if (la < nlines && VOFP_IN(la * n + i, nlines * n, CHK_X_TMA)) x.p[la * n + i] = pt[(2 * pb) * n + i] + va;
+          if (lb < nlines && VOFP_IN(lb * n + i, nlines * n, CHK_X_TMA))
+            x.p[lb * n + i] = pt[(2 * pb + 1) * n + i] + vb;
         } else {
-          if (la < nlines) x.p[la * n + i] = va;
-          if (lb < nlines) x.p[lb * n + i] = vb;
+          if (la < nlines && VOFP_IN(la * n + i, nlines * n, CHK_X_TMA)) x.p[la * n + i] = va;
+          if (lb < nlines && VOFP_IN(lb * n + i, nlines * n, CHK_X_TMA)) x.p[lb * n + i] = vb;
         }
       }
       if (x.mean_out) {

@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(kXtcThreads) k_xtc(const XtcArgs a) {
         const int i = c * g.kc + (cmi % (g.kc >> 2)) * 4 + (within & 3);
         const long l = line0 + r;
         float x = 0.f;
-        if (l < a.nlines && i < n) {
+        if (l < a.nlines && i < n && VOFP_IN(l * n + i, a.nlines * n, CHK_XTC)) {
           if (DIR == 0) {
             const int k = lk[r], j = lj[r];
             const double f = rhs_at<MODE>(a.xa, i, j, k, fbar);
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(kXtcThreads) k_xtc(const XtcArgs a) {
         for (int u = 0; u < 8; ++u) {
           const int r = half * (kXtcLines / 2) + lb + u;
           const long l = line0 + r;
-          if (l >= a.nlines || q >= n) continue;
+          if (l >= a.nlines || q >= n || !VOFP_IN(l * n + q, a.nlines * n, CHK_XTC)) continue;
           if (DIR == 0) {
             reinterpret_cast<float*>(a.xa.S)[l * n + q] = v[u];
           } else {

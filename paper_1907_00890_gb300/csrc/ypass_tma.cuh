@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(kYTmaThreads) k_ypass_tma(const YTmaArgs a, co
   const C* quart = reinterpret_cast<const C*>(y.quart);
   const int bc = y.bc;
   const int nx = y.nx;
+  const size_t cells = (size_t)nx * y.ny * y.nz;  // (bounds-checked builds)
   for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
     const int cur = it & 1;
     const int nxt = tile + gridDim.x;
@@ -276,8 +277,8 @@ __global__ void __launch_bounds__(kYTmaThreads) k_ypass_tma(const YTmaArgs a, co
         T oa, ob;
         fwd_post<C>(Z + c, n, bc, q, quart, oa, ob, B);
         const size_t o = pbase + (size_t)q * nx + i;
-        if (i < nx) S[o] = oa;
-        if (i + 1 < nx) S[o + 1] = ob;
+        if (i < nx && VOFP_IN(o, cells, CHK_Y_TMA)) S[o] = oa;
+        if (i + 1 < nx && VOFP_IN(o + 1, cells, CHK_Y_TMA)) S[o + 1] = ob;
       }
     } else {
       for (int t = threadIdx.x; t < items; t += kYTmaThreads) {
@@ -318,8 +319,8 @@ __global__ void __launch_bounds__(kYTmaThreads) k_ypass_tma(const YTmaArgs a, co
           oa = neg_if(v.x, fl);
           ob = neg_if(v.y, !fl);
         }
-        if (i < nx) S[o] = oa;
-        if (i + 1 < nx) S[o + 1] = ob;
+        if (i < nx && VOFP_IN(o, cells, CHK_Y_TMA)) S[o] = oa;
+        if (i + 1 < nx && VOFP_IN(o + 1, cells, CHK_Y_TMA)) S[o + 1] = ob;
       }
     }
     __syncthreads();  // this tile's buffers are free again

@@ -141,7 +141,7 @@ __device__ __forceinline__ void zsolve_block(const ZArgs& a, int bx, int by, uns
   TS* S = reinterpret_cast<TS*>(a.S);
   for (int t = threadIdx.x; t < nz * TI; t += blockDim.x) {
     const int k = t / TI, c = t - k * TI;
-    d[t] = (i0 + c < a.nx) ? (TA)S[k * plane + col0 + c] : (TA)0;
+    d[t] = (i0 + c < a.nx && VOFP_IN(col0 + c, plane, CHK_Z_COLUMN)) ? (TA)S[k * plane + col0 + c] : (TA)0;
   }
   __syncthreads();
   const int c = threadIdx.x;
@@ -157,7 +157,7 @@ __device__ __forceinline__ void zsolve_block(const ZArgs& a, int bx, int by, uns
   __syncthreads();
   for (int t = threadIdx.x; t < nz * TI; t += blockDim.x) {
     const int k = t / TI, cc2 = t - k * TI;
-    if (i0 + cc2 < a.nx) {
+    if (i0 + cc2 < a.nx && VOFP_IN(col0 + cc2, plane, CHK_Z_COLUMN)) {
       bool low = false;
       if (a.lowthr >= 0) low = fabs(__ldg(a.lamx + i0 + cc2) + __ldg(a.lamy + jq)) <= a.lowthr;
       if (!low) S[k * plane + col0 + cc2] = (TS)d[t];
@@ -179,6 +179,7 @@ static __global__ void k_zfactor_low(ZArgs a, const int2* __restrict__ modes, in
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nlow) return;
   const int2 md = modes[t];
+  if (!VOFP_IN(md.x, a.nx, CHK_Z_TABLE) || !VOFP_IN(md.y, a.ny, CHK_Z_TABLE)) return;
   const double lam = a.lamx[md.x] + a.lamy[md.y];
   const bool sing = a.singular && md.x == 0 && md.y == 0;
   const int k0 = sing ? 1 : 0;
@@ -200,6 +201,7 @@ __device__ __forceinline__ void zlow_system(const ZArgs& a, int2 md, int t, int 
   const size_t plane = (size_t)a.nx * a.ny;
   TS* S = reinterpret_cast<TS*>(a.S);
   const size_t col = (size_t)md.y * a.nx + md.x;
+  if (!VOFP_IN(col, plane, CHK_Z_COLUMN) || !VOFP_IN(md.x, a.nx, CHK_Z_COLUMN)) return;
   if (!tab) {
     double* d = scratch + (size_t)t * 3 * nz;
     for (int k = 0; k < nz; ++k) d[k] = (double)S[k * plane + col];
@@ -295,6 +297,7 @@ static __global__ void k_zfactor(ZArgs a, ZTabArgs zt, TT* tab) {
   const int ux = t % zt.Ux, uy = t / zt.Ux;
   const int qx = zt.bcx == VOFP_BC_P ? (ux ? 2 * ux - 1 : 0) : ux;
   const int qy = zt.bcy == VOFP_BC_P ? (uy ? 2 * uy - 1 : 0) : uy;
+  if (!VOFP_IN(qx, a.nx, CHK_Z_TABLE) || !VOFP_IN(qy, a.ny, CHK_Z_TABLE)) return;
   const double lam = a.lamx[qx] + a.lamy[qy];
   const bool sing = a.singular && ux == 0 && uy == 0;
   const int k0 = sing ? 1 : 0;
@@ -429,6 +432,9 @@ __device__ __forceinline__ void ztab_block(const ZArgs& a, const ZTabArgs& zt, i
   T* col = reinterpret_cast<T*>(a.S) + (size_t)j * a.nx + i;
   T* dsm = reinterpret_cast<T*>(smem_raw) + c;
   const size_t ts = (size_t)zt.Ux * zt.Uy;
+  if (!VOFP_IN((size_t)j * a.nx + i, plane, CHK_Z_COLUMN) ||
+      !VOFP_IN((size_t)distinct_index(j, zt.bcy) * zt.Ux + distinct_index(i, zt.bcx), ts, CHK_Z_TABLE))
+    return;
   const TT* F = reinterpret_cast<const TT*>(zt.tab) + (size_t)distinct_index(j, zt.bcy) * zt.Ux +
                 distinct_index(i, zt.bcx);
   const T* za = reinterpret_cast<const T*>(zt.za);
@@ -600,6 +606,8 @@ __device__ __forceinline__ void zlow_scan_system(const ZArgs& a, int2 md, int t,
                                                  const double2* __restrict__ tab, double* __restrict__ scratch,
                                                  int lane) {
   TS* col = reinterpret_cast<TS*>(a.S) + (size_t)md.y * a.nx + md.x;
+  if (!VOFP_IN((size_t)md.y * a.nx + md.x, (size_t)a.nx * a.ny, CHK_Z_COLUMN) || !VOFP_IN(md.x, a.nx, CHK_Z_COLUMN))
+    return;  // (uniform per warp)
   zscan_system<double, TS, double2>(a, col, (size_t)a.nx * a.ny, tab + t, (size_t)nlow, scratch + t, (size_t)nlow,
                                     a.za, a.singular && md.x == 0 && md.y == 0, lane);
 }
@@ -650,6 +658,9 @@ static __global__ void __launch_bounds__(128) k_ztab_staged(ZArgs a, ZTabArgs zt
   const int cut = zt.lowcut ? __ldg(zt.lowcut + j) : 0;
   const bool sing_here = a.singular && j == 0 && i0 == 0;  // the pinned mode is column 0 of this tile
   const int ncol = a.nx - i0 < TI ? a.nx - i0 : TI;
+  if (!VOFP_IN(i0, a.nx, CHK_Z_COLUMN) || !VOFP_IN((size_t)j * a.nx + i0 + ncol - 1, plane, CHK_Z_COLUMN) ||
+      !VOFP_IN((size_t)distinct_index(j, zt.bcy) * zt.Ux + distinct_index(i0 + ncol - 1, zt.bcx), ts, CHK_Z_TABLE))
+    return;  // (uniform per block)
   // tile load: eight rows per thread in flight (all loads issued before any is used)
   constexpr int UL = 8;
   for (int t0 = threadIdx.x; t0 < nz * TI; t0 += UL * blockDim.x) {
@@ -747,34 +758,48 @@ static __global__ void __launch_bounds__(128) k_ztab_staged(ZArgs a, ZTabArgs zt
 
 // ---- segmented tiles: every warp on the recurrences ---------------------------------------------------
 // The staged kernel leaves three of its four warps idle while warp 0 runs 32 recurrences of nz rows each, so
-// a tile costs 2 nz dependent multiply-adds of latency.  Here a tile of 32 systems ([nz][32] in shared
-// memory, as above) is cut into 8 row segments, one warp each, and every recurrence d_k = alpha_k d_{k-1} +
-// beta_k (then x_k = g_k x_{k+1} + d_k, g_k = -c'_k) is an affine map composed in two levels: each warp composes
-// its segment's rows into one map (A, B), each warp folds the maps of the segments before it (at most 7) into
-// its carry-in, then re-runs its rows from that carry.  Latency per sweep: 2 nz / 8 + 7 steps instead of nz;
-// work: about 2.5 multiply-adds per row and sweep instead of 1.  Used where the arithmetic is cheap: FP32 and
-// FP32 pairs, any grid whose tile fits (measured 2.7x faster than the streaming kernel at 250 x 250 x 128,
-// 1.5x faster than the staged one at 128^3).  FP64 keeps the staged and streaming kernels: its narrow FP64
-// pipe makes the extra multiply-adds cost more than the latency they hide (128^3: 60 us against 48 us).
+// a tile costs 2 nz dependent multiply-adds of latency.  Here a tile of 32 systems is cut into 8 row
+// segments, one warp each, and every recurrence d_k = alpha_k d_{k-1} + beta_k (then x_k = g_k x_{k+1} + d_k,
+// g_k = -c'_k) is an affine map composed in two levels: each warp composes its segment's rows into one map
+// (A, B), each warp folds the maps of the segments before it (at most 7) into its carry-in, then re-runs its
+// rows from that carry.  Latency per sweep: 2 nz / 8 + 7 steps instead of nz; work: about 2.5 multiply-adds
+// per row and sweep instead of 1.  Used where the arithmetic is cheap: FP32 and FP32 pairs (FP64 keeps the
+// staged and streaming kernels: its narrow FP64 pipe makes the extra multiply-adds cost more than the
+// latency they hide).
+//
+// Two layouts of the tile in shared memory ([nz][32] each array):
+//   full: alpha_k, beta_k and c'_k staged as the tile is loaded (three values per cell);
+//   lean: beta_k only (overwritten by d_k, then x_k); alpha_k and c'_k are re-read from the factor table
+//         (the tile's entries, some 100 KB at nz = 512, come from DRAM once and from L2 after).
+// A kernel that holds the SM alone stops the SM's memory traffic during its recurrences, so the plan takes
+// the full layout while two blocks still fit per SM (FP32 up to nz = 279, FP32 pairs up to 134), else the
+// lean one (FP32 up to nz = 822, FP32 pairs up to 395; at 512^3 in FP32: 1.76 -> 1.23 ms per launch), else
+// the streaming kernel.  The full layout is the faster one where both fit twice (128^3 FP32: 13.4 against
+// 14.9 us).
 constexpr int kZSegTI = 32, kZSegW = 8;
-inline size_t ztab_seg_smem(int nz, size_t elem) {
-  return ((size_t)nz * (3 * kZSegTI + 1) + (size_t)4 * kZSegW * kZSegTI) * elem;
+inline size_t ztab_seg_smem(int nz, size_t elem, bool lean) {
+  return ((size_t)nz * ((lean ? 1 : 3) * kZSegTI + 1) + (size_t)4 * kZSegW * kZSegTI) * elem;
 }
-inline bool ztab_use_seg(int nz, size_t elem, bool fp64) {
-  return !fp64 && ztab_seg_smem(nz, elem) <= 200 * 1024;
+// plan code of the segmented kernel for a reduced-precision plan: -1 full, -2 lean, 0 neither (two blocks per
+// SM must fit: 110 KB each)
+inline int ztab_seg_code(int nz, size_t elem) {
+  if (ztab_seg_smem(nz, elem, false) <= 110 * 1024) return -1;
+  if (ztab_seg_smem(nz, elem, true) <= 110 * 1024) return -2;
+  return 0;
 }
 
 // Block body (kZSegW warps): tile bx of row by.
-template <typename T, typename TT>
+template <typename T, typename TT, bool LEAN>
 __device__ __forceinline__ void ztab_seg_block(const ZArgs& a, const ZTabArgs& zt, int bx, int by,
                                                unsigned char* smem_raw) {
   if (launch_skipped(a.skip_conv, a.skip_k, a.tol2)) return;
   constexpr int TI = kZSegTI, W = kZSegW;
   const int nz = a.nz;
   const int i0 = bx * TI, j = by;
-  Pair<T>* ab = reinterpret_cast<Pair<T>*>(smem_raw);  // [nz][TI] (alpha_k, beta_k), then d_k / x_k in .y
-  T* cp = reinterpret_cast<T*>(ab + (size_t)nz * TI);  // [nz][TI] c'_k
-  T* fA = cp + (size_t)nz * TI;                         // [W][TI] segment maps: forward A, B, backward A, B
+  T* yv = reinterpret_cast<T*>(smem_raw);            // [nz][TI] beta_k, then d_k, then x_k
+  T* alv = yv + (LEAN ? 0 : (size_t)nz * TI);         // [nz][TI] alpha_k (full layout)
+  T* cpv = alv + (LEAN ? 0 : (size_t)nz * TI);        // [nz][TI] c'_k (full layout)
+  T* fA = (LEAN ? yv : cpv) + (size_t)nz * TI;        // [W][TI] segment maps: forward A, B, backward A, B
   T* fB = fA + W * TI;
   T* bA = fB + W * TI;
   T* bB = bA + W * TI;
@@ -787,7 +812,10 @@ __device__ __forceinline__ void ztab_seg_block(const ZArgs& a, const ZTabArgs& z
   const int cut = zt.lowcut ? __ldg(zt.lowcut + j) : 0;
   const bool sing_here = a.singular && j == 0 && i0 == 0;  // the pinned mode is column 0 of this tile
   const int ncol = a.nx - i0 < TI ? a.nx - i0 : TI;
-  // tile load: eight rows per thread in flight
+  if (!VOFP_IN(i0, a.nx, CHK_Z_COLUMN) || !VOFP_IN((size_t)j * a.nx + i0 + ncol - 1, plane, CHK_Z_COLUMN) ||
+      !VOFP_IN((size_t)distinct_index(j, zt.bcy) * zt.Ux + distinct_index(i0 + ncol - 1, zt.bcx), ts, CHK_Z_TABLE))
+    return;  // (uniform per block)
+  // tile load: eight rows per thread in flight; beta_k = m_k r_k (scaled)
   constexpr int UL = 8;
   for (int t0 = threadIdx.x; t0 < nz * TI; t0 += UL * blockDim.x) {
     T rv[UL];
@@ -797,7 +825,10 @@ __device__ __forceinline__ void ztab_seg_block(const ZArgs& a, const ZTabArgs& z
       const int t = t0 + u * blockDim.x;
       const int k = t / TI, c = t - k * TI;
       if (t < nz * TI && c < ncol && i0 + c >= cut) {
-        fv[u] = F[k * ts + distinct_index(i0 + c, zt.bcx)];
+        if (LEAN)
+          fv[u].ms = F[k * ts + distinct_index(i0 + c, zt.bcx)].ms;
+        else
+          fv[u] = F[k * ts + distinct_index(i0 + c, zt.bcx)];
         rv[u] = S[k * plane + c];
       }
     }
@@ -806,26 +837,30 @@ __device__ __forceinline__ void ztab_seg_block(const ZArgs& a, const ZTabArgs& z
       const int t = t0 + u * blockDim.x;
       const int k = t / TI, c = t - k * TI;
       if (t < nz * TI && c < ncol && i0 + c >= cut) {
-        Pair<T> v;
-        v.x = fv[u].al;
-        v.y = rv[u] * fv[u].ms;
-        ab[t] = v;
-        cp[t] = fv[u].c;
+        yv[t] = rv[u] * fv[u].ms;
+        if (!LEAN) {
+          alv[t] = fv[u].al;
+          cpv[t] = fv[u].c;
+        }
       }
     }
   }
   __syncthreads();
   const int w = threadIdx.x >> 5, c = threadIdx.x & 31;
-  // lanes without a system of their own (past the row's end, low modes, the pinned mode) run on zeros
+  // lanes without a system of their own (past the row's end, low modes, the pinned mode) run on zeros and
+  // read no factors
   const bool live = c < ncol && i0 + c >= cut && !(sing_here && c == 0);
+  const TT* Fl = F + (live ? distinct_index(i0 + c, zt.bcx) : 0);  // this lane's factor column (stride ts)
+  auto alpha = [&](int k) { return LEAN ? Fl[k * ts].al : alv[k * TI + c]; };
+  auto cprime = [&](int k) { return LEAN ? Fl[k * ts].c : cpv[k * TI + c]; };
   const int L = (nz + W - 1) / W;
   const int k0 = w * L < nz ? w * L : nz;
   const int k1 = k0 + L < nz ? k0 + L : nz;
   {  // forward: this segment's rows as one map d_out = A d_in + B
     T A = (T)1, B = (T)0;
+#pragma unroll 4
     for (int k = k0; k < k1; ++k) {
-      const Pair<T> v = ab[k * TI + c];
-      const T al = live ? v.x : (T)0, be = live ? v.y : (T)0;
+      const T al = live ? alpha(k) : (T)0, be = live ? yv[k * TI + c] : (T)0;
       B = fma_t(al, B, be);
       A = al * A;
     }
@@ -836,18 +871,19 @@ __device__ __forceinline__ void ztab_seg_block(const ZArgs& a, const ZTabArgs& z
   {
     T d = (T)0;
     for (int sg = 0; sg < w; ++sg) d = fma_t(fA[sg * TI + c], d, fB[sg * TI + c]);
+#pragma unroll 4
     for (int k = k0; k < k1; ++k) {
-      const Pair<T> v = ab[k * TI + c];
-      d = live ? fma_t(v.x, d, v.y) : (T)0;
-      ab[k * TI + c].y = d;
+      d = live ? fma_t(alpha(k), d, yv[k * TI + c]) : (T)0;
+      yv[k * TI + c] = d;
     }
   }
   __syncthreads();
   {  // backward: x_{nz-1} = d_{nz-1}, x_k = -c'_k x_{k+1} + d_k
     T A = (T)1, B = (T)0;
+#pragma unroll 4
     for (int k = k1 - 1; k >= k0; --k) {
-      const T g = (k == nz - 1 || !live) ? (T)0 : -cp[k * TI + c];
-      B = fma_t(g, B, ab[k * TI + c].y);
+      const T g = (k == nz - 1 || !live) ? (T)0 : -cprime(k);
+      B = fma_t(g, B, yv[k * TI + c]);
       A = g * A;
     }
     bA[w * TI + c] = A;
@@ -857,10 +893,11 @@ __device__ __forceinline__ void ztab_seg_block(const ZArgs& a, const ZTabArgs& z
   {
     T x = (T)0;
     for (int sg = W - 1; sg > w; --sg) x = fma_t(bA[sg * TI + c], x, bB[sg * TI + c]);
+#pragma unroll 4
     for (int k = k1 - 1; k >= k0; --k) {
-      const T g = (k == nz - 1 || !live) ? (T)0 : -cp[k * TI + c];
-      x = fma_t(g, x, ab[k * TI + c].y);
-      ab[k * TI + c].y = x;
+      const T g = (k == nz - 1 || !live) ? (T)0 : -cprime(k);
+      x = fma_t(g, x, yv[k * TI + c]);
+      yv[k * TI + c] = x;
     }
   }
   if (w == 0 && sing_here && cut == 0) zscan_system<T, T, TT>(a, S, plane, F, ts, scr, 1, za, true, c);
@@ -870,7 +907,7 @@ __device__ __forceinline__ void ztab_seg_block(const ZArgs& a, const ZTabArgs& z
     const int k = t / TI, cc = t - k * TI;
     const int i = i0 + cc;
     if (cc < ncol && i >= cut && !(sing_here && cc == 0)) {
-      const T x = ab[t].y;
+      const T x = yv[t];
       S[k * plane + cc] = x;
       if (a.info) bad |= !isfinite((double)x);
     }
@@ -878,10 +915,10 @@ __device__ __forceinline__ void ztab_seg_block(const ZArgs& a, const ZTabArgs& z
   if (bad) atomicOr(&a.info->nonfinite, 1u);
 }
 
-template <typename T, typename TT>
+template <typename T, typename TT, bool LEAN>
 static __global__ void __launch_bounds__(256) k_ztab_seg(ZArgs a, ZTabArgs zt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ztab_seg_block<T, TT>(a, zt, blockIdx.x, blockIdx.y, smem_raw);
+  ztab_seg_block<T, TT, LEAN>(a, zt, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 }  // namespace vofp

@@ -3,20 +3,23 @@
 Every function keeps the C name and passes device pointers (``tensor.data_ptr()``) and the current CUDA
 stream to the library; all arithmetic of the solve runs in the library's kernels.  Importing this module
 fails loudly if the library has not been built (``python -m paper_1907_00890_gb300.build``); there is no
-CPU fallback.
+CPU fallback.  With ``VOFP_CHECKED=1`` in the environment it loads the bounds-checked library instead.
 """
 import ctypes
 import os
 
 import numpy as np
 
-from .build import LIB
+from .build import lib_path
 
 BC = {"P": 0, "NN": 1, "DD": 2, "ND": 3, "DN": 4}
 FP64, MIXED, FF = 0, 1, 2
 
+CHECKED = os.environ.get("VOFP_CHECKED", "0") == "1"
+LIB = lib_path(CHECKED)
 if not os.path.exists(LIB):
-    raise ImportError("vofp library not built: %s is missing (run paper_1907_00890_gb300.build.build())" % LIB)
+    raise ImportError("vofp library not built: %s is missing (run paper_1907_00890_gb300.build.build(%s))"
+                      % (LIB, "checked=True" if CHECKED else ""))
 _lib = ctypes.CDLL(LIB)
 
 
@@ -85,6 +88,27 @@ EXPORTED = ["vofp_opts_default", "vofp_plan_create", "vofp_plan_destroy", "vofp_
 def vofp_debug_fail_alloc(after):
     """Make the (after + 1)-th next device / pinned allocation of the library fail once (after < 0: off)."""
     return _lib.vofp_debug_fail_alloc(int(after))
+
+
+_lib.vofp_debug_check_word.argtypes = [ctypes.POINTER(ctypes.c_longlong), _I]
+_lib.vofp_debug_check_word.restype = _I
+_lib.vofp_debug_check_selftest.argtypes = [_P]
+_lib.vofp_debug_check_selftest.restype = _I
+EXPORTED += ["vofp_debug_check_word", "vofp_debug_check_selftest"]
+
+
+def vofp_debug_check_word(reset=False):
+    """Bounds-checked library: (status, {count, site, index, extent}) of the failed index tests so far, summed
+    over the library's translation units (status 1; the plain library returns 0 and zeros)."""
+    w = (ctypes.c_longlong * 4)()
+    st = _lib.vofp_debug_check_word(w, 1 if reset else 0)
+    return st, {"count": w[0], "site": w[1], "index": w[2], "extent": w[3]}
+
+
+def vofp_debug_check_selftest():
+    """One index test that fails by construction (no memory access), on the current stream."""
+    import torch
+    return _lib.vofp_debug_check_selftest(_P(torch.cuda.current_stream().cuda_stream))
 
 
 _lib.vofp_project_extend.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P,

@@ -73,3 +73,21 @@ def test_entry_points_refuse_a_null_plan_on_the_host(lib):
     lib.vofp_vof_update.argtypes = [P] * 5 + [D] + [P] * 3
     lib.vofp_vof_update.restype = ctypes.c_int
     assert lib.vofp_vof_update(None, None, None, None, None, 0.01, None, None, None) == -1
+
+
+def test_bounds_checked_library_builds_and_exports_the_same_symbols():
+    """The -DVOFP_CHECKED variant compiles for sm_103a and exports every declared entry point as well."""
+    from paper_1907_00890_gb300 import build
+    lib_c = ctypes.CDLL(build.build(checked=True))
+    missing = [n for n in declared_symbols() if not hasattr(lib_c, n)]
+    assert not missing, missing
+
+
+def test_plain_library_check_word_is_zero_without_a_device_call(lib):
+    """The plain library has no check words: status 0, zeros, and no CUDA call (this machine has no GPU)."""
+    lib.vofp_debug_check_word.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
+    lib.vofp_debug_check_word.restype = ctypes.c_int
+    w = (ctypes.c_longlong * 4)(7, 7, 7, 7)
+    assert lib.vofp_debug_check_word(w, 1) == 0
+    assert list(w) == [0, 0, 0, 0]
+    assert lib.vofp_debug_check_word(None, 0) == -1

@@ -69,3 +69,34 @@ def test_bench_manufactured_stencil_is_the_mac_operator():
     got = bench._torch_laplacian_ppnn(torch, torch.tensor(p), 1.0 / n[0], 0.8 / n[1], dz).numpy()
     want = oracle.apply_laplacian(g, p)
     assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_record_traffic_from_an_ncu_launch_list(tmp_path):
+    """bench.py --record-traffic turns an ncu launch list (CSV, base units) into DRAM bytes per launch and
+    kernel class, keyed to the current sources, instead of numbers typed in by hand."""
+    sys.path.insert(0, ROOT)
+    import bench
+    hdr = '"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size",' \
+          '"Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"'
+    rows = []
+    launches = [(0, "k_xinv<double, double2>(vofp::XInvArgs)", 60000, 1.0e7, 7.0e6),
+                (1, "k_xinv<double, double2>(vofp::XInvArgs)", 62000, 1.1e7, 7.0e6),
+                (2, "k_ypass_tma<float, true, 8, 4>(vofp::YTmaArgs, CUtensorMap_st)", 30000, 4.0e6, 4.0e6),
+                (3, "k_xfwd<double, double2, 1>(vofp::XArgs)", 90000, 5.0e7, 1.7e7)]
+    for i, name, ns, rd, wr in launches:
+        for m, u, v in (("dram__bytes_read.sum", "byte", rd), ("dram__bytes_write.sum", "byte", wr),
+                        ("gpu__time_duration.sum", "nsecond", ns)):
+            rows.append('"%d","1","python","h","%s","1","7","(256, 1, 1)","(64, 1, 1)","0","10.3","","%s","%s","%s"'
+                        % (i, name, m, u, "{:,}".format(int(v))))
+    csv_path = tmp_path / "launches.csv"
+    csv_path.write_text("==PROF== Connected\n" + hdr + "\n" + "\n".join(rows) + "\n")
+    out = tmp_path / "traffic.json"
+
+    class A:
+        record_traffic = str(csv_path)
+        traffic_workload = "w"
+        traffic_out = str(out)
+    bench.record_traffic(A)
+    t = json.loads(out.read_text())
+    assert t["source_sha"] == bench.source_sha()
+    assert t["workloads"]["w"] == {"x_inverse": 17500000, "y_inverse": 8000000, "x_forward_div": 67000000}
