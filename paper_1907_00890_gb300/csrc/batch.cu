@@ -149,7 +149,6 @@ struct EpiArgs {
   double* w;
   double s;           // dt / rho0
   double sx, sy;      // s / dx, s / dy
-  int bpp;            // gradient launch: blocks per plane and axis (face_blocks_per_plane, 256 threads)
   const double* mean; // gauge sum (NULL: no shift)
   double mean_scale;
   double* conv;       // convergence slots, cleared by k_clear_batch
@@ -171,20 +170,22 @@ __global__ void k_shift_batch(const EpiArgs* __restrict__ e, const int* __restri
   for (size_t t = (size_t)l * blockDim.x + threadIdx.x; t < cells; t += (size_t)nb * blockDim.x) a.p[t] -= m;
 }
 
-// Velocity correction of every instance: the single-grid face launch shape (plane k, axis, position in the
-// plane) laid out per instance, 3 bpp blocks per plane (one 32-bit division per thread, none of 64 bits).
-__global__ void __launch_bounds__(256) k_grad_batch(const EpiArgs* __restrict__ e, const int* __restrict__ off,
-                                                    int n) {
+// Velocity correction of every instance: up to 512 blocks per instance striding over its faces (the
+// instance lookup, a dependent binary search, is paid once per block: a block per 256 faces made it the
+// kernel's cost).
+__global__ void k_grad_batch(const EpiArgs* __restrict__ e, const int* __restrict__ off, int n) {
   const int inst = find_instance(off, n, blockIdx.x);
   const EpiArgs& a = e[inst];
+  const int nb = __ldg(off + inst + 1) - __ldg(off + inst);
   const int l = blockIdx.x - __ldg(off + inst);
-  const int per_k = 3 * a.bpp;
-  const int k = l / per_k, r = l - k * per_k;
-  const int axis = r / a.bpp, xb = r - axis * a.bpp;
-  int i, j;
-  size_t o;
-  if (!face_at(a.g, axis, k, xb * blockDim.x + threadIdx.x, i, j, o)) return;
-  grad_face(a.g, a.p, a.u, a.v, a.w, a.s, a.sx, a.sy, axis, i, j, k, o);
+  const GridDev g = a.g;
+  const size_t total = total_faces(g);
+  for (size_t t = (size_t)l * blockDim.x + threadIdx.x; t < total; t += (size_t)nb * blockDim.x) {
+    int i, j, k;
+    size_t o;
+    const int axis = decode_face(g, t, i, j, k, o);
+    if (VOFP_IN(o, nfaces(g, axis), CHK_FACE_STORE)) grad_face(g, a.p, a.u, a.v, a.w, a.s, a.sx, a.sy, axis, i, j, k, o);
+  }
 }
 
 static const int kMaxDynSmem = 200 * 1024;
@@ -222,8 +223,8 @@ struct vofp_batch {
   unsigned char* hstage;  // pinned host copy of the argument records
   size_t args_bytes;
   size_t o_x, o_yf, o_yi, o_z, o_xi, o_low, o_epi;  // per-solve stride arrays start offsets
-  size_t o_offx, o_offy, o_offz, o_offlow, o_offepi, o_offgrad;
-  int tot_x, tot_y, tot_z, tot_low, tot_epi, tot_grad;
+  size_t o_offx, o_offy, o_offz, o_offlow, o_offepi;
+  int tot_x, tot_y, tot_z, tot_low, tot_epi;
   bool ztab;  // every instance has a bounded z axis: factor-table z kernels
   bool zseg;  // ... and every instance's segmented tile fits in shared memory
   bool zlean;  // the segmented kernel's lean tile layout (some instance's full tile would hold an SM alone)
@@ -298,8 +299,6 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
   o = a256(o + sizeof(int) * (n + 1));
   b->o_offepi = o;
   o = a256(o + sizeof(int) * (n + 1));
-  b->o_offgrad = o;
-  o = a256(o + sizeof(int) * (n + 1));
   b->args_bytes = o;
   if (device_alloc(&b->dmem, o) != cudaSuccess) {
     cudaGetLastError();
@@ -319,8 +318,7 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
   int* offz = (int*)(b->hstage + b->o_offz);
   int* offl = (int*)(b->hstage + b->o_offlow);
   int* offe = (int*)(b->hstage + b->o_offepi);
-  int* offg = (int*)(b->hstage + b->o_offgrad);
-  offx[0] = offy[0] = offz[0] = offl[0] = offe[0] = offg[0] = 0;
+  offx[0] = offy[0] = offz[0] = offl[0] = offe[0] = 0;
   b->sm_x = b->sm_y = b->sm_z = 0;
   b->ztab = true;
   for (int i = 0; i < n; ++i)
@@ -340,11 +338,8 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
     offz[i + 1] = offz[i] + (b->zseg ? (nx + kZSegTI - 1) / kZSegTI
                                      : (b->ztab ? (nx + 127) / 128 : (nx + gti - 1) / gti)) * ny;
     offl[i + 1] = offl[i] + p->nlow;
-    // gauge shift: up to 512 blocks striding over the cells; gradient: the face launch shape of the instance
-    // (3 axes, nz + 1 planes)
-    const size_t cells = (size_t)nx * ny * nz;
-    offe[i + 1] = offe[i] + (int)std::min<size_t>(512, (cells + 255) / 256);
-    offg[i + 1] = offg[i] + face_blocks_per_plane(grid_dev(p), 256) * 3 * (nz + 1);
+    // gauge shift and gradient: up to 512 blocks striding over the instance's cells / faces
+    offe[i + 1] = offe[i] + (int)std::min<size_t>(512, (total_faces(grid_dev(p)) + 255) / 256);
     const size_t sx = 2 * (size_t)p->xpb * fft_span(p->ax[0].fd, p->ax[0].blu64) * csz;
     const size_t sy = 2 * (size_t)(p->ytx32 / 2) * y_ld(fft_span(p->ax[1].fd, p->ax[1].blu64)) * csz;
     const ZTabShape zs = ztab_shape(128, nz, rsz);
@@ -359,7 +354,6 @@ extern "C" int vofp_batch_create(vofp_plan* const* plans, int n, vofp_batch** ou
   b->tot_z = offz[n];
   b->tot_low = offl[n];
   b->tot_epi = offe[n];
-  b->tot_grad = offg[n];
   if (first_use_on_device(2)) {
     allow_batch_kernels<float, float2>();
     allow_batch_kernels<ff, cff>();
@@ -483,7 +477,6 @@ static void fill_args(vofp_batch* b, double* const* u, double* const* v, double*
     e.s = dt[i];
     e.sx = dt[i] * e.g.rdx;
     e.sy = dt[i] * e.g.rdy;
-    e.bpp = face_blocks_per_plane(e.g, 256);
     e.mean = (pl->singular && !ffp && p && p[i]) ? conv + VOFP_CONV_MEAN : nullptr;
     e.mean_scale = 1.0 / ((double)pl->n[0] * pl->n[1] * (pl->volume / (pl->n[0] * pl->dx * pl->n[1] * pl->dy)));
     e.conv = conv;
@@ -500,7 +493,6 @@ static void launch_sequence_t(vofp_batch* b, cudaStream_t st) {
   const int* offz = (const int*)(d + b->o_offz);
   const int* offl = (const int*)(d + b->o_offlow);
   const int* offe = (const int*)(d + b->o_offepi);
-  const int* offg = (const int*)(d + b->o_offgrad);
   const EpiArgs* E = (const EpiArgs*)(d + b->o_epi);
   const LowArgs* L = (const LowArgs*)(d + b->o_low);
   VOFP_LAUNCH(KID_BATCHED, st, k_clear_batch<<<n, 32, 0, st>>>(E, n));
@@ -538,7 +530,7 @@ static void launch_sequence_t(vofp_batch* b, cudaStream_t st) {
     VOFP_LAUNCH(KID_XINV, st, (k_xinv_batch<T, C><<<b->tot_x, 256, b->sm_x, st>>>(XI, offx, n)));
   }
   VOFP_LAUNCH(KID_GAUGE, st, k_shift_batch<<<b->tot_epi, 256, 0, st>>>(E, offe, n));
-  VOFP_LAUNCH(KID_GRAD, st, k_grad_batch<<<b->tot_grad, 256, 0, st>>>(E, offg, n));
+  VOFP_LAUNCH(KID_GRAD, st, k_grad_batch<<<b->tot_epi, 256, 0, st>>>(E, offe, n));
 }
 
 static void launch_sequence(vofp_batch* b, cudaStream_t st) {

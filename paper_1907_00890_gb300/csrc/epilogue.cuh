@@ -75,6 +75,35 @@ __host__ __device__ __forceinline__ int face_blocks_per_plane(const GridDev& g, 
 inline dim3 face_grid(const GridDev& g, int threads) {
   return dim3((unsigned)face_blocks_per_plane(g, threads), 3, (unsigned)(g.nz + 1));
 }
+// Decode a flat face index over the three face arrays (u, then v, then w); returns the axis and sets (i, j, k)
+// and the offset in that axis' array.
+__device__ __forceinline__ int decode_face(const GridDev& g, size_t t, int& i, int& j, int& k, size_t& off) {
+  const int nxf = nface(g.nx, g.bcx), nyf = nface(g.ny, g.bcy);
+  const size_t nu = (size_t)nxf * g.ny * g.nz, nv = (size_t)g.nx * nyf * g.nz;
+  int fx = nxf, fy = g.ny, axis = 0;
+  if (t >= nu) {
+    t -= nu;
+    fx = g.nx;
+    fy = nyf;
+    axis = 1;
+    if (t >= nv) {
+      t -= nv;
+      fy = g.ny;
+      axis = 2;
+    }
+  }
+  off = t;
+  i = (int)(t % fx);
+  const size_t r = t / fx;
+  j = (int)(r % fy);
+  k = (int)(r / fy);
+  return axis;
+}
+__host__ __device__ __forceinline__ size_t total_faces(const GridDev& g) {
+  return (size_t)nface(g.nx, g.bcx) * g.ny * g.nz + (size_t)g.nx * nface(g.ny, g.bcy) * g.nz +
+         (size_t)g.nx * g.ny * nface(g.nz, g.bcz);
+}
+
 // Face `idx` of plane k of the `axis` face array: sets (i, j) and the offset; false past the plane or the
 // array.  (32-bit arithmetic, one division.)
 __device__ __forceinline__ bool face_at(const GridDev& g, int axis, int k, int idx, int& i, int& j, size_t& off) {
