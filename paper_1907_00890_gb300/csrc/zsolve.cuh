@@ -815,100 +815,120 @@ __device__ __forceinline__ void ztab_seg_block(const ZArgs& a, const ZTabArgs& z
   if (!VOFP_IN(i0, a.nx, CHK_Z_COLUMN) || !VOFP_IN((size_t)j * a.nx + i0 + ncol - 1, plane, CHK_Z_COLUMN) ||
       !VOFP_IN((size_t)distinct_index(j, zt.bcy) * zt.Ux + distinct_index(i0 + ncol - 1, zt.bcx), ts, CHK_Z_TABLE))
     return;  // (uniform per block)
-  // tile load: eight rows per thread in flight; beta_k = m_k r_k (scaled)
-  constexpr int UL = 8;
-  for (int t0 = threadIdx.x; t0 < nz * TI; t0 += UL * blockDim.x) {
-    T rv[UL];
-    TT fv[UL];
+  // Lane c of every warp works on column c of the tile (32 consecutive x indices: coalesced rows), warp w on rows
+  // w, w + W, ... for the load and the store and on the segment [k0, k1) for the recurrences.  Lanes without a
+  // system of their own (past the row's end, low modes, the pinned mode) skip the loads, the recurrences and the
+  // stores; their segment maps are never read by a live lane.
+  const int w = threadIdx.x >> 5, c = threadIdx.x & 31;
+  const bool mine = c < ncol && i0 + c >= cut;           // column c is solved by this kernel...
+  const bool live = mine && !(sing_here && c == 0);      // ... by the recurrences below (not the pinned mode)
+  const TT* Fl = F + (mine ? distinct_index(i0 + c, zt.bcx) : 0);  // this column's factors (stride ts)
+  T* yc = yv + c;                                         // this column of the tile (stride TI)
+  // tile load: eight rows per thread in flight (four with the full layout's three values per row, which keeps
+  // the registers at four blocks per SM); beta_k = m_k r_k (scaled)
+  constexpr int UL = LEAN ? 8 : 4;
+  if (mine) {
+    const T* Sc = S + c;
+    for (int kb = w; kb < nz; kb += UL * W) {
+      T rv[UL];
+      TT fv[UL];
 #pragma unroll
-    for (int u = 0; u < UL; ++u) {
-      const int t = t0 + u * blockDim.x;
-      const int k = t / TI, c = t - k * TI;
-      if (t < nz * TI && c < ncol && i0 + c >= cut) {
-        if (LEAN)
-          fv[u].ms = F[k * ts + distinct_index(i0 + c, zt.bcx)].ms;
-        else
-          fv[u] = F[k * ts + distinct_index(i0 + c, zt.bcx)];
-        rv[u] = S[k * plane + c];
+      for (int u = 0; u < UL; ++u) {
+        const int k = kb + u * W;
+        if (k < nz) {
+          if (LEAN)
+            fv[u].ms = Fl[(size_t)k * ts].ms;
+          else
+            fv[u] = Fl[(size_t)k * ts];
+          rv[u] = Sc[(size_t)k * plane];
+        }
       }
-    }
 #pragma unroll
-    for (int u = 0; u < UL; ++u) {
-      const int t = t0 + u * blockDim.x;
-      const int k = t / TI, c = t - k * TI;
-      if (t < nz * TI && c < ncol && i0 + c >= cut) {
-        yv[t] = rv[u] * fv[u].ms;
-        if (!LEAN) {
-          alv[t] = fv[u].al;
-          cpv[t] = fv[u].c;
+      for (int u = 0; u < UL; ++u) {
+        const int k = kb + u * W;
+        if (k < nz) {
+          yc[k * TI] = rv[u] * fv[u].ms;
+          if (!LEAN) {
+            alv[k * TI + c] = fv[u].al;
+            cpv[k * TI + c] = fv[u].c;
+          }
         }
       }
     }
   }
   __syncthreads();
-  const int w = threadIdx.x >> 5, c = threadIdx.x & 31;
-  // lanes without a system of their own (past the row's end, low modes, the pinned mode) run on zeros and
-  // read no factors
-  const bool live = c < ncol && i0 + c >= cut && !(sing_here && c == 0);
-  const TT* Fl = F + (live ? distinct_index(i0 + c, zt.bcx) : 0);  // this lane's factor column (stride ts)
-  auto alpha = [&](int k) { return LEAN ? Fl[k * ts].al : alv[k * TI + c]; };
-  auto cprime = [&](int k) { return LEAN ? Fl[k * ts].c : cpv[k * TI + c]; };
   const int L = (nz + W - 1) / W;
   const int k0 = w * L < nz ? w * L : nz;
   const int k1 = k0 + L < nz ? k0 + L : nz;
+  // factors of row k of this column: alpha_k and c'_k from the staged tile (full) or the table (lean)
+  const T* ac = alv + c;
+  const T* cc = cpv + c;
   {  // forward: this segment's rows as one map d_out = A d_in + B
     T A = (T)1, B = (T)0;
+    if (live) {
+      const TT* f = Fl + (size_t)k0 * ts;
 #pragma unroll 4
-    for (int k = k0; k < k1; ++k) {
-      const T al = live ? alpha(k) : (T)0, be = live ? yv[k * TI + c] : (T)0;
-      B = fma_t(al, B, be);
-      A = al * A;
+      for (int k = k0; k < k1; ++k, f += ts) {
+        const T al = LEAN ? f->al : ac[k * TI];
+        B = fma_t(al, B, yc[k * TI]);
+        A = al * A;
+      }
     }
     fA[w * TI + c] = A;
     fB[w * TI + c] = B;
   }
   __syncthreads();
-  {
+  if (live) {
     T d = (T)0;
     for (int sg = 0; sg < w; ++sg) d = fma_t(fA[sg * TI + c], d, fB[sg * TI + c]);
+    const TT* f = Fl + (size_t)k0 * ts;
 #pragma unroll 4
-    for (int k = k0; k < k1; ++k) {
-      d = live ? fma_t(alpha(k), d, yv[k * TI + c]) : (T)0;
-      yv[k * TI + c] = d;
+    for (int k = k0; k < k1; ++k, f += ts) {
+      d = fma_t(LEAN ? f->al : ac[k * TI], d, yc[k * TI]);
+      yc[k * TI] = d;
     }
   }
   __syncthreads();
-  {  // backward: x_{nz-1} = d_{nz-1}, x_k = -c'_k x_{k+1} + d_k
+  // backward: x_{nz-1} = d_{nz-1}, x_k = -c'_k x_{k+1} + d_k (the last row peeled off: it has no c'_k term)
+  const int kt = k1 == nz ? nz - 2 : k1 - 1;  // first row of the segment with a c'_k term
+  {
     T A = (T)1, B = (T)0;
+    if (live) {
+      if (k1 == nz && k0 < k1) {
+        B = yc[(nz - 1) * TI];
+        A = (T)0;
+      }
+      const TT* f = Fl + (size_t)kt * ts;
 #pragma unroll 4
-    for (int k = k1 - 1; k >= k0; --k) {
-      const T g = (k == nz - 1 || !live) ? (T)0 : -cprime(k);
-      B = fma_t(g, B, yv[k * TI + c]);
-      A = g * A;
+      for (int k = kt; k >= k0; --k, f -= ts) {
+        const T g = -(LEAN ? f->c : cc[k * TI]);
+        B = fma_t(g, B, yc[k * TI]);
+        A = g * A;
+      }
     }
     bA[w * TI + c] = A;
     bB[w * TI + c] = B;
   }
   __syncthreads();
-  {
+  if (live) {
     T x = (T)0;
     for (int sg = W - 1; sg > w; --sg) x = fma_t(bA[sg * TI + c], x, bB[sg * TI + c]);
+    if (k1 == nz && k0 < k1) x = yc[(nz - 1) * TI];  // (stored already: x_{nz-1} = d_{nz-1})
+    const TT* f = Fl + (size_t)kt * ts;
 #pragma unroll 4
-    for (int k = k1 - 1; k >= k0; --k) {
-      const T g = (k == nz - 1 || !live) ? (T)0 : -cprime(k);
-      x = fma_t(g, x, yv[k * TI + c]);
-      yv[k * TI + c] = x;
+    for (int k = kt; k >= k0; --k, f -= ts) {
+      x = fma_t(-(LEAN ? f->c : cc[k * TI]), x, yc[k * TI]);
+      yc[k * TI] = x;
     }
   }
   if (w == 0 && sing_here && cut == 0) zscan_system<T, T, TT>(a, S, plane, F, ts, scr, 1, za, true, c);
   __syncthreads();
   bool bad = false;
-  for (int t = threadIdx.x; t < nz * TI; t += blockDim.x) {
-    const int k = t / TI, cc = t - k * TI;
-    const int i = i0 + cc;
-    if (cc < ncol && i >= cut && !(sing_here && cc == 0)) {
-      const T x = yv[t];
-      S[k * plane + cc] = x;
+  if (live) {
+    T* Sc = S + c;
+    for (int k = w; k < nz; k += W) {
+      const T x = yc[k * TI];
+      Sc[(size_t)k * plane] = x;
       if (a.info) bad |= !isfinite((double)x);
     }
   }
