@@ -53,19 +53,21 @@ static void allow_all() {
 // Shared memory a TMA y-pass CTA may take (of the 227 KiB an sm_103a CTA can opt into).
 static const int kYTmaSmem = 225 * 1024;
 
-// The TMA inverse x-pass kernel for nx = 2^lgn (7, 8 or 9), with the tile (2^lgB complex lines) that fills
-// about 130 KB of shared memory; NULL for other lengths.
+// The TMA inverse x-pass kernel for nx = 2^lgn (7, 8 or 9), with a tile (2^lgB complex lines) of about 100 KB
+// of shared memory (8 KB of samples per line pair with the potential's rows), so that two CTAs share an SM:
+// with one 512-thread CTA per SM (tiles of about 200 KB) the pass was issue-latency bound (25% of warps
+// active); two CTAs took the FP32 pass at 512^3 from 1.36 to 1.15 ms per launch.  NULL for other lengths.
 typedef void (*XTmaKernel)(const XTmaArgs, const CUtensorMap, const CUtensorMap);
 template <typename R>
 static int xtma_lgB(int lgn) {
-  return std::is_same<R, float>::value ? (lgn >= 9 ? 3 : 4) : (lgn >= 9 ? 2 : (lgn == 8 ? 3 : 4));
+  return std::is_same<R, float>::value ? (lgn >= 9 ? 2 : 3) : (lgn >= 9 ? 2 : (lgn == 8 ? 3 : 4));
 }
 template <typename R>
 static XTmaKernel xtma_kernel(int lgn) {
   constexpr bool F = std::is_same<R, float>::value;
-  if (lgn == 9) return F ? k_xinv_tma<R, 9, 3> : k_xinv_tma<R, 9, 2>;
-  if (lgn == 8) return F ? k_xinv_tma<R, 8, 4> : k_xinv_tma<R, 8, 3>;
-  if (lgn == 7) return k_xinv_tma<R, 7, 4>;
+  if (lgn == 9) return k_xinv_tma<R, 9, 2>;
+  if (lgn == 8) return k_xinv_tma<R, 8, 3>;
+  if (lgn == 7) return F ? k_xinv_tma<R, 7, 3> : k_xinv_tma<R, 7, 4>;
   return nullptr;
 }
 

@@ -773,9 +773,10 @@ static __global__ void __launch_bounds__(128) k_ztab_staged(ZArgs a, ZTabArgs zt
 //         (the tile's entries, some 100 KB at nz = 512, come from DRAM once and from L2 after).
 // A kernel that holds the SM alone stops the SM's memory traffic during its recurrences, so the plan takes
 // the full layout while two blocks still fit per SM (FP32 up to nz = 279, FP32 pairs up to 134), else the
-// lean one (FP32 up to nz = 822, FP32 pairs up to 395; at 512^3 in FP32: 1.76 -> 1.23 ms per launch), else
-// the streaming kernel.  The full layout is the faster one where both fit twice (128^3 FP32: 13.4 against
-// 14.9 us).
+// lean one (FP32 up to nz = 822, FP32 pairs up to 395; at 512^3 in FP32: 1.76 -> 1.23 ms per launch, 1.07 ms
+// with the loops below), else the streaming kernel.  The full layout is the faster one where both fit twice
+// (128^3 FP32: 13.4 against 14.9 us).  The loops keep each lane on its column with strided pointers and let
+// lanes without a system skip them: ncu had the lean kernel issue-bound at some 160 instructions per cell.
 constexpr int kZSegTI = 32, kZSegW = 8;
 inline size_t ztab_seg_smem(int nz, size_t elem, bool lean) {
   return ((size_t)nz * ((lean ? 1 : 3) * kZSegTI + 1) + (size_t)4 * kZSegW * kZSegTI) * elem;
