@@ -50,8 +50,13 @@ static void allow_all() {
   allow_smem(k_ztab_seg<T, TT, true>);
 }
 
-// Shared memory a TMA y-pass CTA may take (of the 227 KiB an sm_103a CTA can opt into).
+// Shared memory a TMA y-pass CTA may take (of the 227 KiB an sm_103a CTA can opt into), and the tile budget
+// per spectrum type: FP64 tiles of at most 112 KB (two CTAs per SM: ny = 512 passes 4% faster than with one
+// CTA of 196 KB), FP32 and FP32-pair tiles up to the limit (measured the other way round: halving their
+// tiles slowed the 512^3 FP32 + refinement solve from 20.05 to 20.21 ms).
 static const int kYTmaSmem = 225 * 1024;
+template <typename R>
+constexpr size_t kYTmaTile = std::is_same<R, double>::value ? (size_t)112 * 1024 : (size_t)kYTmaSmem;
 
 // The TMA inverse x-pass kernel for nx = 2^lgn (7, 8 or 9), with a tile (2^lgB complex lines) of about 100 KB
 // of shared memory (8 KB of samples per line pair with the potential's rows), so that two CTAs share an SM:
@@ -77,7 +82,7 @@ typedef void (*YTmaKernel)(const YTmaArgs, const CUtensorMap);
 template <typename R>
 static YTmaKernel ytma_kernel(bool inv, int lgn, int lgB) {
   constexpr bool F = std::is_same<R, float>::value;
-  constexpr int B9 = F ? 4 : 3;
+  constexpr int B9 = F ? 4 : (std::is_same<R, double>::value ? 2 : 3);
   if (lgn == 9 && lgB == B9) return inv ? k_ypass_tma<R, true, 9, B9> : k_ypass_tma<R, false, 9, B9>;
   if (lgn == 8 && lgB == 4) return inv ? k_ypass_tma<R, true, 8, 4> : k_ypass_tma<R, false, 8, 4>;
   if (lgn == 7 && lgB == 4) return inv ? k_ypass_tma<R, true, 7, 4> : k_ypass_tma<R, false, 7, 4>;
@@ -137,7 +142,7 @@ static void ytma_setup(vofp_plan* pl, void* spectrum) {
   if (std::is_same<R, double>::value && ny < 256) return;
   int lgB = -1;
   for (int lb = 4; lb >= 2 && lgB < 0; --lb)
-    if ((2 << lb) <= nx && ytma_smem_bytes(ny, lb, 2 * sizeof(R)) <= (size_t)kYTmaSmem) lgB = lb;
+    if ((2 << lb) <= nx && ytma_smem_bytes(ny, lb, 2 * sizeof(R)) <= kYTmaTile<R>) lgB = lb;
   if (lgB < 0) return;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return;
