@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--large-n", type=int, default=512,
                     help="cells per axis of the stretched-z projection variant (512 = the specified workload; "
                          "smaller sizes only for profiling captures)")
+    ap.add_argument("--large-precisions", default="fp64,mixed,ff",
+                    help="precisions of the stretched-z projection variant to run (comma list; one alone for "
+                         "profiling captures)")
     ap.add_argument("--tune", action="store_true",
                     help="autotune the stretched-z projection variant's plans (launch shapes, z kernel, radix order)")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
@@ -228,11 +231,26 @@ def bench_vof(vofp, c, u0, C, md, st, flush, args):
     if "vof_update" in trace:
         tot, cnt = trace["vof_update"]
         hbm, how = peaks()
-        gbs = 40 * cells / (tot / cnt / 1e3) / 1e9  # one launch per update (the fused pass)
-        r["roofline_vof_update"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                                    "frac": gbs / hbm, "bytes_per_cell": 40, "peak_source": how}
+        avg_s = tot / cnt / 1e3  # one launch per update (the fused pass)
+        gbs = 40 * cells / avg_s / 1e9
+        # bound by its FP64 arithmetic (ncu: FP64 pipe 77% busy, DRAM 4%): about 50 flops per cell -- each
+        # implicit one-dimensional step 12 (fluxes, velocity difference, division), the correction 14
+        gf = VOF_FLOPS_PER_CELL * cells / avg_s / 1e9
+        r["roofline_vof_update"] = {"bound": "alu", "achieved": gf, "peak": FP64_NOMINAL_GFLOPS,
+                                    "unit": "GFLOP/s", "frac": gf / FP64_NOMINAL_GFLOPS,
+                                    "flops_per_cell": VOF_FLOPS_PER_CELL,
+                                    "peak_source": "nominal FP64 rate of the recipe",
+                                    "other": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                              "frac": gbs / hbm, "bytes_per_cell": 40, "peak_source": how}}
     plan.close()
     return r
+
+
+VOF_FLOPS_PER_CELL = 50
+# FP64 flops per cell of the refinement path's FP64 passes (their FP32 transforms not counted): the residual's
+# 7-point stencil and defect (13), the divergence and its scale (10), the face epilogues as in `algorithmic`
+MIXED_FP64_FLOPS = {"residual_update": 13, "x_forward_div": 10, "grad_update": 12, "extend_epilogue": 60,
+                    "stefan_source": 40}
 
 
 def mixed_bytes_per_cell(rs):
@@ -256,10 +274,20 @@ def roofline_mixed(trace, n, rs=4, workload=None):
     by = per[name] * cells
     hbm, how = peaks()
     gbs = by / (tot / cnt / 1e3) / 1e9
-    return {"bound": "hbm", "kernel": name, "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-            "launches": cnt, "avg_launch_ms": tot / cnt, "bytes_per_cell": per[name], "peak_source": how,
-            "traffic": measured_traffic(workload, name) if workload else None,
-            "note": "averages include launches that returned at once after convergence"}
+    mem = {"bound": "hbm", "kernel": name, "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+           "launches": cnt, "avg_launch_ms": tot / cnt, "bytes_per_cell": per[name], "peak_source": how,
+           "traffic": measured_traffic(workload, name) if workload else None,
+           "note": "averages include launches that returned at once after convergence"}
+    if name not in MIXED_FP64_FLOPS:
+        return mem
+    # an FP64 pass: bound by the FP64 pipe (ncu), so its roofline is the FP64 rate, the HBM figure beside it
+    gf = MIXED_FP64_FLOPS[name] * cells / (tot / cnt / 1e3) / 1e9
+    out = dict(mem, bound="alu", achieved=gf, peak=FP64_NOMINAL_GFLOPS, unit="GFLOP/s",
+               frac=gf / FP64_NOMINAL_GFLOPS, flops_per_cell=MIXED_FP64_FLOPS[name],
+               peak_source="nominal FP64 rate of the recipe")
+    out.pop("bytes_per_cell")
+    out["other"] = {k: mem[k] for k in ("bound", "achieved", "peak", "unit", "frac", "bytes_per_cell", "peak_source")}
+    return out
 
 
 def _torch_laplacian_ppnn(torch, p, dx, dy, dz):
@@ -320,6 +348,8 @@ def bench_large(vofp, args):
                               "err_estimate: the library's a-posteriori estimate for the projection"}
     reps = max(3, min(args.steps, 8))
     for name, prec, mr in (("fp64", vofp.FP64, 1), ("mixed", vofp.MIXED, 3), ("ff", vofp.FF, 1)):
+        if name not in getattr(args, "large_precisions", "fp64,mixed,ff").split(","):
+            continue
         plan = vofp.Plan(n, dx, dy, dz, bc, prec=prec, max_refine=mr, tune=1 if args.tune else 0)
         st = torch.cuda.current_stream()
 
@@ -1030,7 +1060,7 @@ def run_only(args):
 
 
 # kernel function name (as ncu prints it) -> the library's trace class
-_KCLASS = [(r"k_zlow", "z_low_modes"), (r"k_z", "z_tridiag"), (r"k_xinv", "x_inverse"),
+_KCLASS = [(r"k_zfactor", None), (r"k_zlow", "z_low_modes"), (r"k_z", "z_tridiag"), (r"k_xinv", "x_inverse"),
            (r"k_xtc\b", "x_tensor_core"), (r"k_grad", "grad_update"), (r"k_extend_epi", "extend_epilogue"),
            (r"k_geometry", "stefan_source"), (r"k_vd_predict", "vd_predict"), (r"k_vof_fused", "vof_update"),
            (r"k_shift", "gauge_shift")]
