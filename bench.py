@@ -249,8 +249,8 @@ def bench_vof(vofp, c, u0, C, md, st, flush, args):
 VOF_FLOPS_PER_CELL = 50
 # FP64 flops per cell of the refinement path's FP64 passes (their FP32 transforms not counted): the residual's
 # 7-point stencil and defect (13), the divergence and its scale (10), the face epilogues as in `algorithmic`
-MIXED_FP64_FLOPS = {"residual_update": 13, "x_forward_div": 10, "grad_update": 12, "extend_epilogue": 60,
-                    "stefan_source": 40}
+MIXED_FP64_FLOPS = {"residual_update": 13, "x_forward_div": 10, "grad_update": 10, "extend_epilogue": 24,
+                    "stefan_source": 20}
 
 
 def mixed_bytes_per_cell(rs):
@@ -979,7 +979,10 @@ def algorithmic(kname, n):
     Bytes: each compulsory array read or written once (8 B per FP64 value).  Flops: a real-to-real transform
     of length m counts 2.5 m log2 m per line (half the 5 m log2 m of a complex FFT); the z recurrence with
     plan-time factors 6 per point (forward multiply-add and multiply, back multiply-add, output scale);
-    stencils their adds and multiplies.
+    stencils their adds and multiplies (a multiply-add counts 2): the velocity correction a difference and a
+    multiply-add per face (3, one more product on z faces: 10 per cell), the extension a difference, two face
+    sums, a product and two multiply-adds per face (8, 24 per cell), the geometry its three central differences
+    and scales, |grad C|^2, the reciprocal square root, s and n (20 per cell).
     """
     nx, ny, nz = n
     cells = nx * ny * nz
@@ -996,9 +999,9 @@ def algorithmic(kname, n):
         "y_inverse": (16, 2.5 * lg(ny)),
         "z_tridiag": (16, 6),
         "x_inverse": (16, 2.5 * lg(nx)),
-        "grad_update": (56, 12),
-        "extend_epilogue": (96, 60),
-        "stefan_source": (48, 40),
+        "grad_update": (56, 10),
+        "extend_epilogue": (96, 24),
+        "stefan_source": (48, 20),
     }
     b, f = tab.get(kname, (0, 0))
     return b * cells, f * cells

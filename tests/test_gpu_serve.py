@@ -176,3 +176,71 @@ def test_latency_runs_from_arrival(vp):
                               arrival_s=vp.vofp_server_clock(s) + 10.0)
     assert 0 < vp.vofp_server_wait(s, t, 60.0) < 5.0
     vp.vofp_server_destroy(s)
+
+
+def test_destroy_with_unpolled_requests_then_fresh_server(vp):
+    """A client that submits and never polls (a stalled consumer): destroying the server with requests queued
+    and in flight returns once the in-flight work has finished (nothing hangs), and a new server afterwards
+    serves a request to oracle parity."""
+    import torch
+    o = vp.vofp_opts_default()
+    o.prec = vp.MIXED
+    reqs = requests(24)
+    s = vp.vofp_server_create(3 * 48 ** 3 * 8 * 4, 4, o)
+    keep = []  # the fields stay valid until destroy has waited for the work on them
+    for r in reqs:
+        u = [dev(a) for a in r["u0"]]
+        torch.cuda.synchronize()
+        vp.vofp_server_submit(s, r["n"], r["dx"], r["dy"], r["dz"], r["bc"], *u, dt_over_rho0=r["dt"])
+        keep.append(u)
+    t0 = time.time()
+    vp.vofp_server_destroy(s)
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 60.0
+    del keep
+    fields, lats, stats = serve(vp, reqs[:2], 3 * 48 ** 3 * 8 * 4, 2)
+    assert stats["completed"] == 2
+    for r, (u, p) in zip(reqs[:2], fields):
+        g = oracle.Grid(*r["n"], r["dx"], r["dy"], r["dz"], r["bc"])
+        ou = oracle.project(g, *r["u0"], dt_over_rho0=r["dt"])
+        assert rel(p.cpu().numpy(), ou[3]) < TOL
+
+
+def test_submit_refuses_malformed_requests_and_keeps_serving(vp):
+    """Requests with a non-positive or non-finite step scale, an empty axis or a missing field are refused at
+    submission (INVALID_ARG, no ticket); a boundary-condition code out of range is refused when its plan is
+    built (the request completes with INVALID_ARG); the server then serves a valid request to parity."""
+    import torch
+    o = vp.vofp_opts_default()
+    o.prec = vp.MIXED
+    s = vp.vofp_server_create(64 << 20, 2, o)
+    n = (16, 12, 10)
+    bc = ("P", "P", "NN")
+    dz = synth.uniform_dz(n[2])
+    u0 = synth.random_velocity(n, bc, 91)
+    u = [dev(a) for a in u0]
+    for kw in (dict(dt_over_rho0=0.0), dict(dt_over_rho0=-1.0)):
+        with pytest.raises(vp.VofpError) as e:
+            vp.vofp_server_submit(s, n, 1 / 16, 1 / 12, dz, bc, *u, **kw)
+        assert e.value.status == -1
+    with pytest.raises(vp.VofpError) as e:
+        vp.vofp_server_submit(s, (16, 0, 10), 1 / 16, 1 / 12, dz, bc, *u)
+    assert e.value.status == -1
+    with pytest.raises(vp.VofpError) as e:
+        vp.vofp_server_submit(s, n, 1 / 16, 1 / 12, dz, bc, u[0], None, u[2])
+    assert e.value.status == -1
+    t = vp.vofp_server_submit(s, n, 1 / 16, 1 / 12, dz, (0, 0, 7), *u)
+    with pytest.raises(vp.VofpError) as e:
+        vp.vofp_server_wait(s, t, 60.0)
+    assert e.value.status == -1
+    u = [dev(a) for a in u0]
+    p = torch.empty((n[2], n[1], n[0]), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t = vp.vofp_server_submit(s, n, 1 / 16, 1 / 12, dz, bc, *u, dt_over_rho0=0.7, p=p)
+    vp.vofp_server_wait(s, t, 60.0)
+    vp.vofp_server_destroy(s)
+    g = oracle.Grid(*n, 1 / 16, 1 / 12, dz, bc)
+    ou = oracle.project(g, *u0, dt_over_rho0=0.7)
+    assert rel(p.cpu().numpy(), ou[3]) < TOL
+    for a in range(3):
+        assert rel(u[a].cpu().numpy(), ou[a]) < TOL
