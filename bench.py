@@ -620,7 +620,10 @@ def bench_served(vofp, args):
 
 
 class ClockSampler:
-    """Samples SM clock and throttle reasons with nvidia-smi while the timed region runs."""
+    """Samples SM clock and throttle reasons with nvidia-smi (every 20 ms) while the timed region runs.  The
+    device steps of one timed region take some tens of ms and nvidia-smi about a second to start, so the
+    sampler is started first (``wait_first``) and kept running over the timed, the traced and the end-to-end
+    steps; ``summary(t0, t1)`` keeps the samples read between t0 and t1."""
 
     FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
               "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
@@ -645,7 +648,12 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def wait_first(self, timeout=5.0):
+        t = time.time()
+        while self.proc and not self.lines and time.time() - t < timeout:
+            time.sleep(0.01)
 
     def __exit__(self, *a):
         if self.proc:
@@ -655,10 +663,12 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for tl, ln in self.lines:
+            if (t0 is not None and tl < t0) or (t1 is not None and tl > t1):
+                continue
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) != len(self.FIELDS):
                 continue
@@ -816,14 +826,16 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    clk = ClockSampler(torch.cuda.current_device()).__enter__()
+    clk.wait_first()
+    t_clk0 = time.time()
     l0 = vofp.vofp_launch_count()
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        for i in range(args.steps):
-            prep()
-            ev[i][0].record(st)
-            step()
-            ev[i][1].record(st)
-        torch.cuda.synchronize()
+    for i in range(args.steps):
+        prep()
+        ev[i][0].record(st)
+        step()
+        ev[i][1].record(st)
+    torch.cuda.synchronize()
     launches = vofp.vofp_launch_count() - l0
     # the same steps once more with per-launch events: kernel durations for the roofline
     _, _, trace = timed_steps(vofp, st, prep, step, args.steps)
@@ -857,6 +869,8 @@ def run_ours(args):
         if i > 0:
             ev2[i - 1][1].record(st)
     torch.cuda.synchronize()
+    t_clk1 = time.time()
+    clk.__exit__(None, None, None)
     e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in ev2]))
     _, e2e_value = job_rate(e2e_ms, cells, 2, world, dev)
 
@@ -894,7 +908,7 @@ def run_ours(args):
                            "l2": "flushed between steps (256 MiB write, outside the events)"},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches),
-                "clocks": clk.summary(),
+                "clocks": dict(clk.summary(t_clk0, t_clk1), window="timed, traced and end-to-end steps"),
                 "roofline": roof}
         if not args.no_cpu_baseline:
             sec, nsteps = time_oracle(c, 10, 20.0)
