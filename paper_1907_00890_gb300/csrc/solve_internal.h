@@ -23,7 +23,6 @@ enum KernelId {
   KID_EXTEND_EPI,
   KID_STEFAN,
   KID_RESID,
-  KID_FUSED_YZY,
   KID_BATCHED,
   KID_NOALLOC_TABLES,
   KID_ZLOW,     // refinement plans: the low-eigenvalue z systems in FP64

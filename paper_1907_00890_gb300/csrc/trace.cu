@@ -12,7 +12,7 @@ namespace vofp {
 static const char* kNames[KID_COUNT] = {
     "x_forward",   "x_forward_div",   "x_forward_stefan", "x_forward_div_stefan", "y_forward",
     "z_tridiag",   "y_inverse",       "x_inverse",        "grad_update",          "extend_epilogue",
-    "stefan_source", "residual_update", "fused_yzy",      "batched",              "noalloc_tables",
+    "stefan_source", "residual_update", "batched",        "noalloc_tables",
     "z_low_modes", "gauge_shift",     "vd_predict",
     "vof_update"};
 
