@@ -61,7 +61,8 @@ constexpr size_t kYTmaTile = std::is_same<R, double>::value ? (size_t)112 * 1024
 // The TMA inverse x-pass kernel for nx = 2^lgn (7, 8 or 9), with a tile (2^lgB complex lines) of about 100 KB
 // of shared memory (8 KB of samples per line pair with the potential's rows), so that two CTAs share an SM:
 // with one 512-thread CTA per SM (tiles of about 200 KB) the pass was issue-latency bound (25% of warps
-// active); two CTAs took the FP32 pass at 512^3 from 1.36 to 1.15 ms per launch.  NULL for other lengths.
+// active); two CTAs took the FP32 inverse passes of a 512^3 solve from 2.73 to 2.30 ms.  NULL for other
+// lengths.
 typedef void (*XTmaKernel)(const XTmaArgs, const CUtensorMap, const CUtensorMap);
 template <typename R>
 static int xtma_lgB(int lgn) {
