@@ -61,7 +61,6 @@ __device__ __forceinline__ double face_rdist(const GridDev& g, int axis, int k, 
   return e > 0 ? h + h : h;
 }
 
-
 // Blocks per plane and axis of the face launch shape (face_grid).
 __host__ __device__ __forceinline__ int face_blocks_per_plane(const GridDev& g, int threads) {
   const long a = (long)nface(g.nx, g.bcx) * g.ny, b = (long)g.nx * nface(g.ny, g.bcy), c = (long)g.nx * g.ny;

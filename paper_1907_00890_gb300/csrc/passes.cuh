@@ -291,7 +291,7 @@ __device__ __forceinline__ void ypass_block(const YArgs& a, int bx, int by, unsi
   C* b1 = b0 + B * ld;
   const int i0 = bx * a.tx;
   const size_t base = (size_t)by * a.ny * a.nx;
-  const size_t cells = (size_t)a.nx * a.ny * a.nz;  // (bounds-checked builds)
+  [[maybe_unused]] const size_t cells = (size_t)a.nx * a.ny * a.nz;  // (bounds-checked builds)
   T* S = reinterpret_cast<T*>(a.S);
   const int bc = a.bc;
   const C* quart = reinterpret_cast<const C*>(a.quart);

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kYTmaThreads) k_ypass_tma(const YTmaArgs a, co
   const C* quart = reinterpret_cast<const C*>(y.quart);
   const int bc = y.bc;
   const int nx = y.nx;
-  const size_t cells = (size_t)nx * y.ny * y.nz;  // (bounds-checked builds)
+  [[maybe_unused]] const size_t cells = (size_t)nx * y.ny * y.nz;  // (bounds-checked builds)
   for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
     const int cur = it & 1;
     const int nxt = tile + gridDim.x;

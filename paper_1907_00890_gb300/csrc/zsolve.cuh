@@ -773,8 +773,8 @@ static __global__ void __launch_bounds__(128) k_ztab_staged(ZArgs a, ZTabArgs zt
 //         (the tile's entries, some 100 KB at nz = 512, come from DRAM once and from L2 after).
 // A kernel that holds the SM alone stops the SM's memory traffic during its recurrences, so the plan takes
 // the full layout while two blocks still fit per SM (FP32 up to nz = 279, FP32 pairs up to 134), else the
-// lean one (FP32 up to nz = 822, FP32 pairs up to 395; at 512^3 in FP32: 1.76 -> 1.23 ms per launch, 1.07 ms
-// with the loops below), else the streaming kernel.  The full layout is the faster one where both fit twice
+// lean one (FP32 up to nz = 822, FP32 pairs up to 395; the z passes of a 512^3 FP32 + refinement solve, three
+// working launches: 3.52 -> 2.46 ms, 2.14 ms with the loops below), else the streaming kernel.  The full layout is the faster one where both fit twice
 // (128^3 FP32: 13.4 against 14.9 us).  The loops keep each lane on its column with strided pointers and let
 // lanes without a system skip them: ncu had the lean kernel issue-bound at some 160 instructions per cell.
 constexpr int kZSegTI = 32, kZSegW = 8;
@@ -861,6 +861,10 @@ __device__ __forceinline__ void ztab_seg_block(const ZArgs& a, const ZTabArgs& z
   const int L = (nz + W - 1) / W;
   const int k0 = w * L < nz ? w * L : nz;
   const int k1 = k0 + L < nz ? k0 + L : nz;
+  // unrolling of the recurrence loops: the lean FP32 layout reads alpha_k / c'_k from L2 in them (ncu: stalled
+  // on those loads), and 16 rows of them in flight took the z passes of a 512^3 solve from 2.11 to 1.94 ms
+  // (FP32 pairs, with twice the registers per value, measured no better)
+  constexpr int UR = (LEAN && sizeof(T) == 4) ? 16 : 4;
   // factors of row k of this column: alpha_k and c'_k from the staged tile (full) or the table (lean)
   const T* ac = alv + c;
   const T* cc = cpv + c;
@@ -868,7 +872,7 @@ __device__ __forceinline__ void ztab_seg_block(const ZArgs& a, const ZTabArgs& z
     T A = (T)1, B = (T)0;
     if (live) {
       const TT* f = Fl + (size_t)k0 * ts;
-#pragma unroll 4
+#pragma unroll (UR)
       for (int k = k0; k < k1; ++k, f += ts) {
         const T al = LEAN ? f->al : ac[k * TI];
         B = fma_t(al, B, yc[k * TI]);
@@ -883,7 +887,7 @@ __device__ __forceinline__ void ztab_seg_block(const ZArgs& a, const ZTabArgs& z
     T d = (T)0;
     for (int sg = 0; sg < w; ++sg) d = fma_t(fA[sg * TI + c], d, fB[sg * TI + c]);
     const TT* f = Fl + (size_t)k0 * ts;
-#pragma unroll 4
+#pragma unroll (UR)
     for (int k = k0; k < k1; ++k, f += ts) {
       d = fma_t(LEAN ? f->al : ac[k * TI], d, yc[k * TI]);
       yc[k * TI] = d;
@@ -900,7 +904,7 @@ __device__ __forceinline__ void ztab_seg_block(const ZArgs& a, const ZTabArgs& z
         A = (T)0;
       }
       const TT* f = Fl + (size_t)kt * ts;
-#pragma unroll 4
+#pragma unroll (UR)
       for (int k = kt; k >= k0; --k, f -= ts) {
         const T g = -(LEAN ? f->c : cc[k * TI]);
         B = fma_t(g, B, yc[k * TI]);
@@ -916,7 +920,7 @@ __device__ __forceinline__ void ztab_seg_block(const ZArgs& a, const ZTabArgs& z
     for (int sg = W - 1; sg > w; --sg) x = fma_t(bA[sg * TI + c], x, bB[sg * TI + c]);
     if (k1 == nz && k0 < k1) x = yc[(nz - 1) * TI];  // (stored already: x_{nz-1} = d_{nz-1})
     const TT* f = Fl + (size_t)kt * ts;
-#pragma unroll 4
+#pragma unroll (UR)
     for (int k = kt; k >= k0; --k, f -= ts) {
       x = fma_t(-(LEAN ? f->c : cc[k * TI]), x, yc[k * TI]);
       yc[k * TI] = x;
